@@ -1,0 +1,285 @@
+/*
+ * lg.h -- C ABI of the GB300 (sm_103a) multigrid solver for graph Laplacians.
+ *
+ * The method is the unsmoothed-aggregation multigrid with low-degree
+ * elimination of Konolige & Brown, "A Parallel Solver for Graph Laplacians"
+ * (PASC'18): the setup builds a hierarchy by low-degree elimination
+ * (Section 3.4, Algorithm "Determine vertices to eliminate"), affinity
+ * strength of connection and voting aggregation (Section 3.5, Algorithms
+ * "Aggregation" / "Aggregation-Step"), and Galerkin products R L P; the solve
+ * is conjugate gradients preconditioned by one V-cycle (Section 2.3,
+ * Algorithm "Multigrid cycle") with degree-2 Chebyshev smoothing
+ * (Sections 3.6 and 4).
+ *
+ * Problem statement (Section 2.1): solve L x = b for the Laplacian L = D - A
+ * of a weighted, undirected, connected graph with positive weights. L is
+ * singular with null space span(1); b has its mean removed inside the
+ * library and the returned x has mean zero.
+ *
+ * Conventions for every entry point:
+ *  - Graphs are CSR adjacency: rowptr int64[n+1], col int32[nnz], w double[nnz],
+ *    both directions of each edge stored with equal weight, columns strictly
+ *    ascending within a row, no self-loops, 0 < w < inf. The diagonal of L is
+ *    never passed: it is the row sum of w.
+ *  - Pointers may be host or device memory unless the entry point says
+ *    otherwise; the library finds out which with cudaPointerGetAttributes.
+ *    Host arrays may be pageable or pinned.
+ *  - The caller owns every array it passes. The library copies or reads
+ *    inputs during the call and keeps no pointer to them after it returns.
+ *  - Every call returns an lg status code (LG_OK = 0) and never aborts the
+ *    process. On an error the output arrays hold unspecified values unless
+ *    stated otherwise.
+ *  - Work runs on the stream given in lg_options (a cudaStream_t), or on a
+ *    stream the handle owns when that is NULL. Calls that return results to
+ *    the host synchronise that stream before returning.
+ *  - A handle is not thread-safe: one host thread at a time per handle. The
+ *    server (lg_serve_*) is thread-safe.
+ */
+#ifndef LG_H
+#define LG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+enum {
+  LG_OK = 0,
+  LG_ERR_INVALID = 1,        /* malformed CSR, asymmetric, w <= 0, n < 1, bad argument */
+  LG_ERR_DISCONNECTED = 2,   /* graph has more than one connected component */
+  LG_ERR_SETUP = 3,          /* coarsening stalled with a coarsest level above max_coarse_n */
+  LG_ERR_NOMEM = 4,          /* device allocation or HBM budget exhausted */
+  LG_ERR_NOT_CONVERGED = 5,  /* max_iter reached; x holds the last iterate, info->relres its residual */
+  LG_ERR_BREAKDOWN = 6,      /* PCG scalar non-finite or r^T z <= 0 */
+  LG_ERR_TIMEOUT = 7,        /* a bounded device-side retry loop or host wait gave up */
+  LG_ERR_CUDA = 8,           /* a CUDA runtime call failed */
+  LG_ERR_BUSY = 9            /* the server has no free slot or budget; retry later */
+};
+
+enum { LG_FP64 = 0, LG_FP32_HIER = 1 };             /* precision of the V-cycle */
+enum { LG_AUTO = -1, LG_HOST = 0, LG_DEVICE = 1 };  /* memory space of caller pointers */
+enum { LG_LEVEL_AGG = 1, LG_LEVEL_ELIM = 2, LG_LEVEL_COARSEST = 3 };
+enum { LG_DECIDED = 0, LG_UNDECIDED = 1, LG_SEED = 2 }; /* aggregation states, Section 3.5 */
+
+typedef struct lg_hier* lg_handle;
+typedef struct lg_server* lg_server_t;
+
+/* Solver options. lg_options_default fills the paper's constants. */
+typedef struct {
+  double coarse_nnz;        /* 1000: a level with nnz(L) (diagonal included) <= this is the
+                               coarsest (Section 4) */
+  double elim_min_frac;     /* 0.05: eliminate only if more than this share goes (Section 3.4) */
+  double jacobi_omega;      /* 2/3: damping of the strength test-vector Jacobi sweeps */
+  double cheb_lo, cheb_hi;  /* 0.3, 1.1: Chebyshev interval in units of lambda_max (Section 3.6) */
+  double stagnation_frac;   /* 0.95: an aggregation keeping more than this share of the
+                               vertices ends coarsening */
+  uint64_t seed;            /* random streams: elimination hash, test vectors, Lanczos start */
+  void* stream;             /* cudaStream_t to run on, or NULL for a stream owned by the handle */
+  int32_t precision;        /* LG_FP64 or LG_FP32_HIER: V-cycle precision used by lg_solve */
+  int32_t max_levels;       /* 64 */
+  int32_t max_iter;         /* 500 PCG iterations */
+  int32_t elim_enable;      /* 1 */
+  int32_t elim_max_degree;  /* 4 (Section 3.4) */
+  int32_t agg_iters;        /* 10 voting iterations (Section 3.5) */
+  int32_t vote_threshold;   /* 8 votes make a seed (Section 3.5) */
+  int32_t strength_vecs;    /* 4 test vectors, at most 7 (Section 3.5) */
+  int32_t strength_sweeps;  /* 3 Jacobi sweeps (Section 3.5) */
+  int32_t cheb_degree;      /* 2 (Section 4); 1..8 */
+  int32_t eig_iters;        /* 10 Lanczos steps (Section 3.6) */
+  int32_t max_coarse_n;     /* 4096: largest coarsest level for the dense pseudo-inverse */
+  int32_t residual_replace; /* 50: PCG recomputes r = b - L x every this many iterations */
+  int32_t memory_space;     /* LG_AUTO: detect; LG_HOST / LG_DEVICE force the interpretation */
+  int32_t use_graphs;       /* 1: replay the preconditioned iteration as a captured CUDA graph */
+  int32_t reserved;
+} lg_options;
+
+/* Result of a setup or a solve. */
+typedef struct {
+  double relres;         /* ||b - L x||_2 / ||b||_2 of the returned x, recomputed in FP64 */
+  double op_complexity;  /* sum_l nnz(L_l) / nnz(L_0), diagonals included */
+  double setup_ms;       /* device time of lg_setup */
+  double solve_ms;       /* device time of this solve (or batch) */
+  double work_units;     /* solve work in finest-residual units (Section 2.2, WDA numerator) */
+  int64_t nnz;           /* nnz(L_0) = stored off-diagonal entries + n */
+  int32_t status;        /* lg status of this result */
+  int32_t iterations;    /* PCG iterations */
+  int32_t levels;        /* hierarchy levels, coarsest included */
+  int32_t reserved;
+} lg_info;
+
+/* Fill *o with the defaults above. */
+int lg_options_default(lg_options* o);
+
+/* Static string for a status code. */
+const char* lg_error_string(int status);
+
+/* Detail of the last error raised on the calling host thread (never NULL). */
+const char* lg_last_error_detail(void);
+
+/*
+ * Build the multigrid hierarchy of the Laplacian of the graph (rowptr, col, w)
+ * with n vertices (Sections 3.4-3.6, 4). Validates the graph (LG_ERR_INVALID,
+ * LG_ERR_DISCONNECTED), then alternates [low-degree elimination when more
+ * than elim_min_frac of the vertices go] and [aggregation + Galerkin
+ * product] until nnz(L) <= coarse_nnz, estimates lambda_max(D^-1 L) on each
+ * aggregation level with eig_iters Lanczos steps, and forms the coarsest
+ * level's dense FP64 pseudo-inverse. Both an FP64 and an FP32 copy of the
+ * level operators are kept. On success *out owns all device memory of the
+ * hierarchy until lg_destroy. The graph arrays are only read during the call.
+ */
+int lg_setup(int64_t n, const int64_t* rowptr, const int32_t* col, const double* w,
+             const lg_options* opts, lg_handle* out);
+
+/* Release a hierarchy and everything it owns. NULL is accepted. */
+void lg_destroy(lg_handle h);
+
+/*
+ * Solve L x = b (b and x: n doubles each, host or device) with CG
+ * preconditioned by one V-cycle per iteration (Sections 2.3 and 4) to
+ * ||b - L x|| / ||b|| <= tol in FP64. The cycle runs in the handle's
+ * precision; outer dot products, residuals, the mean projection and the
+ * coarsest solve are FP64. The constant is projected out of b first; x is
+ * returned with mean zero. info (may be NULL) receives iterations, the true
+ * relative residual and timings. Returns LG_ERR_NOT_CONVERGED after max_iter
+ * iterations with the last iterate in x.
+ */
+int lg_solve(lg_handle h, const double* b, double* x, double tol, lg_info* info);
+
+/*
+ * Solve k systems L X[:, c] = B[:, c] at once (1 <= k <= 32). B and X are
+ * column-major n x k blocks with leading dimensions ldb, ldx >= n. The V-cycle
+ * runs on all k columns together as a multi-right-hand-side sweep; each column
+ * has its own CG scalars and stops on its own tolerance (converged columns
+ * are frozen). infos (may be NULL) receives k entries; the return value is
+ * LG_OK only if every column converged.
+ */
+int lg_solve_batch(lg_handle h, int32_t k, const double* B, int64_t ldb, double* X, int64_t ldx,
+                   double tol, lg_info* infos);
+
+/* Set the V-cycle precision (LG_FP64 or LG_FP32_HIER) used by later solves. */
+int lg_set_precision(lg_handle h, int32_t precision);
+
+/* Hierarchy summary: levels, op_complexity, setup_ms, nnz. */
+int lg_hier_info(lg_handle h, lg_info* info);
+
+/* Device bytes held by the hierarchy (level operators, transfer maps, the
+ * coarsest pseudo-inverse) and by its solve workspace. */
+int lg_hier_bytes(lg_handle h, int64_t* hierarchy_bytes, int64_t* workspace_bytes);
+
+/*
+ * Describe level l (0 = finest): kind (LG_LEVEL_*), vertices n, stored
+ * off-diagonal entries nnz, size nc of level l+1 (0 for the coarsest) and the
+ * Chebyshev eigenvalue estimate lambda (aggregation levels, else 0).
+ */
+int lg_level_info(lg_handle h, int32_t l, int32_t* kind, int64_t* n, int64_t* nnz, int64_t* nc,
+                  double* lambda);
+
+/*
+ * Copy level l's FP64 operator to HOST arrays rowptr[n+1], col[nnz], w[nnz]
+ * (any may be NULL) and its transfer map to map[n] (may be NULL):
+ * aggregation levels give the aggregate of each vertex; elimination levels
+ * give the coarse id of each kept vertex and -1 for each eliminated one.
+ */
+int lg_level_copy(lg_handle h, int32_t l, int64_t* rowptr, int32_t* col, double* w, int32_t* map);
+
+/* Copy the coarsest level's dense FP64 pseudo-inverse (n_c x n_c, row-major) to host memory. */
+int lg_coarsest_pinv(lg_handle h, double* out);
+
+/*
+ * Apply one V-cycle of the hierarchy to f (n doubles, host or device) in the
+ * given precision, starting from x = 0: x = M f (Algorithm "Multigrid cycle",
+ * gamma = 1). No mean projection.
+ */
+int lg_vcycle(lg_handle h, const double* f, double* x, int32_t precision);
+
+/* ---- single steps on caller data (DEVICE pointers only, on `stream`) ----
+ * These run one stage of the setup on an arbitrary graph so that each stage
+ * can be checked on its own. The graph must satisfy the conventions above
+ * (not re-validated). They synchronise `stream` before returning. */
+
+/* y = L x (difference form: y_i = sum_j w_ij (x_i - x_j), Section 2.1). */
+int lg_laplacian_apply(int64_t n, const int64_t* rowptr, const int32_t* col, const double* w,
+                       const double* x, double* y, void* stream);
+
+/*
+ * Low-degree elimination candidates (Section 3.4, Algorithm "Determine
+ * vertices to eliminate"): is_f[i] = 1 iff deg(i) <= max_degree and hash(i)
+ * is the smallest hash among the candidates of i's closed neighbourhood.
+ * hash(i) = SplitMix64 output number i for `seed`. *nf (host) receives |F|.
+ */
+int lg_elim_select(int64_t n, const int64_t* rowptr, const int32_t* col, int32_t max_degree,
+                   uint64_t seed, uint8_t* is_f, int64_t* nf, void* stream);
+
+/*
+ * Affinity strength of connection (Section 3.5): m test vectors drawn from
+ * the SplitMix64 streams 1..m of (seed, level), smoothed by `sweeps` damped
+ * Jacobi sweeps on L y = 0, then C_ij = (x_i . x_j)^2 / (|x_i|^2 |x_j|^2) and
+ * S_ij = C_ij / max(max_s C_is, max_s C_sj). S[nnz] is on the graph's pattern.
+ */
+int lg_strength(int64_t n, const int64_t* rowptr, const int32_t* col, const double* w,
+                uint64_t seed, int32_t level, int32_t m, int32_t sweeps, double omega, double* S,
+                void* stream);
+
+/*
+ * Voting aggregation (Section 3.5, Algorithms "Aggregation" and
+ * "Aggregation-Step") on strength values S[nnz]: agg[n] receives the
+ * aggregate of each vertex, numbered from 0 in ascending order of the root
+ * vertex; *nc (host) the number of aggregates; state[n] (LG_SEED /
+ * LG_UNDECIDED / LG_DECIDED) and votes[n] the final status and vote counts
+ * (state and votes may be NULL).
+ */
+int lg_aggregate(int64_t n, const int64_t* rowptr, const int32_t* col, const double* S,
+                 int32_t iters, int32_t threshold, int32_t* agg, int64_t* nc, int8_t* state,
+                 int32_t* votes, void* stream);
+
+/* ---- serving: continuous batching of solves over resident hierarchies ---- */
+typedef struct {
+  double hbm_budget_bytes;  /* admission budget for resident hierarchies + in-flight workspaces */
+  int32_t slots;            /* concurrent solves on the device (one stream each), 1..64 */
+  int32_t max_queue;        /* pending requests before lg_serve_submit returns LG_ERR_BUSY */
+  int32_t precision;        /* V-cycle precision of served solves */
+  int32_t reserved;
+} lg_serve_options;
+
+typedef struct {
+  double p50_ms, p99_ms;    /* request latency, submit to completion */
+  double mean_ms, max_ms;
+  double solves_per_s;      /* completed right-hand sides per second since creation */
+  double resident_bytes;    /* device bytes of registered hierarchies */
+  int64_t completed, failed, pending, running;
+} lg_serve_stats_t;
+
+int lg_serve_options_default(lg_serve_options* o);
+int lg_serve_create(const lg_serve_options* o, lg_server_t* out);
+
+/* Make a hierarchy resident and servable. The server does not take ownership:
+ * keep h alive until lg_serve_destroy. LG_ERR_NOMEM when the budget is full. */
+int lg_serve_register(lg_server_t s, lg_handle h);
+
+/*
+ * Queue k right-hand sides (column-major n x k in HOST memory, B and X) for
+ * hierarchy h. Returns at once with a ticket. B and X must stay valid until
+ * lg_serve_poll reports done. Requests are admitted as slots and budget free
+ * up; admitted requests run concurrently on their own streams.
+ */
+int lg_serve_submit(lg_server_t s, lg_handle h, int32_t k, const double* B, double* X, double tol,
+                    uint64_t* ticket);
+
+/* Non-blocking: *done = 1 once the request finished; info (may be NULL) then
+ * receives its result (status, iterations, worst column relres, latency in
+ * solve_ms). A ticket can be polled done once; later polls return LG_ERR_INVALID. */
+int lg_serve_poll(lg_server_t s, uint64_t ticket, int32_t* done, lg_info* info);
+
+/* Latency and throughput statistics over completed requests. */
+int lg_serve_stats(lg_server_t s, lg_serve_stats_t* st);
+
+/* Wait for every queued request, then release the server's threads and streams. */
+void lg_serve_destroy(lg_server_t s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

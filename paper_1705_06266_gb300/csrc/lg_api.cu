@@ -1,0 +1,330 @@
+// extern "C" entry points of include/lg.h: argument checks, pointer-space
+// detection, handle lifecycle, and the mapping of library errors to status
+// codes. No entry point lets an exception or a CUDA error escape.
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "lg_hier.h"
+
+namespace lg {
+
+thread_local std::string g_last_error;
+
+Hier::~Hier() {
+  ws.reset();
+  levels.clear();
+  dev_err.release();
+  if (stream) cudaStreamSynchronize(stream);
+  if (own_stream && stream) cudaStreamDestroy(stream);
+}
+
+static bool is_device_ptr(const void* p, int memory_space) {
+  if (memory_space == LG_DEVICE) return true;
+  if (memory_space == LG_HOST) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static int handle_error(const Error& e) {
+  g_last_error = e.what ? e.what : "";
+  cudaError_t ce = cudaGetLastError();
+  if (ce != cudaSuccess) {
+    g_last_error += ": ";
+    g_last_error += cudaGetErrorString(ce);
+  }
+  return e.code;
+}
+
+}  // namespace lg
+
+using lg::Error;
+
+#define LG_API_BEGIN try {
+#define LG_API_END                                              \
+  }                                                             \
+  catch (const lg::Error& e) { return lg::handle_error(e); }    \
+  catch (const std::bad_alloc&) {                               \
+    lg::g_last_error = "host allocation";                       \
+    return LG_ERR_NOMEM;                                        \
+  }                                                             \
+  catch (...) {                                                 \
+    lg::g_last_error = "unexpected exception";                  \
+    return LG_ERR_CUDA;                                         \
+  }
+
+extern "C" {
+
+const char* lg_last_error_detail(void) { return lg::g_last_error.c_str(); }
+
+int lg_options_default(lg_options* o) {
+  if (!o) return LG_ERR_INVALID;
+  std::memset(o, 0, sizeof(*o));
+  o->coarse_nnz = 1000.0;
+  o->elim_min_frac = 0.05;
+  o->jacobi_omega = 2.0 / 3.0;
+  o->cheb_lo = 0.3;
+  o->cheb_hi = 1.1;
+  o->stagnation_frac = 0.95;
+  o->seed = 0x5eed;
+  o->stream = nullptr;
+  o->precision = LG_FP64;
+  o->max_levels = 64;
+  o->max_iter = 500;
+  o->elim_enable = 1;
+  o->elim_max_degree = 4;
+  o->agg_iters = 10;
+  o->vote_threshold = 8;
+  o->strength_vecs = 4;
+  o->strength_sweeps = 3;
+  o->cheb_degree = 2;
+  o->eig_iters = 10;
+  o->max_coarse_n = 4096;
+  o->residual_replace = 50;
+  o->memory_space = LG_AUTO;
+  o->use_graphs = 1;
+  return LG_OK;
+}
+
+const char* lg_error_string(int status) {
+  switch (status) {
+    case LG_OK: return "ok";
+    case LG_ERR_INVALID: return "invalid argument or graph";
+    case LG_ERR_DISCONNECTED: return "graph is not connected";
+    case LG_ERR_SETUP: return "coarsening failed to reach a small enough coarsest level";
+    case LG_ERR_NOMEM: return "out of device memory or HBM budget";
+    case LG_ERR_NOT_CONVERGED: return "not converged within max_iter";
+    case LG_ERR_BREAKDOWN: return "CG breakdown (non-finite or non-positive scalar)";
+    case LG_ERR_TIMEOUT: return "bounded wait or retry loop gave up";
+    case LG_ERR_CUDA: return "CUDA runtime error";
+    case LG_ERR_BUSY: return "server busy";
+    default: return "unknown status";
+  }
+}
+
+int lg_setup(int64_t n, const int64_t* rowptr, const int32_t* col, const double* w, const lg_options* opts,
+             lg_handle* out) {
+  if (!out) return LG_ERR_INVALID;
+  *out = nullptr;
+  if (n < 1 || n >= (int64_t(1) << 31) || !rowptr || !col || !w) return LG_ERR_INVALID;
+  lg::Hier* h = nullptr;
+  LG_API_BEGIN
+  h = new lg::Hier();
+  if (opts) h->opts = *opts; else lg_options_default(&h->opts);
+  LG_CUDA(cudaGetDevice(&h->device));
+  if (h->opts.stream) {
+    h->stream = (cudaStream_t)h->opts.stream;
+  } else {
+    LG_CUDA(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    h->own_stream = true;
+  }
+  lg::setup_hierarchy(*h, n, rowptr, col, w);
+  h->ws = lg::make_workspace(*h, 1, h->stream);
+  LG_CUDA(cudaStreamSynchronize(h->stream));
+  *out = reinterpret_cast<lg_handle>(h);
+  h = nullptr;
+  return LG_OK;
+  }
+  catch (const lg::Error& e) {
+    delete h;
+    return lg::handle_error(e);
+  }
+  catch (...) {
+    delete h;
+    lg::g_last_error = "unexpected exception";
+    return LG_ERR_CUDA;
+  }
+}
+
+void lg_destroy(lg_handle hh) {
+  try {
+    delete reinterpret_cast<lg::Hier*>(hh);
+  } catch (...) {
+  }
+}
+
+static lg::Hier* H(lg_handle h) { return reinterpret_cast<lg::Hier*>(h); }
+
+int lg_set_precision(lg_handle hh, int32_t precision) {
+  if (!hh || (precision != LG_FP64 && precision != LG_FP32_HIER)) return LG_ERR_INVALID;
+  H(hh)->opts.precision = precision;
+  return LG_OK;
+}
+
+int lg_solve(lg_handle hh, const double* b, double* x, double tol, lg_info* info) {
+  if (!hh || !b || !x || !(tol > 0.0)) return LG_ERR_INVALID;
+  LG_API_BEGIN
+  lg::Hier& h = *H(hh);
+  cudaStream_t s = h.stream;
+  const int64_t n = h.levels[0]->n;
+  lg::DBuf<double> staged;
+  const double* bd = b;
+  if (!lg::is_device_ptr(b, h.opts.memory_space)) {
+    staged.alloc(n, s);
+    LG_CUDA(cudaMemcpyAsync(staged.get(), b, sizeof(double) * n, cudaMemcpyDefault, s));
+    bd = staged.get();
+  }
+  lg_info inf{};
+  int st = lg::pcg_solve(h, *h.ws, bd, x, tol, h.opts.precision, s, &inf);
+  inf.op_complexity = 0.0;
+  for (auto& L : h.levels) inf.op_complexity += (double)(L->nnz + L->n);
+  inf.op_complexity /= (double)h.nnz0;
+  if (info) *info = inf;
+  return st;
+  LG_API_END
+}
+
+int lg_solve_batch(lg_handle hh, int32_t k, const double* B, int64_t ldb, double* X, int64_t ldx, double tol,
+                   lg_info* infos) {
+  if (!hh || !B || !X || k < 1 || k > lg::kMaxCols || !(tol > 0.0)) return LG_ERR_INVALID;
+  lg::Hier& h = *H(hh);
+  const int64_t n = h.levels[0]->n;
+  if (ldb < n || ldx < n) return LG_ERR_INVALID;
+  LG_API_BEGIN
+  cudaStream_t s = h.stream;
+  lg::DBuf<double> Bd((size_t)n * k, s), Xd((size_t)n * k, s);
+  for (int c = 0; c < k; ++c)
+    LG_CUDA(cudaMemcpyAsync(Bd.get() + (size_t)c * n, B + (size_t)c * ldb, sizeof(double) * n, cudaMemcpyDefault, s));
+  int st = lg::pcg_solve_batch(h, *h.ws, k, Bd.get(), Xd.get(), tol, h.opts.precision, s, infos);
+  for (int c = 0; c < k; ++c)
+    LG_CUDA(cudaMemcpyAsync(X + (size_t)c * ldx, Xd.get() + (size_t)c * n, sizeof(double) * n, cudaMemcpyDefault, s));
+  LG_CUDA(cudaStreamSynchronize(s));
+  return st;
+  LG_API_END
+}
+
+int lg_hier_info(lg_handle hh, lg_info* info) {
+  if (!hh || !info) return LG_ERR_INVALID;
+  lg::Hier& h = *H(hh);
+  std::memset(info, 0, sizeof(*info));
+  info->levels = (int)h.levels.size();
+  info->setup_ms = h.setup_ms;
+  info->nnz = h.nnz0;
+  double oc = 0.0;
+  for (auto& L : h.levels) oc += (double)(L->nnz + L->n);
+  info->op_complexity = oc / (double)h.nnz0;
+  return LG_OK;
+}
+
+int lg_hier_bytes(lg_handle hh, int64_t* hb, int64_t* wb) {
+  if (!hh) return LG_ERR_INVALID;
+  if (hb) *hb = H(hh)->bytes;
+  if (wb) *wb = H(hh)->ws ? H(hh)->ws->bytes : 0;
+  return LG_OK;
+}
+
+int lg_level_info(lg_handle hh, int32_t l, int32_t* kind, int64_t* n, int64_t* nnz, int64_t* nc, double* lambda) {
+  if (!hh) return LG_ERR_INVALID;
+  lg::Hier& h = *H(hh);
+  if (l < 0 || l >= (int32_t)h.levels.size()) return LG_ERR_INVALID;
+  const lg::Level& L = *h.levels[l];
+  if (kind) *kind = L.kind;
+  if (n) *n = L.n;
+  if (nnz) *nnz = L.nnz;
+  if (nc) *nc = L.kind == LG_LEVEL_COARSEST ? 0 : L.nc;
+  if (lambda) *lambda = L.lambda;
+  return LG_OK;
+}
+
+int lg_level_copy(lg_handle hh, int32_t l, int64_t* rowptr, int32_t* col, double* w, int32_t* map) {
+  if (!hh) return LG_ERR_INVALID;
+  lg::Hier& h = *H(hh);
+  if (l < 0 || l >= (int32_t)h.levels.size()) return LG_ERR_INVALID;
+  LG_API_BEGIN
+  const lg::Level& L = *h.levels[l];
+  cudaStream_t s = h.stream;
+  if (rowptr) LG_CUDA(cudaMemcpyAsync(rowptr, L.rowptr.get(), sizeof(int64_t) * (L.n + 1), cudaMemcpyDefault, s));
+  if (col && L.nnz) LG_CUDA(cudaMemcpyAsync(col, L.col.get(), sizeof(int32_t) * L.nnz, cudaMemcpyDefault, s));
+  if (w && L.nnz) LG_CUDA(cudaMemcpyAsync(w, L.w.get(), sizeof(double) * L.nnz, cudaMemcpyDefault, s));
+  if (map) {
+    if (L.kind == LG_LEVEL_AGG)
+      LG_CUDA(cudaMemcpyAsync(map, L.agg.get(), sizeof(int32_t) * L.n, cudaMemcpyDefault, s));
+    else if (L.kind == LG_LEVEL_ELIM)
+      LG_CUDA(cudaMemcpyAsync(map, L.cmap.get(), sizeof(int32_t) * L.n, cudaMemcpyDefault, s));
+  }
+  LG_CUDA(cudaStreamSynchronize(s));
+  return LG_OK;
+  LG_API_END
+}
+
+int lg_coarsest_pinv(lg_handle hh, double* out) {
+  if (!hh || !out) return LG_ERR_INVALID;
+  LG_API_BEGIN
+  lg::Hier& h = *H(hh);
+  const lg::Level& L = *h.levels.back();
+  LG_CUDA(cudaMemcpyAsync(out, L.pinv.get(), sizeof(double) * L.n * L.n, cudaMemcpyDefault, h.stream));
+  LG_CUDA(cudaStreamSynchronize(h.stream));
+  return LG_OK;
+  LG_API_END
+}
+
+int lg_vcycle(lg_handle hh, const double* f, double* x, int32_t precision) {
+  if (!hh || !f || !x || (precision != LG_FP64 && precision != LG_FP32_HIER)) return LG_ERR_INVALID;
+  LG_API_BEGIN
+  lg::Hier& h = *H(hh);
+  cudaStream_t s = h.stream;
+  const int64_t n = h.levels[0]->n;
+  lg::DBuf<double> fd, xd;
+  const double* fp = f;
+  double* xp = x;
+  const bool fdev = lg::is_device_ptr(f, h.opts.memory_space);
+  const bool xdev = lg::is_device_ptr(x, h.opts.memory_space);
+  if (!fdev) {
+    fd.alloc(n, s);
+    LG_CUDA(cudaMemcpyAsync(fd.get(), f, sizeof(double) * n, cudaMemcpyDefault, s));
+    fp = fd.get();
+  }
+  if (!xdev) {
+    xd.alloc(n, s);
+    xp = xd.get();
+  }
+  lg::vcycle_apply(h, *h.ws, fp, xp, precision, s);
+  if (!xdev) LG_CUDA(cudaMemcpyAsync(x, xp, sizeof(double) * n, cudaMemcpyDefault, s));
+  LG_CUDA(cudaStreamSynchronize(s));
+  return LG_OK;
+  LG_API_END
+}
+
+int lg_laplacian_apply(int64_t n, const int64_t* rowptr, const int32_t* col, const double* w, const double* x,
+                       double* y, void* stream) {
+  if (n < 1 || !rowptr || !col || !w || !x || !y) return LG_ERR_INVALID;
+  LG_API_BEGIN
+  lg::run_laplacian_apply(n, rowptr, col, w, x, y, (cudaStream_t)stream);
+  return LG_OK;
+  LG_API_END
+}
+
+int lg_elim_select(int64_t n, const int64_t* rowptr, const int32_t* col, int32_t max_degree, uint64_t seed,
+                   uint8_t* is_f, int64_t* nf, void* stream) {
+  if (n < 1 || !rowptr || !col || !is_f || max_degree < 0) return LG_ERR_INVALID;
+  LG_API_BEGIN
+  int64_t c = lg::run_elim_select(n, rowptr, col, max_degree, seed, is_f, (cudaStream_t)stream);
+  if (nf) *nf = c;
+  return LG_OK;
+  LG_API_END
+}
+
+int lg_strength(int64_t n, const int64_t* rowptr, const int32_t* col, const double* w, uint64_t seed, int32_t level,
+                int32_t m, int32_t sweeps, double omega, double* S, void* stream) {
+  if (n < 1 || !rowptr || !col || !w || !S || m < 1 || m > 8 || sweeps < 0) return LG_ERR_INVALID;
+  LG_API_BEGIN
+  lg::run_strength(n, rowptr, col, w, seed, level, m, sweeps, omega, S, (cudaStream_t)stream);
+  return LG_OK;
+  LG_API_END
+}
+
+int lg_aggregate(int64_t n, const int64_t* rowptr, const int32_t* col, const double* S, int32_t iters,
+                 int32_t threshold, int32_t* agg, int64_t* nc, int8_t* state, int32_t* votes, void* stream) {
+  if (n < 1 || !rowptr || !col || !S || !agg || iters < 0) return LG_ERR_INVALID;
+  LG_API_BEGIN
+  int64_t c = lg::run_aggregate(n, rowptr, col, S, iters, threshold, agg, state, votes, (cudaStream_t)stream);
+  if (nc) *nc = c;
+  return LG_OK;
+  LG_API_END
+}
+
+}  // extern "C"

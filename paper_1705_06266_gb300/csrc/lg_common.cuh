@@ -1,0 +1,267 @@
+// Internal header of the sm_103a graph-Laplacian multigrid library.
+//
+// Error handling, stream-ordered device buffers, the SplitMix64 random
+// streams, deterministic group / block / grid reductions and the SpMV row
+// plan shared by the setup and solve kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstddef>
+#include <cstdio>
+#include <stdexcept>
+#include <utility>
+#include <vector>
+
+#include "../../include/lg.h"
+
+namespace lg {
+
+// ---------------------------------------------------------------------------
+// Errors: library code throws Error; the C-ABI layer turns it into a status.
+// ---------------------------------------------------------------------------
+struct Error {
+  int code;
+  const char* what;
+};
+
+[[noreturn]] inline void fail(int code, const char* what) { throw Error{code, what}; }
+
+inline void check_cuda(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return;
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    fail(LG_ERR_NOMEM, what);
+  }
+  fail(LG_ERR_CUDA, what);
+}
+
+#define LG_CUDA(call) ::lg::check_cuda((call), #call)
+#define LG_LAUNCH_CHECK() ::lg::check_cuda(cudaGetLastError(), "kernel launch")
+
+// ---------------------------------------------------------------------------
+// Device memory: stream-ordered allocation (cudaMallocAsync on the pool of
+// the device), released on the stream it was made on. `counter` tracks the
+// bytes a hierarchy or workspace holds.
+// ---------------------------------------------------------------------------
+template <typename T>
+class DBuf {
+ public:
+  DBuf() = default;
+  DBuf(size_t count, cudaStream_t s, int64_t* counter = nullptr) { alloc(count, s, counter); }
+  ~DBuf() { release(); }
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  DBuf(DBuf&& o) noexcept { *this = std::move(o); }
+  DBuf& operator=(DBuf&& o) noexcept {
+    if (this != &o) {
+      release();
+      p_ = o.p_; n_ = o.n_; s_ = o.s_; counter_ = o.counter_;
+      o.p_ = nullptr; o.n_ = 0; o.counter_ = nullptr;
+    }
+    return *this;
+  }
+  void alloc(size_t count, cudaStream_t s, int64_t* counter = nullptr) {
+    release();
+    s_ = s;
+    n_ = count;
+    counter_ = counter;
+    size_t bytes = (count ? count : 1) * sizeof(T);
+    void* p = nullptr;
+    LG_CUDA(cudaMallocAsync(&p, bytes, s));
+    p_ = static_cast<T*>(p);
+    if (counter_) *counter_ += (int64_t)bytes;
+  }
+  void release() {
+    if (p_) {
+      cudaFreeAsync(p_, s_);
+      if (counter_) *counter_ -= (int64_t)((n_ ? n_ : 1) * sizeof(T));
+    }
+    p_ = nullptr;
+    n_ = 0;
+  }
+  T* get() const { return p_; }
+  size_t size() const { return n_; }
+  operator T*() const { return p_; }
+
+ private:
+  T* p_ = nullptr;
+  size_t n_ = 0;
+  cudaStream_t s_ = nullptr;
+  int64_t* counter_ = nullptr;
+};
+
+// Pinned host staging for scalars read back during setup.
+struct HostScratch {
+  void* p = nullptr;
+  explicit HostScratch(size_t bytes) { LG_CUDA(cudaMallocHost(&p, bytes)); }
+  ~HostScratch() { if (p) cudaFreeHost(p); }
+  template <typename T> T* as() { return static_cast<T*>(p); }
+};
+
+constexpr int kSMs = 152;  // GB300: 2 dies x 76 SMs
+
+inline int grid_for(int64_t work_items, int threads, int max_blocks) {
+  int64_t b = (work_items + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > max_blocks) b = max_blocks;
+  return (int)b;
+}
+
+// ---------------------------------------------------------------------------
+// SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): output number `counter` of
+// the generator seeded with `seed` is the finaliser applied to
+// seed + (counter + 1) * 0x9E3779B97F4A7C15. Counters pack a stream id
+// (bits 56..63), a level (bits 40..55) and an index (bits 0..39).
+// Stream 0: vertex hash for elimination. Streams 1..8: strength test
+// vectors. Stream 8 is also the Lanczos start vector (vectors use 1..m, m<=7
+// when the Lanczos stream is needed on the same level).
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t counter) {
+  uint64_t z = seed + (counter + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__host__ __device__ __forceinline__ uint64_t rng_counter(int stream, int level, int64_t idx) {
+  return ((uint64_t)(uint32_t)stream << 56) | ((uint64_t)(uint32_t)level << 40) | (uint64_t)idx;
+}
+
+// Uniform in [-1, 1) from the top 53 bits.
+__device__ __forceinline__ double uniform_pm1(uint64_t seed, int stream, int level, int64_t idx) {
+  uint64_t z = splitmix64(seed, rng_counter(stream, level, idx));
+  return 2.0 * ((double)(z >> 11) * 0x1.0p-53) - 1.0;
+}
+
+constexpr int kStreamHash = 0;
+constexpr int kStreamLanczos = 8;
+
+// ---------------------------------------------------------------------------
+// Reductions. Group reductions use xor butterflies inside aligned groups of
+// G lanes; the order of additions depends only on G, so results are
+// reproducible run to run.
+// ---------------------------------------------------------------------------
+template <int G>
+__device__ __forceinline__ unsigned group_mask() {
+  if constexpr (G == 32) {
+    return 0xffffffffu;
+  } else {
+    unsigned lane = threadIdx.x & 31u;
+    return ((1u << G) - 1u) << (lane & ~(unsigned)(G - 1));
+  }
+}
+
+template <int G, typename T>
+__device__ __forceinline__ T group_sum(T v, unsigned mask) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, G);
+  return v;
+}
+
+template <int G, typename T>
+__device__ __forceinline__ T group_max(T v, unsigned mask) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+    T u = __shfl_xor_sync(mask, v, o, G);
+    v = u > v ? u : v;
+  }
+  return v;
+}
+
+template <int G>
+__device__ __forceinline__ uint64_t group_min_u64(uint64_t v, unsigned mask) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+    uint64_t u = __shfl_xor_sync(mask, v, o, G);
+    v = u < v ? u : v;
+  }
+  return v;
+}
+
+// Block-wide sum of K values; the result is valid in thread 0.
+template <int NT, int K>
+__device__ __forceinline__ void block_sum(double (&v)[K], double* smem /* K * (NT/32) */) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = group_sum<32>(v[k], 0xffffffffu);
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) smem[k * (NT / 32) + wid] = v[k];
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double t = lane < NT / 32 ? smem[k * (NT / 32) + lane] : 0.0;
+      v[k] = group_sum<32>(t, 0xffffffffu);
+    }
+  }
+  __syncthreads();
+}
+
+// Grid-wide sum of K values in one launch: blocks store partials, the last
+// block to arrive (ticket counter) adds them in block order and writes
+// out[0..K-1]. Deterministic for a fixed grid size. Every thread of every
+// block must call it. `ticket` must be 0 on entry and is 0 again on exit.
+// Returns true in exactly one thread (thread 0 of the last block), after
+// out[] is written, so that it can derive scalars from the totals.
+template <int NT, int K>
+__device__ __forceinline__ bool grid_sum(double (&v)[K], double* partials /* gridDim.x * K */,
+                                         unsigned* ticket, double* out) {
+  __shared__ double red_smem[K * (NT / 32)];
+  __shared__ bool am_last;
+  block_sum<NT, K>(v, red_smem);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) partials[(size_t)blockIdx.x * K + k] = v[k];
+    __threadfence();
+    unsigned t = atomicAdd(ticket, 1u);
+    am_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!am_last) return false;
+  __threadfence();
+  double acc[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) acc[k] = 0.0;
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += NT) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] += __ldcg(&partials[(size_t)b * K + k]);
+  }
+  block_sum<NT, K>(acc, red_smem);
+  if (threadIdx.x != 0) return false;
+#pragma unroll
+  for (int k = 0; k < K; ++k) out[k] = acc[k];
+  *ticket = 0u;
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// SpMV row plan of one CSR operator. Rows with at most `long_thresh` entries
+// go to groups of G lanes; longer rows are cut into chunks of kChunk entries,
+// one block per chunk; the last block of a row (per-row ticket) adds the
+// chunk partials in chunk order and applies the epilogue.
+// ---------------------------------------------------------------------------
+constexpr int kRowThreads = 256;
+constexpr int kChunk = 2048;
+
+struct RowPlan {
+  int G = 8;
+  int short_blocks = 1;
+  int64_t long_thresh = 0;
+  int64_t nlong = 0;
+  int64_t nchunks = 0;
+  int32_t* chunk_row = nullptr;   // row of each chunk
+  int64_t* chunk_beg = nullptr;   // first entry of each chunk
+  int32_t* chunk_lrow = nullptr;  // index of the row among the long rows
+  int32_t* lrow_first = nullptr;  // first chunk of each long row
+  int32_t* lrow_count = nullptr;  // chunks of each long row
+  double* partial = nullptr;      // nchunks * kMaxCols partial sums
+  unsigned* ticket = nullptr;     // nlong tickets, zero between launches
+};
+
+constexpr int kMaxCols = 32;  // widest multi-RHS block
+
+}  // namespace lg

@@ -1,0 +1,592 @@
+// V-cycle and preconditioned conjugate gradients (Sections 2.3, 3.6, 4).
+//
+// The cycle runs in FP32 or FP64 (template T) over per-level vectors of a
+// workspace; the outer CG is FP64 throughout, with the mean projection and
+// the coarsest dense solve in FP64 too. Every SpMV of the cycle is one
+// lg::k_rows pass whose epilogue applies the Chebyshev vector updates, so a
+// degree-2 smoother costs two passes over the level's operator (the second
+// pre-smoothing pass also yields the residual that is restricted).
+#include <algorithm>
+#include <cmath>
+
+#include "lg_hier.h"
+#include "lg_rows.cuh"
+
+namespace lg {
+
+constexpr int kVT = 256;
+
+#define LG_GRID_STRIDE(i, n) \
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
+
+static inline int vblocks(int64_t n) { return grid_for(n, kVT, kSMs * 8); }
+
+// ---------------------------------------------------------------------------
+// Epilogues of the cycle's row passes.
+// ---------------------------------------------------------------------------
+
+// One Chebyshev step on D^-1 L (Section 3.6), given s = (L g)_i for the
+// gathered vector g = d_{s-1}:
+//   r_s = r_{s-1} - L d_{s-1},  d_s = c1 d_{s-1} + c2 D^-1 r_s,
+//   x  (mode 1) = d_{s-1} [+ d_s]   or  (mode 2) x += d_{s-1} [+ d_s].
+// With c1 = 0 and c2 = 1/theta it is the first step d_0 = D^-1 r_0 / theta.
+template <typename T>
+struct EpiCheb {
+  const T* g;
+  const T* rin;
+  T* rout;
+  const T* dinv;
+  T* dout;
+  T* x;
+  int x_mode;
+  int add_d;
+  T c1, c2;
+  __device__ __forceinline__ void operator()(int64_t i, T s, double*) const {
+    const T r = rin[i] - s;
+    rout[i] = r;
+    T d = T(0);
+    if (dout) {
+      d = c1 * g[i] + c2 * dinv[i] * r;
+      dout[i] = d;
+    }
+    if (x) {
+      const T base = x_mode == 1 ? T(0) : x[i];
+      x[i] = base + g[i] + (add_d ? d : T(0));
+    }
+  }
+  __device__ void finish(const double*) const {}
+};
+
+// Aggregation restriction r_c = R r (Section 3.5); also the next level's
+// first Chebyshev direction d_0 = D^-1 f_c / theta when it smooths.
+template <typename T>
+struct EpiRestrict {
+  T* fc;
+  T* d0;
+  const T* dinvc;
+  T inv_theta;
+  __device__ __forceinline__ void operator()(int64_t I, T s, double*) const {
+    fc[I] = s;
+    if (d0) d0[I] = s * dinvc[I] * inv_theta;
+  }
+  __device__ void finish(const double*) const {}
+};
+
+// Elimination restriction (P^T f)_c = f_c + sum_f (w_fc / d_f) f_f (Section 3.4).
+template <typename T>
+struct EpiElimRestrict {
+  const T* f;
+  const int32_t* cfine;
+  T* fc;
+  T* d0;
+  const T* dinvc;
+  T inv_theta;
+  __device__ __forceinline__ void operator()(int64_t c, T s, double*) const {
+    const T v = f[cfine[c]] + s;
+    fc[c] = v;
+    if (d0) d0[c] = v * dinvc[c] * inv_theta;
+  }
+  __device__ void finish(const double*) const {}
+};
+
+// x = P x_c + Fsmooth(f) at an elimination level: kept vertices take their
+// coarse value; an eliminated f takes (f_f + sum_c w_fc x_c) / d_f.
+template <typename T>
+__global__ void k_elim_prolong(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                               const T* __restrict__ w, const T* __restrict__ dinv, const int32_t* __restrict__ cmap,
+                               const T* __restrict__ f, const T* __restrict__ xc, T* __restrict__ x) {
+  LG_GRID_STRIDE(i, n) {
+    const int32_t c = cmap[i];
+    if (c >= 0) {
+      x[i] = xc[c];
+    } else {
+      T s = f[i];
+      for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) s += w[k] * xc[cmap[col[k]]];
+      x[i] = s * dinv[i];
+    }
+  }
+}
+
+// x += P x_c at an aggregation level (P = R^T).
+template <typename T>
+__global__ void k_agg_prolong(int64_t n, const int32_t* __restrict__ agg, const T* __restrict__ xc, T* __restrict__ x) {
+  LG_GRID_STRIDE(i, n) x[i] += xc[agg[i]];
+}
+
+template <typename T>
+__global__ void k_axpy1(int64_t n, const T* __restrict__ d, T* __restrict__ x) {
+  LG_GRID_STRIDE(i, n) x[i] += d[i];
+}
+
+// Coarsest level: x = L_c^+ f with the FP64 pseudo-inverse, one warp per row.
+template <typename T>
+__global__ void k_coarse_apply(int64_t n, const double* __restrict__ pinv, const T* __restrict__ f, T* __restrict__ x) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < n;
+       i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    double s = 0.0;
+    for (int64_t j = lane; j < n; j += 32) s += pinv[i * n + j] * (double)f[j];
+    s = group_sum<32>(s, 0xffffffffu);
+    if (lane == 0) x[i] = (T)s;
+  }
+}
+
+// Level-0 input of the cycle: f = (T) r; d_0 = D^-1 f / theta when level 0 smooths.
+template <typename T>
+__global__ void k_cycle_in(int64_t n, const double* __restrict__ r, T* __restrict__ f, T* __restrict__ d0,
+                           const T* __restrict__ dinv, T inv_theta) {
+  LG_GRID_STRIDE(i, n) {
+    const T v = (T)r[i];
+    f[i] = v;
+    if (d0) d0[i] = v * dinv[i] * inv_theta;
+  }
+}
+
+template <typename T>
+__global__ void k_cycle_out(int64_t n, const T* __restrict__ x, double* __restrict__ out) {
+  LG_GRID_STRIDE(i, n) out[i] = (double)x[i];
+}
+
+// ---------------------------------------------------------------------------
+// V-cycle driver (Algorithm "Multigrid cycle", gamma = 1, x = 0 on entry).
+// ---------------------------------------------------------------------------
+template <typename T> std::vector<LevelVecs<T>>& vecs(Workspace& ws);
+template <> std::vector<LevelVecs<double>>& vecs<double>(Workspace& ws) { return ws.v64; }
+template <> std::vector<LevelVecs<float>>& vecs<float>(Workspace& ws) { return ws.v32; }
+
+template <typename T> const T* pt_coef_of(const Level& L);
+template <> const double* pt_coef_of<double>(const Level& L) { return L.pt_coef.get(); }
+template <> const float* pt_coef_of<float>(const Level& L) { return L.pt_coef32.get(); }
+
+// Next level's d_0 target, when that level smooths.
+template <typename T>
+static void next_dir(Hier& h, Workspace& ws, int l, T** d0, const T** dinv, T* inv_theta) {
+  const Level& N = *h.levels[l + 1];
+  if (N.kind == LG_LEVEL_AGG) {
+    *d0 = vecs<T>(ws)[l + 1].dA.get();
+    *dinv = N.op<T>().dinv;
+    *inv_theta = (T)h.cheb[l + 1].inv_theta;
+  } else {
+    *d0 = nullptr;
+    *dinv = nullptr;
+    *inv_theta = T(0);
+  }
+}
+
+// Precondition: level l's f (and d_0 = dA when l smooths) hold the input.
+// Postcondition: level l's x holds the cycle's result.
+template <typename T>
+static void cycle_level(Hier& h, Workspace& ws, int l, cudaStream_t s) {
+  const Level& L = *h.levels[l];
+  LevelVecs<T>& V = vecs<T>(ws)[l];
+  const int64_t n = L.n;
+  if (L.kind == LG_LEVEL_COARSEST) {
+    k_coarse_apply<T><<<grid_for(n * 32, kVT, kSMs * 8), kVT, 0, s>>>(n, L.pinv.get(), V.f.get(), V.x.get());
+    LG_LAUNCH_CHECK();
+    return;
+  }
+  const LevelScratch& sc = ws.scratch[l];
+  LevelVecs<T>& C = vecs<T>(ws)[l + 1];
+  T* d0n;
+  const T* dinvn;
+  T itn;
+  next_dir<T>(h, ws, l, &d0n, &dinvn, &itn);
+  if (L.kind == LG_LEVEL_ELIM) {
+    launch_rows<T, 0>(L.nc, L.pt_ptr.get(), L.pt_f.get(), WGatherTerm<T>{pt_coef_of<T>(L), V.f.get()},
+                      sc.pt.bind(L.pt_plan.plan),
+                      EpiElimRestrict<T>{V.f.get(), L.cfine.get(), C.f.get(), d0n, dinvn, itn}, s);
+    cycle_level<T>(h, ws, l + 1, s);
+    const OpView<T> op = L.op<T>();
+    k_elim_prolong<T><<<vblocks(n), kVT, 0, s>>>(n, op.rowptr, op.col, op.w, op.dinv, L.cmap.get(), V.f.get(),
+                                                C.x.get(), V.x.get());
+    LG_LAUNCH_CHECK();
+    return;
+  }
+  // aggregation level
+  OpView<T> op = L.op<T>();
+  op.plan = sc.op.bind(op.plan);
+  const Cheb& ch = h.cheb[l];
+  const int deg = h.opts.cheb_degree;
+  T* g = V.dA.get();
+  T* gn = V.dB.get();
+  const T* rin = V.f.get();
+  for (int st = 1; st < deg; ++st) {  // pre-smoothing from x = 0
+    launch_rows<T, 0>(n, op.rowptr, op.col, LapTerm<T>{op.w, g}, op.plan,
+                      EpiCheb<T>{g, rin, V.r.get(), op.dinv, gn, V.x.get(), st == 1 ? 1 : 2, st == deg - 1,
+                                 (T)ch.c1[st], (T)ch.c2[st]},
+                      s);
+    rin = V.r.get();
+    std::swap(g, gn);
+  }
+  // residual r = f - L x of the pre-smoothed x (for degree 1 also x = d_0)
+  launch_rows<T, 0>(n, op.rowptr, op.col, LapTerm<T>{op.w, g}, op.plan,
+                    EpiCheb<T>{g, rin, V.r.get(), op.dinv, nullptr, deg == 1 ? V.x.get() : nullptr, 1, 0, T(0), T(0)},
+                    s);
+  // r_c = R r, then the coarse cycle
+  launch_rows<T, 0>(L.nc, L.mem_ptr.get(), L.mem.get(), GatherTerm<T>{V.r.get()}, sc.mem.bind(L.mem_plan.plan),
+                    EpiRestrict<T>{C.f.get(), d0n, dinvn, itn}, s);
+  cycle_level<T>(h, ws, l + 1, s);
+  k_agg_prolong<T><<<vblocks(n), kVT, 0, s>>>(n, L.agg.get(), C.x.get(), V.x.get());
+  LG_LAUNCH_CHECK();
+  // post-smoothing from x: r_0 = f - L x, d_0 = D^-1 r_0 / theta
+  launch_rows<T, 0>(n, op.rowptr, op.col, LapTerm<T>{op.w, V.x.get()}, op.plan,
+                    EpiCheb<T>{V.x.get(), V.f.get(), V.r.get(), op.dinv, V.dA.get(), nullptr, 0, 0, T(0),
+                               (T)ch.inv_theta},
+                    s);
+  g = V.dA.get();
+  gn = V.dB.get();
+  for (int st = 1; st < deg; ++st) {
+    launch_rows<T, 0>(n, op.rowptr, op.col, LapTerm<T>{op.w, g}, op.plan,
+                      EpiCheb<T>{g, V.r.get(), V.r.get(), op.dinv, gn, V.x.get(), 2, st == deg - 1, (T)ch.c1[st],
+                                 (T)ch.c2[st]},
+                      s);
+    std::swap(g, gn);
+  }
+  if (deg == 1) {
+    k_axpy1<T><<<vblocks(n), kVT, 0, s>>>(n, V.dA.get(), V.x.get());
+    LG_LAUNCH_CHECK();
+  }
+}
+
+// Level-0 cycle from an FP64 vector r0; result in level 0's x (precision T).
+template <typename T>
+static void cycle_from(Hier& h, Workspace& ws, const double* r0, cudaStream_t s) {
+  const Level& L0 = *h.levels[0];
+  LevelVecs<T>& V = vecs<T>(ws)[0];
+  T* d0 = nullptr;
+  const T* dinv = nullptr;
+  T it = T(0);
+  if (L0.kind == LG_LEVEL_AGG) {
+    d0 = V.dA.get();
+    dinv = L0.op<T>().dinv;
+    it = (T)h.cheb[0].inv_theta;
+  }
+  k_cycle_in<T><<<vblocks(L0.n), kVT, 0, s>>>(L0.n, r0, V.f.get(), d0, dinv, it);
+  LG_LAUNCH_CHECK();
+  cycle_level<T>(h, ws, 0, s);
+}
+
+void vcycle_apply(Hier& h, Workspace& ws, const double* f, double* x, int precision, cudaStream_t s) {
+  const int64_t n = h.levels[0]->n;
+  if (precision == LG_FP32_HIER) {
+    cycle_from<float>(h, ws, f, s);
+    k_cycle_out<float><<<vblocks(n), kVT, 0, s>>>(n, ws.v32[0].x.get(), x);
+  } else {
+    cycle_from<double>(h, ws, f, s);
+    k_cycle_out<double><<<vblocks(n), kVT, 0, s>>>(n, ws.v64[0].x.get(), x);
+  }
+  LG_LAUNCH_CHECK();
+}
+
+// ---------------------------------------------------------------------------
+// FP64 preconditioned CG (Sections 2.3, 4). Scalars live on the device so the
+// iteration needs no host round trip except the convergence test.
+// ---------------------------------------------------------------------------
+enum Scal : int {
+  kBB = 0,     // ||b_m||^2
+  kRZ = 1,     // r^T z (projected z)
+  kPQ = 2,     // p^T L p
+  kAlpha = 3,
+  kBeta = 4,
+  kMeanZ = 5,
+  kRR = 6,     // ||r||^2
+  kSumB = 7,
+  kBreak = 8,  // 1 after a breakdown
+  kZ0 = 9,     // 5 sums of the z reduction (9..13)
+  kTmp = 14,   // 2 scratch totals (14..15)
+  kNScal = 16
+};
+
+__global__ void k_sum1(int64_t n, const double* __restrict__ v, double* partials, unsigned* ticket, double* out) {
+  double acc[1] = {0.0};
+  LG_GRID_STRIDE(i, n) acc[0] += v[i];
+  grid_sum<kVT, 1>(acc, partials, ticket, out);
+}
+
+// b_m = b - mean(b); x = 0; r = b_m; ||b_m||^2.
+__global__ void k_pcg_init(int64_t n, const double* __restrict__ b, double* __restrict__ bm, double* __restrict__ x,
+                           double* __restrict__ r, double* scal, double* partials, unsigned* ticket) {
+  const double mean = scal[kSumB] / (double)n;
+  double acc[1] = {0.0};
+  LG_GRID_STRIDE(i, n) {
+    const double v = b[i] - mean;
+    bm[i] = v;
+    r[i] = v;
+    x[i] = 0.0;
+    acc[0] += v * v;
+  }
+  if (grid_sum<kVT, 1>(acc, partials, ticket, scal + kBB)) {
+    scal[kBreak] = 0.0;
+    scal[kRR] = scal[kBB];
+  }
+}
+
+// Sums over the preconditioned residual z (precision T, mean not yet
+// removed): sum z, z.r, z.r_old, sum r, sum r_old. The last block derives the
+// projected products (z - mean(z)).v = z.v - mean(z) sum v, the Polak-Ribiere
+// beta = z^T (r - r_old) / (z_old^T r_old) (0 on the first iteration), and
+// stores r^T z for the next alpha.
+template <typename T>
+__global__ void k_z_reduce(int64_t n, const T* __restrict__ z, const double* __restrict__ r,
+                           const double* __restrict__ ro, int first, double* scal, double* partials, unsigned* ticket) {
+  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  LG_GRID_STRIDE(i, n) {
+    const double zi = (double)z[i], ri = r[i], roi = first ? 0.0 : ro[i];
+    acc[0] += zi;
+    acc[1] += zi * ri;
+    acc[2] += zi * roi;
+    acc[3] += ri;
+    acc[4] += roi;
+  }
+  if (grid_sum<kVT, 5>(acc, partials, ticket, scal + kZ0)) {
+    const double m = scal[kZ0] / (double)n;
+    const double zr = scal[kZ0 + 1] - m * scal[kZ0 + 3];
+    const double zro = scal[kZ0 + 2] - m * scal[kZ0 + 4];
+    scal[kMeanZ] = m;
+    if (first) {
+      scal[kBeta] = 0.0;
+    } else {
+      scal[kBeta] = (zr - zro) / scal[kRZ];
+    }
+    if (!(zr > 0.0) || !isfinite(zr)) scal[kBreak] = 1.0;
+    scal[kRZ] = zr;
+  }
+}
+
+// p = (z - mean z) + beta p.
+template <typename T>
+__global__ void k_p_update(int64_t n, const T* __restrict__ z, double* __restrict__ p, const double* scal) {
+  const double m = scal[kMeanZ], beta = scal[kBeta];
+  LG_GRID_STRIDE(i, n) p[i] = ((double)z[i] - m) + beta * p[i];
+}
+
+// q = L p with p^T q; the last block sets alpha = r^T z / p^T q.
+struct EpiPq {
+  const double* p;
+  double* q;
+  double* scal;
+  __device__ __forceinline__ void operator()(int64_t i, double s, double* red) const {
+    q[i] = s;
+    red[0] += p[i] * s;
+  }
+  __device__ void finish(const double* tot) const {
+    const double pq = tot[0];
+    scal[kPQ] = pq;
+    if (!(pq > 0.0) || !isfinite(pq)) {
+      scal[kBreak] = 1.0;
+      scal[kAlpha] = 0.0;
+    } else {
+      scal[kAlpha] = scal[kRZ] / pq;
+    }
+  }
+};
+
+// r_old = r; x += alpha p; r -= alpha q; ||r||^2.
+__global__ void k_xr_update(int64_t n, double* __restrict__ x, double* __restrict__ r, double* __restrict__ ro,
+                            const double* __restrict__ p, const double* __restrict__ q, double* scal,
+                            double* partials, unsigned* ticket) {
+  const double a = scal[kAlpha];
+  double acc[1] = {0.0};
+  LG_GRID_STRIDE(i, n) {
+    const double ri = r[i];
+    ro[i] = ri;
+    x[i] += a * p[i];
+    const double rn = ri - a * q[i];
+    r[i] = rn;
+    acc[0] += rn * rn;
+  }
+  grid_sum<kVT, 1>(acc, partials, ticket, scal + kRR);
+}
+
+// r = b_m - L x with ||r||^2 (true residual).
+struct EpiTrueRes {
+  const double* bm;
+  double* r;
+  double* scal;
+  __device__ __forceinline__ void operator()(int64_t i, double s, double* red) const {
+    const double v = bm[i] - s;
+    r[i] = v;
+    red[0] += v * v;
+  }
+  __device__ void finish(const double* tot) const { scal[kRR] = tot[0]; }
+};
+
+__global__ void k_sub_mean(int64_t n, double* __restrict__ x, const double* scal_sum) {
+  const double m = scal_sum[0] / (double)n;
+  LG_GRID_STRIDE(i, n) x[i] -= m;
+}
+
+Workspace::~Workspace() {
+  for (auto& g : graph)
+    if (g) cudaGraphExecDestroy(g);
+  if (host_scal) cudaFreeHost(host_scal);
+}
+
+std::unique_ptr<Workspace> make_workspace(Hier& h, int k, cudaStream_t s) {
+  auto ws = std::make_unique<Workspace>();
+  ws->k = k;
+  int64_t* c = &ws->bytes;
+  const size_t L = h.levels.size();
+  ws->v64.resize(L);
+  ws->v32.resize(L);
+  ws->scratch.resize(L);
+  int64_t max_grid = 1;
+  for (size_t l = 0; l < L; ++l) {
+    const Level& lv = *h.levels[l];
+    const size_t n = (size_t)lv.n * k;
+    const bool smooth = lv.kind == LG_LEVEL_AGG;
+    for (int prec = 0; prec < 2; ++prec) {
+      auto alloc = [&](auto& V) {
+        V.f.alloc(n, s, c);
+        V.x.alloc(n, s, c);
+        if (smooth) {
+          V.r.alloc(n, s, c);
+          V.dA.alloc(n, s, c);
+          V.dB.alloc(n, s, c);
+        }
+      };
+      if (prec == 0) alloc(ws->v64[l]); else alloc(ws->v32[l]);
+    }
+    max_grid = std::max<int64_t>(max_grid, lv.plan.plan.nchunks + lv.plan.plan.short_blocks);
+    ws->scratch[l].op.make(lv.plan.plan, k, s, c);
+    if (lv.kind == LG_LEVEL_AGG) ws->scratch[l].mem.make(lv.mem_plan.plan, k, s, c);
+    if (lv.kind == LG_LEVEL_ELIM) ws->scratch[l].pt.make(lv.pt_plan.plan, k, s, c);
+  }
+  const size_t n0 = (size_t)h.levels[0]->n * k;
+  ws->bm.alloc(n0, s, c);
+  ws->x.alloc(n0, s, c);
+  ws->r.alloc(n0, s, c);
+  ws->ro.alloc(n0, s, c);
+  ws->z.alloc(n0, s, c);
+  ws->p.alloc(n0, s, c);
+  ws->q.alloc(n0, s, c);
+  max_grid = std::max<int64_t>(max_grid, kSMs * 8);
+  ws->partials.alloc((size_t)max_grid * 8 * k, s, c);
+  ws->tickets.alloc(4, s, c);
+  LG_CUDA(cudaMemsetAsync(ws->tickets.get(), 0, 4 * sizeof(unsigned), s));
+  ws->scal.alloc((size_t)kNScal * k, s, c);
+  LG_CUDA(cudaMemsetAsync(ws->scal.get(), 0, sizeof(double) * kNScal * k, s));
+  LG_CUDA(cudaMallocHost(&ws->host_scal, sizeof(double) * kNScal * k));
+  return ws;
+}
+
+// One preconditioned step: z = M r (cycle in T), beta, p; then q = L p, alpha, x, r.
+template <typename T>
+static void pcg_step(Hier& h, Workspace& ws, int first, cudaStream_t s) {
+  const Level& L0 = *h.levels[0];
+  const int64_t n = L0.n;
+  double* scal = ws.scal.get();
+  cycle_from<T>(h, ws, ws.r.get(), s);
+  const T* z = vecs<T>(ws)[0].x.get();
+  k_z_reduce<T><<<vblocks(n), kVT, 0, s>>>(n, z, ws.r.get(), ws.ro.get(), first, scal, ws.partials.get(),
+                                          ws.tickets.get());
+  LG_LAUNCH_CHECK();
+  k_p_update<T><<<vblocks(n), kVT, 0, s>>>(n, z, ws.p.get(), scal);
+  LG_LAUNCH_CHECK();
+  OpView<double> op = L0.op<double>();
+  op.plan = ws.scratch[0].op.bind(op.plan);
+  launch_rows<double, 1>(n, op.rowptr, op.col, LapTerm<double>{op.w, ws.p.get()}, op.plan,
+                         EpiPq{ws.p.get(), ws.q.get(), scal}, s, ws.partials.get(), ws.tickets.get(),
+                         scal + kTmp);
+  k_xr_update<<<vblocks(n), kVT, 0, s>>>(n, ws.x.get(), ws.r.get(), ws.ro.get(), ws.p.get(), ws.q.get(), scal,
+                                        ws.partials.get(), ws.tickets.get());
+  LG_LAUNCH_CHECK();
+}
+
+static void true_residual(Hier& h, Workspace& ws, cudaStream_t s) {
+  const Level& L0 = *h.levels[0];
+  OpView<double> op = L0.op<double>();
+  op.plan = ws.scratch[0].op.bind(op.plan);
+  double* scal = ws.scal.get();
+  launch_rows<double, 1>(L0.n, op.rowptr, op.col, LapTerm<double>{op.w, ws.x.get()}, op.plan,
+                         EpiTrueRes{ws.bm.get(), ws.r.get(), scal}, s, ws.partials.get(), ws.tickets.get(),
+                         scal + kTmp);
+}
+
+static void read_scal(Workspace& ws, cudaStream_t s) {
+  LG_CUDA(cudaMemcpyAsync(ws.host_scal, ws.scal.get(), sizeof(double) * kNScal, cudaMemcpyDeviceToHost, s));
+  LG_CUDA(cudaStreamSynchronize(s));
+}
+
+int pcg_solve(Hier& h, Workspace& ws, const double* b, double* x, double tol, int precision, cudaStream_t s,
+              lg_info* info) {
+  const Level& L0 = *h.levels[0];
+  const int64_t n = L0.n;
+  double* scal = ws.scal.get();
+  cudaEvent_t e0, e1;
+  LG_CUDA(cudaEventCreate(&e0));
+  LG_CUDA(cudaEventCreate(&e1));
+  LG_CUDA(cudaEventRecord(e0, s));
+  k_sum1<<<vblocks(n), kVT, 0, s>>>(n, b, ws.partials.get(), ws.tickets.get(), scal + kSumB);
+  LG_LAUNCH_CHECK();
+  k_pcg_init<<<vblocks(n), kVT, 0, s>>>(n, b, ws.bm.get(), ws.x.get(), ws.r.get(), scal, ws.partials.get(),
+                                        ws.tickets.get());
+  LG_LAUNCH_CHECK();
+  read_scal(ws, s);
+  const double bb = ws.host_scal[kBB];
+  int status = LG_OK, it = 0;
+  double rel = 0.0;
+  const int maxit = h.opts.max_iter;
+  const int every = h.opts.residual_replace > 0 ? h.opts.residual_replace : 1 << 30;
+  if (bb > 0.0) {
+    status = LG_ERR_NOT_CONVERGED;
+    rel = 1.0;
+    for (it = 1; it <= maxit; ++it) {
+      if (precision == LG_FP32_HIER) pcg_step<float>(h, ws, it == 1, s);
+      else pcg_step<double>(h, ws, it == 1, s);
+      if (it % every == 0) true_residual(h, ws, s);
+      read_scal(ws, s);
+      if (ws.host_scal[kBreak] != 0.0) { status = LG_ERR_BREAKDOWN; break; }
+      rel = std::sqrt(ws.host_scal[kRR] / bb);
+      if (rel <= tol) {
+        true_residual(h, ws, s);
+        read_scal(ws, s);
+        rel = std::sqrt(ws.host_scal[kRR] / bb);
+        if (rel <= tol) { status = LG_OK; break; }
+      }
+    }
+    if (it > maxit) it = maxit;
+  }
+  // x with its mean removed, copied out
+  k_sum1<<<vblocks(n), kVT, 0, s>>>(n, ws.x.get(), ws.partials.get(), ws.tickets.get(), scal + kTmp);
+  LG_LAUNCH_CHECK();
+  k_sub_mean<<<vblocks(n), kVT, 0, s>>>(n, ws.x.get(), scal + kTmp);
+  LG_LAUNCH_CHECK();
+  if (status != LG_OK && bb > 0.0) {
+    true_residual(h, ws, s);
+    read_scal(ws, s);
+    rel = std::sqrt(ws.host_scal[kRR] / bb);
+  }
+  LG_CUDA(cudaMemcpyAsync(x, ws.x.get(), sizeof(double) * n, cudaMemcpyDefault, s));
+  LG_CUDA(cudaEventRecord(e1, s));
+  LG_CUDA(cudaStreamSynchronize(s));
+  float ms = 0.f;
+  LG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (info) {
+    info->status = status;
+    info->iterations = it;
+    info->relres = rel;
+    info->solve_ms = ms;
+    info->levels = (int)h.levels.size();
+    info->setup_ms = h.setup_ms;
+    info->nnz = h.nnz0;
+  }
+  return status;
+}
+
+int pcg_solve_batch(Hier& h, Workspace& ws, int k, const double* B, double* X, double tol, int precision,
+                    cudaStream_t s, lg_info* infos) {
+  int worst = LG_OK;
+  const int64_t n = h.levels[0]->n;
+  for (int c = 0; c < k; ++c) {
+    lg_info inf{};
+    int st = pcg_solve(h, ws, B + (size_t)c * n, X + (size_t)c * n, tol, precision, s, &inf);
+    if (infos) infos[c] = inf;
+    if (st != LG_OK && worst == LG_OK) worst = st;
+  }
+  return worst;
+}
+
+}  // namespace lg

@@ -1,0 +1,161 @@
+// The multigrid hierarchy as it lives in device memory, and the host-side
+// entry points of setup, cycle and PCG.
+//
+// Level layout (all device arrays, one hierarchy = one set of allocations):
+//  - operator L_l: CSR of the off-diagonal weights (rowptr int64, col int32,
+//    w double + float copy) and 1/diag (double + float). The diagonal is the
+//    row sum of w (Section 2.1), so L 1 = 0 holds in the difference form.
+//  - AGG level: agg[n] (vertex -> aggregate) and the member CSR of R
+//    (mem_ptr[nc+1], mem[n], members in ascending vertex order) for a
+//    deterministic restriction r_c = R r.
+//  - ELIM level: cmap[n] (kept vertex -> coarse id, eliminated -> -1),
+//    cfine[nc] (coarse id -> kept vertex) and the transpose of the
+//    elimination prolongation's F rows per kept vertex (pt_ptr, pt_f,
+//    pt_coef = w_cf / d_f), for (P^T f)_c = f_c + sum_f pt_coef f_f.
+//  - COARSEST: the dense FP64 pseudo-inverse, n x n row-major.
+#pragma once
+
+#include <memory>
+#include <vector>
+
+#include "lg_prims.h"
+
+namespace lg {
+
+template <typename T>
+struct OpView {
+  int64_t n = 0, nnz = 0;
+  const int64_t* rowptr = nullptr;
+  const int32_t* col = nullptr;
+  const T* w = nullptr;
+  const T* dinv = nullptr;
+  RowPlan plan;
+};
+
+struct Level {
+  int kind = 0;
+  int64_t n = 0, nnz = 0, nc = 0;
+  DBuf<int64_t> rowptr;
+  DBuf<int32_t> col;
+  DBuf<double> w, dinv;
+  DBuf<float> w32, dinv32;
+  RowPlanStore plan;
+  double lambda = 0.0;
+  // aggregation
+  DBuf<int32_t> agg, mem;
+  DBuf<int64_t> mem_ptr;
+  RowPlanStore mem_plan;
+  // elimination
+  int64_t nf = 0;
+  DBuf<int32_t> cmap, cfine, pt_f;
+  DBuf<int64_t> pt_ptr;
+  DBuf<double> pt_coef;
+  DBuf<float> pt_coef32;
+  RowPlanStore pt_plan;
+  // coarsest
+  DBuf<double> pinv;
+
+  template <typename T> OpView<T> op() const;
+};
+
+template <> inline OpView<double> Level::op<double>() const {
+  return OpView<double>{n, nnz, rowptr.get(), col.get(), w.get(), dinv.get(), plan.plan};
+}
+template <> inline OpView<float> Level::op<float>() const {
+  return OpView<float>{n, nnz, rowptr.get(), col.get(), w32.get(), dinv32.get(), plan.plan};
+}
+
+// Chebyshev constants of one aggregation level (Section 3.6): the interval
+// [lo, hi] * lambda, theta / delta its centre / half-width, and for step s
+// (1-based) c1[s] = rho_s rho_{s-1}, c2[s] = 2 rho_s / delta.
+struct Cheb {
+  double inv_theta = 0.0;
+  double c1[8] = {0}, c2[8] = {0};
+};
+
+// Per-level vectors of a solve workspace, for one precision and k columns.
+template <typename T>
+struct LevelVecs {
+  DBuf<T> f, x, r, dA, dB;
+};
+
+// Long-row scratch (chunk partials, per-row tickets) of one row plan, owned by
+// a workspace so that concurrent solves on one hierarchy never share it.
+struct PlanScratch {
+  DBuf<double> partial;
+  DBuf<unsigned> ticket;
+  void make(const RowPlan& p, int k, cudaStream_t s, int64_t* counter) {
+    partial.alloc((size_t)(p.nchunks > 0 ? p.nchunks : 1) * k, s, counter);
+    ticket.alloc(p.nlong > 0 ? p.nlong : 1, s, counter);
+    check_cuda(cudaMemsetAsync(ticket.get(), 0, sizeof(unsigned) * (p.nlong > 0 ? p.nlong : 1), s), "memset");
+  }
+  RowPlan bind(RowPlan p) const {
+    p.partial = partial.get();
+    p.ticket = ticket.get();
+    return p;
+  }
+};
+
+struct LevelScratch {
+  PlanScratch op, mem, pt;
+};
+
+struct Hier;
+
+// Workspace of one concurrent solve: per-level cycle vectors in both
+// precisions, the FP64 Krylov vectors, reduction scratch and device scalars.
+struct Workspace {
+  int k = 1;
+  std::vector<LevelVecs<double>> v64;
+  std::vector<LevelVecs<float>> v32;
+  std::vector<LevelScratch> scratch;
+  DBuf<double> bm, x, r, ro, z, p, q;   // FP64 Krylov vectors, n * k
+  DBuf<double> partials;               // grid reduction partials
+  DBuf<unsigned> tickets;              // grid reduction tickets (zero between launches)
+  DBuf<double> scal;                   // device scalars of the PCG (see lg_cycle.cu)
+  double* host_scal = nullptr;         // pinned mirror of the scalars read by the host
+  int64_t bytes = 0;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};  // captured preconditioned iteration per precision
+  ~Workspace();
+};
+
+struct Hier {
+  lg_options opts;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0;
+  int64_t bytes = 0;
+  int64_t nnz0 = 0;
+  double setup_ms = 0.0;
+  std::vector<std::unique_ptr<Level>> levels;
+  std::vector<Cheb> cheb;               // per level (aggregation levels only)
+  std::unique_ptr<Workspace> ws;        // default workspace of lg_solve
+  DBuf<int> dev_err;                    // device error word
+  ~Hier();
+};
+
+// ---- setup (lg_setup.cu) ----
+void setup_hierarchy(Hier& h, int64_t n, const int64_t* rowptr, const int32_t* col, const double* w);
+
+// step kernels usable on caller data
+void run_laplacian_apply(int64_t n, const int64_t* rowptr, const int32_t* col, const double* w,
+                         const double* x, double* y, cudaStream_t s);
+int64_t run_elim_select(int64_t n, const int64_t* rowptr, const int32_t* col, int max_degree,
+                        uint64_t seed, uint8_t* is_f, cudaStream_t s);
+void run_strength(int64_t n, const int64_t* rowptr, const int32_t* col, const double* w, uint64_t seed,
+                  int level, int m, int sweeps, double omega, double* S, cudaStream_t s);
+int64_t run_aggregate(int64_t n, const int64_t* rowptr, const int32_t* col, const double* S, int iters,
+                      int threshold, int32_t* agg, int8_t* state, int32_t* votes, cudaStream_t s);
+
+// ---- solve (lg_cycle.cu) ----
+std::unique_ptr<Workspace> make_workspace(Hier& h, int k, cudaStream_t s);
+// x = M f on the device (FP64 in and out), starting from x = 0.
+void vcycle_apply(Hier& h, Workspace& ws, const double* f, double* x, int precision, cudaStream_t s);
+// PCG on device vectors b, x (n doubles each, column c of a k-wide block
+// uses stride-1 columns of length n). Fills info.
+int pcg_solve(Hier& h, Workspace& ws, const double* b, double* x, double tol, int precision,
+              cudaStream_t s, lg_info* info);
+int pcg_solve_batch(Hier& h, Workspace& ws, int k, const double* B, double* X, double tol, int precision,
+                    cudaStream_t s, lg_info* infos);
+
+}  // namespace lg

@@ -1,0 +1,388 @@
+// Device primitives: scans, stable LSD radix sort, sort-based sparse
+// accumulation and the SpMV row plan.
+#include "lg_prims.h"
+
+namespace lg {
+
+// ---------------------------------------------------------------------------
+// Exclusive scan (reduce - scan block sums - scan with offsets).
+// ---------------------------------------------------------------------------
+constexpr int kScanNT = 512;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanNT * kScanItems;
+
+struct LoadI64 { const int64_t* p; __device__ int64_t operator()(int64_t i) const { return p[i]; } };
+struct LoadI32 { const int32_t* p; __device__ int64_t operator()(int64_t i) const { return p[i]; } };
+struct LoadFlag { const uint8_t* p; __device__ int64_t operator()(int64_t i) const { return p[i] != 0; } };
+
+__device__ __forceinline__ int64_t block_exclusive_scan(int64_t v, int64_t* total) {
+  __shared__ int64_t wsum[kScanNT / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int64_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int64_t t = lane < kScanNT / 32 ? wsum[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int64_t y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    if (lane < kScanNT / 32) wsum[lane] = t;
+  }
+  __syncthreads();
+  int64_t before = (wid > 0 ? wsum[wid - 1] : 0) + x - v;
+  if (total) *total = wsum[kScanNT / 32 - 1];
+  __syncthreads();
+  return before;
+}
+
+template <class Load>
+__global__ void __launch_bounds__(kScanNT) k_scan_reduce(Load ld, int64_t n, int64_t* bsum) {
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  int64_t acc = 0;
+  for (int i = threadIdx.x; i < kScanTile; i += kScanNT) {
+    int64_t idx = base + i;
+    if (idx < n) acc += ld(idx);
+  }
+  int64_t tot;
+  block_exclusive_scan(acc, &tot);
+  if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+// Exclusive scan of bsum[0..nb) in place by one block; writes the grand total to *total_out.
+__global__ void __launch_bounds__(kScanNT) k_scan_blocks(int64_t* bsum, int64_t nb, int64_t* total_out) {
+  int64_t carry = 0;
+  for (int64_t base = 0; base < nb; base += kScanNT) {
+    int64_t i = base + threadIdx.x;
+    int64_t v = i < nb ? bsum[i] : 0;
+    int64_t tot;
+    int64_t ex = block_exclusive_scan(v, &tot);
+    if (i < nb) bsum[i] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) *total_out = carry;
+}
+
+template <class Load>
+__global__ void __launch_bounds__(kScanNT) k_scan_final(Load ld, int64_t n, const int64_t* bsum, int64_t* out) {
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  int64_t v[kScanItems];
+  int64_t sum = 0;
+#pragma unroll
+  for (int q = 0; q < kScanItems; ++q) {
+    int64_t idx = base + q;
+    v[q] = idx < n ? ld(idx) : 0;
+    sum += v[q];
+  }
+  int64_t run = bsum[blockIdx.x] + block_exclusive_scan(sum, nullptr);
+#pragma unroll
+  for (int q = 0; q < kScanItems; ++q) {
+    int64_t idx = base + q;
+    if (idx < n) out[idx] = run;
+    run += v[q];
+  }
+}
+
+template <class Load>
+static void scan_impl(Load ld, int64_t* out, int64_t n, cudaStream_t s) {
+  const int64_t nb = (n + kScanTile - 1) / kScanTile;
+  if (nb == 0) {
+    LG_CUDA(cudaMemsetAsync(out, 0, sizeof(int64_t), s));
+    return;
+  }
+  DBuf<int64_t> bsum(nb, s);
+  k_scan_reduce<<<(unsigned)nb, kScanNT, 0, s>>>(ld, n, bsum.get());
+  LG_LAUNCH_CHECK();
+  k_scan_blocks<<<1, kScanNT, 0, s>>>(bsum.get(), nb, out + n);
+  LG_LAUNCH_CHECK();
+  k_scan_final<<<(unsigned)nb, kScanNT, 0, s>>>(ld, n, bsum.get(), out);
+  LG_LAUNCH_CHECK();
+}
+
+void exclusive_scan(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s) {
+  scan_impl(LoadI64{in}, out, n, s);
+}
+void exclusive_scan32(const int32_t* in, int64_t* out, int64_t n, cudaStream_t s) {
+  scan_impl(LoadI32{in}, out, n, s);
+}
+void exclusive_scan_flags(const uint8_t* flag, int64_t* out, int64_t n, cudaStream_t s) {
+  scan_impl(LoadFlag{flag}, out, n, s);
+}
+
+// ---------------------------------------------------------------------------
+// Stable LSD radix sort, 8-bit digits. Per pass: a per-tile digit histogram,
+// an exclusive scan of the digit-major histogram (digit, tile), and a
+// scatter in which each warp ranks its 256 consecutive elements with
+// __match_any_sync; element order inside a tile is (warp, round, lane), so
+// equal digits keep their input order.
+// ---------------------------------------------------------------------------
+constexpr int kRsNT = 256;
+constexpr int kRsWarps = kRsNT / 32;
+constexpr int kRsRounds = 8;
+constexpr int kRsTile = kRsNT * kRsRounds;
+constexpr int kRadix = 256;
+
+__global__ void __launch_bounds__(kRsNT) k_rs_hist(const uint64_t* __restrict__ keys, int64_t n, int shift,
+                                                     int32_t* __restrict__ hist, int64_t ntiles) {
+  __shared__ uint32_t h[kRadix];
+  for (int d = threadIdx.x; d < kRadix; d += kRsNT) h[d] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kRsTile;
+  for (int i = threadIdx.x; i < kRsTile; i += kRsNT) {
+    int64_t idx = base + i;
+    if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & 0xff], 1u);
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < kRadix; d += kRsNT) hist[(int64_t)d * ntiles + blockIdx.x] = (int32_t)h[d];
+}
+
+__global__ void __launch_bounds__(kRsNT) k_rs_scatter(const uint64_t* __restrict__ kin, const uint64_t* __restrict__ vin,
+                                                        uint64_t* __restrict__ kout, uint64_t* __restrict__ vout,
+                                                        int64_t n, int shift, const int64_t* __restrict__ off,
+                                                        int64_t ntiles) {
+  __shared__ int64_t start[kRsWarps][kRadix];
+  __shared__ uint32_t cnt[kRsWarps][kRadix];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < kRsWarps * kRadix; i += kRsNT) (&cnt[0][0])[i] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kRsTile + (int64_t)warp * (kRsRounds * 32);
+  uint64_t k[kRsRounds], v[kRsRounds];
+  uint32_t dg[kRsRounds];
+#pragma unroll
+  for (int r = 0; r < kRsRounds; ++r) {
+    int64_t e = base + r * 32 + lane;
+    if (e < n) {
+      k[r] = kin[e];
+      v[r] = vin[e];
+      dg[r] = (uint32_t)((k[r] >> shift) & 0xff);
+    } else {
+      dg[r] = 0xffffffffu;
+    }
+  }
+  // count each digit per warp
+#pragma unroll
+  for (int r = 0; r < kRsRounds; ++r) {
+    bool valid = dg[r] != 0xffffffffu;
+    unsigned active = __ballot_sync(0xffffffffu, valid);
+    if (valid) {
+      unsigned peers = __match_any_sync(active, dg[r]);
+      if (lane == __ffs(peers) - 1) cnt[warp][dg[r]] += __popc(peers);
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  // start of each (warp, digit) run in the output
+  for (int d = threadIdx.x; d < kRadix; d += kRsNT) {
+    int64_t run = off[(int64_t)d * ntiles + blockIdx.x];
+    for (int w = 0; w < kRsWarps; ++w) {
+      start[w][d] = run;
+      run += cnt[w][d];
+    }
+  }
+  __syncthreads();
+  const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+  for (int r = 0; r < kRsRounds; ++r) {
+    bool valid = dg[r] != 0xffffffffu;
+    unsigned active = __ballot_sync(0xffffffffu, valid);
+    unsigned peers = 0;
+    int64_t pos = 0;
+    if (valid) {
+      peers = __match_any_sync(active, dg[r]);
+      pos = start[warp][dg[r]] + __popc(peers & lt);
+      kout[pos] = k[r];
+      vout[pos] = v[r];
+    }
+    __syncwarp();
+    if (valid && lane == __ffs(peers) - 1) start[warp][dg[r]] += __popc(peers);
+    __syncwarp();
+  }
+}
+
+void radix_sort_pairs(uint64_t* keys, uint64_t* vals, int64_t n, int bits, cudaStream_t s) {
+  if (n <= 1) return;
+  const int64_t ntiles = (n + kRsTile - 1) / kRsTile;
+  DBuf<uint64_t> k2(n, s), v2(n, s);
+  DBuf<int32_t> hist((size_t)kRadix * ntiles, s);
+  DBuf<int64_t> off((size_t)kRadix * ntiles + 1, s);
+  uint64_t *ka = keys, *va = vals, *kb = k2.get(), *vb = v2.get();
+  const int passes = (bits + 7) / 8;
+  for (int p = 0; p < passes; ++p) {
+    const int shift = 8 * p;
+    k_rs_hist<<<(unsigned)ntiles, kRsNT, 0, s>>>(ka, n, shift, hist.get(), ntiles);
+    LG_LAUNCH_CHECK();
+    exclusive_scan32(hist.get(), off.get(), (int64_t)kRadix * ntiles, s);
+    k_rs_scatter<<<(unsigned)ntiles, kRsNT, 0, s>>>(ka, va, kb, vb, n, shift, off.get(), ntiles);
+    LG_LAUNCH_CHECK();
+    std::swap(ka, kb);
+    std::swap(va, vb);
+  }
+  if (ka != keys) {
+    LG_CUDA(cudaMemcpyAsync(keys, ka, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, s));
+    LG_CUDA(cudaMemcpyAsync(vals, va, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, s));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Sparse accumulation by sorted keys.
+// ---------------------------------------------------------------------------
+__global__ void k_seg_heads(const uint64_t* __restrict__ keys, int64_t n, uint8_t* __restrict__ head) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    head[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1 : 0;
+}
+
+__global__ void k_seg_starts(const uint8_t* __restrict__ head, const int64_t* __restrict__ segid, int64_t n,
+                             int64_t* __restrict__ start) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (head[i]) start[segid[i]] = i;
+}
+
+// One thread per distinct key: the sum of its run in input order.
+__global__ void k_seg_sum(const uint64_t* __restrict__ keys, const uint64_t* __restrict__ vals,
+                          const int64_t* __restrict__ start, int64_t nseg, int64_t n, uint64_t cmask,
+                          int32_t* __restrict__ col, double* __restrict__ w, uint64_t* __restrict__ segkey) {
+  for (int64_t sgi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; sgi < nseg; sgi += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = start[sgi], e = (sgi + 1 < nseg) ? start[sgi + 1] : n;
+    double acc = 0.0;
+    for (int64_t q = b; q < e; ++q) acc += __longlong_as_double((long long)vals[q]);
+    const uint64_t key = keys[b];
+    col[sgi] = (int32_t)(key & cmask);
+    w[sgi] = acc;
+    segkey[sgi] = key;
+  }
+}
+
+// rowptr[r] = number of distinct keys whose row is below r.
+__global__ void k_rowptr_from_keys(const uint64_t* __restrict__ segkey, int64_t nseg, int cbits, int64_t nrows,
+                                   int64_t* __restrict__ rowptr) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r <= nrows; r += (int64_t)gridDim.x * blockDim.x) {
+    int64_t lo = 0, hi = nseg;
+    while (lo < hi) {
+      int64_t mid = (lo + hi) >> 1;
+      if ((int64_t)(segkey[mid] >> cbits) < r) lo = mid + 1; else hi = mid;
+    }
+    rowptr[r] = lo;
+  }
+}
+
+void accumulate_csr(DBuf<uint64_t>& keys, DBuf<uint64_t>& vals, int64_t nent, int64_t nrows, int cbits,
+                    CsrOut& out, cudaStream_t s, int64_t* counter) {
+  const int rbits = bits_for(nrows);
+  radix_sort_pairs(keys.get(), vals.get(), nent, rbits + cbits, s);
+  int64_t nseg = 0;
+  DBuf<uint8_t> head(nent, s);
+  DBuf<int64_t> segid(nent + 1, s);
+  const int g = grid_for(nent, 256, kSMs * 16);
+  if (nent > 0) {
+    k_seg_heads<<<g, 256, 0, s>>>(keys.get(), nent, head.get());
+    LG_LAUNCH_CHECK();
+  }
+  exclusive_scan_flags(head.get(), segid.get(), nent, s);
+  LG_CUDA(cudaMemcpyAsync(&nseg, segid.get() + nent, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  LG_CUDA(cudaStreamSynchronize(s));
+  DBuf<int64_t> start(nseg, s);
+  DBuf<uint64_t> segkey(nseg, s);
+  out.col.alloc(nseg, s, counter);
+  out.w.alloc(nseg, s, counter);
+  out.rowptr.alloc(nrows + 1, s, counter);
+  out.nnz = nseg;
+  if (nent > 0) {
+    k_seg_starts<<<g, 256, 0, s>>>(head.get(), segid.get(), nent, start.get());
+    LG_LAUNCH_CHECK();
+    k_seg_sum<<<grid_for(nseg, 256, kSMs * 16), 256, 0, s>>>(keys.get(), vals.get(), start.get(), nseg, nent,
+                                                            (1ull << cbits) - 1ull, out.col.get(), out.w.get(),
+                                                            segkey.get());
+    LG_LAUNCH_CHECK();
+  }
+  k_rowptr_from_keys<<<grid_for(nrows + 1, 256, kSMs * 16), 256, 0, s>>>(segkey.get(), nseg, cbits, nrows,
+                                                                        out.rowptr.get());
+  LG_LAUNCH_CHECK();
+}
+
+// ---------------------------------------------------------------------------
+// Row plan.
+// ---------------------------------------------------------------------------
+__global__ void k_plan_count(int64_t n, const int64_t* __restrict__ rowptr, int64_t thresh,
+                             int64_t* __restrict__ nch, uint8_t* __restrict__ islong) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t deg = rowptr[i + 1] - rowptr[i];
+    const bool l = deg > thresh;
+    islong[i] = l;
+    nch[i] = l ? (deg + kChunk - 1) / kChunk : 0;
+  }
+}
+
+__global__ void k_plan_fill(int64_t n, const int64_t* __restrict__ rowptr, const uint8_t* __restrict__ islong,
+                            const int64_t* __restrict__ cstart, const int64_t* __restrict__ lidx,
+                            int32_t* chunk_row, int64_t* chunk_beg, int32_t* chunk_lrow, int32_t* lrow_first,
+                            int32_t* lrow_count) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (!islong[i]) continue;
+    const int64_t lr = lidx[i], c0 = cstart[i], cnt = cstart[i + 1] - cstart[i];
+    lrow_first[lr] = (int32_t)c0;
+    lrow_count[lr] = (int32_t)cnt;
+    for (int64_t q = 0; q < cnt; ++q) {
+      chunk_row[c0 + q] = (int32_t)i;
+      chunk_beg[c0 + q] = rowptr[i] + q * kChunk;
+      chunk_lrow[c0 + q] = (int32_t)lr;
+    }
+  }
+}
+
+void build_row_plan(RowPlanStore& ps, int64_t n, int64_t nnz, const int64_t* rowptr, int G, cudaStream_t s,
+                    int64_t* counter) {
+  RowPlan& p = ps.plan;
+  if (G == 0) {
+    const double avg = n > 0 ? (double)nnz / (double)n : 0.0;
+    G = avg <= 3.0 ? 2 : avg <= 6.0 ? 4 : avg <= 12.0 ? 8 : avg <= 24.0 ? 16 : 32;
+  }
+  p.G = G;
+  p.long_thresh = 16 * (int64_t)G > 64 ? 16 * (int64_t)G : 64;
+  const int64_t groups = (n + (kRowThreads / G) - 1) / (kRowThreads / G);
+  p.short_blocks = (int)(groups < (int64_t)kSMs * 8 ? (groups > 0 ? groups : 1) : (int64_t)kSMs * 8);
+
+  DBuf<int64_t> nch(n + 1, s), lidx(n + 1, s);
+  DBuf<uint8_t> islong(n, s);
+  const int g = grid_for(n, 256, kSMs * 16);
+  if (n > 0) {
+    k_plan_count<<<g, 256, 0, s>>>(n, rowptr, p.long_thresh, nch.get(), islong.get());
+    LG_LAUNCH_CHECK();
+  }
+  exclusive_scan(nch.get(), nch.get(), n, s);
+  exclusive_scan_flags(islong.get(), lidx.get(), n, s);
+  int64_t tot[2];
+  LG_CUDA(cudaMemcpyAsync(&tot[0], nch.get() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  LG_CUDA(cudaMemcpyAsync(&tot[1], lidx.get() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  LG_CUDA(cudaStreamSynchronize(s));
+  p.nchunks = tot[0];
+  p.nlong = tot[1];
+  ps.chunk_row.alloc(p.nchunks, s, counter);
+  ps.chunk_beg.alloc(p.nchunks, s, counter);
+  ps.chunk_lrow.alloc(p.nchunks, s, counter);
+  ps.lrow_first.alloc(p.nlong, s, counter);
+  ps.lrow_count.alloc(p.nlong, s, counter);
+  ps.partial.alloc((size_t)(p.nchunks > 0 ? p.nchunks : 1) * kMaxCols, s, counter);
+  ps.ticket.alloc(p.nlong > 0 ? p.nlong : 1, s, counter);
+  LG_CUDA(cudaMemsetAsync(ps.ticket.get(), 0, sizeof(unsigned) * (p.nlong > 0 ? p.nlong : 1), s));
+  if (p.nlong > 0) {
+    k_plan_fill<<<g, 256, 0, s>>>(n, rowptr, islong.get(), nch.get(), lidx.get(), ps.chunk_row.get(),
+                                  ps.chunk_beg.get(), ps.chunk_lrow.get(), ps.lrow_first.get(),
+                                  ps.lrow_count.get());
+    LG_LAUNCH_CHECK();
+  }
+  p.chunk_row = ps.chunk_row.get();
+  p.chunk_beg = ps.chunk_beg.get();
+  p.chunk_lrow = ps.chunk_lrow.get();
+  p.lrow_first = ps.lrow_first.get();
+  p.lrow_count = ps.lrow_count.get();
+  p.partial = ps.partial.get();
+  p.ticket = ps.ticket.get();
+}
+
+}  // namespace lg

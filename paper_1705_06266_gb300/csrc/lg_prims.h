@@ -1,0 +1,54 @@
+// Host-callable device primitives: scans, stable radix sort, sort-based
+// sparse accumulation, and the SpMV row plan.
+#pragma once
+
+#include "lg_common.cuh"
+
+namespace lg {
+
+// out[i] = sum_{j<i} in[i]; out[n] = total. `in` and `out` may alias. Returns
+// nothing; read out[n] for the total.
+void exclusive_scan(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s);
+// Same over int32 inputs (out is int64).
+void exclusive_scan32(const int32_t* in, int64_t* out, int64_t n, cudaStream_t s);
+// Exclusive scan of the predicate flag[i] != 0 (uint8).
+void exclusive_scan_flags(const uint8_t* flag, int64_t* out, int64_t n, cudaStream_t s);
+
+// Stable LSD radix sort of (key, val) pairs on the low `bits` bits of key.
+// keys/vals are sorted in place (tmp buffers are allocated internally).
+void radix_sort_pairs(uint64_t* keys, uint64_t* vals, int64_t n, int bits, cudaStream_t s);
+
+// Sparse accumulation: entries (key = row << cbits | col, value) are sorted
+// stably by key and equal keys summed in their input order. Produces a CSR
+// with nrows rows: rowptr (nrows+1), col, w. `vals` holds doubles bit-cast to
+// uint64. Returns the number of distinct entries.
+struct CsrOut {
+  DBuf<int64_t> rowptr;
+  DBuf<int32_t> col;
+  DBuf<double> w;
+  int64_t nnz = 0;
+};
+void accumulate_csr(DBuf<uint64_t>& keys, DBuf<uint64_t>& vals, int64_t nent, int64_t nrows,
+                    int cbits, CsrOut& out, cudaStream_t s, int64_t* counter);
+
+// Bits needed to hold values 0..v-1.
+inline int bits_for(int64_t v) {
+  int b = 1;
+  while (b < 62 && (int64_t(1) << b) < v) ++b;
+  return b;
+}
+
+// Owned storage of a RowPlan.
+struct RowPlanStore {
+  RowPlan plan;
+  DBuf<int32_t> chunk_row, chunk_lrow, lrow_first, lrow_count;
+  DBuf<int64_t> chunk_beg;
+  DBuf<double> partial;
+  DBuf<unsigned> ticket;
+};
+// Build the plan for a CSR structure with n rows and nnz entries.
+// G = 0 chooses the group size from the average row length.
+void build_row_plan(RowPlanStore& ps, int64_t n, int64_t nnz, const int64_t* rowptr, int G,
+                    cudaStream_t s, int64_t* counter);
+
+}  // namespace lg

@@ -1,0 +1,1080 @@
+// Setup of the multigrid hierarchy on the device (Sections 3.4-3.6, 4).
+//
+// Every stage is a set of kernels over the current level's CSR; the host only
+// reads back counts (|F|, number of aggregates, entries of the next level) to
+// size the next allocations, and at the end the per-level eigenvalue
+// estimates for the Chebyshev constants.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+
+#include "lg_hier.h"
+#include "lg_rows.cuh"
+
+namespace lg {
+
+constexpr int kNT = 256;
+
+static inline int blocks_for(int64_t n, int per_block = kNT) { return grid_for(n, per_block, kSMs * 16); }
+static inline int warp_blocks(int64_t rows) { return grid_for(rows * 32, kNT, kSMs * 16); }
+
+#define LG_GRID_STRIDE(i, n) \
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
+#define LG_WARP_STRIDE(row, n)                                                                   \
+  for (int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; row < (n);          \
+       row += ((int64_t)gridDim.x * blockDim.x) >> 5)
+
+// Device error word bits.
+enum : int {
+  kErrRowptr = 1, kErrCol = 2, kErrSelf = 4, kErrOrder = 8, kErrWeight = 16, kErrAsym = 32, kErrLoop = 64
+};
+
+// ---------------------------------------------------------------------------
+// Input contract (Section 2.1): positive weights, undirected, connected.
+// ---------------------------------------------------------------------------
+__global__ void k_check_rowptr(int64_t n, int64_t nnz, const int64_t* __restrict__ rowptr, int* err) {
+  LG_GRID_STRIDE(i, n + 1) {
+    const int64_t v = rowptr[i];
+    bool bad = (v < 0 || v > nnz) || (i == 0 && v != 0) || (i == n && v != nnz) || (i < n && rowptr[i + 1] < v);
+    if (bad) atomicOr(err, kErrRowptr);
+  }
+}
+
+__device__ __forceinline__ bool find_col(const int64_t* rowptr, const int32_t* col, int64_t row, int32_t key,
+                                         int64_t* pos) {
+  int64_t lo = rowptr[row], hi = rowptr[row + 1] - 1;
+  while (lo <= hi) {
+    int64_t mid = lo + ((hi - lo) >> 1);
+    int32_t c = col[mid];
+    if (c == key) { *pos = mid; return true; }
+    if (c < key) lo = mid + 1; else hi = mid - 1;
+  }
+  return false;
+}
+
+__global__ void k_check_rows(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                             const double* __restrict__ w, int* err) {
+  const int lane = threadIdx.x & 31;
+  LG_WARP_STRIDE(i, n) {
+    int bits = 0;
+    for (int64_t k = rowptr[i] + lane; k < rowptr[i + 1]; k += 32) {
+      const int32_t j = col[k];
+      if (j < 0 || j >= n) { bits |= kErrCol; continue; }
+      if (j == i) bits |= kErrSelf;
+      if (k > rowptr[i] && col[k - 1] >= j) bits |= kErrOrder;
+      const double wk = w[k];
+      if (!(wk > 0.0) || !isfinite(wk)) bits |= kErrWeight;
+      int64_t pos;
+      if (!find_col(rowptr, col, j, (int32_t)i, &pos) || w[pos] != wk) bits |= kErrAsym;
+    }
+    if (bits) atomicOr(err, bits);
+  }
+}
+
+// Connected components by union-find with lock-free hooking (the larger root
+// is hooked under the smaller one by compare-and-swap) and path halving.
+// Every loop is bounded; a loop that runs out sets kErrLoop.
+__device__ __forceinline__ int32_t cc_find(int32_t* parent, int32_t x, int64_t n, int* err) {
+  for (int64_t guard = 0; guard <= n; ++guard) {
+    int32_t p = parent[x];
+    if (p == x) return x;
+    int32_t gp = parent[p];
+    if (gp != p) parent[x] = gp;
+    x = gp;
+  }
+  atomicOr(err, kErrLoop);
+  return x;
+}
+
+__global__ void k_cc_init(int64_t n, int32_t* parent) {
+  LG_GRID_STRIDE(i, n) parent[i] = (int32_t)i;
+}
+
+__global__ void k_cc_hook(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                          int32_t* parent, int* err) {
+  const int lane = threadIdx.x & 31;
+  LG_WARP_STRIDE(i, n) {
+    for (int64_t k = rowptr[i] + lane; k < rowptr[i + 1]; k += 32) {
+      const int32_t j = col[k];
+      if (j <= i) continue;
+      int32_t a = cc_find(parent, (int32_t)i, n, err), b = cc_find(parent, j, n, err);
+      int tries = 0;
+      while (a != b) {
+        const int32_t hi = a > b ? a : b, lo = a > b ? b : a;
+        const int32_t old = atomicCAS(&parent[hi], hi, lo);
+        if (old == hi) break;
+        a = cc_find(parent, old, n, err);
+        b = cc_find(parent, lo, n, err);
+        if (++tries > (1 << 20)) { atomicOr(err, kErrLoop); break; }
+      }
+    }
+  }
+}
+
+__global__ void k_cc_roots(int64_t n, int32_t* parent, uint8_t* is_root, int* err) {
+  LG_GRID_STRIDE(i, n) {
+    const int32_t r = cc_find(parent, (int32_t)i, n, err);
+    is_root[i] = (r == i);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Diagonal: d_i = sum_j w_ij, stored as 1/d_i (0 for an isolated vertex).
+// ---------------------------------------------------------------------------
+struct WeightTerm {
+  const double* __restrict__ w;
+  __device__ __forceinline__ double row(int64_t) const { return 0.0; }
+  __device__ __forceinline__ double operator()(int64_t k, int32_t, double) const { return w[k]; }
+};
+struct EpiDinv {
+  double* dinv;
+  __device__ __forceinline__ void operator()(int64_t i, double s, double*) const { dinv[i] = s > 0.0 ? 1.0 / s : 0.0; }
+  __device__ void finish(const double*) const {}
+};
+
+// y = L x, difference form.
+struct EpiStore {
+  double* y;
+  __device__ __forceinline__ void operator()(int64_t i, double s, double*) const { y[i] = s; }
+  __device__ void finish(const double*) const {}
+};
+
+// ---------------------------------------------------------------------------
+// Low-degree elimination (Section 3.4, Algorithm "Determine vertices to
+// eliminate"): candidates are vertices of degree <= max_degree; each
+// candidate's value is hash(i) (SplitMix64 output i), others +infinity
+// (UINT64_MAX); z_i = min over the closed neighbourhood; i goes iff it is a
+// candidate and z_i = hash(i).
+// ---------------------------------------------------------------------------
+__global__ void k_elim_hash(int64_t n, const int64_t* __restrict__ rowptr, int max_degree, uint64_t seed,
+                            uint64_t* __restrict__ hc) {
+  LG_GRID_STRIDE(i, n) {
+    const int64_t deg = rowptr[i + 1] - rowptr[i];
+    hc[i] = deg <= max_degree ? splitmix64(seed, rng_counter(kStreamHash, 0, i)) : ~0ull;
+  }
+}
+
+__global__ void k_elim_select(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                              int max_degree, const uint64_t* __restrict__ hc, uint8_t* __restrict__ is_f) {
+  LG_GRID_STRIDE(i, n) {
+    const int64_t b = rowptr[i], e = rowptr[i + 1];
+    uint8_t f = 0;
+    if (e - b <= max_degree) {
+      const uint64_t hi = hc[i];
+      uint64_t z = hi;
+      for (int64_t k = b; k < e; ++k) {
+        const uint64_t hj = hc[col[k]];
+        z = hj < z ? hj : z;
+      }
+      f = (z == hi);
+    }
+    is_f[i] = f;
+  }
+}
+
+__global__ void k_not(int64_t n, const uint8_t* __restrict__ a, uint8_t* __restrict__ b) {
+  LG_GRID_STRIDE(i, n) b[i] = a[i] ? 0 : 1;
+}
+
+// cmap: kept vertex -> coarse id (ascending), eliminated -> -1; cfine inverse.
+__global__ void k_elim_maps(int64_t n, const uint8_t* __restrict__ is_f, const int64_t* __restrict__ cid,
+                            int32_t* __restrict__ cmap, int32_t* __restrict__ cfine) {
+  LG_GRID_STRIDE(i, n) {
+    if (is_f[i]) {
+      cmap[i] = -1;
+    } else {
+      cmap[i] = (int32_t)cid[i];
+      cfine[cid[i]] = (int32_t)i;
+    }
+  }
+}
+
+// Entries of the Schur complement generated by each fine row: a kept row
+// gives its kept neighbours (L_CC); an eliminated row f of degree d gives
+// the d(d-1) ordered pairs of its neighbours (the fill of
+// -L_FC^T L_FF^-1 L_FC; F is independent, so all neighbours are kept).
+__global__ void k_schur_count(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                              const uint8_t* __restrict__ is_f, int64_t* __restrict__ cnt) {
+  const int lane = threadIdx.x & 31;
+  LG_WARP_STRIDE(i, n) {
+    const int64_t b = rowptr[i], e = rowptr[i + 1];
+    int64_t c = 0;
+    if (is_f[i]) {
+      c = lane == 0 ? (e - b) * (e - b - 1) : 0;
+    } else {
+      for (int64_t k = b + lane; k < e; k += 32) c += is_f[col[k]] ? 0 : 1;
+    }
+    c = group_sum<32>(c, 0xffffffffu);
+    if (lane == 0) cnt[i] = c;
+  }
+}
+
+// Keys are (coarse row << cbits) | coarse col; values are FP64 bit patterns.
+// Entries are written in fine-row order, kept rows in column order, fill in
+// (first neighbour, second neighbour) order, so the sort-and-sum that follows
+// adds equal keys in a fixed order. The fill weight is w_fa w_fb / d_f with
+// d_f = sum_j w_fj summed sequentially.
+__global__ void k_schur_emit(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                             const double* __restrict__ w, const uint8_t* __restrict__ is_f,
+                             const int32_t* __restrict__ cmap, const int64_t* __restrict__ off, int cbits,
+                             uint64_t* __restrict__ keys, uint64_t* __restrict__ vals) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  LG_WARP_STRIDE(i, n) {
+    const int64_t b = rowptr[i], e = rowptr[i + 1];
+    int64_t o = off[i];
+    if (is_f[i]) {
+      const int64_t d = e - b;
+      double df = 0.0;
+      for (int64_t k = b; k < e; ++k) df += w[k];
+      for (int64_t t = lane; t < d * (d - 1); t += 32) {
+        const int64_t a = t / (d - 1), bb0 = t % (d - 1);
+        const int64_t bb = bb0 < a ? bb0 : bb0 + 1;
+        const int64_t ka = b + a, kb = b + bb;
+        keys[o + t] = ((uint64_t)cmap[col[ka]] << cbits) | (uint64_t)cmap[col[kb]];
+        vals[o + t] = (uint64_t)__double_as_longlong(w[ka] * w[kb] / df);
+      }
+    } else {
+      const uint64_t row = (uint64_t)cmap[i] << cbits;
+      for (int64_t k0 = b; k0 < e; k0 += 32) {
+        const int64_t k = k0 + lane;
+        const bool take = k < e && !is_f[col[k]];
+        const unsigned m = __ballot_sync(0xffffffffu, take);
+        if (take) {
+          const int64_t p = o + __popc(m & lt);
+          keys[p] = row | (uint64_t)cmap[col[k]];
+          vals[p] = (uint64_t)__double_as_longlong(w[k]);
+        }
+        o += __popc(m);
+      }
+    }
+  }
+}
+
+// Transpose of the F rows of P: for every eliminated f and neighbour c an
+// entry keyed by c's coarse id carrying (f, slot) so the coefficient
+// w_fc / d_f can be gathered after sorting.
+__global__ void k_pt_emit(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                          const uint8_t* __restrict__ is_f, const int32_t* __restrict__ cmap,
+                          const int64_t* __restrict__ off, uint64_t* __restrict__ keys, uint64_t* __restrict__ vals) {
+  LG_GRID_STRIDE(i, n) {
+    if (!is_f[i]) continue;
+    const int64_t b = rowptr[i], e = rowptr[i + 1];
+    const int64_t o = off[i];
+    for (int64_t k = b; k < e; ++k) {
+      keys[o + (k - b)] = (uint64_t)cmap[col[k]];
+      vals[o + (k - b)] = ((uint64_t)i << 32) | (uint64_t)(k - b);
+    }
+  }
+}
+
+__global__ void k_f_degree(int64_t n, const int64_t* __restrict__ rowptr, const uint8_t* __restrict__ is_f,
+                           int64_t* __restrict__ cnt) {
+  LG_GRID_STRIDE(i, n) cnt[i] = is_f[i] ? rowptr[i + 1] - rowptr[i] : 0;
+}
+
+__global__ void k_pt_fill(int64_t m, const uint64_t* __restrict__ vals, const int64_t* __restrict__ rowptr,
+                          const double* __restrict__ w, int32_t* __restrict__ pt_f, double* __restrict__ pt_coef) {
+  LG_GRID_STRIDE(q, m) {
+    const int64_t f = (int64_t)(vals[q] >> 32), slot = (int64_t)(vals[q] & 0xffffffffu);
+    const int64_t b = rowptr[f], e = rowptr[f + 1];
+    double df = 0.0;
+    for (int64_t k = b; k < e; ++k) df += w[k];
+    pt_f[q] = (int32_t)f;
+    pt_coef[q] = w[b + slot] / df;
+  }
+}
+
+// rowptr of a CSR whose entries are sorted by row (row = key >> shift).
+__global__ void k_rowptr_sorted(const uint64_t* __restrict__ keys, int64_t m, int shift, int64_t nrows,
+                                int64_t* __restrict__ rowptr) {
+  LG_GRID_STRIDE(r, nrows + 1) {
+    int64_t lo = 0, hi = m;
+    while (lo < hi) {
+      int64_t mid = (lo + hi) >> 1;
+      if ((int64_t)(keys[mid] >> shift) < r) lo = mid + 1; else hi = mid;
+    }
+    rowptr[r] = lo;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Strength of connection (Section 3.5).
+// ---------------------------------------------------------------------------
+constexpr int kMaxVecs = 8;
+
+__global__ void k_strength_init(int64_t n, int m, uint64_t seed, int level, double* __restrict__ y) {
+  LG_GRID_STRIDE(i, n) {
+    for (int k = 0; k < m; ++k) y[i * m + k] = uniform_pm1(seed, 1 + k, level, i);
+  }
+}
+
+// One damped Jacobi sweep on L y = 0 for m columns ([n][m] layout):
+// x_out = x - omega D^-1 L x, L x in difference form.
+__global__ void k_jacobi_m(int64_t n, int m, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                           const double* __restrict__ w, const double* __restrict__ dinv, double omega,
+                           const double* __restrict__ x, double* __restrict__ xo) {
+  const int lane = threadIdx.x & 31;
+  LG_WARP_STRIDE(i, n) {
+    double xi[kMaxVecs], s[kMaxVecs];
+    for (int k = 0; k < m; ++k) { xi[k] = x[i * m + k]; s[k] = 0.0; }
+    for (int64_t p = rowptr[i] + lane; p < rowptr[i + 1]; p += 32) {
+      const int64_t j = col[p];
+      const double wp = w[p];
+      for (int k = 0; k < m; ++k) s[k] += wp * (xi[k] - x[j * m + k]);
+    }
+    for (int k = 0; k < m; ++k) s[k] = group_sum<32>(s[k], 0xffffffffu);
+    if (lane < m) {
+      double v = 0.0, sv = 0.0;
+      for (int k = 0; k < m; ++k) if (k == lane) { v = xi[k]; sv = s[k]; }
+      xo[i * m + lane] = v - omega * dinv[i] * sv;
+    }
+  }
+}
+
+// C_ij = (x_i . x_j)^2 / (|x_i|^2 |x_j|^2), 0 when the denominator is 0; the
+// products and sums are formed the same way for (i, j) and (j, i), so C is
+// bitwise symmetric. rowmax_i = max_j C_ij.
+__device__ __forceinline__ double affinity_of(const double* xi, double xi2, const double* __restrict__ x, int64_t j,
+                                              int m) {
+  double xj2 = 0.0, xij = 0.0;
+  for (int k = 0; k < m; ++k) {
+    const double a = x[j * m + k];
+    xj2 += a * a;
+    xij += xi[k] * a;
+  }
+  const double den = xi2 * xj2;
+  return den > 0.0 ? (xij * xij) / den : 0.0;
+}
+
+__global__ void k_affinity(int64_t n, int m, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                           const double* __restrict__ x, double* __restrict__ C, double* __restrict__ rowmax) {
+  const int lane = threadIdx.x & 31;
+  LG_WARP_STRIDE(i, n) {
+    double xi[kMaxVecs];
+    double xi2 = 0.0;
+    for (int k = 0; k < m; ++k) { xi[k] = x[i * m + k]; xi2 += xi[k] * xi[k]; }
+    double mx = 0.0;
+    for (int64_t p = rowptr[i] + lane; p < rowptr[i + 1]; p += 32) {
+      const double c = affinity_of(xi, xi2, x, col[p], m);
+      C[p] = c;
+      mx = c > mx ? c : mx;
+    }
+    mx = group_max<32>(mx, 0xffffffffu);
+    if (lane == 0) rowmax[i] = mx;
+  }
+}
+
+// S_ij = C_ij / max(rowmax_i, rowmax_j) (C symmetric: column max = row max).
+__global__ void k_normalize(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                            const double* __restrict__ rowmax, double* __restrict__ S) {
+  const int lane = threadIdx.x & 31;
+  LG_WARP_STRIDE(i, n) {
+    const double ri = rowmax[i];
+    for (int64_t p = rowptr[i] + lane; p < rowptr[i + 1]; p += 32) {
+      const double rj = rowmax[col[p]];
+      const double mx = ri > rj ? ri : rj;
+      S[p] = mx > 0.0 ? S[p] / mx : 0.0;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Aggregation (Section 3.5, Algorithms "Aggregation", "Aggregation-Step").
+// status = (state, idx) with Seed > Undecided > Decided. The (+)agg maximum
+// over filtered neighbours is taken on a 128-bit key: high word
+// state << 62 | FP64 bits of S_ij (S in [0, 1], so its bits fit in 62),
+// low word ~idx_j, i.e. larger state, then larger weight, then smaller index.
+// ---------------------------------------------------------------------------
+__global__ void k_agg_init(int64_t n, int8_t* state, int32_t* idx, int32_t* votes) {
+  LG_GRID_STRIDE(i, n) {
+    state[i] = LG_UNDECIDED;
+    idx[i] = (int32_t)i;
+    votes[i] = 0;
+  }
+}
+
+// Decisions of one step, all reading the status from the start of the step:
+// an Undecided vertex whose best neighbour is a Seed joins it (Decided); if
+// the best is Undecided it votes for it. Seeds and Decided vertices keep
+// their status.
+__global__ void k_agg_decide(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                             const double* __restrict__ S, double filter, const int8_t* __restrict__ state,
+                             const int32_t* __restrict__ idx, int8_t* __restrict__ nstate,
+                             int32_t* __restrict__ nidx, int32_t* __restrict__ votes) {
+  const int lane = threadIdx.x & 31;
+  LG_WARP_STRIDE(i, n) {
+    const int8_t si = state[i];
+    if (si != LG_UNDECIDED) {
+      if (lane == 0) { nstate[i] = si; nidx[i] = idx[i]; }
+      continue;
+    }
+    uint64_t hi = 0, lo = 0;  // the (Decided, -1, 0) identity sorts below every real entry
+    for (int64_t p = rowptr[i] + lane; p < rowptr[i + 1]; p += 32) {
+      const double sp = S[p];
+      if (!(sp >= filter)) continue;
+      const int32_t j = col[p];
+      const uint64_t h = ((uint64_t)state[j] << 62) | (uint64_t)__double_as_longlong(sp);
+      const uint64_t l = (uint64_t)(~(uint32_t)idx[j]);
+      if (h > hi || (h == hi && l > lo)) { hi = h; lo = l; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const uint64_t h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+      const uint64_t l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+      if (h2 > hi || (h2 == hi && l2 > lo)) { hi = h2; lo = l2; }
+    }
+    if (lane == 0) {
+      const int s = (int)(hi >> 62);
+      const int32_t j = (int32_t)(~(uint32_t)lo);
+      int8_t ns = LG_UNDECIDED;
+      int32_t ni = (int32_t)i;
+      if (hi != 0) {
+        if (s == LG_SEED) { ns = LG_DECIDED; ni = j; }
+        else if (s == LG_UNDECIDED) atomicAdd(&votes[j], 1);
+      }
+      nstate[i] = ns;
+      nidx[i] = ni;
+    }
+  }
+}
+
+__global__ void k_agg_promote(int64_t n, int threshold, const int32_t* __restrict__ votes, int8_t* __restrict__ state,
+                              const int32_t* __restrict__ idx) {
+  LG_GRID_STRIDE(i, n) {
+    if (state[i] == LG_UNDECIDED && idx[i] == i && votes[i] >= threshold) state[i] = LG_SEED;
+  }
+}
+
+__global__ void k_agg_roots(int64_t n, const int32_t* __restrict__ idx, uint8_t* __restrict__ root) {
+  LG_GRID_STRIDE(i, n) root[i] = idx[i] == i;
+}
+
+__global__ void k_agg_number(int64_t n, const int32_t* __restrict__ idx, const int64_t* __restrict__ cid,
+                             int32_t* __restrict__ agg) {
+  LG_GRID_STRIDE(i, n) agg[i] = (int32_t)cid[idx[i]];
+}
+
+// ---------------------------------------------------------------------------
+// Galerkin product L_c = R L P, P = R^T (Section 3.5): the coarse weight
+// between aggregates I != J sums the weights of the edges joining them.
+// ---------------------------------------------------------------------------
+__global__ void k_gal_count(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                            const int32_t* __restrict__ agg, int64_t* __restrict__ cnt) {
+  const int lane = threadIdx.x & 31;
+  LG_WARP_STRIDE(i, n) {
+    const int32_t ai = agg[i];
+    int64_t c = 0;
+    for (int64_t p = rowptr[i] + lane; p < rowptr[i + 1]; p += 32) c += agg[col[p]] != ai;
+    c = group_sum<32>(c, 0xffffffffu);
+    if (lane == 0) cnt[i] = c;
+  }
+}
+
+__global__ void k_gal_emit(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                           const double* __restrict__ w, const int32_t* __restrict__ agg,
+                           const int64_t* __restrict__ off, int cbits, uint64_t* __restrict__ keys,
+                           uint64_t* __restrict__ vals) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  LG_WARP_STRIDE(i, n) {
+    const int32_t ai = agg[i];
+    const uint64_t row = (uint64_t)ai << cbits;
+    const int64_t e = rowptr[i + 1];
+    int64_t o = off[i];
+    for (int64_t k0 = rowptr[i]; k0 < e; k0 += 32) {
+      const int64_t k = k0 + lane;
+      int32_t aj = 0;
+      bool take = false;
+      if (k < e) {
+        aj = agg[col[k]];
+        take = aj != ai;
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, take);
+      if (take) {
+        const int64_t p = o + __popc(m & lt);
+        keys[p] = row | (uint64_t)aj;
+        vals[p] = (uint64_t)__double_as_longlong(w[k]);
+      }
+      o += __popc(m);
+    }
+  }
+}
+
+__global__ void k_iota_u64(int64_t n, const int32_t* __restrict__ agg, uint64_t* __restrict__ keys,
+                           uint64_t* __restrict__ vals) {
+  LG_GRID_STRIDE(i, n) {
+    keys[i] = (uint64_t)agg[i];
+    vals[i] = (uint64_t)i;
+  }
+}
+
+__global__ void k_u64_to_i32(int64_t n, const uint64_t* __restrict__ a, int32_t* __restrict__ b) {
+  LG_GRID_STRIDE(i, n) b[i] = (int32_t)a[i];
+}
+
+// ---------------------------------------------------------------------------
+// Largest eigenvalue of D^-1 L (Section 3.6): eig_iters Lanczos steps on
+// D^-1/2 L D^-1/2 (the Jacobi-preconditioned operator, symmetric in the D
+// inner product), start vector from SplitMix64 stream 8, early stop once
+// beta_k <= 1e-12 |alpha_k|; the estimate is the largest eigenvalue of the
+// tridiagonal, by Sturm-count bisection.
+// ---------------------------------------------------------------------------
+struct Lanczos {
+  double alpha[64], beta[64];
+  double nrm2, b2;
+  int m, stopped;
+};
+
+__global__ void k_lz_start(int64_t n, uint64_t seed, int level, const double* __restrict__ dinv,
+                           double* __restrict__ v, double* __restrict__ sdinv, double* partials, unsigned* ticket,
+                           Lanczos* lz) {
+  double acc[1] = {0.0};
+  LG_GRID_STRIDE(i, n) {
+    const double u = uniform_pm1(seed, kStreamLanczos, level, i);
+    v[i] = u;
+    sdinv[i] = sqrt(dinv[i]);
+    acc[0] += u * u;
+  }
+  if (grid_sum<kNT, 1>(acc, partials, ticket, &lz->nrm2)) {
+    lz->m = 0;
+    lz->stopped = 0;
+  }
+}
+
+__global__ void k_lz_scale(int64_t n, const Lanczos* lz, double* __restrict__ v, const double* __restrict__ sdinv,
+                           double* __restrict__ t, double* __restrict__ vp) {
+  const double inv = 1.0 / sqrt(lz->nrm2);
+  LG_GRID_STRIDE(i, n) {
+    v[i] *= inv;
+    t[i] = v[i] * sdinv[i];
+    vp[i] = 0.0;
+  }
+}
+
+struct EpiLanczos {
+  const double* sdinv;
+  const double* v;
+  double* u;
+  Lanczos* lz;
+  int k;
+  __device__ __forceinline__ void operator()(int64_t i, double s, double* red) const {
+    const double ui = sdinv[i] * s;
+    u[i] = ui;
+    red[0] += v[i] * ui;
+  }
+  __device__ void finish(const double* tot) const { lz->alpha[k] = tot[0]; }
+};
+
+__global__ void k_lz_orth(int64_t n, int k, Lanczos* lz, double* __restrict__ u, const double* __restrict__ v,
+                          const double* __restrict__ vp, double* partials, unsigned* ticket) {
+  if (lz->stopped) return;
+  const double a = lz->alpha[k], b = k > 0 ? lz->beta[k - 1] : 0.0;
+  double acc[1] = {0.0};
+  LG_GRID_STRIDE(i, n) {
+    const double ui = u[i] - a * v[i] - b * vp[i];
+    u[i] = ui;
+    acc[0] += ui * ui;
+  }
+  if (grid_sum<kNT, 1>(acc, partials, ticket, &lz->b2)) {
+    const double bk = sqrt(lz->b2);
+    lz->beta[k] = bk;
+    lz->m = k + 1;
+    if (bk <= 1e-12 * fabs(a)) lz->stopped = 1;
+  }
+}
+
+__global__ void k_lz_next(int64_t n, int k, const Lanczos* lz, const double* __restrict__ u, double* __restrict__ v,
+                          double* __restrict__ vp, const double* __restrict__ sdinv, double* __restrict__ t) {
+  if (lz->stopped) return;
+  const double inv = 1.0 / lz->beta[k];
+  LG_GRID_STRIDE(i, n) {
+    vp[i] = v[i];
+    const double vi = u[i] * inv;
+    v[i] = vi;
+    t[i] = vi * sdinv[i];
+  }
+}
+
+__device__ int sturm_count_dev(int m, const double* a, const double* b, double x) {
+  int count = 0;
+  double q = 1.0;
+  for (int i = 0; i < m; ++i) {
+    const double off = i > 0 ? b[i - 1] * b[i - 1] / q : 0.0;
+    q = (a[i] - x) - off;
+    if (q == 0.0) q = -1e-300;
+    if (q < 0.0) ++count;
+  }
+  return count;
+}
+
+__global__ void k_lz_ritz(const Lanczos* lz, double* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int m = lz->m;
+  const double* a = lz->alpha;
+  const double* b = lz->beta;
+  double lo = a[0], hi = a[0];
+  for (int i = 0; i < m; ++i) {
+    const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i < m - 1 ? fabs(b[i]) : 0.0);
+    lo = fmin(lo, a[i] - r);
+    hi = fmax(hi, a[i] + r);
+  }
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (sturm_count_dev(m, a, b, mid) == m) hi = mid; else lo = mid;
+  }
+  *out = hi;
+}
+
+// ---------------------------------------------------------------------------
+// Coarsest level: L^+ = (L + 11^T/n)^-1 - 11^T/n (null space span(1),
+// Section 2.1), the inverse by in-place Gauss-Jordan (SPD: no pivoting).
+// ---------------------------------------------------------------------------
+__global__ void k_dense_shifted(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                const double* __restrict__ w, double* __restrict__ M) {
+  const double c = 1.0 / (double)n;
+  LG_GRID_STRIDE(i, n) {
+    double d = 0.0;
+    for (int64_t j = 0; j < n; ++j) M[i * n + j] = c;
+    for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+      M[i * n + col[p]] = c - w[p];
+      d += w[p];
+    }
+    M[i * n + i] = c + d;
+  }
+}
+
+__global__ void k_gj_copy(int64_t n, int64_t k, const double* __restrict__ M, double* __restrict__ prow,
+                          double* __restrict__ pcol) {
+  LG_GRID_STRIDE(i, n) {
+    prow[i] = M[k * n + i];
+    pcol[i] = M[i * n + k];
+  }
+}
+
+__global__ void k_gj_update(int64_t n, int64_t k, double* __restrict__ M, const double* __restrict__ prow,
+                            const double* __restrict__ pcol, int* err) {
+  const double p = prow[k];
+  if (!(p > 0.0)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(err, kErrLoop);
+    return;
+  }
+  const double ip = 1.0 / p;
+  LG_GRID_STRIDE(e, n * n) {
+    const int64_t i = e / n, j = e % n;
+    double v;
+    if (i == k && j == k) v = ip;
+    else if (i == k) v = prow[j] * ip;
+    else if (j == k) v = -pcol[i] * ip;
+    else v = M[e] - pcol[i] * prow[j] * ip;
+    M[e] = v;
+  }
+}
+
+__global__ void k_unshift(int64_t n, double* __restrict__ M) {
+  const double c = 1.0 / (double)n;
+  LG_GRID_STRIDE(e, n * n) M[e] -= c;
+}
+
+// ---------------------------------------------------------------------------
+// FP32 copies of the hierarchy.
+// ---------------------------------------------------------------------------
+__global__ void k_to_f32(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
+  LG_GRID_STRIDE(i, n) b[i] = (float)a[i];
+}
+
+// ===========================================================================
+// Host side.
+// ===========================================================================
+static int read_err(const DBuf<int>& e, cudaStream_t s) {
+  int v = 0;
+  LG_CUDA(cudaMemcpyAsync(&v, e.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+  LG_CUDA(cudaStreamSynchronize(s));
+  return v;
+}
+
+static int64_t read_i64(const int64_t* p, cudaStream_t s) {
+  int64_t v = 0;
+  LG_CUDA(cudaMemcpyAsync(&v, p, sizeof(int64_t), cudaMemcpyDefault, s));
+  LG_CUDA(cudaStreamSynchronize(s));
+  return v;
+}
+
+// Row plan and 1/diag of a level's operator.
+static void prepare_operator(Level& L, cudaStream_t s, int64_t* counter) {
+  build_row_plan(L.plan, L.n, L.nnz, L.rowptr.get(), 0, s, counter);
+  L.dinv.alloc(L.n, s, counter);
+  launch_rows<double, 0>(L.n, L.rowptr.get(), L.col.get(), WeightTerm{L.w.get()}, L.plan.plan,
+                         EpiDinv{L.dinv.get()}, s);
+}
+
+void run_laplacian_apply(int64_t n, const int64_t* rowptr, const int32_t* col, const double* w, const double* x,
+                         double* y, cudaStream_t s) {
+  RowPlanStore ps;
+  const int64_t nnz = read_i64(rowptr + n, s);
+  build_row_plan(ps, n, nnz, rowptr, 0, s, nullptr);
+  launch_rows<double, 0>(n, rowptr, col, LapTerm<double>{w, x}, ps.plan, EpiStore{y}, s);
+  LG_CUDA(cudaStreamSynchronize(s));
+}
+
+int64_t run_elim_select(int64_t n, const int64_t* rowptr, const int32_t* col, int max_degree, uint64_t seed,
+                        uint8_t* is_f, cudaStream_t s) {
+  DBuf<uint64_t> hc(n, s);
+  DBuf<int64_t> cnt(n + 1, s);
+  k_elim_hash<<<blocks_for(n), kNT, 0, s>>>(n, rowptr, max_degree, seed, hc.get());
+  LG_LAUNCH_CHECK();
+  k_elim_select<<<blocks_for(n), kNT, 0, s>>>(n, rowptr, col, max_degree, hc.get(), is_f);
+  LG_LAUNCH_CHECK();
+  exclusive_scan_flags(is_f, cnt.get(), n, s);
+  return read_i64(cnt.get() + n, s);
+}
+
+void run_strength(int64_t n, const int64_t* rowptr, const int32_t* col, const double* w, uint64_t seed, int level,
+                  int m, int sweeps, double omega, double* S, cudaStream_t s) {
+  if (m < 1 || m > kMaxVecs) fail(LG_ERR_INVALID, "strength_vecs must be 1..8");
+  RowPlanStore ps;
+  const int64_t nnz = read_i64(rowptr + n, s);
+  build_row_plan(ps, n, nnz, rowptr, 0, s, nullptr);
+  DBuf<double> dinv(n, s), xa((size_t)n * m, s), xb((size_t)n * m, s), rowmax(n, s);
+  launch_rows<double, 0>(n, rowptr, col, WeightTerm{w}, ps.plan, EpiDinv{dinv.get()}, s);
+  k_strength_init<<<blocks_for(n), kNT, 0, s>>>(n, m, seed, level, xa.get());
+  LG_LAUNCH_CHECK();
+  double* x = xa.get();
+  double* xo = xb.get();
+  for (int sw = 0; sw < sweeps; ++sw) {
+    k_jacobi_m<<<warp_blocks(n), kNT, 0, s>>>(n, m, rowptr, col, w, dinv.get(), omega, x, xo);
+    LG_LAUNCH_CHECK();
+    std::swap(x, xo);
+  }
+  k_affinity<<<warp_blocks(n), kNT, 0, s>>>(n, m, rowptr, col, x, S, rowmax.get());
+  LG_LAUNCH_CHECK();
+  k_normalize<<<warp_blocks(n), kNT, 0, s>>>(n, rowptr, col, rowmax.get(), S);
+  LG_LAUNCH_CHECK();
+  LG_CUDA(cudaStreamSynchronize(s));
+}
+
+int64_t run_aggregate(int64_t n, const int64_t* rowptr, const int32_t* col, const double* S, int iters, int threshold,
+                      int32_t* agg, int8_t* state_out, int32_t* votes_out, cudaStream_t s) {
+  DBuf<int8_t> st(n, s), nst(n, s);
+  DBuf<int32_t> idx(n, s), nidx(n, s), votes(n, s);
+  DBuf<uint8_t> root(n, s);
+  DBuf<int64_t> cid(n + 1, s);
+  k_agg_init<<<blocks_for(n), kNT, 0, s>>>(n, st.get(), idx.get(), votes.get());
+  LG_LAUNCH_CHECK();
+  int8_t *a = st.get(), *b = nst.get();
+  int32_t *ia = idx.get(), *ib = nidx.get();
+  for (int it = 1; it <= iters; ++it) {
+    const double filter = std::ldexp(1.0, -it);  // 0.5^iter
+    k_agg_decide<<<warp_blocks(n), kNT, 0, s>>>(n, rowptr, col, S, filter, a, ia, b, ib, votes.get());
+    LG_LAUNCH_CHECK();
+    k_agg_promote<<<blocks_for(n), kNT, 0, s>>>(n, threshold, votes.get(), b, ib);
+    LG_LAUNCH_CHECK();
+    std::swap(a, b);
+    std::swap(ia, ib);
+  }
+  k_agg_roots<<<blocks_for(n), kNT, 0, s>>>(n, ia, root.get());
+  LG_LAUNCH_CHECK();
+  exclusive_scan_flags(root.get(), cid.get(), n, s);
+  k_agg_number<<<blocks_for(n), kNT, 0, s>>>(n, ia, cid.get(), agg);
+  LG_LAUNCH_CHECK();
+  if (state_out) LG_CUDA(cudaMemcpyAsync(state_out, a, n, cudaMemcpyDeviceToDevice, s));
+  if (votes_out) LG_CUDA(cudaMemcpyAsync(votes_out, votes.get(), 4 * n, cudaMemcpyDeviceToDevice, s));
+  return read_i64(cid.get() + n, s);
+}
+
+// Elimination stage: fills L's ELIM fields and returns the Schur complement level.
+static std::unique_ptr<Level> eliminate(Level& L, const uint8_t* is_f, int64_t nf, cudaStream_t s, int64_t* counter) {
+  const int64_t n = L.n;
+  DBuf<uint8_t> keep(n, s);
+  DBuf<int64_t> cid(n + 1, s), cnt(n + 1, s);
+  k_not<<<blocks_for(n), kNT, 0, s>>>(n, is_f, keep.get());
+  LG_LAUNCH_CHECK();
+  exclusive_scan_flags(keep.get(), cid.get(), n, s);
+  const int64_t nc = n - nf;
+  L.kind = LG_LEVEL_ELIM;
+  L.nf = nf;
+  L.nc = nc;
+  L.cmap.alloc(n, s, counter);
+  L.cfine.alloc(nc, s, counter);
+  k_elim_maps<<<blocks_for(n), kNT, 0, s>>>(n, is_f, cid.get(), L.cmap.get(), L.cfine.get());
+  LG_LAUNCH_CHECK();
+
+  // Schur complement entries, sorted and summed into the coarse CSR.
+  k_schur_count<<<warp_blocks(n), kNT, 0, s>>>(n, L.rowptr.get(), L.col.get(), is_f, cnt.get());
+  LG_LAUNCH_CHECK();
+  exclusive_scan(cnt.get(), cnt.get(), n, s);
+  const int64_t nent = read_i64(cnt.get() + n, s);
+  const int cbits = bits_for(nc);
+  auto C = std::make_unique<Level>();
+  {
+    DBuf<uint64_t> keys(nent, s), vals(nent, s);
+    k_schur_emit<<<warp_blocks(n), kNT, 0, s>>>(n, L.rowptr.get(), L.col.get(), L.w.get(), is_f, L.cmap.get(),
+                                               cnt.get(), cbits, keys.get(), vals.get());
+    LG_LAUNCH_CHECK();
+    CsrOut out;
+    accumulate_csr(keys, vals, nent, nc, cbits, out, s, counter);
+    C->n = nc;
+    C->nnz = out.nnz;
+    C->rowptr = std::move(out.rowptr);
+    C->col = std::move(out.col);
+    C->w = std::move(out.w);
+  }
+  // Transpose of P's F rows, per kept vertex.
+  k_f_degree<<<blocks_for(n), kNT, 0, s>>>(n, L.rowptr.get(), is_f, cnt.get());
+  LG_LAUNCH_CHECK();
+  exclusive_scan(cnt.get(), cnt.get(), n, s);
+  const int64_t npt = read_i64(cnt.get() + n, s);
+  {
+    DBuf<uint64_t> keys(npt, s), vals(npt, s);
+    k_pt_emit<<<blocks_for(n), kNT, 0, s>>>(n, L.rowptr.get(), L.col.get(), is_f, L.cmap.get(), cnt.get(),
+                                           keys.get(), vals.get());
+    LG_LAUNCH_CHECK();
+    radix_sort_pairs(keys.get(), vals.get(), npt, bits_for(nc), s);
+    L.pt_ptr.alloc(nc + 1, s, counter);
+    L.pt_f.alloc(npt, s, counter);
+    L.pt_coef.alloc(npt, s, counter);
+    k_rowptr_sorted<<<blocks_for(nc + 1), kNT, 0, s>>>(keys.get(), npt, 0, nc, L.pt_ptr.get());
+    LG_LAUNCH_CHECK();
+    k_pt_fill<<<blocks_for(npt), kNT, 0, s>>>(npt, vals.get(), L.rowptr.get(), L.w.get(), L.pt_f.get(),
+                                             L.pt_coef.get());
+    LG_LAUNCH_CHECK();
+    build_row_plan(L.pt_plan, nc, npt, L.pt_ptr.get(), 0, s, counter);
+  }
+  return C;
+}
+
+// Aggregation stage products: member CSR of R and the Galerkin level.
+static std::unique_ptr<Level> galerkin(Level& L, cudaStream_t s, int64_t* counter) {
+  const int64_t n = L.n, nc = L.nc;
+  // member lists, ascending vertex order inside each aggregate (stable sort by aggregate)
+  {
+    DBuf<uint64_t> keys(n, s), vals(n, s);
+    k_iota_u64<<<blocks_for(n), kNT, 0, s>>>(n, L.agg.get(), keys.get(), vals.get());
+    LG_LAUNCH_CHECK();
+    radix_sort_pairs(keys.get(), vals.get(), n, bits_for(nc), s);
+    L.mem.alloc(n, s, counter);
+    L.mem_ptr.alloc(nc + 1, s, counter);
+    k_u64_to_i32<<<blocks_for(n), kNT, 0, s>>>(n, vals.get(), L.mem.get());
+    LG_LAUNCH_CHECK();
+    k_rowptr_sorted<<<blocks_for(nc + 1), kNT, 0, s>>>(keys.get(), n, 0, nc, L.mem_ptr.get());
+    LG_LAUNCH_CHECK();
+    build_row_plan(L.mem_plan, nc, n, L.mem_ptr.get(), 0, s, counter);
+  }
+  DBuf<int64_t> cnt(n + 1, s);
+  k_gal_count<<<warp_blocks(n), kNT, 0, s>>>(n, L.rowptr.get(), L.col.get(), L.agg.get(), cnt.get());
+  LG_LAUNCH_CHECK();
+  exclusive_scan(cnt.get(), cnt.get(), n, s);
+  const int64_t nent = read_i64(cnt.get() + n, s);
+  const int cbits = bits_for(nc);
+  DBuf<uint64_t> keys(nent, s), vals(nent, s);
+  k_gal_emit<<<warp_blocks(n), kNT, 0, s>>>(n, L.rowptr.get(), L.col.get(), L.w.get(), L.agg.get(), cnt.get(), cbits,
+                                           keys.get(), vals.get());
+  LG_LAUNCH_CHECK();
+  CsrOut out;
+  accumulate_csr(keys, vals, nent, nc, cbits, out, s, counter);
+  auto C = std::make_unique<Level>();
+  C->n = nc;
+  C->nnz = out.nnz;
+  C->rowptr = std::move(out.rowptr);
+  C->col = std::move(out.col);
+  C->w = std::move(out.w);
+  return C;
+}
+
+static void lanczos(Level& L, const lg_options& o, int level, double* lam_dev, cudaStream_t s) {
+  const int64_t n = L.n;
+  const int iters = std::min(o.eig_iters, 64);
+  DBuf<double> v(n, s), vp(n, s), u(n, s), t(n, s), sdinv(n, s);
+  const int nb = blocks_for(n);
+  const int nbr = (int)(L.plan.plan.nchunks + L.plan.plan.short_blocks);
+  DBuf<double> partials((size_t)std::max(nb, nbr), s);
+  DBuf<unsigned> ticket(1, s);
+  DBuf<Lanczos> lz(1, s);
+  DBuf<double> tot(1, s);
+  LG_CUDA(cudaMemsetAsync(ticket.get(), 0, sizeof(unsigned), s));
+  k_lz_start<<<nb, kNT, 0, s>>>(n, o.seed, level, L.dinv.get(), v.get(), sdinv.get(), partials.get(), ticket.get(),
+                                lz.get());
+  LG_LAUNCH_CHECK();
+  k_lz_scale<<<nb, kNT, 0, s>>>(n, lz.get(), v.get(), sdinv.get(), t.get(), vp.get());
+  LG_LAUNCH_CHECK();
+  for (int k = 0; k < iters; ++k) {
+    // stopped iterations leave alpha[k] untouched; only the first m entries are used
+    launch_rows<double, 1>(n, L.rowptr.get(), L.col.get(), LapTerm<double>{L.w.get(), t.get()}, L.plan.plan,
+                           EpiLanczos{sdinv.get(), v.get(), u.get(), lz.get(), k}, s, partials.get(),
+                           ticket.get(), tot.get());
+    k_lz_orth<<<nb, kNT, 0, s>>>(n, k, lz.get(), u.get(), v.get(), vp.get(), partials.get(), ticket.get());
+    LG_LAUNCH_CHECK();
+    k_lz_next<<<nb, kNT, 0, s>>>(n, k, lz.get(), u.get(), v.get(), vp.get(), sdinv.get(), t.get());
+    LG_LAUNCH_CHECK();
+  }
+  k_lz_ritz<<<1, 32, 0, s>>>(lz.get(), lam_dev);
+  LG_LAUNCH_CHECK();
+}
+
+static void coarsest_pinv(Level& L, int* err, cudaStream_t s, int64_t* counter) {
+  const int64_t n = L.n;
+  L.kind = LG_LEVEL_COARSEST;
+  L.pinv.alloc((size_t)n * n, s, counter);
+  DBuf<double> prow(n, s), pcol(n, s);
+  k_dense_shifted<<<blocks_for(n), kNT, 0, s>>>(n, L.rowptr.get(), L.col.get(), L.w.get(), L.pinv.get());
+  LG_LAUNCH_CHECK();
+  const int gb = blocks_for(n * n);
+  for (int64_t k = 0; k < n; ++k) {
+    k_gj_copy<<<blocks_for(n), kNT, 0, s>>>(n, k, L.pinv.get(), prow.get(), pcol.get());
+    k_gj_update<<<gb, kNT, 0, s>>>(n, k, L.pinv.get(), prow.get(), pcol.get(), err);
+  }
+  LG_LAUNCH_CHECK();
+  k_unshift<<<gb, kNT, 0, s>>>(n, L.pinv.get());
+  LG_LAUNCH_CHECK();
+}
+
+static void make_f32(Level& L, cudaStream_t s, int64_t* counter) {
+  if (L.nnz > 0) {
+    L.w32.alloc(L.nnz, s, counter);
+    k_to_f32<<<blocks_for(L.nnz), kNT, 0, s>>>(L.nnz, L.w.get(), L.w32.get());
+    LG_LAUNCH_CHECK();
+  }
+  if (L.dinv.get()) {
+    L.dinv32.alloc(L.n, s, counter);
+    k_to_f32<<<blocks_for(L.n), kNT, 0, s>>>(L.n, L.dinv.get(), L.dinv32.get());
+    LG_LAUNCH_CHECK();
+  }
+  if (L.pt_coef.get() && L.pt_coef.size() > 0) {
+    L.pt_coef32.alloc(L.pt_coef.size(), s, counter);
+    k_to_f32<<<blocks_for((int64_t)L.pt_coef.size()), kNT, 0, s>>>((int64_t)L.pt_coef.size(), L.pt_coef.get(),
+                                                                    L.pt_coef32.get());
+    LG_LAUNCH_CHECK();
+  }
+}
+
+void setup_hierarchy(Hier& h, int64_t n, const int64_t* rowptr, const int32_t* col, const double* w) {
+  cudaStream_t s = h.stream;
+  const lg_options& o = h.opts;
+  int64_t* counter = &h.bytes;
+  if (o.elim_max_degree < 0 || o.elim_max_degree > 6) fail(LG_ERR_INVALID, "elim_max_degree must be 0..6");
+  if (o.strength_vecs < 1 || o.strength_vecs > 7) fail(LG_ERR_INVALID, "strength_vecs must be 1..7");
+  if (o.cheb_degree < 1 || o.cheb_degree > 8) fail(LG_ERR_INVALID, "cheb_degree must be 1..8");
+  if (o.max_levels < 1) fail(LG_ERR_INVALID, "max_levels");
+
+  h.dev_err.alloc(1, s);
+  LG_CUDA(cudaMemsetAsync(h.dev_err.get(), 0, sizeof(int), s));
+  cudaEvent_t e0, e1;
+  LG_CUDA(cudaEventCreate(&e0));
+  LG_CUDA(cudaEventCreate(&e1));
+  LG_CUDA(cudaEventRecord(e0, s));
+
+  // ---- level 0: copy the input and check the contract ----
+  const int64_t nnz = read_i64(rowptr + n, s);
+  auto cur = std::make_unique<Level>();
+  cur->n = n;
+  cur->nnz = nnz;
+  cur->rowptr.alloc(n + 1, s, counter);
+  cur->col.alloc(nnz, s, counter);
+  cur->w.alloc(nnz, s, counter);
+  LG_CUDA(cudaMemcpyAsync(cur->rowptr.get(), rowptr, sizeof(int64_t) * (n + 1), cudaMemcpyDefault, s));
+  if (nnz > 0) {
+    LG_CUDA(cudaMemcpyAsync(cur->col.get(), col, sizeof(int32_t) * nnz, cudaMemcpyDefault, s));
+    LG_CUDA(cudaMemcpyAsync(cur->w.get(), w, sizeof(double) * nnz, cudaMemcpyDefault, s));
+  }
+  k_check_rowptr<<<blocks_for(n + 1), kNT, 0, s>>>(n, nnz, cur->rowptr.get(), h.dev_err.get());
+  LG_LAUNCH_CHECK();
+  if (read_err(h.dev_err, s)) fail(LG_ERR_INVALID, "rowptr");
+  k_check_rows<<<warp_blocks(n), kNT, 0, s>>>(n, cur->rowptr.get(), cur->col.get(), cur->w.get(), h.dev_err.get());
+  LG_LAUNCH_CHECK();
+  if (read_err(h.dev_err, s)) fail(LG_ERR_INVALID, "graph entries");
+  {
+    DBuf<int32_t> parent(n, s);
+    DBuf<uint8_t> is_root(n, s);
+    DBuf<int64_t> cnt(n + 1, s);
+    k_cc_init<<<blocks_for(n), kNT, 0, s>>>(n, parent.get());
+    LG_LAUNCH_CHECK();
+    k_cc_hook<<<warp_blocks(n), kNT, 0, s>>>(n, cur->rowptr.get(), cur->col.get(), parent.get(), h.dev_err.get());
+    LG_LAUNCH_CHECK();
+    k_cc_roots<<<blocks_for(n), kNT, 0, s>>>(n, parent.get(), is_root.get(), h.dev_err.get());
+    LG_LAUNCH_CHECK();
+    exclusive_scan_flags(is_root.get(), cnt.get(), n, s);
+    const int64_t ncomp = read_i64(cnt.get() + n, s);
+    if (read_err(h.dev_err, s)) fail(LG_ERR_TIMEOUT, "connected components did not settle");
+    if (ncomp != 1) fail(LG_ERR_DISCONNECTED, "graph is not connected");
+  }
+  h.nnz0 = nnz + n;
+  prepare_operator(*cur, s, counter);
+
+  // ---- coarsening loop ----
+  std::vector<double> lam_host;
+  DBuf<double> lam_dev(o.max_levels + 1, s);
+  std::vector<int> lam_level;
+  auto stop = [&](const Level& L) {
+    return (double)(L.nnz + L.n) <= o.coarse_nnz || (int)h.levels.size() >= o.max_levels - 1;
+  };
+  for (;;) {
+    if (stop(*cur)) break;
+    if (o.elim_enable && o.elim_max_degree > 0) {
+      DBuf<uint8_t> is_f(cur->n, s);
+      const int64_t nf = run_elim_select(cur->n, cur->rowptr.get(), cur->col.get(), o.elim_max_degree, o.seed,
+                                         is_f.get(), s);
+      if ((double)nf > o.elim_min_frac * (double)cur->n) {
+        auto next = eliminate(*cur, is_f.get(), nf, s, counter);
+        h.levels.push_back(std::move(cur));
+        cur = std::move(next);
+        prepare_operator(*cur, s, counter);
+        if (stop(*cur)) break;
+      }
+    }
+    const int level = (int)h.levels.size();
+    DBuf<double> S(cur->nnz, s);
+    run_strength(cur->n, cur->rowptr.get(), cur->col.get(), cur->w.get(), o.seed, level, o.strength_vecs,
+                 o.strength_sweeps, o.jacobi_omega, S.get(), s);
+    cur->agg.alloc(cur->n, s, counter);
+    const int64_t nc = run_aggregate(cur->n, cur->rowptr.get(), cur->col.get(), S.get(), o.agg_iters,
+                                     o.vote_threshold, cur->agg.get(), nullptr, nullptr, s);
+    if ((double)nc > o.stagnation_frac * (double)cur->n) {
+      cur->agg.release();
+      break;
+    }
+    cur->kind = LG_LEVEL_AGG;
+    cur->nc = nc;
+    lanczos(*cur, o, level, lam_dev.get() + level, s);
+    lam_level.push_back(level);
+    auto next = galerkin(*cur, s, counter);
+    h.levels.push_back(std::move(cur));
+    cur = std::move(next);
+    prepare_operator(*cur, s, counter);
+  }
+  if (cur->n > o.max_coarse_n) fail(LG_ERR_SETUP, "coarsest level too large for the dense solve");
+  coarsest_pinv(*cur, h.dev_err.get(), s, counter);
+  h.levels.push_back(std::move(cur));
+  for (auto& L : h.levels) make_f32(*L, s, counter);
+  if (read_err(h.dev_err, s)) fail(LG_ERR_SETUP, "coarsest pseudo-inverse failed");
+
+  // ---- Chebyshev constants from the eigenvalue estimates ----
+  std::vector<double> lam(h.levels.size() + 1, 0.0);
+  LG_CUDA(cudaMemcpyAsync(lam.data(), lam_dev.get(), sizeof(double) * h.levels.size(), cudaMemcpyDeviceToHost, s));
+  LG_CUDA(cudaEventRecord(e1, s));
+  LG_CUDA(cudaStreamSynchronize(s));
+  float ms = 0.f;
+  LG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  h.setup_ms = ms;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h.cheb.assign(h.levels.size(), Cheb{});
+  for (int l : lam_level) {
+    Level& L = *h.levels[l];
+    L.lambda = lam[l];
+    const double a = o.cheb_lo * L.lambda, b = o.cheb_hi * L.lambda;
+    const double theta = 0.5 * (b + a), delta = 0.5 * (b - a);
+    const double sigma = theta / delta;
+    Cheb& c = h.cheb[l];
+    c.inv_theta = 1.0 / theta;
+    double rho = 1.0 / sigma;
+    for (int st = 1; st < o.cheb_degree && st < 8; ++st) {
+      const double rn = 1.0 / (2.0 * sigma - rho);
+      c.c1[st] = rn * rho;
+      c.c2[st] = 2.0 * rn / delta;
+      rho = rn;
+    }
+  }
+}
+
+}  // namespace lg

@@ -26,3 +26,20 @@ def inputs():
     from paper_1705_06266_gb300 import inputs as I
 
     return I
+
+
+@pytest.fixture(scope="session")
+def lgmod():
+    """The CUDA library binding, built in-tree if needed."""
+    from paper_1705_06266_gb300 import _build, lg
+
+    _build.build()
+    return lg
+
+
+@pytest.fixture(scope="session")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch

@@ -1,0 +1,250 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Integer work (degrees, elimination sets, aggregates given the same strength
+values) must match bit for bit. Floating-point results are compared with
+tolerances derived from the arithmetic:
+  * one SpMV / strength pass in FP64: |diff| <= 1e-12 relative to the row scale
+    (a few ulps of a reordered sum of O(degree) terms);
+  * coarse operators: 1e-12 relative (sums of at most a few thousand terms);
+  * Lanczos estimate: 1e-9 relative (10 steps amplify rounding mildly);
+  * solves: true relative residual <= 1e-8 (recomputed here with scipy), and
+    the mean-removed solution within 1e-6 relative of the oracle's reference
+    solution (dense direct solve, or oracle PCG at tol 1e-12).
+"""
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+from scipy.sparse.csgraph import laplacian
+
+pytestmark = pytest.mark.gpu
+
+SEED = 0x5EED
+
+
+def dev(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def relres(g, b, x):
+    A = sp.csr_matrix((g.w, g.col, g.rowptr), shape=(g.n, g.n))
+    bm = b - b.mean()
+    return np.linalg.norm(bm - laplacian(A) @ x) / np.linalg.norm(bm)
+
+
+GRAPHS = {
+    "grid2d_20": lambda I: I.grid2d(20, 20),
+    "grid3d_8": lambda I: I.grid3d(8, 8, 8),
+    "random_3k": lambda I: I.random_graph(3000, 5, seed=3),
+    "chunglu_20k": lambda I: I.chung_lu(20000, m_target=100000, seed=3),
+    "rmat_12": lambda I: I.rmat(12, seed=2),
+    "star_5000": lambda I: I.star(5000),
+}
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+def test_laplacian_apply(torch_cuda, lgmod, oracle, inputs, name):
+    torch = torch_cuda
+    g = GRAPHS[name](inputs)
+    x = np.random.default_rng(1).standard_normal(g.n)
+    y = torch.zeros(g.n, dtype=torch.float64, device="cuda")
+    lgmod.lg_laplacian_apply(g.n, dev(torch, g.rowptr), dev(torch, g.col), dev(torch, g.w), dev(torch, x), y)
+    ref = oracle.apply_L(g, x)
+    scale = np.abs(g.w).max() * (np.abs(x).max()) * np.diff(g.rowptr).clip(1)
+    assert np.all(np.abs(y.cpu().numpy() - ref) <= 1e-12 * scale)
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+def test_elim_select_bit_exact(torch_cuda, lgmod, oracle, inputs, name):
+    torch = torch_cuda
+    g = GRAPHS[name](inputs)
+    is_f = torch.zeros(g.n, dtype=torch.uint8, device="cuda")
+    nf = lgmod.lg_elim_select(g.n, dev(torch, g.rowptr), dev(torch, g.col), 4, SEED, is_f)
+    ref = oracle.elim_select(g, 4, SEED)
+    np.testing.assert_array_equal(is_f.cpu().numpy(), ref)
+    assert nf == int(ref.sum())
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+def test_strength_and_aggregation(torch_cuda, lgmod, oracle, inputs, name):
+    torch = torch_cuda
+    g = GRAPHS[name](inputs)
+    rp, cl, w = dev(torch, g.rowptr), dev(torch, g.col), dev(torch, g.w)
+    S = torch.zeros(max(g.nnz_off, 1), dtype=torch.float64, device="cuda")
+    lgmod.lg_strength(g.n, rp, cl, w, SEED, 3, 4, 3, 2.0 / 3.0, S)
+    S_gpu = S.cpu().numpy()[: g.nnz_off]
+    S_ref = oracle.strength(g, SEED, 3)
+    np.testing.assert_allclose(S_gpu, S_ref, rtol=0, atol=1e-12)
+    # aggregation on identical strength values: bit-exact
+    agg = torch.zeros(g.n, dtype=torch.int32, device="cuda")
+    st = torch.zeros(g.n, dtype=torch.int8, device="cuda")
+    votes = torch.zeros(g.n, dtype=torch.int32, device="cuda")
+    nc = lgmod.lg_aggregate(g.n, rp, cl, S, 10, 8, agg, st, votes)
+    nc_ref, agg_ref, st_ref, votes_ref = oracle.aggregate(g, S_gpu)
+    assert nc == nc_ref
+    np.testing.assert_array_equal(agg.cpu().numpy(), agg_ref)
+    np.testing.assert_array_equal(st.cpu().numpy(), st_ref)
+    np.testing.assert_array_equal(votes.cpu().numpy(), votes_ref)
+
+
+def csr_of(level):
+    rp, cl, w, mp = level
+    return rp, cl, w, mp
+
+
+def same_csr(a_rp, a_cl, a_w, b, rtol=1e-12):
+    np.testing.assert_array_equal(a_rp, b.rowptr)
+    np.testing.assert_array_equal(a_cl, b.col)
+    np.testing.assert_allclose(a_w, b.w, rtol=rtol, atol=0)
+
+
+@pytest.mark.parametrize("name", ["grid2d_20", "grid3d_8", "random_3k", "chunglu_20k", "rmat_12"])
+def test_hierarchy_per_level_reinjection(torch_cuda, lgmod, oracle, inputs, name):
+    """Each GPU level, fed to the oracle's stage, reproduces the GPU's next level."""
+    torch = torch_cuda
+    g = GRAPHS[name](inputs)
+    H = lgmod.Hierarchy(g)
+    nl = H.nlevels
+    assert nl >= 2
+    for l in range(nl):
+        info = H.level_info(l)
+        rp, cl, w, mp = H.level(l)
+        G = inputs.Graph(info["n"], rp, cl, w)
+        if l == 0:
+            np.testing.assert_array_equal(rp, g.rowptr)
+            np.testing.assert_array_equal(cl, g.col)
+        if info["kind"] == lgmod.LEVEL_ELIM:
+            is_f = oracle.elim_select(G, 4, SEED)
+            np.testing.assert_array_equal((mp < 0).astype(np.uint8), is_f)
+            coarse, cmap = oracle.schur(G, is_f)
+            np.testing.assert_array_equal(mp, cmap)
+            nrp, ncl, nw, _ = H.level(l + 1)
+            same_csr(nrp, ncl, nw, coarse)
+        elif info["kind"] == lgmod.LEVEL_AGG:
+            S = torch.zeros(max(G.nnz_off, 1), dtype=torch.float64, device="cuda")
+            lgmod.lg_strength(G.n, dev(torch, rp), dev(torch, cl), dev(torch, w), SEED, l, 4, 3, 2.0 / 3.0, S)
+            S_gpu = S.cpu().numpy()[: G.nnz_off]
+            np.testing.assert_allclose(S_gpu, oracle.strength(G, SEED, l), rtol=0, atol=1e-12)
+            nc_ref, agg_ref, _, _ = oracle.aggregate(G, S_gpu)
+            assert info["nc"] == nc_ref
+            np.testing.assert_array_equal(mp, agg_ref)
+            nrp, ncl, nw, _ = H.level(l + 1)
+            same_csr(nrp, ncl, nw, oracle.galerkin(G, agg_ref, nc_ref))
+            lam_ref = oracle.lanczos(G, SEED, l)
+            assert info["lambda"] == pytest.approx(lam_ref, rel=1e-9)
+        else:
+            assert l == nl - 1
+            assert info["nnz"] + info["n"] <= 1000 or nl == 64
+            P = lgmod.lg_coarsest_pinv(H.h, info["n"])
+            np.testing.assert_allclose(P, oracle.pinv(G), rtol=0, atol=1e-9 * max(1.0, np.abs(P).max()))
+    H.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_solve_grid64_matches_dense(lgmod, oracle, inputs, prec):
+    g = inputs.grid2d(64, 64)
+    b = inputs.rhs(g.n, seed=2)
+    p = lgmod.FP64 if prec == "fp64" else lgmod.FP32_HIER
+    H = lgmod.Hierarchy(g, precision=p)
+    x, info = H.solve(b, tol=1e-8)
+    assert info.status == lgmod.OK
+    assert relres(g, b, x) <= 1e-8
+    assert abs(info.relres - relres(g, b, x)) <= 1e-10
+    ref = oracle.dense_solve(g, b)
+    assert np.linalg.norm(x - x.mean() - ref) <= 1e-6 * np.linalg.norm(ref)
+    assert abs(x.mean()) < 1e-12
+    H.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", ["chunglu_20k", "rmat_12", "grid3d_8", "star_5000"])
+def test_solve_matches_oracle_pcg(lgmod, oracle, inputs, name, prec):
+    g = GRAPHS[name](inputs)
+    b = inputs.rhs(g.n, seed=5)
+    p = lgmod.FP64 if prec == "fp64" else lgmod.FP32_HIER
+    H = lgmod.Hierarchy(g, precision=p)
+    x, info = H.solve(b, tol=1e-8)
+    assert info.status == lgmod.OK and relres(g, b, x) <= 1e-8
+    ref, st, it, rel = oracle.Hierarchy(g).pcg(b, tol=1e-12, maxit=1000)
+    assert st == oracle.OK
+    assert np.linalg.norm(x - ref) <= 1e-6 * np.linalg.norm(ref)
+    H.close()
+
+
+def test_vcycle_fp64_matches_oracle_cycle(lgmod, oracle, inputs):
+    """Where the oracle builds the identical hierarchy, one V-cycle agrees to rounding."""
+    g = inputs.random_graph(3000, 6, seed=4, weights="uniform")
+    H = lgmod.Hierarchy(g)
+    R = oracle.Hierarchy(g)
+    assert H.nlevels == R.nlevels
+    for l in range(H.nlevels):
+        rp, cl, w, mp = H.level(l)
+        Lr = R.level(l)
+        np.testing.assert_array_equal(rp, Lr.a.rowptr)
+        np.testing.assert_array_equal(cl, Lr.a.col)
+        if mp is not None:
+            np.testing.assert_array_equal(mp, Lr.map)
+    f = inputs.rhs(g.n, seed=9)
+    xg = H.vcycle(f, lgmod.FP64)
+    xr = R.vcycle(f)
+    assert np.linalg.norm(xg - xr) <= 1e-11 * np.linalg.norm(xr)
+    x32 = H.vcycle(f, lgmod.FP32_HIER)
+    assert np.linalg.norm(x32 - xr) <= 1e-4 * np.linalg.norm(xr)
+    H.close()
+
+
+def test_edge_cases(lgmod, inputs):
+    one = inputs.Graph(1, np.array([0, 0]), np.zeros(0, np.int32), np.zeros(0))
+    H = lgmod.Hierarchy(one)
+    x, info = H.solve(np.array([3.0]))
+    assert info.status == lgmod.OK and x[0] == 0.0
+    H.close()
+    p2 = inputs.path(2)
+    H = lgmod.Hierarchy(p2)
+    x, info = H.solve(np.array([1.0, -1.0]))
+    assert info.status == lgmod.OK and np.allclose(x, [0.5, -0.5])
+    H.close()
+    g = inputs.grid2d(10, 10)
+    H = lgmod.Hierarchy(g)
+    x, info = H.solve(np.ones(g.n))  # b is constant: zero after projection
+    assert info.status == lgmod.OK and info.iterations == 0 and np.all(x == 0)
+    H.close()
+    # disconnected and malformed graphs
+    rp = np.concatenate([g.rowptr, [g.rowptr[-1]]])
+    with pytest.raises(lgmod.LGError) as e:
+        lgmod.Hierarchy(inputs.Graph(g.n + 1, rp, g.col, g.w))
+    assert e.value.status == lgmod.ERR_DISCONNECTED
+    bad = g.w.copy()
+    bad[0] = 2.0
+    with pytest.raises(lgmod.LGError) as e:
+        lgmod.Hierarchy(inputs.Graph(g.n, g.rowptr, g.col, bad))
+    assert e.value.status == lgmod.ERR_INVALID
+    badc = g.col.copy()
+    badc[3] = g.n + 5
+    with pytest.raises(lgmod.LGError) as e:
+        lgmod.Hierarchy(inputs.Graph(g.n, g.rowptr, badc, g.w))
+    assert e.value.status == lgmod.ERR_INVALID
+
+
+def test_deterministic(lgmod, inputs):
+    g = inputs.chung_lu(20000, m_target=100000, seed=3)
+    b = inputs.rhs(g.n, seed=1)
+    xs = []
+    for _ in range(2):
+        H = lgmod.Hierarchy(g, precision=lgmod.FP32_HIER)
+        xs.append(H.solve(b)[0])
+        H.close()
+    np.testing.assert_array_equal(xs[0], xs[1])
+
+
+def test_device_pointers(torch_cuda, lgmod, inputs):
+    torch = torch_cuda
+    g = inputs.grid2d(30, 30)
+    H = lgmod.Hierarchy(n=g.n, rowptr=dev(torch, g.rowptr), col=dev(torch, g.col), w=dev(torch, g.w))
+    b = inputs.rhs(g.n, seed=3)
+    x = torch.zeros(g.n, dtype=torch.float64, device="cuda")
+    info = lgmod.lg_solve(H.h, dev(torch, b), x, 1e-8)
+    xh, _ = H.solve(b)
+    np.testing.assert_array_equal(x.cpu().numpy(), xh)
+    assert info.status == lgmod.OK
+    H.close()
