@@ -1,0 +1,381 @@
+#!/usr/bin/env python
+"""Benchmark: nnz/s to a 1e-8 relative residual on one GB300 per rank.
+
+Workload (default): Chung-Lu power-law graph, 1M vertices, expected degrees
+Pareto(2.1) truncated to [1, 50000], 10M sampled edges, weights U[0.5, 1.5],
+largest component kept. A step is one pass of the whole path on that graph:
+hierarchy setup (elimination, strength, aggregation, Galerkin, eigenvalue
+estimates, coarsest pseudo-inverse), then one PCG solve with the FP64 V-cycle
+and one with the FP32 hierarchy, each to ||b - L x|| / ||b|| <= 1e-8 in FP64.
+
+value = nnz(L_0) / T_solve(FP64), whole job (summed over ranks, each rank
+solving its own replica; timings are the max over ranks). The FP32-hierarchy
+solve, setup time and setup-inclusive throughput are reported beside it.
+
+--impl reference times the FP64 oracle on the host cores instead, on a
+bounded sample of the same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "nnz/s to 1e-8 rel-res, FP32-hier vs FP64 on same GB300; serve p50/p99 ms"
+UNIT = "nnz/s"
+TOL = 1e-8
+L2_BYTES = 129 * 2 ** 20
+FALLBACK_HBM_GBS = 6800.0
+
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["lg", "reference"], default="lg")
+    ap.add_argument("--workload", default="chung_lu_1m")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    return ap.parse_args()
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def allreduce_max(vals, world):
+    if world == 1:
+        return list(vals)
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor(vals, dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.cpu().tolist()
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("lg_rows.cuh", "lg_cycle.cu", "lg_common.cuh"):
+        with open(os.path.join(ROOT, "paper_1705_06266_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload):
+    """DRAM bytes per launch of the dominant kernel from a committed ncu summary,
+    or None when there is none or the kernel source changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", f"k_rows_lap_{workload}.txt")
+    if not os.path.exists(path):
+        return None, None
+    fields = {}
+    for line in open(path):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            fields[k.strip()] = v.strip()
+    if fields.get("kernel_source_hash") != kernel_source_hash():
+        return None, fields.get("kernel_source_hash")
+    try:
+        return float(fields["dram_bytes_per_launch"]), fields.get("kernel_source_hash")
+    except (KeyError, ValueError):
+        return None, None
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.p = None
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(device)], stdout=subprocess.PIPE,
+                                      stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=10)
+        except Exception:
+            self.p.kill()
+            out = ""
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(workload_name, g, b):
+    """The oracle as it stands, single-threaded, on a bounded sample of the
+    workload: the same graph and right-hand side, one solve."""
+    import oracle
+
+    oracle.build()
+    t0 = time.perf_counter()
+    h = oracle.Hierarchy(g)
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    x, st, it, rel = h.pcg(b, tol=TOL)
+    t_solve = time.perf_counter() - t0
+    return {
+        "value": g.nnz / t_solve, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "sample": f"{workload_name} (n={g.n}, nnz(L)={g.nnz}), one right-hand side: oracle setup "
+                  f"{t_setup:.1f} s untimed, one FP64 PCG solve to 1e-8 timed ({it} iterations, "
+                  f"relres {rel:.2e})",
+        "solve_s": t_solve, "setup_s": t_setup,
+    }
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    import oracle
+    from paper_1705_06266_gb300 import inputs
+
+    oracle.build()
+    g = inputs.workload(args.workload)
+    b = inputs.rhs(g.n, seed=2)
+    h = oracle.Hierarchy(g)
+    times = []
+    for step in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        x, st, it, rel = h.pcg(b, tol=TOL)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+    mean = sum(times) / len(times)
+    value = g.nnz / mean
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "rhs": 1, "tol": TOL, "precision": "fp64",
+                   "parallelism": "replicas"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.workload} (n={g.n}, nnz(L)={g.nnz}); each step one FP64 PCG solve "
+                                   f"to 1e-8 ({it} iterations) on one host core, oracle setup untimed"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import torch
+
+    from paper_1705_06266_gb300 import _build, inputs, lg
+
+    _build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    g = inputs.workload(args.workload)
+    b = inputs.rhs(g.n, seed=2)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    with torch.cuda.stream(stream):
+        rp = torch.from_numpy(g.rowptr).to(dev)
+        cl = torch.from_numpy(g.col).to(dev)
+        w = torch.from_numpy(g.w).to(dev)
+        bd = torch.from_numpy(b).to(dev)
+        x64 = torch.zeros(g.n, dtype=torch.float64, device=dev)
+        x32 = torch.zeros(g.n, dtype=torch.float64, device=dev)
+        opts = lg.options(stream=stream.cuda_stream)
+
+        def step(profile):
+            flush.fill_(1.0)
+            h = lg.lg_setup(g.n, rp, cl, w, opts)
+            hi = lg.lg_hier_info(h)
+            if profile:
+                lg.lg_profile(h, True)
+            flush.fill_(2.0)
+            lg.lg_set_precision(h, lg.FP64)
+            i64 = lg.lg_solve(h, bd, x64, TOL)
+            prof = None
+            if profile:
+                levels = []
+                for l in range(hi.levels):
+                    p = lg.lg_profile_read(h, l)
+                    levels.append((p.total_ms, p.bytes, p.launches))
+                prof = levels
+                lg.lg_profile(h, False)
+            flush.fill_(3.0)
+            lg.lg_set_precision(h, lg.FP32_HIER)
+            i32 = lg.lg_solve(h, bd, x32, TOL)
+            nb = lg.lg_hier_bytes(h)
+            lg.lg_destroy(h)
+            return hi, i64, i32, prof, nb
+
+        for _ in range(args.warmup):
+            step(False)
+        stream.synchronize()
+        barrier(world)
+        torch.cuda.synchronize()
+        clocks = Clocks(local)
+        launches0 = lg.lg_kernel_launches()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        t0 = time.perf_counter()
+        recs = [step(True) for _ in range(args.steps)]
+        ev1.record(stream)
+        stream.synchronize()
+        wall = time.perf_counter() - t0
+        torch.cuda.synchronize()
+        barrier(world)
+        clk = clocks.stop()
+        launches = lg.lg_kernel_launches() - launches0
+        step_ms = ev0.elapsed_time(ev1) / args.steps
+
+        # end to end through the C ABI with host buffers (pinned), per step:
+        # H2D of b, the solve, D2H of x, all inside the timed call.
+        h = lg.lg_setup(g.n, g.rowptr, g.col, g.w, lg.options())
+        bh = torch.from_numpy(b).pin_memory()
+        xh = torch.zeros(g.n, dtype=torch.float64).pin_memory()
+        bnp, xnp = bh.numpy(), xh.numpy()
+        lg.lg_solve(h, bnp, xnp, TOL)
+        e2e_t = []
+        for _ in range(args.e2e_steps):
+            t1 = time.perf_counter()
+            lg.lg_solve(h, bnp, xnp, TOL)
+            e2e_t.append(time.perf_counter() - t1)
+        t1 = time.perf_counter()
+        h2 = lg.lg_setup(g.n, g.rowptr, g.col, g.w, lg.options())
+        setup_e2e = time.perf_counter() - t1
+        lg.lg_destroy(h2)
+        lg.lg_destroy(h)
+
+    setup_ms = sum(r[0].setup_ms for r in recs) / len(recs)
+    solve64_ms = sum(r[1].solve_ms for r in recs) / len(recs)
+    solve32_ms = sum(r[2].solve_ms for r in recs) / len(recs)
+    e2e_s = sum(e2e_t) / len(e2e_t)
+    mx = allreduce_max([step_ms, setup_ms, solve64_ms, solve32_ms, e2e_s], world)
+    step_ms, setup_ms, solve64_ms, solve32_ms, e2e_s = mx
+    nnz = g.nnz
+    value = world * nnz / (solve64_ms * 1e-3)
+
+    # roofline of the dominant kernel: the operator row pass of the level with the most device time
+    nlev = len(recs[0][3])
+    tot = [[0.0, 0.0, 0] for _ in range(nlev)]
+    for r in recs:
+        for l, (ms, by, la) in enumerate(r[3]):
+            tot[l][0] += ms
+            tot[l][1] += by
+            tot[l][2] += la
+    dom = max(range(nlev), key=lambda l: tot[l][0])
+    d_ms, d_bytes, d_launch = tot[dom]
+    peak, peak_kind = measured_peak()
+    achieved = d_bytes / (d_ms * 1e-3) / 1e9 if d_ms > 0 else 0.0
+    traffic, _ = ncu_traffic(args.workload)
+    all_ms = sum(t[0] for t in tot)
+    all_bytes = sum(t[1] for t in tot)
+    i64, i32 = recs[-1][1], recs[-1][2]
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "graph": g.name, "n": g.n, "nnz": nnz, "rhs": 1, "tol": TOL,
+                   "precision": "fp64 (FP32-hierarchy solve reported in fp32_hier)",
+                   "l2": "flushed (512 MiB write) before setup and before each solve",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "solve_ms": solve64_ms, "setup_ms": setup_ms,
+        "iterations": i64.iterations, "relres": i64.relres, "levels": i64.levels,
+        "op_complexity": recs[-1][0].op_complexity,
+        "setup_inclusive_nnz_per_s": world * nnz / ((setup_ms + solve64_ms) * 1e-3),
+        "fp32_hier": {"value": world * nnz / (solve32_ms * 1e-3), "solve_ms": solve32_ms,
+                      "iterations": i32.iterations, "relres": i32.relres,
+                      "speedup_vs_fp64": solve64_ms / solve32_ms},
+        "tda_ms_per_digit": solve64_ms / -math.log10(max(i64.relres, 1e-300)),
+        "hierarchy_bytes": recs[-1][4][0], "workspace_bytes": recs[-1][4][1],
+        "e2e": {"value": world * nnz / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * g.n,
+                "d2h_bytes_per_step": 8 * g.n, "setup_from_host_ms": setup_e2e * 1e3,
+                "note": "lg_solve with pinned host b and x: H2D of b, solve, D2H of x inside the timed call"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": f"k_rows<double, LapTerm, *> operator passes of level {dom} "
+                               f"(n={recs[-1][0].nnz}) in the timed FP64 solves".replace(
+                                   f"(n={recs[-1][0].nnz})", f"({tot[dom][2] // len(recs)} per solve)"),
+                     "launches": d_launch, "avg_launch_us": d_ms * 1e3 / max(d_launch, 1),
+                     "bytes_per_launch": d_bytes / max(d_launch, 1), "peak_kind": peak_kind,
+                     "share_of_solve": d_ms / (solve64_ms * len(recs)),
+                     "all_levels_achieved": all_bytes / (all_ms * 1e-3) / 1e9 if all_ms > 0 else 0.0},
+        "clocks": clk,
+        "gpu_launches": launches,
+        "wall_s_timed": wall,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.workload, g, b)
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

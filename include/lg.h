@@ -93,7 +93,9 @@ typedef struct {
   int32_t residual_replace; /* 50: PCG recomputes r = b - L x every this many iterations */
   int32_t memory_space;     /* LG_AUTO: detect; LG_HOST / LG_DEVICE force the interpretation */
   int32_t use_graphs;       /* 1: replay the preconditioned iteration as a captured CUDA graph */
-  int32_t reserved;
+  int32_t autotune;         /* 1: time the SpMV lane-group sizes of each large level at setup and keep
+                               the fastest (cached per level shape for the life of the process);
+                               0: a fixed rule on the average row length */
 } lg_options;
 
 /* Result of a setup or a solve. */
@@ -194,6 +196,30 @@ int lg_coarsest_pinv(lg_handle h, double* out);
  * gamma = 1). No mean projection.
  */
 int lg_vcycle(lg_handle h, const double* f, double* x, int32_t precision);
+
+/* ---- instrumentation ---- */
+
+/* Kernels the library has launched in this process so far. */
+uint64_t lg_kernel_launches(void);
+
+/* Per-kernel timing of the operator passes: the row passes that apply a
+ * level's Laplacian (the PCG product and true residual on level 0, the
+ * Chebyshev steps of every aggregation level). When enabled on a handle,
+ * each such launch of lg_solve is bracketed by CUDA events on the handle's
+ * stream. lg_profile_read returns, for one level (or every level with
+ * level = -1), the launches, their summed device time and their summed
+ * algorithmic bytes (compulsory traffic: the CSR arrays once, the gathered
+ * vector once, each epilogue vector stream once). lg_profile also clears the
+ * counters. */
+typedef struct {
+  double total_ms;         /* summed event-measured device time of those launches */
+  double bytes;            /* summed algorithmic bytes */
+  int64_t launches;
+  int64_t reserved;
+} lg_kernel_profile;
+
+int lg_profile(lg_handle h, int32_t enable);
+int lg_profile_read(lg_handle h, int32_t level, lg_kernel_profile* out);
 
 /* ---- single steps on caller data (DEVICE pointers only, on `stream`) ----
  * These run one stage of the setup on an arbitrary graph so that each stage

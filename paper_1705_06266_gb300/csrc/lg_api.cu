@@ -10,6 +10,7 @@
 namespace lg {
 
 thread_local std::string g_last_error;
+std::atomic<uint64_t> g_launches{0};
 
 Hier::~Hier() {
   ws.reset();
@@ -87,6 +88,7 @@ int lg_options_default(lg_options* o) {
   o->residual_replace = 50;
   o->memory_space = LG_AUTO;
   o->use_graphs = 1;
+  o->autotune = 1;
   return LG_OK;
 }
 
@@ -285,6 +287,40 @@ int lg_vcycle(lg_handle hh, const double* f, double* x, int32_t precision) {
   lg::vcycle_apply(h, *h.ws, fp, xp, precision, s);
   if (!xdev) LG_CUDA(cudaMemcpyAsync(x, xp, sizeof(double) * n, cudaMemcpyDefault, s));
   LG_CUDA(cudaStreamSynchronize(s));
+  return LG_OK;
+  LG_API_END
+}
+
+uint64_t lg_kernel_launches(void) { return lg::g_launches.load(); }
+
+int lg_profile(lg_handle hh, int32_t enable) {
+  if (!hh) return LG_ERR_INVALID;
+  lg::Hier& h = *H(hh);
+  if (!h.ws) return LG_ERR_INVALID;
+  LG_API_BEGIN
+  LG_CUDA(cudaStreamSynchronize(h.stream));
+  h.ws->prof.collect();
+  h.ws->prof.stats.clear();
+  h.ws->prof.on = enable != 0;
+  return LG_OK;
+  LG_API_END
+}
+
+int lg_profile_read(lg_handle hh, int32_t level, lg_kernel_profile* out) {
+  if (!hh || !out) return LG_ERR_INVALID;
+  LG_API_BEGIN
+  lg::Hier& h = *H(hh);
+  if (level < -1 || level >= (int32_t)h.levels.size()) return LG_ERR_INVALID;
+  LG_CUDA(cudaStreamSynchronize(h.stream));
+  lg::Prof& p = h.ws->prof;
+  p.collect();
+  std::memset(out, 0, sizeof(*out));
+  for (size_t l = 0; l < p.stats.size(); ++l) {
+    if (level >= 0 && (int32_t)l != level) continue;
+    out->total_ms += p.stats[l].ms;
+    out->bytes += p.stats[l].bytes;
+    out->launches += p.stats[l].launches;
+  }
   return LG_OK;
   LG_API_END
 }

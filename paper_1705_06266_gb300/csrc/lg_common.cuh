@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <cstddef>
 #include <cstdio>
 #include <stdexcept>
@@ -38,7 +39,15 @@ inline void check_cuda(cudaError_t e, const char* what) {
 }
 
 #define LG_CUDA(call) ::lg::check_cuda((call), #call)
-#define LG_LAUNCH_CHECK() ::lg::check_cuda(cudaGetLastError(), "kernel launch")
+
+// Every kernel launch site is followed by LG_LAUNCH_CHECK(), which also
+// counts the launch.
+extern std::atomic<uint64_t> g_launches;
+#define LG_LAUNCH_CHECK()                                           \
+  do {                                                              \
+    ::lg::g_launches.fetch_add(1, std::memory_order_relaxed);      \
+    ::lg::check_cuda(cudaGetLastError(), "kernel launch");          \
+  } while (0)
 
 // ---------------------------------------------------------------------------
 // Device memory: stream-ordered allocation (cudaMallocAsync on the pool of
@@ -239,18 +248,24 @@ __device__ __forceinline__ bool grid_sum(double (&v)[K], double* partials /* gri
 }
 
 // ---------------------------------------------------------------------------
-// SpMV row plan of one CSR operator. Rows with at most `long_thresh` entries
-// go to groups of G lanes; longer rows are cut into chunks of kChunk entries,
-// one block per chunk; the last block of a row (per-row ticket) adds the
-// chunk partials in chunk order and applies the epilogue.
+// SpMV row plan of one CSR operator (see lg_rows.cuh). Rows with at most
+// kShortMax entries go to groups of G lanes (G64 / G32 for FP64 / FP32
+// passes); rows up to long_thresh entries to one warp each (med_rows list);
+// longer rows are cut into chunks of kChunk entries, one block per chunk;
+// the last block of a row (per-row ticket) adds the chunk partials in chunk
+// order and applies the epilogue.
 // ---------------------------------------------------------------------------
 constexpr int kRowThreads = 256;
 constexpr int kChunk = 2048;
+constexpr int64_t kShortMax = 32;
 
 struct RowPlan {
-  int G = 8;
-  int short_blocks = 1;
-  int64_t long_thresh = 0;
+  int G64 = 4, G32 = 4;
+  int short_blocks64 = 1, short_blocks32 = 1;
+  int med_blocks = 0;
+  int64_t long_thresh = kChunk;
+  int64_t nmed = 0;
+  int32_t* med_rows = nullptr;    // rows with kShortMax < deg <= long_thresh
   int64_t nlong = 0;
   int64_t nchunks = 0;
   int32_t* chunk_row = nullptr;   // row of each chunk
@@ -260,6 +275,11 @@ struct RowPlan {
   int32_t* lrow_count = nullptr;  // chunks of each long row
   double* partial = nullptr;      // nchunks * kMaxCols partial sums
   unsigned* ticket = nullptr;     // nlong tickets, zero between launches
+
+  int grid(int elem_bytes) const {
+    return (int)(nchunks + med_blocks + (elem_bytes == 8 ? short_blocks64 : short_blocks32));
+  }
+  int max_grid() const { return (int)(nchunks + med_blocks + (short_blocks64 > short_blocks32 ? short_blocks64 : short_blocks32)); }
 };
 
 constexpr int kMaxCols = 32;  // widest multi-RHS block

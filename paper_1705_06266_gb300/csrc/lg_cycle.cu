@@ -21,6 +21,39 @@ constexpr int kVT = 256;
 
 static inline int vblocks(int64_t n) { return grid_for(n, kVT, kSMs * 8); }
 
+void Prof::begin(cudaStream_t s) {
+  const size_t i = pending.size();
+  while (ev.size() < 2 * i + 2) {
+    cudaEvent_t e;
+    LG_CUDA(cudaEventCreate(&e));
+    ev.push_back(e);
+  }
+  LG_CUDA(cudaEventRecord(ev[2 * i], s));
+}
+
+void Prof::end(cudaStream_t s, int level, double bytes) {
+  const size_t i = pending.size();
+  LG_CUDA(cudaEventRecord(ev[2 * i + 1], s));
+  pending.push_back(Pending{level, bytes});
+}
+
+void Prof::collect() {
+  for (size_t i = 0; i < pending.size(); ++i) {
+    float ms = 0.f;
+    LG_CUDA(cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]));
+    const int l = pending[i].level;
+    if ((int)stats.size() <= l) stats.resize(l + 1);
+    stats[l].ms += ms;
+    stats[l].bytes += pending[i].bytes;
+    stats[l].launches += 1;
+  }
+  pending.clear();
+}
+
+Prof::~Prof() {
+  for (auto e : ev) cudaEventDestroy(e);
+}
+
 // ---------------------------------------------------------------------------
 // Epilogues of the cycle's row passes.
 // ---------------------------------------------------------------------------
@@ -41,18 +74,21 @@ struct EpiCheb {
   int x_mode;
   int add_d;
   T c1, c2;
-  __device__ __forceinline__ void operator()(int64_t i, T s, double*) const {
-    const T r = rin[i] - s;
+  struct Pre {
+    T rin, g, dinv, x;
+  };
+  __device__ __forceinline__ Pre pre(int64_t i) const {
+    return Pre{rin[i], g[i], dout ? dinv[i] : T(0), (x && x_mode == 2) ? x[i] : T(0)};
+  }
+  __device__ __forceinline__ void operator()(int64_t i, T s, const Pre& p, double*) const {
+    const T r = p.rin - s;
     rout[i] = r;
     T d = T(0);
     if (dout) {
-      d = c1 * g[i] + c2 * dinv[i] * r;
+      d = c1 * p.g + c2 * p.dinv * r;
       dout[i] = d;
     }
-    if (x) {
-      const T base = x_mode == 1 ? T(0) : x[i];
-      x[i] = base + g[i] + (add_d ? d : T(0));
-    }
+    if (x) x[i] = p.x + p.g + (add_d ? d : T(0));
   }
   __device__ void finish(const double*) const {}
 };
@@ -65,9 +101,10 @@ struct EpiRestrict {
   T* d0;
   const T* dinvc;
   T inv_theta;
-  __device__ __forceinline__ void operator()(int64_t I, T s, double*) const {
+  __device__ __forceinline__ T pre(int64_t I) const { return d0 ? dinvc[I] : T(0); }
+  __device__ __forceinline__ void operator()(int64_t I, T s, T dv, double*) const {
     fc[I] = s;
-    if (d0) d0[I] = s * dinvc[I] * inv_theta;
+    if (d0) d0[I] = s * dv * inv_theta;
   }
   __device__ void finish(const double*) const {}
 };
@@ -81,13 +118,39 @@ struct EpiElimRestrict {
   T* d0;
   const T* dinvc;
   T inv_theta;
-  __device__ __forceinline__ void operator()(int64_t c, T s, double*) const {
-    const T v = f[cfine[c]] + s;
+  struct Pre {
+    T f, dv;
+  };
+  __device__ __forceinline__ Pre pre(int64_t c) const { return Pre{f[cfine[c]], d0 ? dinvc[c] : T(0)}; }
+  __device__ __forceinline__ void operator()(int64_t c, T s, const Pre& p, double*) const {
+    const T v = p.f + s;
     fc[c] = v;
-    if (d0) d0[c] = v * dinvc[c] * inv_theta;
+    if (d0) d0[c] = v * p.dv * inv_theta;
   }
   __device__ void finish(const double*) const {}
 };
+
+// Algorithmic bytes of one row pass over an operator with elements of size t:
+// the CSR arrays once, the gathered vector once, and `streams` further
+// length-n vector streams (reads or writes) of the epilogue.
+static double pass_bytes(int64_t n, int64_t nnz, int t, int streams) {
+  return (double)nnz * (4.0 + t) + (double)(n + 1) * 8.0 + (double)n * t * (1 + streams);
+}
+
+template <typename T>
+static int cheb_streams(const EpiCheb<T>& e) {
+  return 2 + (e.dout ? 2 : 0) + (e.x ? (e.x_mode == 2 ? 2 : 1) : 0);
+}
+
+// A row pass over level `level`'s operator, timed when the workspace profiles.
+template <typename T, int NRED, class Term, class Epi>
+static void op_pass(Workspace& ws, int level, const OpView<T>& op, const Term& term, const Epi& epi, int streams,
+                    cudaStream_t s, double* rp = nullptr, unsigned* rt = nullptr, double* ro = nullptr) {
+  const bool timed = ws.prof.on;
+  if (timed) ws.prof.begin(s);
+  launch_rows<T, NRED>(op.n, op.rowptr, op.col, term, op.plan, epi, s, rp, rt, ro);
+  if (timed) ws.prof.end(s, level, pass_bytes(op.n, op.nnz, (int)sizeof(T), streams));
+}
 
 // x = P x_c + Fsmooth(f) at an elimination level: kept vertices take their
 // coarse value; an eliminated f takes (f_f + sum_c w_fc x_c) / d_f.
@@ -211,35 +274,32 @@ static void cycle_level(Hier& h, Workspace& ws, int l, cudaStream_t s) {
   T* gn = V.dB.get();
   const T* rin = V.f.get();
   for (int st = 1; st < deg; ++st) {  // pre-smoothing from x = 0
-    launch_rows<T, 0>(n, op.rowptr, op.col, LapTerm<T>{op.w, g}, op.plan,
-                      EpiCheb<T>{g, rin, V.r.get(), op.dinv, gn, V.x.get(), st == 1 ? 1 : 2, st == deg - 1,
-                                 (T)ch.c1[st], (T)ch.c2[st]},
-                      s);
+    const EpiCheb<T> e{g, rin, V.r.get(), op.dinv, gn, V.x.get(), st == 1 ? 1 : 2, st == deg - 1,
+                       (T)ch.c1[st], (T)ch.c2[st]};
+    op_pass<T, 0>(ws, l, op, LapTerm<T>{op.w, g, op.d}, e, cheb_streams(e), s);
     rin = V.r.get();
     std::swap(g, gn);
   }
-  // residual r = f - L x of the pre-smoothed x (for degree 1 also x = d_0)
-  launch_rows<T, 0>(n, op.rowptr, op.col, LapTerm<T>{op.w, g}, op.plan,
-                    EpiCheb<T>{g, rin, V.r.get(), op.dinv, nullptr, deg == 1 ? V.x.get() : nullptr, 1, 0, T(0), T(0)},
-                    s);
+  {  // residual r = f - L x of the pre-smoothed x (for degree 1 also x = d_0)
+    const EpiCheb<T> e{g, rin, V.r.get(), op.dinv, nullptr, deg == 1 ? V.x.get() : nullptr, 1, 0, T(0), T(0)};
+    op_pass<T, 0>(ws, l, op, LapTerm<T>{op.w, g, op.d}, e, cheb_streams(e), s);
+  }
   // r_c = R r, then the coarse cycle
   launch_rows<T, 0>(L.nc, L.mem_ptr.get(), L.mem.get(), GatherTerm<T>{V.r.get()}, sc.mem.bind(L.mem_plan.plan),
                     EpiRestrict<T>{C.f.get(), d0n, dinvn, itn}, s);
   cycle_level<T>(h, ws, l + 1, s);
   k_agg_prolong<T><<<vblocks(n), kVT, 0, s>>>(n, L.agg.get(), C.x.get(), V.x.get());
   LG_LAUNCH_CHECK();
-  // post-smoothing from x: r_0 = f - L x, d_0 = D^-1 r_0 / theta
-  launch_rows<T, 0>(n, op.rowptr, op.col, LapTerm<T>{op.w, V.x.get()}, op.plan,
-                    EpiCheb<T>{V.x.get(), V.f.get(), V.r.get(), op.dinv, V.dA.get(), nullptr, 0, 0, T(0),
-                               (T)ch.inv_theta},
-                    s);
+  {  // post-smoothing from x: r_0 = f - L x, d_0 = D^-1 r_0 / theta
+    const EpiCheb<T> e{V.x.get(), V.f.get(), V.r.get(), op.dinv, V.dA.get(), nullptr, 0, 0, T(0), (T)ch.inv_theta};
+    op_pass<T, 0>(ws, l, op, LapTerm<T>{op.w, V.x.get(), op.d}, e, cheb_streams(e), s);
+  }
   g = V.dA.get();
   gn = V.dB.get();
   for (int st = 1; st < deg; ++st) {
-    launch_rows<T, 0>(n, op.rowptr, op.col, LapTerm<T>{op.w, g}, op.plan,
-                      EpiCheb<T>{g, V.r.get(), V.r.get(), op.dinv, gn, V.x.get(), 2, st == deg - 1, (T)ch.c1[st],
-                                 (T)ch.c2[st]},
-                      s);
+    const EpiCheb<T> e{g, V.r.get(), V.r.get(), op.dinv, gn, V.x.get(), 2, st == deg - 1, (T)ch.c1[st],
+                       (T)ch.c2[st]};
+    op_pass<T, 0>(ws, l, op, LapTerm<T>{op.w, g, op.d}, e, cheb_streams(e), s);
     std::swap(g, gn);
   }
   if (deg == 1) {
@@ -365,9 +425,10 @@ struct EpiPq {
   const double* p;
   double* q;
   double* scal;
-  __device__ __forceinline__ void operator()(int64_t i, double s, double* red) const {
+  __device__ __forceinline__ double pre(int64_t i) const { return p[i]; }
+  __device__ __forceinline__ void operator()(int64_t i, double s, double pi, double* red) const {
     q[i] = s;
-    red[0] += p[i] * s;
+    red[0] += pi * s;
   }
   __device__ void finish(const double* tot) const {
     const double pq = tot[0];
@@ -403,8 +464,9 @@ struct EpiTrueRes {
   const double* bm;
   double* r;
   double* scal;
-  __device__ __forceinline__ void operator()(int64_t i, double s, double* red) const {
-    const double v = bm[i] - s;
+  __device__ __forceinline__ double pre(int64_t i) const { return bm[i]; }
+  __device__ __forceinline__ void operator()(int64_t i, double s, double b, double* red) const {
+    const double v = b - s;
     r[i] = v;
     red[0] += v * v;
   }
@@ -447,7 +509,7 @@ std::unique_ptr<Workspace> make_workspace(Hier& h, int k, cudaStream_t s) {
       };
       if (prec == 0) alloc(ws->v64[l]); else alloc(ws->v32[l]);
     }
-    max_grid = std::max<int64_t>(max_grid, lv.plan.plan.nchunks + lv.plan.plan.short_blocks);
+    max_grid = std::max<int64_t>(max_grid, lv.plan.plan.max_grid());
     ws->scratch[l].op.make(lv.plan.plan, k, s, c);
     if (lv.kind == LG_LEVEL_AGG) ws->scratch[l].mem.make(lv.mem_plan.plan, k, s, c);
     if (lv.kind == LG_LEVEL_ELIM) ws->scratch[l].pt.make(lv.pt_plan.plan, k, s, c);
@@ -485,9 +547,8 @@ static void pcg_step(Hier& h, Workspace& ws, int first, cudaStream_t s) {
   LG_LAUNCH_CHECK();
   OpView<double> op = L0.op<double>();
   op.plan = ws.scratch[0].op.bind(op.plan);
-  launch_rows<double, 1>(n, op.rowptr, op.col, LapTerm<double>{op.w, ws.p.get()}, op.plan,
-                         EpiPq{ws.p.get(), ws.q.get(), scal}, s, ws.partials.get(), ws.tickets.get(),
-                         scal + kTmp);
+  op_pass<double, 1>(ws, 0, op, LapTerm<double>{op.w, ws.p.get(), op.d}, EpiPq{ws.p.get(), ws.q.get(), scal}, 1, s,
+                     ws.partials.get(), ws.tickets.get(), scal + kTmp);
   k_xr_update<<<vblocks(n), kVT, 0, s>>>(n, ws.x.get(), ws.r.get(), ws.ro.get(), ws.p.get(), ws.q.get(), scal,
                                         ws.partials.get(), ws.tickets.get());
   LG_LAUNCH_CHECK();
@@ -498,14 +559,14 @@ static void true_residual(Hier& h, Workspace& ws, cudaStream_t s) {
   OpView<double> op = L0.op<double>();
   op.plan = ws.scratch[0].op.bind(op.plan);
   double* scal = ws.scal.get();
-  launch_rows<double, 1>(L0.n, op.rowptr, op.col, LapTerm<double>{op.w, ws.x.get()}, op.plan,
-                         EpiTrueRes{ws.bm.get(), ws.r.get(), scal}, s, ws.partials.get(), ws.tickets.get(),
-                         scal + kTmp);
+  op_pass<double, 1>(ws, 0, op, LapTerm<double>{op.w, ws.x.get(), op.d}, EpiTrueRes{ws.bm.get(), ws.r.get(), scal}, 2,
+                     s, ws.partials.get(), ws.tickets.get(), scal + kTmp);
 }
 
 static void read_scal(Workspace& ws, cudaStream_t s) {
   LG_CUDA(cudaMemcpyAsync(ws.host_scal, ws.scal.get(), sizeof(double) * kNScal, cudaMemcpyDeviceToHost, s));
   LG_CUDA(cudaStreamSynchronize(s));
+  if (ws.prof.on) ws.prof.collect();
 }
 
 int pcg_solve(Hier& h, Workspace& ws, const double* b, double* x, double tol, int precision, cudaStream_t s,

@@ -29,6 +29,7 @@ struct OpView {
   const int32_t* col = nullptr;
   const T* w = nullptr;
   const T* dinv = nullptr;
+  const double* d = nullptr;  // FP64 row sums (used by the FP64 passes)
   RowPlan plan;
 };
 
@@ -37,7 +38,7 @@ struct Level {
   int64_t n = 0, nnz = 0, nc = 0;
   DBuf<int64_t> rowptr;
   DBuf<int32_t> col;
-  DBuf<double> w, dinv;
+  DBuf<double> w, d, dinv;
   DBuf<float> w32, dinv32;
   RowPlanStore plan;
   double lambda = 0.0;
@@ -59,10 +60,10 @@ struct Level {
 };
 
 template <> inline OpView<double> Level::op<double>() const {
-  return OpView<double>{n, nnz, rowptr.get(), col.get(), w.get(), dinv.get(), plan.plan};
+  return OpView<double>{n, nnz, rowptr.get(), col.get(), w.get(), dinv.get(), d.get(), plan.plan};
 }
 template <> inline OpView<float> Level::op<float>() const {
-  return OpView<float>{n, nnz, rowptr.get(), col.get(), w32.get(), dinv32.get(), plan.plan};
+  return OpView<float>{n, nnz, rowptr.get(), col.get(), w32.get(), dinv32.get(), d.get(), plan.plan};
 }
 
 // Chebyshev constants of one aggregation level (Section 3.6): the interval
@@ -102,6 +103,27 @@ struct LevelScratch {
 
 struct Hier;
 
+// Event timing of the operator passes (Laplacian row passes) of one
+// workspace, per level.
+struct Prof {
+  struct Stat {
+    double ms = 0.0, bytes = 0.0;
+    int64_t launches = 0;
+  };
+  struct Pending {
+    int level;
+    double bytes;
+  };
+  bool on = false;
+  std::vector<cudaEvent_t> ev;  // pairs
+  std::vector<Pending> pending;
+  std::vector<Stat> stats;      // indexed by level
+  void begin(cudaStream_t s);
+  void end(cudaStream_t s, int level, double bytes);
+  void collect();  // after the stream has been synchronised
+  ~Prof();
+};
+
 // Workspace of one concurrent solve: per-level cycle vectors in both
 // precisions, the FP64 Krylov vectors, reduction scratch and device scalars.
 struct Workspace {
@@ -115,6 +137,7 @@ struct Workspace {
   DBuf<double> scal;                   // device scalars of the PCG (see lg_cycle.cu)
   double* host_scal = nullptr;         // pinned mirror of the scalars read by the host
   int64_t bytes = 0;
+  Prof prof;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // captured preconditioned iteration per precision
   ~Workspace();
 };

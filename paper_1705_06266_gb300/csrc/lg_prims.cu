@@ -309,20 +309,23 @@ void accumulate_csr(DBuf<uint64_t>& keys, DBuf<uint64_t>& vals, int64_t nent, in
 // Row plan.
 // ---------------------------------------------------------------------------
 __global__ void k_plan_count(int64_t n, const int64_t* __restrict__ rowptr, int64_t thresh,
-                             int64_t* __restrict__ nch, uint8_t* __restrict__ islong) {
+                             int64_t* __restrict__ nch, uint8_t* __restrict__ islong, uint8_t* __restrict__ ismed) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t deg = rowptr[i + 1] - rowptr[i];
     const bool l = deg > thresh;
     islong[i] = l;
+    ismed[i] = !l && deg > kShortMax;
     nch[i] = l ? (deg + kChunk - 1) / kChunk : 0;
   }
 }
 
 __global__ void k_plan_fill(int64_t n, const int64_t* __restrict__ rowptr, const uint8_t* __restrict__ islong,
                             const int64_t* __restrict__ cstart, const int64_t* __restrict__ lidx,
+                            const uint8_t* __restrict__ ismed, const int64_t* __restrict__ midx, int32_t* med_rows,
                             int32_t* chunk_row, int64_t* chunk_beg, int32_t* chunk_lrow, int32_t* lrow_first,
                             int32_t* lrow_count) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (ismed[i]) med_rows[midx[i]] = (int32_t)i;
     if (!islong[i]) continue;
     const int64_t lr = lidx[i], c0 = cstart[i], cnt = cstart[i + 1] - cstart[i];
     lrow_first[lr] = (int32_t)c0;
@@ -335,33 +338,41 @@ __global__ void k_plan_fill(int64_t n, const int64_t* __restrict__ rowptr, const
   }
 }
 
-void build_row_plan(RowPlanStore& ps, int64_t n, int64_t nnz, const int64_t* rowptr, int G, cudaStream_t s,
+void set_plan_group(RowPlan& p, int64_t n, int elem_bytes, int G) {
+  const int64_t groups = (n + (kRowThreads / G) - 1) / (kRowThreads / G);
+  const int blocks = (int)(groups < (int64_t)kSMs * 8 ? (groups > 0 ? groups : 1) : (int64_t)kSMs * 8);
+  if (elem_bytes == 8) {
+    p.G64 = G;
+    p.short_blocks64 = blocks;
+  } else {
+    p.G32 = G;
+    p.short_blocks32 = blocks;
+  }
+}
+
+void build_row_plan(RowPlanStore& ps, int64_t n, int64_t nnz, const int64_t* rowptr, cudaStream_t s,
                     int64_t* counter) {
   RowPlan& p = ps.plan;
-  if (G == 0) {
-    const double avg = n > 0 ? (double)nnz / (double)n : 0.0;
-    G = avg <= 3.0 ? 2 : avg <= 6.0 ? 4 : avg <= 12.0 ? 8 : avg <= 24.0 ? 16 : 32;
-  }
-  p.G = G;
-  p.long_thresh = 16 * (int64_t)G > 64 ? 16 * (int64_t)G : 64;
-  const int64_t groups = (n + (kRowThreads / G) - 1) / (kRowThreads / G);
-  p.short_blocks = (int)(groups < (int64_t)kSMs * 8 ? (groups > 0 ? groups : 1) : (int64_t)kSMs * 8);
-
-  DBuf<int64_t> nch(n + 1, s), lidx(n + 1, s);
-  DBuf<uint8_t> islong(n, s);
+  p.long_thresh = kChunk;
+  DBuf<int64_t> nch(n + 1, s), lidx(n + 1, s), midx(n + 1, s);
+  DBuf<uint8_t> islong(n, s), ismed(n, s);
   const int g = grid_for(n, 256, kSMs * 16);
   if (n > 0) {
-    k_plan_count<<<g, 256, 0, s>>>(n, rowptr, p.long_thresh, nch.get(), islong.get());
+    k_plan_count<<<g, 256, 0, s>>>(n, rowptr, p.long_thresh, nch.get(), islong.get(), ismed.get());
     LG_LAUNCH_CHECK();
   }
   exclusive_scan(nch.get(), nch.get(), n, s);
   exclusive_scan_flags(islong.get(), lidx.get(), n, s);
-  int64_t tot[2];
+  exclusive_scan_flags(ismed.get(), midx.get(), n, s);
+  int64_t tot[3];
   LG_CUDA(cudaMemcpyAsync(&tot[0], nch.get() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   LG_CUDA(cudaMemcpyAsync(&tot[1], lidx.get() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  LG_CUDA(cudaMemcpyAsync(&tot[2], midx.get() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   LG_CUDA(cudaStreamSynchronize(s));
   p.nchunks = tot[0];
   p.nlong = tot[1];
+  p.nmed = tot[2];
+  ps.med_rows.alloc(p.nmed, s, counter);
   ps.chunk_row.alloc(p.nchunks, s, counter);
   ps.chunk_beg.alloc(p.nchunks, s, counter);
   ps.chunk_lrow.alloc(p.nchunks, s, counter);
@@ -370,12 +381,14 @@ void build_row_plan(RowPlanStore& ps, int64_t n, int64_t nnz, const int64_t* row
   ps.partial.alloc((size_t)(p.nchunks > 0 ? p.nchunks : 1) * kMaxCols, s, counter);
   ps.ticket.alloc(p.nlong > 0 ? p.nlong : 1, s, counter);
   LG_CUDA(cudaMemsetAsync(ps.ticket.get(), 0, sizeof(unsigned) * (p.nlong > 0 ? p.nlong : 1), s));
-  if (p.nlong > 0) {
-    k_plan_fill<<<g, 256, 0, s>>>(n, rowptr, islong.get(), nch.get(), lidx.get(), ps.chunk_row.get(),
-                                  ps.chunk_beg.get(), ps.chunk_lrow.get(), ps.lrow_first.get(),
-                                  ps.lrow_count.get());
+  if (p.nlong > 0 || p.nmed > 0) {
+    k_plan_fill<<<g, 256, 0, s>>>(n, rowptr, islong.get(), nch.get(), lidx.get(), ismed.get(), midx.get(),
+                                  ps.med_rows.get(), ps.chunk_row.get(), ps.chunk_beg.get(), ps.chunk_lrow.get(),
+                                  ps.lrow_first.get(), ps.lrow_count.get());
     LG_LAUNCH_CHECK();
   }
+  p.med_blocks = p.nmed > 0 ? grid_for(p.nmed * 32, kRowThreads, kSMs * 8) : 0;
+  p.med_rows = ps.med_rows.get();
   p.chunk_row = ps.chunk_row.get();
   p.chunk_beg = ps.chunk_beg.get();
   p.chunk_lrow = ps.chunk_lrow.get();
@@ -383,6 +396,10 @@ void build_row_plan(RowPlanStore& ps, int64_t n, int64_t nnz, const int64_t* row
   p.lrow_count = ps.lrow_count.get();
   p.partial = ps.partial.get();
   p.ticket = ps.ticket.get();
+  // heuristic group sizes from the average length of a row (the autotuner may revise them)
+  const double avg = n > 0 ? (double)nnz / (double)n : 0.0;
+  set_plan_group(p, n, 8, avg <= 3.0 ? 1 : avg <= 8.0 ? 2 : avg <= 20.0 ? 4 : 8);
+  set_plan_group(p, n, 4, avg <= 2.0 ? 1 : avg <= 5.0 ? 2 : avg <= 12.0 ? 4 : 8);
 }
 
 }  // namespace lg

@@ -7,6 +7,9 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "lg_hier.h"
 #include "lg_rows.cuh"
@@ -125,17 +128,25 @@ struct WeightTerm {
   const double* __restrict__ w;
   __device__ __forceinline__ double row(int64_t) const { return 0.0; }
   __device__ __forceinline__ double operator()(int64_t k, int32_t, double) const { return w[k]; }
+  __device__ __forceinline__ double finish(double, double s) const { return s; }
 };
 struct EpiDinv {
+  double* d;
   double* dinv;
-  __device__ __forceinline__ void operator()(int64_t i, double s, double*) const { dinv[i] = s > 0.0 ? 1.0 / s : 0.0; }
+  __device__ __forceinline__ NoPre pre(int64_t) const { return NoPre{}; }
+  __device__ __forceinline__ void operator()(int64_t i, double s, NoPre, double*) const {
+    d[i] = s;
+    dinv[i] = s > 0.0 ? 1.0 / s : 0.0;
+  }
   __device__ void finish(const double*) const {}
 };
 
-// y = L x, difference form.
+// y = L x.
+template <typename T>
 struct EpiStore {
-  double* y;
-  __device__ __forceinline__ void operator()(int64_t i, double s, double*) const { y[i] = s; }
+  T* y;
+  __device__ __forceinline__ NoPre pre(int64_t) const { return NoPre{}; }
+  __device__ __forceinline__ void operator()(int64_t i, T s, NoPre, double*) const { y[i] = s; }
   __device__ void finish(const double*) const {}
 };
 
@@ -558,10 +569,14 @@ struct EpiLanczos {
   double* u;
   Lanczos* lz;
   int k;
-  __device__ __forceinline__ void operator()(int64_t i, double s, double* red) const {
-    const double ui = sdinv[i] * s;
+  struct Pre {
+    double sd, v;
+  };
+  __device__ __forceinline__ Pre pre(int64_t i) const { return Pre{sdinv[i], v[i]}; }
+  __device__ __forceinline__ void operator()(int64_t i, double s, const Pre& p, double* red) const {
+    const double ui = p.sd * s;
     u[i] = ui;
-    red[0] += v[i] * ui;
+    red[0] += p.v * ui;
   }
   __device__ void finish(const double* tot) const { lz->alpha[k] = tot[0]; }
 };
@@ -703,18 +718,21 @@ static int64_t read_i64(const int64_t* p, cudaStream_t s) {
 
 // Row plan and 1/diag of a level's operator.
 static void prepare_operator(Level& L, cudaStream_t s, int64_t* counter) {
-  build_row_plan(L.plan, L.n, L.nnz, L.rowptr.get(), 0, s, counter);
+  build_row_plan(L.plan, L.n, L.nnz, L.rowptr.get(), s, counter);
+  L.d.alloc(L.n, s, counter);
   L.dinv.alloc(L.n, s, counter);
   launch_rows<double, 0>(L.n, L.rowptr.get(), L.col.get(), WeightTerm{L.w.get()}, L.plan.plan,
-                         EpiDinv{L.dinv.get()}, s);
+                         EpiDinv{L.d.get(), L.dinv.get()}, s);
 }
 
 void run_laplacian_apply(int64_t n, const int64_t* rowptr, const int32_t* col, const double* w, const double* x,
                          double* y, cudaStream_t s) {
   RowPlanStore ps;
   const int64_t nnz = read_i64(rowptr + n, s);
-  build_row_plan(ps, n, nnz, rowptr, 0, s, nullptr);
-  launch_rows<double, 0>(n, rowptr, col, LapTerm<double>{w, x}, ps.plan, EpiStore{y}, s);
+  build_row_plan(ps, n, nnz, rowptr, s, nullptr);
+  DBuf<double> d(n, s), dinv(n, s);
+  launch_rows<double, 0>(n, rowptr, col, WeightTerm{w}, ps.plan, EpiDinv{d.get(), dinv.get()}, s);
+  launch_rows<double, 0>(n, rowptr, col, LapTerm<double>{w, x, d.get()}, ps.plan, EpiStore<double>{y}, s);
   LG_CUDA(cudaStreamSynchronize(s));
 }
 
@@ -735,9 +753,9 @@ void run_strength(int64_t n, const int64_t* rowptr, const int32_t* col, const do
   if (m < 1 || m > kMaxVecs) fail(LG_ERR_INVALID, "strength_vecs must be 1..8");
   RowPlanStore ps;
   const int64_t nnz = read_i64(rowptr + n, s);
-  build_row_plan(ps, n, nnz, rowptr, 0, s, nullptr);
-  DBuf<double> dinv(n, s), xa((size_t)n * m, s), xb((size_t)n * m, s), rowmax(n, s);
-  launch_rows<double, 0>(n, rowptr, col, WeightTerm{w}, ps.plan, EpiDinv{dinv.get()}, s);
+  build_row_plan(ps, n, nnz, rowptr, s, nullptr);
+  DBuf<double> d(n, s), dinv(n, s), xa((size_t)n * m, s), xb((size_t)n * m, s), rowmax(n, s);
+  launch_rows<double, 0>(n, rowptr, col, WeightTerm{w}, ps.plan, EpiDinv{d.get(), dinv.get()}, s);
   k_strength_init<<<blocks_for(n), kNT, 0, s>>>(n, m, seed, level, xa.get());
   LG_LAUNCH_CHECK();
   double* x = xa.get();
@@ -839,7 +857,7 @@ static std::unique_ptr<Level> eliminate(Level& L, const uint8_t* is_f, int64_t n
     k_pt_fill<<<blocks_for(npt), kNT, 0, s>>>(npt, vals.get(), L.rowptr.get(), L.w.get(), L.pt_f.get(),
                                              L.pt_coef.get());
     LG_LAUNCH_CHECK();
-    build_row_plan(L.pt_plan, nc, npt, L.pt_ptr.get(), 0, s, counter);
+    build_row_plan(L.pt_plan, nc, npt, L.pt_ptr.get(), s, counter);
   }
   return C;
 }
@@ -859,7 +877,7 @@ static std::unique_ptr<Level> galerkin(Level& L, cudaStream_t s, int64_t* counte
     LG_LAUNCH_CHECK();
     k_rowptr_sorted<<<blocks_for(nc + 1), kNT, 0, s>>>(keys.get(), n, 0, nc, L.mem_ptr.get());
     LG_LAUNCH_CHECK();
-    build_row_plan(L.mem_plan, nc, n, L.mem_ptr.get(), 0, s, counter);
+    build_row_plan(L.mem_plan, nc, n, L.mem_ptr.get(), s, counter);
   }
   DBuf<int64_t> cnt(n + 1, s);
   k_gal_count<<<warp_blocks(n), kNT, 0, s>>>(n, L.rowptr.get(), L.col.get(), L.agg.get(), cnt.get());
@@ -887,7 +905,7 @@ static void lanczos(Level& L, const lg_options& o, int level, double* lam_dev, c
   const int iters = std::min(o.eig_iters, 64);
   DBuf<double> v(n, s), vp(n, s), u(n, s), t(n, s), sdinv(n, s);
   const int nb = blocks_for(n);
-  const int nbr = (int)(L.plan.plan.nchunks + L.plan.plan.short_blocks);
+  const int nbr = L.plan.plan.max_grid();
   DBuf<double> partials((size_t)std::max(nb, nbr), s);
   DBuf<unsigned> ticket(1, s);
   DBuf<Lanczos> lz(1, s);
@@ -900,7 +918,7 @@ static void lanczos(Level& L, const lg_options& o, int level, double* lam_dev, c
   LG_LAUNCH_CHECK();
   for (int k = 0; k < iters; ++k) {
     // stopped iterations leave alpha[k] untouched; only the first m entries are used
-    launch_rows<double, 1>(n, L.rowptr.get(), L.col.get(), LapTerm<double>{L.w.get(), t.get()}, L.plan.plan,
+    launch_rows<double, 1>(n, L.rowptr.get(), L.col.get(), LapTerm<double>{L.w.get(), t.get(), L.d.get()}, L.plan.plan,
                            EpiLanczos{sdinv.get(), v.get(), u.get(), lz.get(), k}, s, partials.get(),
                            ticket.get(), tot.get());
     k_lz_orth<<<nb, kNT, 0, s>>>(n, k, lz.get(), u.get(), v.get(), vp.get(), partials.get(), ticket.get());
@@ -922,9 +940,10 @@ static void coarsest_pinv(Level& L, int* err, cudaStream_t s, int64_t* counter) 
   const int gb = blocks_for(n * n);
   for (int64_t k = 0; k < n; ++k) {
     k_gj_copy<<<blocks_for(n), kNT, 0, s>>>(n, k, L.pinv.get(), prow.get(), pcol.get());
+    LG_LAUNCH_CHECK();
     k_gj_update<<<gb, kNT, 0, s>>>(n, k, L.pinv.get(), prow.get(), pcol.get(), err);
+    LG_LAUNCH_CHECK();
   }
-  LG_LAUNCH_CHECK();
   k_unshift<<<gb, kNT, 0, s>>>(n, L.pinv.get());
   LG_LAUNCH_CHECK();
 }
@@ -946,6 +965,63 @@ static void make_f32(Level& L, cudaStream_t s, int64_t* counter) {
                                                                     L.pt_coef32.get());
     LG_LAUNCH_CHECK();
   }
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner of the short-row lane-group size: each candidate G is timed on
+// the level's own operator (plain y = L x, 1 warm-up + 3 timed launches) and
+// the fastest kept. Choices are cached per (n, nnz, precision) for the life
+// of the process, so rebuilding a hierarchy of the same graph gives the same
+// launch plans and bitwise the same results.
+// ---------------------------------------------------------------------------
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int64_t, int64_t, int>, int> g_tune_cache;
+
+template <typename T>
+static float time_apply(const Level& L, int G, const T* x, T* y, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
+  OpView<T> op = L.op<T>();
+  set_plan_group(op.plan, L.n, (int)sizeof(T), G);
+  const LapTerm<T> term{op.w, x, op.d};
+  launch_rows<T, 0>(op.n, op.rowptr, op.col, term, op.plan, EpiStore<T>{y}, s);
+  LG_CUDA(cudaEventRecord(e0, s));
+  for (int r = 0; r < 3; ++r) launch_rows<T, 0>(op.n, op.rowptr, op.col, term, op.plan, EpiStore<T>{y}, s);
+  LG_CUDA(cudaEventRecord(e1, s));
+  LG_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  LG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  return ms;
+}
+
+template <typename T>
+static void tune_level(Level& L, cudaStream_t s) {
+  const auto key = std::make_tuple(L.n, L.nnz, (int)sizeof(T));
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      set_plan_group(L.plan.plan, L.n, (int)sizeof(T), it->second);
+      return;
+    }
+  }
+  DBuf<T> x(L.n, s), y(L.n, s);
+  LG_CUDA(cudaMemsetAsync(x.get(), 0, sizeof(T) * L.n, s));
+  cudaEvent_t e0, e1;
+  LG_CUDA(cudaEventCreate(&e0));
+  LG_CUDA(cudaEventCreate(&e1));
+  int best = 0;
+  float best_ms = 0.f;
+  for (int G : {1, 2, 4, 8}) {
+    const float ms = time_apply<T>(L, G, x.get(), y.get(), s, e0, e1);
+    if (best == 0 || ms < best_ms) {
+      best = G;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  set_plan_group(L.plan.plan, L.n, (int)sizeof(T), best);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache.emplace(key, best);
 }
 
 void setup_hierarchy(Hier& h, int64_t n, const int64_t* rowptr, const int32_t* col, const double* w) {
@@ -1047,6 +1123,13 @@ void setup_hierarchy(Hier& h, int64_t n, const int64_t* rowptr, const int32_t* c
   h.levels.push_back(std::move(cur));
   for (auto& L : h.levels) make_f32(*L, s, counter);
   if (read_err(h.dev_err, s)) fail(LG_ERR_SETUP, "coarsest pseudo-inverse failed");
+  if (o.autotune) {
+    for (auto& L : h.levels) {
+      if (L->nnz < 20000) continue;
+      tune_level<double>(*L, s);
+      tune_level<float>(*L, s);
+    }
+  }
 
   // ---- Chebyshev constants from the eigenvalue estimates ----
   std::vector<double> lam(h.levels.size() + 1, 0.0);

@@ -35,7 +35,7 @@ class Options(C.Structure):
         ("vote_threshold", C.c_int32), ("strength_vecs", C.c_int32), ("strength_sweeps", C.c_int32),
         ("cheb_degree", C.c_int32), ("eig_iters", C.c_int32), ("max_coarse_n", C.c_int32),
         ("residual_replace", C.c_int32), ("memory_space", C.c_int32), ("use_graphs", C.c_int32),
-        ("reserved", C.c_int32),
+        ("autotune", C.c_int32),
     ]
 
 
@@ -48,6 +48,10 @@ class Info(C.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class KernelProfile(C.Structure):
+    _fields_ = [("total_ms", C.c_double), ("bytes", C.c_double), ("launches", C.c_int64), ("reserved", C.c_int64)]
 
 
 class ServeOptions(C.Structure):
@@ -85,6 +89,9 @@ _SIGS = {
     "lg_elim_select": (C.c_int, [_I64, _P, _P, _I32, _U64, _P, _P, _P]),
     "lg_strength": (C.c_int, [_I64, _P, _P, _P, _U64, _I32, _I32, _I32, _D, _P, _P]),
     "lg_aggregate": (C.c_int, [_I64, _P, _P, _P, _I32, _I32, _P, _P, _P, _P, _P]),
+    "lg_kernel_launches": (C.c_uint64, []),
+    "lg_profile": (C.c_int, [_P, _I32]),
+    "lg_profile_read": (C.c_int, [_P, _I32, _P]),
     "lg_serve_options_default": (C.c_int, [_P]),
     "lg_serve_create": (C.c_int, [_P, _P]),
     "lg_serve_register": (C.c_int, [_P, _P]),
@@ -219,6 +226,20 @@ def lg_coarsest_pinv(h, nc: int) -> np.ndarray:
 
 def lg_vcycle(h, f, x, precision: int = FP64):
     _check(_load().lg_vcycle(h, _ptr(f), _ptr(x), int(precision)), "lg_vcycle")
+
+
+def lg_kernel_launches() -> int:
+    return int(_load().lg_kernel_launches())
+
+
+def lg_profile(h, enable: bool):
+    _check(_load().lg_profile(h, 1 if enable else 0), "lg_profile")
+
+
+def lg_profile_read(h, level: int = -1) -> KernelProfile:
+    p = KernelProfile()
+    _check(_load().lg_profile_read(h, int(level), C.byref(p)), "lg_profile_read")
+    return p
 
 
 def _stream(stream):
