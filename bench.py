@@ -248,29 +248,32 @@ def main():
         x32 = torch.zeros(g.n, dtype=torch.float64, device=dev)
         opts = lg.options(stream=stream.cuda_stream)
 
+        def per_level(h, nlev):
+            out = []
+            for l in range(nlev):
+                p = lg.lg_profile_read(h, l)
+                out.append((p.total_ms, p.bytes, p.launches))
+            return out
+
         def step(profile):
             flush.fill_(1.0)
             h = lg.lg_setup(g.n, rp, cl, w, opts)
             hi = lg.lg_hier_info(h)
-            if profile:
-                lg.lg_profile(h, True)
-            flush.fill_(2.0)
-            lg.lg_set_precision(h, lg.FP64)
-            i64 = lg.lg_solve(h, bd, x64, TOL)
-            prof = None
-            if profile:
-                levels = []
-                for l in range(hi.levels):
-                    p = lg.lg_profile_read(h, l)
-                    levels.append((p.total_ms, p.bytes, p.launches))
-                prof = levels
-                lg.lg_profile(h, False)
-            flush.fill_(3.0)
-            lg.lg_set_precision(h, lg.FP32_HIER)
-            i32 = lg.lg_solve(h, bd, x32, TOL)
+            res = {}
+            for tag, prec, x in (("fp64", lg.FP64, x64), ("fp32", lg.FP32_HIER, x32)):
+                lg.lg_set_precision(h, prec)
+                flush.fill_(2.0)
+                res[tag] = lg.lg_solve(h, bd, x, TOL)  # graph-driven, unprofiled: the timed solve
+                if profile:  # the same solve again with every operator pass bracketed by events
+                    lg.lg_profile(h, True)
+                    flush.fill_(3.0)
+                    lg.lg_solve(h, bd, x, TOL)
+                    res[tag + "_prof"] = per_level(h, hi.levels)
+                    lg.lg_profile(h, False)
             nb = lg.lg_hier_bytes(h)
+            lv = [dict(lg.lg_level_info(h, l), **lg.lg_level_plan(h, l)) for l in range(hi.levels)]
             lg.lg_destroy(h)
-            return hi, i64, i32, prof, nb
+            return hi, res["fp64"], res["fp32"], res.get("fp64_prof"), nb, res.get("fp32_prof"), lv
 
         for _ in range(args.warmup):
             step(False)
@@ -336,6 +339,18 @@ def main():
     all_ms = sum(t[0] for t in tot)
     all_bytes = sum(t[1] for t in tot)
     i64, i32 = recs[-1][1], recs[-1][2]
+    # per-level operator-pass table, both precisions (ms per solve, GB/s)
+    levels = []
+    for l in range(nlev):
+        row = dict(recs[-1][6][l])
+        for tag, idx in (("fp64", 3), ("fp32", 5)):
+            ms = sum(r[idx][l][0] for r in recs) / len(recs)
+            by = sum(r[idx][l][1] for r in recs) / len(recs)
+            la = sum(r[idx][l][2] for r in recs) / len(recs)
+            row[f"{tag}_ms_per_solve"] = ms
+            row[f"{tag}_launches_per_solve"] = la
+            row[f"{tag}_gbs"] = by / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+        levels.append(row)
 
     if rank != 0:
         return
@@ -345,6 +360,9 @@ def main():
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "graph": g.name, "n": g.n, "nnz": nnz, "rhs": 1, "tol": TOL,
                    "precision": "fp64 (FP32-hierarchy solve reported in fp32_hier)",
+                   "step": "setup; FP64 solve; FP64 solve with per-pass events; FP32-hier solve; "
+                           "FP32-hier solve with per-pass events (value and fp32_hier from the solves "
+                           "without events)",
                    "l2": "flushed (512 MiB write) before setup and before each solve",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "solve_ms": solve64_ms, "setup_ms": setup_ms,
@@ -368,6 +386,7 @@ def main():
                      "bytes_per_launch": d_bytes / max(d_launch, 1), "peak_kind": peak_kind,
                      "share_of_solve": d_ms / (solve64_ms * len(recs)),
                      "all_levels_achieved": all_bytes / (all_ms * 1e-3) / 1e9 if all_ms > 0 else 0.0},
+        "levels": levels,
         "clocks": clk,
         "gpu_launches": launches,
         "wall_s_timed": wall,

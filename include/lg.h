@@ -93,9 +93,15 @@ typedef struct {
   int32_t residual_replace; /* 50: PCG recomputes r = b - L x every this many iterations */
   int32_t memory_space;     /* LG_AUTO: detect; LG_HOST / LG_DEVICE force the interpretation */
   int32_t use_graphs;       /* 1: replay the preconditioned iteration as a captured CUDA graph */
-  int32_t autotune;         /* 1: time the SpMV lane-group sizes of each large level at setup and keep
+  int32_t autotune;         /* 1: time the row-binning choices of each large level at setup and keep
                                the fastest (cached per level shape for the life of the process);
-                               0: a fixed rule on the average row length */
+                               0: a fixed rule */
+  int32_t reorder;          /* 1: renumber the vertices by descending degree before the setup (ties
+                               by id), so the gathered values of high-degree vertices share cache
+                               lines; solves take and return vectors in the caller's numbering.
+                               0: keep the caller's numbering (the paper's random ordering, Section
+                               3.3, serves a 2D distribution this library does not use) */
+  int32_t reserved;
 } lg_options;
 
 /* Result of a setup or a solve. */
@@ -187,6 +193,10 @@ int lg_level_info(lg_handle h, int32_t l, int32_t* kind, int64_t* n, int64_t* nn
  */
 int lg_level_copy(lg_handle h, int32_t l, int64_t* rowptr, int32_t* col, double* w, int32_t* map);
 
+/* Vertex numbering of level 0: perm[i] = the caller's id of level-0 vertex i
+ * (the identity unless the options asked for reordering). HOST array of n. */
+int lg_permutation(lg_handle h, int32_t* perm);
+
 /* Copy the coarsest level's dense FP64 pseudo-inverse (n_c x n_c, row-major) to host memory. */
 int lg_coarsest_pinv(lg_handle h, double* out);
 
@@ -219,6 +229,13 @@ typedef struct {
 } lg_kernel_profile;
 
 int lg_profile(lg_handle h, int32_t enable);
+
+/* Launch plan of level l's operator passes: out[0] = entries per lane E of
+ * the row binning (a row of class c, E 2^(c-1) < deg <= E 2^c, is served by
+ * 2^c lanes), out[1] = rows served by groups of 1..16 lanes, out[2] = rows
+ * served by a whole warp, out[3] = rows cut into chunks, out[4] = chunks,
+ * out[5] = blocks of one pass. */
+int lg_level_plan(lg_handle h, int32_t l, int64_t out[6]);
 int lg_profile_read(lg_handle h, int32_t level, lg_kernel_profile* out);
 
 /* ---- single steps on caller data (DEVICE pointers only, on `stream`) ----

@@ -1,6 +1,8 @@
 // extern "C" entry points of include/lg.h: argument checks, pointer-space
 // detection, handle lifecycle, and the mapping of library errors to status
 // codes. No entry point lets an exception or a CUDA error escape.
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -11,11 +13,33 @@ namespace lg {
 
 thread_local std::string g_last_error;
 std::atomic<uint64_t> g_launches{0};
+static thread_local char g_launch_msg[256];
+
+bool debug_sync() {
+  static const bool on = [] {
+    const char* v = std::getenv("LG_DEBUG_SYNC");
+    return v && v[0] == '1';
+  }();
+  return on;
+}
+
+void check_launch(const char* file, int line) {
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && debug_sync()) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) return;
+  const char* base = std::strrchr(file, '/');
+  std::snprintf(g_launch_msg, sizeof(g_launch_msg), "kernel at %s:%d: %s", base ? base + 1 : file, line,
+                cudaGetErrorName(e));
+  fail(e == cudaErrorMemoryAllocation ? LG_ERR_NOMEM : LG_ERR_CUDA, g_launch_msg);
+}
 
 Hier::~Hier() {
+  // every stream-ordered buffer goes back on the handle's stream before that
+  // stream is destroyed
   ws.reset();
   levels.clear();
   dev_err.release();
+  perm.release();
   if (stream) cudaStreamSynchronize(stream);
   if (own_stream && stream) cudaStreamDestroy(stream);
 }
@@ -36,7 +60,7 @@ static int handle_error(const Error& e) {
   cudaError_t ce = cudaGetLastError();
   if (ce != cudaSuccess) {
     g_last_error += ": ";
-    g_last_error += cudaGetErrorString(ce);
+    g_last_error += cudaGetErrorName(ce);
   }
   return e.code;
 }
@@ -89,6 +113,7 @@ int lg_options_default(lg_options* o) {
   o->memory_space = LG_AUTO;
   o->use_graphs = 1;
   o->autotune = 1;
+  o->reorder = 1;
   return LG_OK;
 }
 
@@ -253,6 +278,17 @@ int lg_level_copy(lg_handle hh, int32_t l, int64_t* rowptr, int32_t* col, double
   LG_API_END
 }
 
+int lg_permutation(lg_handle hh, int32_t* perm) {
+  if (!hh || !perm) return LG_ERR_INVALID;
+  LG_API_BEGIN
+  lg::Hier& h = *H(hh);
+  const int64_t n = h.levels[0]->n;
+  LG_CUDA(cudaMemcpyAsync(perm, h.perm.get(), sizeof(int32_t) * n, cudaMemcpyDefault, h.stream));
+  LG_CUDA(cudaStreamSynchronize(h.stream));
+  return LG_OK;
+  LG_API_END
+}
+
 int lg_coarsest_pinv(lg_handle hh, double* out) {
   if (!hh || !out) return LG_ERR_INVALID;
   LG_API_BEGIN
@@ -304,6 +340,20 @@ int lg_profile(lg_handle hh, int32_t enable) {
   h.ws->prof.on = enable != 0;
   return LG_OK;
   LG_API_END
+}
+
+int lg_level_plan(lg_handle hh, int32_t l, int64_t out[6]) {
+  if (!hh || !out) return LG_ERR_INVALID;
+  lg::Hier& h = *H(hh);
+  if (l < 0 || l >= (int32_t)h.levels.size()) return LG_ERR_INVALID;
+  const lg::RowPlan& p = h.levels[l]->plan.plan;
+  out[0] = p.E;
+  out[1] = p.cls_off[lg::kClasses - 1] - p.cls_off[0];  // rows served by groups of 1..16 lanes
+  out[2] = p.cls_off[lg::kClasses] - p.cls_off[lg::kClasses - 1];  // rows served by a warp
+  out[3] = p.nlong;
+  out[4] = p.nchunks;
+  out[5] = p.grid();
+  return LG_OK;
 }
 
 int lg_profile_read(lg_handle hh, int32_t level, lg_kernel_profile* out) {

@@ -31,22 +31,29 @@ struct Error {
 
 inline void check_cuda(cudaError_t e, const char* what) {
   if (e == cudaSuccess) return;
+  static thread_local char msg[256];
+  std::snprintf(msg, sizeof(msg), "%s: %s", what, cudaGetErrorName(e));
   if (e == cudaErrorMemoryAllocation) {
     cudaGetLastError();
-    fail(LG_ERR_NOMEM, what);
+    fail(LG_ERR_NOMEM, msg);
   }
-  fail(LG_ERR_CUDA, what);
+  fail(LG_ERR_CUDA, msg);
 }
 
 #define LG_CUDA(call) ::lg::check_cuda((call), #call)
 
-// Every kernel launch site is followed by LG_LAUNCH_CHECK(), which also
-// counts the launch.
+// Every kernel launch site is followed by LG_LAUNCH_CHECK(), which counts the
+// launch and turns a launch error into an Error naming the site and the CUDA
+// error. With LG_DEBUG_SYNC=1 in the environment it also waits for the
+// kernel, so an asynchronous fault is reported at the kernel that caused it
+// (and solves run without graph capture).
 extern std::atomic<uint64_t> g_launches;
+bool debug_sync();
+void check_launch(const char* file, int line);
 #define LG_LAUNCH_CHECK()                                           \
   do {                                                              \
     ::lg::g_launches.fetch_add(1, std::memory_order_relaxed);      \
-    ::lg::check_cuda(cudaGetLastError(), "kernel launch");          \
+    ::lg::check_launch(__FILE__, __LINE__);                         \
   } while (0)
 
 // ---------------------------------------------------------------------------
@@ -84,7 +91,8 @@ class DBuf {
   }
   void release() {
     if (p_) {
-      cudaFreeAsync(p_, s_);
+      // a failed free must not leave its error behind for an unrelated later check
+      if (cudaFreeAsync(p_, s_) != cudaSuccess) cudaGetLastError();
       if (counter_) *counter_ -= (int64_t)((n_ ? n_ : 1) * sizeof(T));
     }
     p_ = nullptr;
@@ -169,6 +177,19 @@ __device__ __forceinline__ T group_sum(T v, unsigned mask) {
   return v;
 }
 
+// Sum into the group's first lane only: at each step just the lanes that
+// still hold partial sums add (G - 1 additions in all instead of G log2 G),
+// which matters for FP64, whose pipe is narrow on this part.
+template <int G, typename T>
+__device__ __forceinline__ T group_sum_first(T v, unsigned mask, int lane) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+    const T t = __shfl_down_sync(mask, v, o, G);
+    if (lane < o) v += t;
+  }
+  return v;
+}
+
 template <int G, typename T>
 __device__ __forceinline__ T group_max(T v, unsigned mask) {
 #pragma unroll
@@ -212,13 +233,15 @@ __device__ __forceinline__ void block_sum(double (&v)[K], double* smem /* K * (N
 
 // Grid-wide sum of K values in one launch: blocks store partials, the last
 // block to arrive (ticket counter) adds them in block order and writes
-// out[0..K-1]. Deterministic for a fixed grid size. Every thread of every
-// block must call it. `ticket` must be 0 on entry and is 0 again on exit.
-// Returns true in exactly one thread (thread 0 of the last block), after
-// out[] is written, so that it can derive scalars from the totals.
+// out[0..K-1]. Deterministic for a fixed grid size. Meant for the vector
+// kernels (grids of at most a few thousand blocks of uniform work); the
+// row passes write their results and leave dot products to those kernels.
+// Every thread of every block must call it; `partials` holds K values per
+// block; `ticket` must be 0 on entry and is 0 again on exit. Returns true in
+// exactly one thread (thread 0 of the last block), after out[] is written,
+// so that it can derive scalars from the totals.
 template <int NT, int K>
-__device__ __forceinline__ bool grid_sum(double (&v)[K], double* partials /* gridDim.x * K */,
-                                         unsigned* ticket, double* out) {
+__device__ __forceinline__ bool grid_sum(double (&v)[K], double* partials, unsigned* ticket, double* out) {
   __shared__ double red_smem[K * (NT / 32)];
   __shared__ bool am_last;
   block_sum<NT, K>(v, red_smem);
@@ -248,24 +271,23 @@ __device__ __forceinline__ bool grid_sum(double (&v)[K], double* partials /* gri
 }
 
 // ---------------------------------------------------------------------------
-// SpMV row plan of one CSR operator (see lg_rows.cuh). Rows with at most
-// kShortMax entries go to groups of G lanes (G64 / G32 for FP64 / FP32
-// passes); rows up to long_thresh entries to one warp each (med_rows list);
-// longer rows are cut into chunks of kChunk entries, one block per chunk;
-// the last block of a row (per-row ticket) adds the chunk partials in chunk
-// order and applies the epilogue.
+// SpMV row plan of one CSR operator (see lg_rows.cuh). Rows are binned by
+// length into classes c = 0..5 served by groups of G = 2^c lanes: class c
+// holds the rows with E 2^(c-1) < deg <= E 2^c (class 0: deg <= E, class 5:
+// up to kChunk entries), E the entries per lane, so every group of a warp
+// does about the same work. Rows longer than kChunk are cut into chunks of
+// kChunk entries, one block per chunk; the last block of a row (per-row
+// ticket) adds the chunk partials in chunk order and applies the epilogue.
 // ---------------------------------------------------------------------------
 constexpr int kRowThreads = 256;
 constexpr int kChunk = 2048;
-constexpr int64_t kShortMax = 32;
+constexpr int kClasses = 6;
 
 struct RowPlan {
-  int G64 = 4, G32 = 4;
-  int short_blocks64 = 1, short_blocks32 = 1;
-  int med_blocks = 0;
-  int64_t long_thresh = kChunk;
-  int64_t nmed = 0;
-  int32_t* med_rows = nullptr;    // rows with kShortMax < deg <= long_thresh
+  int E = 4;                          // entries per lane (class boundaries)
+  int64_t cls_off[kClasses + 1] = {};  // class c rows: rows_by_class[cls_off[c] .. cls_off[c+1])
+  int blk_off[kClasses + 1] = {};      // class c blocks: [nchunks + blk_off[c], nchunks + blk_off[c+1])
+  const int32_t* rows_by_class = nullptr;
   int64_t nlong = 0;
   int64_t nchunks = 0;
   int32_t* chunk_row = nullptr;   // row of each chunk
@@ -276,10 +298,7 @@ struct RowPlan {
   double* partial = nullptr;      // nchunks * kMaxCols partial sums
   unsigned* ticket = nullptr;     // nlong tickets, zero between launches
 
-  int grid(int elem_bytes) const {
-    return (int)(nchunks + med_blocks + (elem_bytes == 8 ? short_blocks64 : short_blocks32));
-  }
-  int max_grid() const { return (int)(nchunks + med_blocks + (short_blocks64 > short_blocks32 ? short_blocks64 : short_blocks32)); }
+  int grid() const { return (int)nchunks + blk_off[kClasses]; }
 };
 
 constexpr int kMaxCols = 32;  // widest multi-RHS block

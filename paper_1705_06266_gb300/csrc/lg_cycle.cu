@@ -145,10 +145,11 @@ static int cheb_streams(const EpiCheb<T>& e) {
 // A row pass over level `level`'s operator, timed when the workspace profiles.
 template <typename T, int NRED, class Term, class Epi>
 static void op_pass(Workspace& ws, int level, const OpView<T>& op, const Term& term, const Epi& epi, int streams,
-                    cudaStream_t s, double* rp = nullptr, unsigned* rt = nullptr, double* ro = nullptr) {
-  const bool timed = ws.prof.on;
+                    cudaStream_t s, double* rp = nullptr, unsigned* rt = nullptr, double* ro = nullptr,
+                    const double* gate = nullptr) {
+  const bool timed = ws.prof.on && gate == nullptr;  // a gated pass may do nothing: not timed
   if (timed) ws.prof.begin(s);
-  launch_rows<T, NRED>(op.n, op.rowptr, op.col, term, op.plan, epi, s, rp, rt, ro);
+  launch_rows<T, NRED>(op.n, op.rowptr, op.col, term, op.plan, epi, s, rp, rt, ro, gate);
   if (timed) ws.prof.end(s, level, pass_bytes(op.n, op.nnz, (int)sizeof(T), streams));
 }
 
@@ -326,15 +327,29 @@ static void cycle_from(Hier& h, Workspace& ws, const double* r0, cudaStream_t s)
   cycle_level<T>(h, ws, 0, s);
 }
 
+__global__ void k_gather_perm(int64_t n, const int32_t* __restrict__ perm, const double* __restrict__ src,
+                              double* __restrict__ dst) {
+  LG_GRID_STRIDE(i, n) dst[i] = src[perm[i]];
+}
+
+__global__ void k_scatter_perm(int64_t n, const int32_t* __restrict__ perm, const double* __restrict__ src,
+                               double* __restrict__ dst) {
+  LG_GRID_STRIDE(i, n) dst[perm[i]] = src[i];
+}
+
 void vcycle_apply(Hier& h, Workspace& ws, const double* f, double* x, int precision, cudaStream_t s) {
   const int64_t n = h.levels[0]->n;
+  k_gather_perm<<<vblocks(n), kVT, 0, s>>>(n, h.perm.get(), f, ws.z.get());
+  LG_LAUNCH_CHECK();
   if (precision == LG_FP32_HIER) {
-    cycle_from<float>(h, ws, f, s);
-    k_cycle_out<float><<<vblocks(n), kVT, 0, s>>>(n, ws.v32[0].x.get(), x);
+    cycle_from<float>(h, ws, ws.z.get(), s);
+    k_cycle_out<float><<<vblocks(n), kVT, 0, s>>>(n, ws.v32[0].x.get(), ws.io.get());
   } else {
-    cycle_from<double>(h, ws, f, s);
-    k_cycle_out<double><<<vblocks(n), kVT, 0, s>>>(n, ws.v64[0].x.get(), x);
+    cycle_from<double>(h, ws, ws.z.get(), s);
+    k_cycle_out<double><<<vblocks(n), kVT, 0, s>>>(n, ws.v64[0].x.get(), ws.io.get());
   }
+  LG_LAUNCH_CHECK();
+  k_scatter_perm<<<vblocks(n), kVT, 0, s>>>(n, h.perm.get(), ws.io.get(), x);
   LG_LAUNCH_CHECK();
 }
 
@@ -354,7 +369,13 @@ enum Scal : int {
   kBreak = 8,  // 1 after a breakdown
   kZ0 = 9,     // 5 sums of the z reduction (9..13)
   kTmp = 14,   // 2 scratch totals (14..15)
-  kNScal = 16
+  kIter = 16,  // iterations done
+  kDone = 17,  // 1 once the true residual met the tolerance
+  kTol2BB = 18,  // tol^2 ||b_m||^2
+  kMaxit = 19,
+  kEvery = 20,   // true-residual replacement period
+  kNeedTrue = 21,  // 1 when this iteration recomputes the true residual
+  kNScal = 24
 };
 
 __global__ void k_sum1(int64_t n, const double* __restrict__ v, double* partials, unsigned* ticket, double* out) {
@@ -363,13 +384,15 @@ __global__ void k_sum1(int64_t n, const double* __restrict__ v, double* partials
   grid_sum<kVT, 1>(acc, partials, ticket, out);
 }
 
-// b_m = b - mean(b); x = 0; r = b_m; ||b_m||^2.
-__global__ void k_pcg_init(int64_t n, const double* __restrict__ b, double* __restrict__ bm, double* __restrict__ x,
-                           double* __restrict__ r, double* scal, double* partials, unsigned* ticket) {
+// b_m = b - mean(b) (b in the caller's numbering, gathered into level-0
+// order); x = 0; r = b_m; ||b_m||^2; loop control scalars.
+__global__ void k_pcg_init(int64_t n, const double* __restrict__ b, const int32_t* __restrict__ perm,
+                           double* __restrict__ bm, double* __restrict__ x, double* __restrict__ r, double* scal,
+                           double* partials, unsigned* ticket, double tol, int maxit, int every) {
   const double mean = scal[kSumB] / (double)n;
   double acc[1] = {0.0};
   LG_GRID_STRIDE(i, n) {
-    const double v = b[i] - mean;
+    const double v = b[perm[i]] - mean;
     bm[i] = v;
     r[i] = v;
     x[i] = 0.0;
@@ -378,7 +401,35 @@ __global__ void k_pcg_init(int64_t n, const double* __restrict__ b, double* __re
   if (grid_sum<kVT, 1>(acc, partials, ticket, scal + kBB)) {
     scal[kBreak] = 0.0;
     scal[kRR] = scal[kBB];
+    scal[kIter] = 0.0;
+    scal[kDone] = 0.0;
+    scal[kTol2BB] = tol * tol * scal[kBB];
+    scal[kMaxit] = (double)maxit;
+    scal[kEvery] = (double)every;
+    scal[kNeedTrue] = 0.0;
   }
+}
+
+// After the x, r update of an iteration: count it, and ask for the true
+// residual on replacement iterations or when the recurrence residual meets
+// the tolerance.
+__global__ void k_pcg_gate(double* scal) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double it = scal[kIter] + 1.0;
+  scal[kIter] = it;
+  const bool need = fmod(it, scal[kEvery]) == 0.0 || scal[kRR] <= scal[kTol2BB];
+  scal[kNeedTrue] = need ? 1.0 : 0.0;
+}
+
+// End of an iteration: converged once the true residual meets the tolerance;
+// stop on convergence, breakdown or max_iter. Inside the graph it sets the
+// loop condition of the WHILE node; the iteration bound always holds.
+__global__ void k_pcg_cond(double* scal, cudaGraphConditionalHandle handle, int in_graph) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const bool conv = scal[kNeedTrue] != 0.0 && scal[kRR] <= scal[kTol2BB];
+  if (conv) scal[kDone] = 1.0;
+  const bool cont = !conv && scal[kBreak] == 0.0 && scal[kIter] < scal[kMaxit];
+  if (in_graph) cudaGraphSetConditional(handle, cont ? 1u : 0u);
 }
 
 // Sums over the preconditioned residual z (precision T, mean not yet
@@ -388,7 +439,8 @@ __global__ void k_pcg_init(int64_t n, const double* __restrict__ b, double* __re
 // stores r^T z for the next alpha.
 template <typename T>
 __global__ void k_z_reduce(int64_t n, const T* __restrict__ z, const double* __restrict__ r,
-                           const double* __restrict__ ro, int first, double* scal, double* partials, unsigned* ticket) {
+                           const double* __restrict__ ro, double* scal, double* partials, unsigned* ticket) {
+  const int first = scal[kIter] == 0.0;
   double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
   LG_GRID_STRIDE(i, n) {
     const double zi = (double)z[i], ri = r[i], roi = first ? 0.0 : ro[i];
@@ -420,27 +472,30 @@ __global__ void k_p_update(int64_t n, const T* __restrict__ z, double* __restric
   LG_GRID_STRIDE(i, n) p[i] = ((double)z[i] - m) + beta * p[i];
 }
 
-// q = L p with p^T q; the last block sets alpha = r^T z / p^T q.
-struct EpiPq {
-  const double* p;
+// q = L p.
+struct EpiQ {
   double* q;
-  double* scal;
-  __device__ __forceinline__ double pre(int64_t i) const { return p[i]; }
-  __device__ __forceinline__ void operator()(int64_t i, double s, double pi, double* red) const {
-    q[i] = s;
-    red[0] += pi * s;
-  }
-  __device__ void finish(const double* tot) const {
-    const double pq = tot[0];
+  __device__ __forceinline__ NoPre pre(int64_t) const { return NoPre{}; }
+  __device__ __forceinline__ void operator()(int64_t i, double s, NoPre, double*) const { q[i] = s; }
+  __device__ void finish(const double*) const {}
+};
+
+// p^T q; the last block sets alpha = r^T z / p^T q (0 after a breakdown).
+__global__ void k_pq_dot(int64_t n, const double* __restrict__ p, const double* __restrict__ q, double* scal,
+                         double* partials, unsigned* ticket) {
+  double acc[1] = {0.0};
+  LG_GRID_STRIDE(i, n) acc[0] += p[i] * q[i];
+  if (grid_sum<kVT, 1>(acc, partials, ticket, scal + kTmp)) {
+    const double pq = scal[kTmp];
     scal[kPQ] = pq;
-    if (!(pq > 0.0) || !isfinite(pq)) {
+    if (!(pq > 0.0) || !isfinite(pq) || scal[kBreak] != 0.0) {
       scal[kBreak] = 1.0;
       scal[kAlpha] = 0.0;
     } else {
       scal[kAlpha] = scal[kRZ] / pq;
     }
   }
-};
+}
 
 // r_old = r; x += alpha p; r -= alpha q; ||r||^2.
 __global__ void k_xr_update(int64_t n, double* __restrict__ x, double* __restrict__ r, double* __restrict__ ro,
@@ -459,23 +514,29 @@ __global__ void k_xr_update(int64_t n, double* __restrict__ x, double* __restric
   grid_sum<kVT, 1>(acc, partials, ticket, scal + kRR);
 }
 
-// r = b_m - L x with ||r||^2 (true residual).
+// r = b_m - L x (true residual).
 struct EpiTrueRes {
   const double* bm;
   double* r;
-  double* scal;
   __device__ __forceinline__ double pre(int64_t i) const { return bm[i]; }
-  __device__ __forceinline__ void operator()(int64_t i, double s, double b, double* red) const {
-    const double v = b - s;
-    r[i] = v;
-    red[0] += v * v;
-  }
-  __device__ void finish(const double* tot) const { scal[kRR] = tot[0]; }
+  __device__ __forceinline__ void operator()(int64_t i, double s, double b, double*) const { r[i] = b - s; }
+  __device__ void finish(const double*) const {}
 };
 
-__global__ void k_sub_mean(int64_t n, double* __restrict__ x, const double* scal_sum) {
+// ||r||^2 into scal[kRR]; skipped like the pass before it when gated off.
+__global__ void k_rr(int64_t n, const double* __restrict__ r, double* scal, double* partials, unsigned* ticket,
+                     const double* gate) {
+  if (gate && *gate == 0.0) return;
+  double acc[1] = {0.0};
+  LG_GRID_STRIDE(i, n) acc[0] += r[i] * r[i];
+  grid_sum<kVT, 1>(acc, partials, ticket, scal + kRR);
+}
+
+// out[perm[i]] = x[i] - mean(x): back to the caller's numbering, mean removed.
+__global__ void k_sub_mean_out(int64_t n, const double* __restrict__ x, const int32_t* __restrict__ perm,
+                               const double* scal_sum, double* __restrict__ out) {
   const double m = scal_sum[0] / (double)n;
-  LG_GRID_STRIDE(i, n) x[i] -= m;
+  LG_GRID_STRIDE(i, n) out[perm[i]] = x[i] - m;
 }
 
 Workspace::~Workspace() {
@@ -509,7 +570,7 @@ std::unique_ptr<Workspace> make_workspace(Hier& h, int k, cudaStream_t s) {
       };
       if (prec == 0) alloc(ws->v64[l]); else alloc(ws->v32[l]);
     }
-    max_grid = std::max<int64_t>(max_grid, lv.plan.plan.max_grid());
+    max_grid = std::max<int64_t>(max_grid, lv.plan.plan.grid());
     ws->scratch[l].op.make(lv.plan.plan, k, s, c);
     if (lv.kind == LG_LEVEL_AGG) ws->scratch[l].mem.make(lv.mem_plan.plan, k, s, c);
     if (lv.kind == LG_LEVEL_ELIM) ws->scratch[l].pt.make(lv.pt_plan.plan, k, s, c);
@@ -522,6 +583,7 @@ std::unique_ptr<Workspace> make_workspace(Hier& h, int k, cudaStream_t s) {
   ws->z.alloc(n0, s, c);
   ws->p.alloc(n0, s, c);
   ws->q.alloc(n0, s, c);
+  ws->io.alloc(n0, s, c);
   max_grid = std::max<int64_t>(max_grid, kSMs * 8);
   ws->partials.alloc((size_t)max_grid * 8 * k, s, c);
   ws->tickets.alloc(4, s, c);
@@ -532,41 +594,87 @@ std::unique_ptr<Workspace> make_workspace(Hier& h, int k, cudaStream_t s) {
   return ws;
 }
 
-// One preconditioned step: z = M r (cycle in T), beta, p; then q = L p, alpha, x, r.
+// One PCG iteration: z = M r (cycle in T), beta, p; q = L p, alpha, x, r;
+// then the gate, the gated true residual and the loop condition.
+static void true_residual(Hier& h, Workspace& ws, cudaStream_t s, const double* gate);
+
 template <typename T>
-static void pcg_step(Hier& h, Workspace& ws, int first, cudaStream_t s) {
+static void pcg_body(Hier& h, Workspace& ws, cudaStream_t s, cudaGraphConditionalHandle handle, int in_graph) {
   const Level& L0 = *h.levels[0];
   const int64_t n = L0.n;
   double* scal = ws.scal.get();
   cycle_from<T>(h, ws, ws.r.get(), s);
   const T* z = vecs<T>(ws)[0].x.get();
-  k_z_reduce<T><<<vblocks(n), kVT, 0, s>>>(n, z, ws.r.get(), ws.ro.get(), first, scal, ws.partials.get(),
-                                          ws.tickets.get());
+  k_z_reduce<T><<<vblocks(n), kVT, 0, s>>>(n, z, ws.r.get(), ws.ro.get(), scal, ws.partials.get(), ws.tickets.get());
   LG_LAUNCH_CHECK();
   k_p_update<T><<<vblocks(n), kVT, 0, s>>>(n, z, ws.p.get(), scal);
   LG_LAUNCH_CHECK();
   OpView<double> op = L0.op<double>();
   op.plan = ws.scratch[0].op.bind(op.plan);
-  op_pass<double, 1>(ws, 0, op, LapTerm<double>{op.w, ws.p.get(), op.d}, EpiPq{ws.p.get(), ws.q.get(), scal}, 1, s,
-                     ws.partials.get(), ws.tickets.get(), scal + kTmp);
+  op_pass<double, 0>(ws, 0, op, LapTerm<double>{op.w, ws.p.get(), op.d}, EpiQ{ws.q.get()}, 0, s);
+  k_pq_dot<<<vblocks(n), kVT, 0, s>>>(n, ws.p.get(), ws.q.get(), scal, ws.partials.get(), ws.tickets.get());
+  LG_LAUNCH_CHECK();
   k_xr_update<<<vblocks(n), kVT, 0, s>>>(n, ws.x.get(), ws.r.get(), ws.ro.get(), ws.p.get(), ws.q.get(), scal,
                                         ws.partials.get(), ws.tickets.get());
   LG_LAUNCH_CHECK();
+  k_pcg_gate<<<1, 32, 0, s>>>(scal);
+  LG_LAUNCH_CHECK();
+  true_residual(h, ws, s, scal + kNeedTrue);
+  k_pcg_cond<<<1, 32, 0, s>>>(scal, handle, in_graph);
+  LG_LAUNCH_CHECK();
 }
 
-static void true_residual(Hier& h, Workspace& ws, cudaStream_t s) {
+static void true_residual(Hier& h, Workspace& ws, cudaStream_t s, const double* gate) {
   const Level& L0 = *h.levels[0];
   OpView<double> op = L0.op<double>();
   op.plan = ws.scratch[0].op.bind(op.plan);
   double* scal = ws.scal.get();
-  op_pass<double, 1>(ws, 0, op, LapTerm<double>{op.w, ws.x.get(), op.d}, EpiTrueRes{ws.bm.get(), ws.r.get(), scal}, 2,
-                     s, ws.partials.get(), ws.tickets.get(), scal + kTmp);
+  op_pass<double, 0>(ws, 0, op, LapTerm<double>{op.w, ws.x.get(), op.d}, EpiTrueRes{ws.bm.get(), ws.r.get()}, 2, s,
+                     nullptr, nullptr, nullptr, gate);
+  k_rr<<<vblocks(L0.n), kVT, 0, s>>>(L0.n, ws.r.get(), scal, ws.partials.get(), ws.tickets.get(), gate);
+  LG_LAUNCH_CHECK();
 }
 
 static void read_scal(Workspace& ws, cudaStream_t s) {
   LG_CUDA(cudaMemcpyAsync(ws.host_scal, ws.scal.get(), sizeof(double) * kNScal, cudaMemcpyDeviceToHost, s));
   LG_CUDA(cudaStreamSynchronize(s));
   if (ws.prof.on) ws.prof.collect();
+}
+
+// The whole PCG loop as one graph: a WHILE node whose body is one iteration
+// (captured once per workspace and precision) and whose condition the
+// iteration's last kernel sets.
+template <typename T>
+static cudaGraphExec_t pcg_graph(Hier& h, Workspace& ws, cudaStream_t s) {
+  const int slot = sizeof(T) == 4 ? 1 : 0;
+  if (ws.graph[slot]) return ws.graph[slot];
+  cudaGraph_t g = nullptr;
+  LG_CUDA(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle handle;
+  LG_CUDA(cudaGraphConditionalHandleCreate(&handle, g, 1u, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = handle;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  LG_CUDA(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np));
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  LG_CUDA(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  try {
+    pcg_body<T>(h, ws, s, handle, 1);
+  } catch (...) {
+    cudaGraph_t dummy;
+    cudaStreamEndCapture(s, &dummy);
+    cudaGraphDestroy(g);
+    throw;
+  }
+  LG_CUDA(cudaStreamEndCapture(s, &body));
+  cudaGraphExec_t exec = nullptr;
+  LG_CUDA(cudaGraphInstantiate(&exec, g, 0));
+  cudaGraphDestroy(g);
+  ws.graph[slot] = exec;
+  return exec;
 }
 
 int pcg_solve(Hier& h, Workspace& ws, const double* b, double* x, double tol, int precision, cudaStream_t s,
@@ -578,47 +686,51 @@ int pcg_solve(Hier& h, Workspace& ws, const double* b, double* x, double tol, in
   LG_CUDA(cudaEventCreate(&e0));
   LG_CUDA(cudaEventCreate(&e1));
   LG_CUDA(cudaEventRecord(e0, s));
+  const int maxit = h.opts.max_iter;
+  const int every = h.opts.residual_replace > 0 ? h.opts.residual_replace : 1 << 30;
   k_sum1<<<vblocks(n), kVT, 0, s>>>(n, b, ws.partials.get(), ws.tickets.get(), scal + kSumB);
   LG_LAUNCH_CHECK();
-  k_pcg_init<<<vblocks(n), kVT, 0, s>>>(n, b, ws.bm.get(), ws.x.get(), ws.r.get(), scal, ws.partials.get(),
-                                        ws.tickets.get());
+  k_pcg_init<<<vblocks(n), kVT, 0, s>>>(n, b, h.perm.get(), ws.bm.get(), ws.x.get(), ws.r.get(), scal,
+                                        ws.partials.get(), ws.tickets.get(), tol, maxit, every);
   LG_LAUNCH_CHECK();
   read_scal(ws, s);
   const double bb = ws.host_scal[kBB];
-  int status = LG_OK, it = 0;
-  double rel = 0.0;
-  const int maxit = h.opts.max_iter;
-  const int every = h.opts.residual_replace > 0 ? h.opts.residual_replace : 1 << 30;
-  if (bb > 0.0) {
-    status = LG_ERR_NOT_CONVERGED;
-    rel = 1.0;
-    for (it = 1; it <= maxit; ++it) {
-      if (precision == LG_FP32_HIER) pcg_step<float>(h, ws, it == 1, s);
-      else pcg_step<double>(h, ws, it == 1, s);
-      if (it % every == 0) true_residual(h, ws, s);
-      read_scal(ws, s);
-      if (ws.host_scal[kBreak] != 0.0) { status = LG_ERR_BREAKDOWN; break; }
-      rel = std::sqrt(ws.host_scal[kRR] / bb);
-      if (rel <= tol) {
-        true_residual(h, ws, s);
+  const bool fp32 = precision == LG_FP32_HIER;
+  if (bb > 0.0 && maxit > 0) {
+    if (h.opts.use_graphs && !ws.prof.on && !debug_sync()) {
+      cudaGraphExec_t ge = fp32 ? pcg_graph<float>(h, ws, s) : pcg_graph<double>(h, ws, s);
+      LG_CUDA(cudaGraphLaunch(ge, s));
+    } else {
+      for (int it = 0; it < maxit; ++it) {
+        if (fp32) pcg_body<float>(h, ws, s, cudaGraphConditionalHandle{}, 0);
+        else pcg_body<double>(h, ws, s, cudaGraphConditionalHandle{}, 0);
         read_scal(ws, s);
-        rel = std::sqrt(ws.host_scal[kRR] / bb);
-        if (rel <= tol) { status = LG_OK; break; }
+        const double* hs = ws.host_scal;
+        const bool conv = hs[kDone] != 0.0;
+        if (conv || hs[kBreak] != 0.0 || hs[kIter] >= hs[kMaxit]) break;
       }
     }
-    if (it > maxit) it = maxit;
+    read_scal(ws, s);
   }
-  // x with its mean removed, copied out
-  k_sum1<<<vblocks(n), kVT, 0, s>>>(n, ws.x.get(), ws.partials.get(), ws.tickets.get(), scal + kTmp);
-  LG_LAUNCH_CHECK();
-  k_sub_mean<<<vblocks(n), kVT, 0, s>>>(n, ws.x.get(), scal + kTmp);
-  LG_LAUNCH_CHECK();
+  const double* hs = ws.host_scal;
+  int status = LG_OK, it = 0;
+  double rel = 0.0;
+  if (bb > 0.0) {
+    it = (int)hs[kIter];
+    status = hs[kDone] != 0.0 ? LG_OK : hs[kBreak] != 0.0 ? LG_ERR_BREAKDOWN : LG_ERR_NOT_CONVERGED;
+    rel = std::sqrt(hs[kRR] / bb);
+  }
   if (status != LG_OK && bb > 0.0) {
-    true_residual(h, ws, s);
+    true_residual(h, ws, s, nullptr);
     read_scal(ws, s);
     rel = std::sqrt(ws.host_scal[kRR] / bb);
   }
-  LG_CUDA(cudaMemcpyAsync(x, ws.x.get(), sizeof(double) * n, cudaMemcpyDefault, s));
+  // x with its mean removed, in the caller's numbering, copied out
+  k_sum1<<<vblocks(n), kVT, 0, s>>>(n, ws.x.get(), ws.partials.get(), ws.tickets.get(), scal + kTmp);
+  LG_LAUNCH_CHECK();
+  k_sub_mean_out<<<vblocks(n), kVT, 0, s>>>(n, ws.x.get(), h.perm.get(), scal + kTmp, ws.io.get());
+  LG_LAUNCH_CHECK();
+  LG_CUDA(cudaMemcpyAsync(x, ws.io.get(), sizeof(double) * n, cudaMemcpyDefault, s));
   LG_CUDA(cudaEventRecord(e1, s));
   LG_CUDA(cudaStreamSynchronize(s));
   float ms = 0.f;

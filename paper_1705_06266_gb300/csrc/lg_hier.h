@@ -131,7 +131,8 @@ struct Workspace {
   std::vector<LevelVecs<double>> v64;
   std::vector<LevelVecs<float>> v32;
   std::vector<LevelScratch> scratch;
-  DBuf<double> bm, x, r, ro, z, p, q;   // FP64 Krylov vectors, n * k
+  DBuf<double> bm, x, r, ro, z, p, q;   // FP64 Krylov vectors, n * k (level-0 numbering)
+  DBuf<double> io;                     // input / output in the caller's numbering
   DBuf<double> partials;               // grid reduction partials
   DBuf<unsigned> tickets;              // grid reduction tickets (zero between launches)
   DBuf<double> scal;                   // device scalars of the PCG (see lg_cycle.cu)
@@ -154,6 +155,7 @@ struct Hier {
   std::vector<Cheb> cheb;               // per level (aggregation levels only)
   std::unique_ptr<Workspace> ws;        // default workspace of lg_solve
   DBuf<int> dev_err;                    // device error word
+  DBuf<int32_t> perm;                   // level-0 vertex i is the caller's vertex perm[i]
   ~Hier();
 };
 

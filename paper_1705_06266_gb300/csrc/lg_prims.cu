@@ -308,24 +308,20 @@ void accumulate_csr(DBuf<uint64_t>& keys, DBuf<uint64_t>& vals, int64_t nent, in
 // ---------------------------------------------------------------------------
 // Row plan.
 // ---------------------------------------------------------------------------
-__global__ void k_plan_count(int64_t n, const int64_t* __restrict__ rowptr, int64_t thresh,
-                             int64_t* __restrict__ nch, uint8_t* __restrict__ islong, uint8_t* __restrict__ ismed) {
+__global__ void k_plan_count(int64_t n, const int64_t* __restrict__ rowptr, int64_t* __restrict__ nch,
+                             uint8_t* __restrict__ islong) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t deg = rowptr[i + 1] - rowptr[i];
-    const bool l = deg > thresh;
+    const bool l = deg > kChunk;
     islong[i] = l;
-    ismed[i] = !l && deg > kShortMax;
     nch[i] = l ? (deg + kChunk - 1) / kChunk : 0;
   }
 }
 
 __global__ void k_plan_fill(int64_t n, const int64_t* __restrict__ rowptr, const uint8_t* __restrict__ islong,
-                            const int64_t* __restrict__ cstart, const int64_t* __restrict__ lidx,
-                            const uint8_t* __restrict__ ismed, const int64_t* __restrict__ midx, int32_t* med_rows,
-                            int32_t* chunk_row, int64_t* chunk_beg, int32_t* chunk_lrow, int32_t* lrow_first,
-                            int32_t* lrow_count) {
+                            const int64_t* __restrict__ cstart, const int64_t* __restrict__ lidx, int32_t* chunk_row,
+                            int64_t* chunk_beg, int32_t* chunk_lrow, int32_t* lrow_first, int32_t* lrow_count) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    if (ismed[i]) med_rows[midx[i]] = (int32_t)i;
     if (!islong[i]) continue;
     const int64_t lr = lidx[i], c0 = cstart[i], cnt = cstart[i + 1] - cstart[i];
     lrow_first[lr] = (int32_t)c0;
@@ -338,41 +334,78 @@ __global__ void k_plan_fill(int64_t n, const int64_t* __restrict__ rowptr, const
   }
 }
 
-void set_plan_group(RowPlan& p, int64_t n, int elem_bytes, int G) {
-  const int64_t groups = (n + (kRowThreads / G) - 1) / (kRowThreads / G);
-  const int blocks = (int)(groups < (int64_t)kSMs * 8 ? (groups > 0 ? groups : 1) : (int64_t)kSMs * 8);
-  if (elem_bytes == 8) {
-    p.G64 = G;
-    p.short_blocks64 = blocks;
-  } else {
-    p.G32 = G;
-    p.short_blocks32 = blocks;
+// Class of each row: the smallest c with deg <= E 2^c (capped at the last
+// class); kClasses for rows cut into chunks.
+__global__ void k_plan_class(int64_t n, const int64_t* __restrict__ rowptr, int E, uint64_t* __restrict__ key,
+                             uint64_t* __restrict__ val) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t deg = rowptr[i + 1] - rowptr[i];
+    int c = 0;
+    while (c < kClasses - 1 && deg > (int64_t)E << c) ++c;
+    key[i] = deg > kChunk ? (uint64_t)kClasses : (uint64_t)c;
+    val[i] = (uint64_t)i;
   }
+}
+
+__global__ void k_plan_lists(int64_t n, const uint64_t* __restrict__ key, const uint64_t* __restrict__ val,
+                             int32_t* __restrict__ rows, int64_t* __restrict__ off) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    rows[i] = (int32_t)val[i];
+    if (i == 0 || key[i] != key[i - 1])
+      for (uint64_t c = (i == 0 ? 0 : key[i - 1] + 1); c <= key[i]; ++c) off[c] = i;
+    if (i == n - 1)
+      for (uint64_t c = key[i] + 1; c <= (uint64_t)kClasses; ++c) off[c] = n;
+  }
+}
+
+void bin_rows(RowPlanStore& ps, int64_t n, const int64_t* rowptr, int E, cudaStream_t s) {
+  RowPlan& p = ps.plan;
+  p.E = E;
+  int64_t off[kClasses + 1] = {0};
+  if (n > 0) {
+    DBuf<uint64_t> key(n, s), val(n, s);
+    DBuf<int64_t> doff(kClasses + 1, s);
+    const int g = grid_for(n, 256, kSMs * 16);
+    k_plan_class<<<g, 256, 0, s>>>(n, rowptr, E, key.get(), val.get());
+    LG_LAUNCH_CHECK();
+    radix_sort_pairs(key.get(), val.get(), n, 8, s);
+    k_plan_lists<<<g, 256, 0, s>>>(n, key.get(), val.get(), ps.rows_by_class.get(), doff.get());
+    LG_LAUNCH_CHECK();
+    LG_CUDA(cudaMemcpyAsync(off, doff.get(), sizeof(off), cudaMemcpyDeviceToHost, s));
+    LG_CUDA(cudaStreamSynchronize(s));
+  }
+  int blk = 0;
+  for (int c = 0; c < kClasses; ++c) {
+    p.cls_off[c] = off[c];
+    p.blk_off[c] = blk;
+    const int64_t rows = off[c + 1] - off[c];
+    const int64_t per_block = kRowThreads >> c;  // groups of 2^c lanes
+    blk += (int)((rows + per_block - 1) / per_block);
+  }
+  p.cls_off[kClasses] = off[kClasses];
+  p.blk_off[kClasses] = blk;
+  p.rows_by_class = ps.rows_by_class.get();
 }
 
 void build_row_plan(RowPlanStore& ps, int64_t n, int64_t nnz, const int64_t* rowptr, cudaStream_t s,
                     int64_t* counter) {
   RowPlan& p = ps.plan;
-  p.long_thresh = kChunk;
-  DBuf<int64_t> nch(n + 1, s), lidx(n + 1, s), midx(n + 1, s);
-  DBuf<uint8_t> islong(n, s), ismed(n, s);
+  DBuf<int64_t> nch(n + 1, s), lidx(n + 1, s);
+  DBuf<uint8_t> islong(n, s);
   const int g = grid_for(n, 256, kSMs * 16);
   if (n > 0) {
-    k_plan_count<<<g, 256, 0, s>>>(n, rowptr, p.long_thresh, nch.get(), islong.get(), ismed.get());
+    k_plan_count<<<g, 256, 0, s>>>(n, rowptr, nch.get(), islong.get());
     LG_LAUNCH_CHECK();
   }
   exclusive_scan(nch.get(), nch.get(), n, s);
   exclusive_scan_flags(islong.get(), lidx.get(), n, s);
-  exclusive_scan_flags(ismed.get(), midx.get(), n, s);
-  int64_t tot[3];
+  int64_t tot[2];
   LG_CUDA(cudaMemcpyAsync(&tot[0], nch.get() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   LG_CUDA(cudaMemcpyAsync(&tot[1], lidx.get() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  LG_CUDA(cudaMemcpyAsync(&tot[2], midx.get() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   LG_CUDA(cudaStreamSynchronize(s));
   p.nchunks = tot[0];
   p.nlong = tot[1];
-  p.nmed = tot[2];
-  ps.med_rows.alloc(p.nmed, s, counter);
+  ps.rows_by_class.alloc(n, s, counter);
   ps.chunk_row.alloc(p.nchunks, s, counter);
   ps.chunk_beg.alloc(p.nchunks, s, counter);
   ps.chunk_lrow.alloc(p.nchunks, s, counter);
@@ -381,14 +414,11 @@ void build_row_plan(RowPlanStore& ps, int64_t n, int64_t nnz, const int64_t* row
   ps.partial.alloc((size_t)(p.nchunks > 0 ? p.nchunks : 1) * kMaxCols, s, counter);
   ps.ticket.alloc(p.nlong > 0 ? p.nlong : 1, s, counter);
   LG_CUDA(cudaMemsetAsync(ps.ticket.get(), 0, sizeof(unsigned) * (p.nlong > 0 ? p.nlong : 1), s));
-  if (p.nlong > 0 || p.nmed > 0) {
-    k_plan_fill<<<g, 256, 0, s>>>(n, rowptr, islong.get(), nch.get(), lidx.get(), ismed.get(), midx.get(),
-                                  ps.med_rows.get(), ps.chunk_row.get(), ps.chunk_beg.get(), ps.chunk_lrow.get(),
-                                  ps.lrow_first.get(), ps.lrow_count.get());
+  if (p.nlong > 0) {
+    k_plan_fill<<<g, 256, 0, s>>>(n, rowptr, islong.get(), nch.get(), lidx.get(), ps.chunk_row.get(),
+                                  ps.chunk_beg.get(), ps.chunk_lrow.get(), ps.lrow_first.get(), ps.lrow_count.get());
     LG_LAUNCH_CHECK();
   }
-  p.med_blocks = p.nmed > 0 ? grid_for(p.nmed * 32, kRowThreads, kSMs * 8) : 0;
-  p.med_rows = ps.med_rows.get();
   p.chunk_row = ps.chunk_row.get();
   p.chunk_beg = ps.chunk_beg.get();
   p.chunk_lrow = ps.chunk_lrow.get();
@@ -396,10 +426,8 @@ void build_row_plan(RowPlanStore& ps, int64_t n, int64_t nnz, const int64_t* row
   p.lrow_count = ps.lrow_count.get();
   p.partial = ps.partial.get();
   p.ticket = ps.ticket.get();
-  // heuristic group sizes from the average length of a row (the autotuner may revise them)
-  const double avg = n > 0 ? (double)nnz / (double)n : 0.0;
-  set_plan_group(p, n, 8, avg <= 3.0 ? 1 : avg <= 8.0 ? 2 : avg <= 20.0 ? 4 : 8);
-  set_plan_group(p, n, 4, avg <= 2.0 ? 1 : avg <= 5.0 ? 2 : avg <= 12.0 ? 4 : 8);
+  (void)nnz;
+  bin_rows(ps, n, rowptr, 4, s);
 }
 
 }  // namespace lg

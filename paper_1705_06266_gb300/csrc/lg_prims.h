@@ -41,16 +41,16 @@ inline int bits_for(int64_t v) {
 // Owned storage of a RowPlan.
 struct RowPlanStore {
   RowPlan plan;
-  DBuf<int32_t> med_rows, chunk_row, chunk_lrow, lrow_first, lrow_count;
+  DBuf<int32_t> rows_by_class, chunk_row, chunk_lrow, lrow_first, lrow_count;
   DBuf<int64_t> chunk_beg;
   DBuf<double> partial;
   DBuf<unsigned> ticket;
 };
-// Build the plan for a CSR structure with n rows and nnz entries; the
-// short-row group sizes start from a heuristic on the average row length.
+// Build the plan for a CSR structure with n rows and nnz entries (rows binned
+// with E = 4 entries per lane).
 void build_row_plan(RowPlanStore& ps, int64_t n, int64_t nnz, const int64_t* rowptr, cudaStream_t s,
                     int64_t* counter);
-// Set the short-row group size of one precision (and the matching grid).
-void set_plan_group(RowPlan& p, int64_t n, int elem_bytes, int G);
+// Re-bin the rows of a built plan for E entries per lane.
+void bin_rows(RowPlanStore& ps, int64_t n, const int64_t* rowptr, int E, cudaStream_t s);
 
 }  // namespace lg

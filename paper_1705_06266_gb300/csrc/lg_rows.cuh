@@ -2,18 +2,16 @@
 //
 // A pass computes, for every row i of a CSR structure,
 //   s_i = finish_i( sum_k term(i, k) )
-// over the row's entries, then calls an epilogue with (i, s_i). Rows are
-// split into three tiers when the plan is built:
-//  - short rows (at most kShortMax entries): aligned groups of G lanes, G in
-//    {1, 2, 4, 8} chosen per precision by the setup's autotuner; the group
-//    walks its rows with a stride over the grid and prefetches the next row's
-//    extent and the epilogue operands before the entry loop;
-//  - medium rows (up to plan.long_thresh entries): one warp per row, from a
-//    row list;
-//  - long rows: chunks of kChunk entries, one block each; the last block of a
-//    row to finish (a per-row ticket) adds the chunk partials in chunk order.
-// Every addition happens in an order fixed by the row lengths and the plan,
-// never by timing, so each pass is bitwise reproducible.
+// over the row's entries, then calls an epilogue with (i, s_i). The plan
+// (lg_common.cuh) bins the rows by length: a row of class c is handled by one
+// aligned group of G = 2^c lanes, every lane taking about E entries, so the
+// groups of a warp finish together and each lane has its loads in flight at
+// once; the group reduces into its first lane, which applies the epilogue
+// with operands prefetched before the entry loop. Rows longer than kChunk
+// entries are cut into chunks, one block each; the last block of a row to
+// finish (a per-row ticket) adds the chunk partials in chunk order. Every
+// addition happens in an order fixed by the row lengths and the plan, never
+// by timing, so each pass is bitwise reproducible.
 //
 // An epilogue may contribute NRED values to grid-wide sums (dot products of
 // the Krylov solver); these are combined with lg::grid_sum at the end of the
@@ -93,11 +91,30 @@ __device__ __forceinline__ T row_sum(const Term& term, const int32_t* __restrict
   return s0 + s1;
 }
 
-template <typename T, int G, int NRED, class Term, class Epi>
+// One row of class G: group of G lanes, reduction into the group's lane 0.
+template <typename T, int G, class Term, class Epi>
+__device__ __forceinline__ void class_row(const RowPlan& plan, int c, int64_t b, const int64_t* __restrict__ rowptr,
+                                          const int32_t* __restrict__ col, const Term& term, const Epi& epi,
+                                          double* red) {
+  const int64_t idx = b * (kRowThreads / G) + threadIdx.x / G;
+  const int64_t lo = plan.cls_off[c], hi = plan.cls_off[c + 1];
+  const int lane = threadIdx.x & (G - 1);
+  if (lo + idx >= hi) return;  // the whole group leaves together
+  const int64_t row = plan.rows_by_class[lo + idx];
+  const int64_t beg = rowptr[row], end = rowptr[row + 1];
+  const auto pre = epi.pre(row);
+  const T rv = term.row(row);
+  T s = row_sum<T, G>(term, col, beg, end, lane, rv);
+  s = group_sum_first<G>(s, group_mask<G>(), lane);
+  if (lane == 0) epi(row, term.finish(rv, s), pre, red);
+}
+
+template <typename T, int NRED, class Term, class Epi>
 __global__ void __launch_bounds__(kRowThreads)
-k_rows(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, Term term,
-       RowPlan plan, Epi epi, double* __restrict__ red_partials, unsigned* red_ticket,
-       double* red_out) {
+k_rows(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, Term term, RowPlan plan, Epi epi,
+       double* __restrict__ red_partials, unsigned* red_ticket, double* red_out, const double* gate) {
+  // a pass gated off (gate[0] == 0, read by every block alike) does nothing
+  if (gate && *gate == 0.0) return;
   double red[NRED > 0 ? NRED : 1];
 #pragma unroll
   for (int q = 0; q < (NRED > 0 ? NRED : 1); ++q) red[q] = 0.0;
@@ -113,12 +130,12 @@ k_rows(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict_
     const int64_t end = beg + kChunk < rend ? beg + kChunk : rend;
     const T rv = term.row(row);
     T s = row_sum<T, kRowThreads>(term, col, beg, end, threadIdx.x, rv);
-    s = group_sum<32>(s, 0xffffffffu);
+    s = group_sum_first<32>(s, 0xffffffffu, threadIdx.x & 31);
     if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = s;
     __syncthreads();
     if (threadIdx.x < 32) {
       T t = threadIdx.x < kRowThreads / 32 ? sred[threadIdx.x] : T(0);
-      t = group_sum<32>(t, 0xffffffffu);
+      t = group_sum_first<kRowThreads / 32>(t, 0xffffffffu, threadIdx.x);
       if (threadIdx.x == 0) {
         const int32_t lr = plan.chunk_lrow[c];
         plan.partial[c] = (double)t;
@@ -134,44 +151,20 @@ k_rows(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict_
         }
       }
     }
-  } else if (bid < plan.nchunks + plan.med_blocks) {
-    // ---- medium rows: one warp per row ----
-    const int lane = threadIdx.x & 31;
-    const int64_t w0 = (bid - plan.nchunks) * (kRowThreads / 32) + (threadIdx.x >> 5);
-    const int64_t stride = (int64_t)plan.med_blocks * (kRowThreads / 32);
-    for (int64_t m = w0; m < plan.nmed; m += stride) {
-      const int64_t row = plan.med_rows[m];
-      const int64_t beg = rowptr[row], end = rowptr[row + 1];
-      const auto pre = epi.pre(row);
-      const T rv = term.row(row);
-      T s = row_sum<T, 32>(term, col, beg, end, lane, rv);
-      s = group_sum<32>(s, 0xffffffffu);
-      if (lane == 0) epi(row, term.finish(rv, s), pre, red);
-    }
   } else {
-    // ---- short rows: one aligned group of G lanes per row ----
-    const int64_t sb = bid - plan.nchunks - plan.med_blocks;
-    constexpr int64_t kGroups = kRowThreads / G;
-    const int lane = threadIdx.x & (G - 1);
-    const unsigned mask = group_mask<G>();
-    const int64_t stride = (int64_t)(sizeof(T) == 8 ? plan.short_blocks64 : plan.short_blocks32) * kGroups;
-    int64_t row = sb * kGroups + threadIdx.x / G;
-    int64_t beg = 0, end = 0;
-    if (row < n) { beg = rowptr[row]; end = rowptr[row + 1]; }
-    while (row < n) {
-      const int64_t nrow = row + stride;
-      int64_t nbeg = 0, nend = 0;
-      if (nrow < n) { nbeg = rowptr[nrow]; nend = rowptr[nrow + 1]; }
-      if (end - beg <= kShortMax) {
-        const auto pre = epi.pre(row);
-        const T rv = term.row(row);
-        T s = row_sum<T, G>(term, col, beg, end, lane, rv);
-        s = group_sum<G>(s, mask);
-        if (lane == 0) epi(row, term.finish(rv, s), pre, red);
-      }
-      row = nrow;
-      beg = nbeg;
-      end = nend;
+    // ---- binned rows: find the class of this block ----
+    const int b = (int)(bid - plan.nchunks);
+    int c = 0;
+#pragma unroll
+    for (int q = 1; q < kClasses; ++q) c += b >= plan.blk_off[q];
+    const int64_t bb = b - plan.blk_off[c];
+    switch (c) {
+      case 0: class_row<T, 1>(plan, 0, bb, rowptr, col, term, epi, red); break;
+      case 1: class_row<T, 2>(plan, 1, bb, rowptr, col, term, epi, red); break;
+      case 2: class_row<T, 4>(plan, 2, bb, rowptr, col, term, epi, red); break;
+      case 3: class_row<T, 8>(plan, 3, bb, rowptr, col, term, epi, red); break;
+      case 4: class_row<T, 16>(plan, 4, bb, rowptr, col, term, epi, red); break;
+      default: class_row<T, 32>(plan, 5, bb, rowptr, col, term, epi, red); break;
     }
   }
   if constexpr (NRED > 0) {
@@ -180,26 +173,14 @@ k_rows(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict_
 }
 
 template <typename T, int NRED, class Term, class Epi>
-inline void launch_rows(int64_t n, const int64_t* rowptr, const int32_t* col, const Term& term,
+inline void launch_rows(int64_t /*n*/, const int64_t* rowptr, const int32_t* col, const Term& term,
                         const RowPlan& plan, const Epi& epi, cudaStream_t s,
                         double* red_partials = nullptr, unsigned* red_ticket = nullptr,
-                        double* red_out = nullptr) {
-  const int grid = plan.grid((int)sizeof(T));
-  const int G = sizeof(T) == 8 ? plan.G64 : plan.G32;
-#define LG_ROWS_CASE(GG)                                                                         \
-  case GG:                                                                                       \
-    k_rows<T, GG, NRED, Term, Epi><<<grid, kRowThreads, 0, s>>>(n, rowptr, col, term, plan, epi, \
-                                                                 red_partials, red_ticket, red_out); \
-    break;
-  switch (G) {
-    LG_ROWS_CASE(1)
-    LG_ROWS_CASE(2)
-    LG_ROWS_CASE(4)
-    LG_ROWS_CASE(8)
-    default:
-      fail(LG_ERR_INVALID, "row plan group size");
-  }
-#undef LG_ROWS_CASE
+                        double* red_out = nullptr, const double* gate = nullptr) {
+  const int grid = plan.grid();
+  if (grid <= 0) return;
+  k_rows<T, NRED, Term, Epi><<<grid, kRowThreads, 0, s>>>(rowptr, col, term, plan, epi, red_partials, red_ticket,
+                                                          red_out, gate);
   LG_LAUNCH_CHECK();
 }
 

@@ -563,23 +563,23 @@ __global__ void k_lz_scale(int64_t n, const Lanczos* lz, double* __restrict__ v,
   }
 }
 
+// u = D^-1/2 L D^-1/2 v, from s = (L t)_i with t = D^-1/2 v.
 struct EpiLanczos {
   const double* sdinv;
-  const double* v;
   double* u;
-  Lanczos* lz;
-  int k;
-  struct Pre {
-    double sd, v;
-  };
-  __device__ __forceinline__ Pre pre(int64_t i) const { return Pre{sdinv[i], v[i]}; }
-  __device__ __forceinline__ void operator()(int64_t i, double s, const Pre& p, double* red) const {
-    const double ui = p.sd * s;
-    u[i] = ui;
-    red[0] += p.v * ui;
-  }
-  __device__ void finish(const double* tot) const { lz->alpha[k] = tot[0]; }
+  __device__ __forceinline__ double pre(int64_t i) const { return sdinv[i]; }
+  __device__ __forceinline__ void operator()(int64_t i, double s, double sd, double*) const { u[i] = sd * s; }
+  __device__ void finish(const double*) const {}
 };
+
+// alpha_k = v . u
+__global__ void k_lz_alpha(int64_t n, int k, Lanczos* lz, const double* __restrict__ v, const double* __restrict__ u,
+                           double* partials, unsigned* ticket) {
+  if (lz->stopped) return;
+  double acc[1] = {0.0};
+  LG_GRID_STRIDE(i, n) acc[0] += v[i] * u[i];
+  grid_sum<kNT, 1>(acc, partials, ticket, &lz->alpha[k]);
+}
 
 __global__ void k_lz_orth(int64_t n, int k, Lanczos* lz, double* __restrict__ u, const double* __restrict__ v,
                           const double* __restrict__ vp, double* partials, unsigned* ticket) {
@@ -697,6 +697,45 @@ __global__ void k_unshift(int64_t n, double* __restrict__ M) {
 // ---------------------------------------------------------------------------
 __global__ void k_to_f32(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
   LG_GRID_STRIDE(i, n) b[i] = (float)a[i];
+}
+
+// ---------------------------------------------------------------------------
+// Vertex renumbering by descending degree (stable: ties keep their order).
+// ---------------------------------------------------------------------------
+__global__ void k_degree_keys(int64_t n, const int64_t* __restrict__ rowptr, uint64_t* __restrict__ key,
+                              uint64_t* __restrict__ val) {
+  LG_GRID_STRIDE(i, n) {
+    const int64_t deg = rowptr[i + 1] - rowptr[i];
+    key[i] = 0xffffffffull - (uint64_t)deg;
+    val[i] = (uint64_t)i;
+  }
+}
+
+__global__ void k_perm_from_sorted(int64_t n, const uint64_t* __restrict__ val, int32_t* __restrict__ perm,
+                                   int32_t* __restrict__ inv) {
+  LG_GRID_STRIDE(i, n) {
+    const int32_t old = (int32_t)val[i];
+    perm[i] = old;
+    inv[old] = (int32_t)i;
+  }
+}
+
+__global__ void k_iota_i32(int64_t n, int32_t* __restrict__ a) {
+  LG_GRID_STRIDE(i, n) a[i] = (int32_t)i;
+}
+
+// Entries of the renumbered graph: (inv[i], inv[j]) for every stored (i, j).
+__global__ void k_perm_emit(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                            const double* __restrict__ w, const int32_t* __restrict__ inv, int cbits,
+                            uint64_t* __restrict__ keys, uint64_t* __restrict__ vals) {
+  const int lane = threadIdx.x & 31;
+  LG_WARP_STRIDE(i, n) {
+    const uint64_t row = (uint64_t)inv[i] << cbits;
+    for (int64_t k = rowptr[i] + lane; k < rowptr[i + 1]; k += 32) {
+      keys[k] = row | (uint64_t)inv[col[k]];
+      vals[k] = (uint64_t)__double_as_longlong(w[k]);
+    }
+  }
 }
 
 // ===========================================================================
@@ -905,11 +944,9 @@ static void lanczos(Level& L, const lg_options& o, int level, double* lam_dev, c
   const int iters = std::min(o.eig_iters, 64);
   DBuf<double> v(n, s), vp(n, s), u(n, s), t(n, s), sdinv(n, s);
   const int nb = blocks_for(n);
-  const int nbr = L.plan.plan.max_grid();
-  DBuf<double> partials((size_t)std::max(nb, nbr), s);
+  DBuf<double> partials((size_t)nb, s);
   DBuf<unsigned> ticket(1, s);
   DBuf<Lanczos> lz(1, s);
-  DBuf<double> tot(1, s);
   LG_CUDA(cudaMemsetAsync(ticket.get(), 0, sizeof(unsigned), s));
   k_lz_start<<<nb, kNT, 0, s>>>(n, o.seed, level, L.dinv.get(), v.get(), sdinv.get(), partials.get(), ticket.get(),
                                 lz.get());
@@ -918,9 +955,10 @@ static void lanczos(Level& L, const lg_options& o, int level, double* lam_dev, c
   LG_LAUNCH_CHECK();
   for (int k = 0; k < iters; ++k) {
     // stopped iterations leave alpha[k] untouched; only the first m entries are used
-    launch_rows<double, 1>(n, L.rowptr.get(), L.col.get(), LapTerm<double>{L.w.get(), t.get(), L.d.get()}, L.plan.plan,
-                           EpiLanczos{sdinv.get(), v.get(), u.get(), lz.get(), k}, s, partials.get(),
-                           ticket.get(), tot.get());
+    launch_rows<double, 0>(n, L.rowptr.get(), L.col.get(), LapTerm<double>{L.w.get(), t.get(), L.d.get()}, L.plan.plan,
+                           EpiLanczos{sdinv.get(), u.get()}, s);
+    k_lz_alpha<<<nb, kNT, 0, s>>>(n, k, lz.get(), v.get(), u.get(), partials.get(), ticket.get());
+    LG_LAUNCH_CHECK();
     k_lz_orth<<<nb, kNT, 0, s>>>(n, k, lz.get(), u.get(), v.get(), vp.get(), partials.get(), ticket.get());
     LG_LAUNCH_CHECK();
     k_lz_next<<<nb, kNT, 0, s>>>(n, k, lz.get(), u.get(), v.get(), vp.get(), sdinv.get(), t.get());
@@ -968,19 +1006,18 @@ static void make_f32(Level& L, cudaStream_t s, int64_t* counter) {
 }
 
 // ---------------------------------------------------------------------------
-// Autotuner of the short-row lane-group size: each candidate G is timed on
-// the level's own operator (plain y = L x, 1 warm-up + 3 timed launches) and
-// the fastest kept. Choices are cached per (n, nnz, precision) for the life
-// of the process, so rebuilding a hierarchy of the same graph gives the same
-// launch plans and bitwise the same results.
+// Autotuner of the row binning: each candidate E (entries per lane) is timed
+// on the level's own operator, one FP64 and one FP32 plain y = L x pass
+// (1 warm-up + 3 timed launches each), and the fastest kept. Choices are
+// cached per (n, nnz) for the life of the process, so rebuilding a hierarchy
+// of the same graph gives the same launch plans and bitwise the same results.
 // ---------------------------------------------------------------------------
 static std::mutex g_tune_mu;
-static std::map<std::tuple<int64_t, int64_t, int>, int> g_tune_cache;
+static std::map<std::pair<int64_t, int64_t>, int> g_tune_cache;
 
 template <typename T>
-static float time_apply(const Level& L, int G, const T* x, T* y, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
+static float time_apply(const Level& L, const T* x, T* y, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
   OpView<T> op = L.op<T>();
-  set_plan_group(op.plan, L.n, (int)sizeof(T), G);
   const LapTerm<T> term{op.w, x, op.d};
   launch_rows<T, 0>(op.n, op.rowptr, op.col, term, op.plan, EpiStore<T>{y}, s);
   LG_CUDA(cudaEventRecord(e0, s));
@@ -992,34 +1029,37 @@ static float time_apply(const Level& L, int G, const T* x, T* y, cudaStream_t s,
   return ms;
 }
 
-template <typename T>
 static void tune_level(Level& L, cudaStream_t s) {
-  const auto key = std::make_tuple(L.n, L.nnz, (int)sizeof(T));
+  const auto key = std::make_pair(L.n, L.nnz);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) {
-      set_plan_group(L.plan.plan, L.n, (int)sizeof(T), it->second);
+      if (it->second != L.plan.plan.E) bin_rows(L.plan, L.n, L.rowptr.get(), it->second, s);
       return;
     }
   }
-  DBuf<T> x(L.n, s), y(L.n, s);
-  LG_CUDA(cudaMemsetAsync(x.get(), 0, sizeof(T) * L.n, s));
+  DBuf<double> x(L.n, s), y(L.n, s);
+  DBuf<float> x32(L.n, s), y32(L.n, s);
+  LG_CUDA(cudaMemsetAsync(x.get(), 0, sizeof(double) * L.n, s));
+  LG_CUDA(cudaMemsetAsync(x32.get(), 0, sizeof(float) * L.n, s));
   cudaEvent_t e0, e1;
   LG_CUDA(cudaEventCreate(&e0));
   LG_CUDA(cudaEventCreate(&e1));
   int best = 0;
   float best_ms = 0.f;
-  for (int G : {1, 2, 4, 8}) {
-    const float ms = time_apply<T>(L, G, x.get(), y.get(), s, e0, e1);
+  for (int E : {2, 4, 8}) {
+    bin_rows(L.plan, L.n, L.rowptr.get(), E, s);
+    const float ms = time_apply<double>(L, x.get(), y.get(), s, e0, e1) +
+                     time_apply<float>(L, x32.get(), y32.get(), s, e0, e1);
     if (best == 0 || ms < best_ms) {
-      best = G;
+      best = E;
       best_ms = ms;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  set_plan_group(L.plan.plan, L.n, (int)sizeof(T), best);
+  if (best != L.plan.plan.E) bin_rows(L.plan, L.n, L.rowptr.get(), best, s);
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune_cache.emplace(key, best);
 }
@@ -1075,6 +1115,29 @@ void setup_hierarchy(Hier& h, int64_t n, const int64_t* rowptr, const int32_t* c
     if (ncomp != 1) fail(LG_ERR_DISCONNECTED, "graph is not connected");
   }
   h.nnz0 = nnz + n;
+  h.perm.alloc(n, s, counter);
+  if (o.reorder && n > 1) {
+    DBuf<uint64_t> key(n, s), val(n, s);
+    DBuf<int32_t> inv(n, s);
+    k_degree_keys<<<blocks_for(n), kNT, 0, s>>>(n, cur->rowptr.get(), key.get(), val.get());
+    LG_LAUNCH_CHECK();
+    radix_sort_pairs(key.get(), val.get(), n, 32, s);
+    k_perm_from_sorted<<<blocks_for(n), kNT, 0, s>>>(n, val.get(), h.perm.get(), inv.get());
+    LG_LAUNCH_CHECK();
+    const int cbits = bits_for(n);
+    DBuf<uint64_t> keys(nnz, s), vals(nnz, s);
+    k_perm_emit<<<warp_blocks(n), kNT, 0, s>>>(n, cur->rowptr.get(), cur->col.get(), cur->w.get(), inv.get(), cbits,
+                                              keys.get(), vals.get());
+    LG_LAUNCH_CHECK();
+    CsrOut out;
+    accumulate_csr(keys, vals, nnz, n, cbits, out, s, counter);
+    cur->rowptr = std::move(out.rowptr);
+    cur->col = std::move(out.col);
+    cur->w = std::move(out.w);
+  } else {
+    k_iota_i32<<<blocks_for(n), kNT, 0, s>>>(n, h.perm.get());
+    LG_LAUNCH_CHECK();
+  }
   prepare_operator(*cur, s, counter);
 
   // ---- coarsening loop ----
@@ -1126,8 +1189,7 @@ void setup_hierarchy(Hier& h, int64_t n, const int64_t* rowptr, const int32_t* c
   if (o.autotune) {
     for (auto& L : h.levels) {
       if (L->nnz < 20000) continue;
-      tune_level<double>(*L, s);
-      tune_level<float>(*L, s);
+      tune_level(*L, s);
     }
   }
 

@@ -35,7 +35,7 @@ class Options(C.Structure):
         ("vote_threshold", C.c_int32), ("strength_vecs", C.c_int32), ("strength_sweeps", C.c_int32),
         ("cheb_degree", C.c_int32), ("eig_iters", C.c_int32), ("max_coarse_n", C.c_int32),
         ("residual_replace", C.c_int32), ("memory_space", C.c_int32), ("use_graphs", C.c_int32),
-        ("autotune", C.c_int32),
+        ("autotune", C.c_int32), ("reorder", C.c_int32), ("reserved", C.c_int32),
     ]
 
 
@@ -84,6 +84,7 @@ _SIGS = {
     "lg_level_info": (C.c_int, [_P, _I32, _P, _P, _P, _P, _P]),
     "lg_level_copy": (C.c_int, [_P, _I32, _P, _P, _P, _P]),
     "lg_coarsest_pinv": (C.c_int, [_P, _P]),
+    "lg_permutation": (C.c_int, [_P, _P]),
     "lg_vcycle": (C.c_int, [_P, _P, _P, _I32]),
     "lg_laplacian_apply": (C.c_int, [_I64, _P, _P, _P, _P, _P, _P]),
     "lg_elim_select": (C.c_int, [_I64, _P, _P, _I32, _U64, _P, _P, _P]),
@@ -92,6 +93,7 @@ _SIGS = {
     "lg_kernel_launches": (C.c_uint64, []),
     "lg_profile": (C.c_int, [_P, _I32]),
     "lg_profile_read": (C.c_int, [_P, _I32, _P]),
+    "lg_level_plan": (C.c_int, [_P, _I32, _P]),
     "lg_serve_options_default": (C.c_int, [_P]),
     "lg_serve_create": (C.c_int, [_P, _P]),
     "lg_serve_register": (C.c_int, [_P, _P]),
@@ -218,6 +220,12 @@ def lg_level_copy(h, l: int):
     return rp, cl[: d["nnz"]], w[: d["nnz"]], mp
 
 
+def lg_permutation(h, n: int) -> np.ndarray:
+    perm = np.zeros(n, np.int32)
+    _check(_load().lg_permutation(h, _ptr(perm)), "lg_permutation")
+    return perm
+
+
 def lg_coarsest_pinv(h, nc: int) -> np.ndarray:
     out = np.zeros((nc, nc))
     _check(_load().lg_coarsest_pinv(h, _ptr(out)), "lg_coarsest_pinv")
@@ -240,6 +248,13 @@ def lg_profile_read(h, level: int = -1) -> KernelProfile:
     p = KernelProfile()
     _check(_load().lg_profile_read(h, int(level), C.byref(p)), "lg_profile_read")
     return p
+
+
+def lg_level_plan(h, l: int) -> dict:
+    out = (C.c_int64 * 6)()
+    _check(_load().lg_level_plan(h, int(l), out), "lg_level_plan")
+    return {"E": out[0], "group_rows": out[1], "warp_rows": out[2], "long_rows": out[3], "chunks": out[4],
+            "blocks": out[5]}
 
 
 def _stream(stream):
@@ -348,6 +363,9 @@ class Hierarchy:
 
     def level(self, l):
         return lg_level_copy(self.h, l)
+
+    def permutation(self):
+        return lg_permutation(self.h, self.n)
 
     def solve(self, b, x=None, tol=1e-8, precision=None, check=True):
         if precision is not None:

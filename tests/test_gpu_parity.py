@@ -87,9 +87,16 @@ def test_strength_and_aggregation(torch_cuda, lgmod, oracle, inputs, name):
     np.testing.assert_array_equal(votes.cpu().numpy(), votes_ref)
 
 
-def csr_of(level):
-    rp, cl, w, mp = level
-    return rp, cl, w, mp
+def renumbered(g, perm):
+    """The graph with vertex i of the result being vertex perm[i] of g."""
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(g.n, dtype=perm.dtype)
+    rows = inv[np.repeat(np.arange(g.n), np.diff(g.rowptr))].astype(np.int64)
+    cols = inv[g.col].astype(np.int64)
+    order = np.lexsort((cols, rows))
+    rp = np.zeros(g.n + 1, np.int64)
+    np.cumsum(np.bincount(rows, minlength=g.n), out=rp[1:])
+    return rp, cols[order].astype(np.int32), g.w[order]
 
 
 def same_csr(a_rp, a_cl, a_w, b, rtol=1e-12):
@@ -111,8 +118,10 @@ def test_hierarchy_per_level_reinjection(torch_cuda, lgmod, oracle, inputs, name
         rp, cl, w, mp = H.level(l)
         G = inputs.Graph(info["n"], rp, cl, w)
         if l == 0:
-            np.testing.assert_array_equal(rp, g.rowptr)
-            np.testing.assert_array_equal(cl, g.col)
+            prp, pcl, pw = renumbered(g, H.permutation())
+            np.testing.assert_array_equal(rp, prp)
+            np.testing.assert_array_equal(cl, pcl)
+            np.testing.assert_array_equal(w, pw)
         if info["kind"] == lgmod.LEVEL_ELIM:
             is_f = oracle.elim_select(G, 4, SEED)
             np.testing.assert_array_equal((mp < 0).astype(np.uint8), is_f)
@@ -174,7 +183,7 @@ def test_solve_matches_oracle_pcg(lgmod, oracle, inputs, name, prec):
 def test_vcycle_fp64_matches_oracle_cycle(lgmod, oracle, inputs):
     """Where the oracle builds the identical hierarchy, one V-cycle agrees to rounding."""
     g = inputs.random_graph(3000, 6, seed=4, weights="uniform")
-    H = lgmod.Hierarchy(g)
+    H = lgmod.Hierarchy(g, reorder=0)  # the oracle works in the caller's numbering
     R = oracle.Hierarchy(g)
     assert H.nlevels == R.nlevels
     for l in range(H.nlevels):
@@ -248,3 +257,59 @@ def test_device_pointers(torch_cuda, lgmod, inputs):
     np.testing.assert_array_equal(x.cpu().numpy(), xh)
     assert info.status == lgmod.OK
     H.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_graph_loop_matches_host_loop(lgmod, inputs, prec):
+    """The PCG loop replayed as one CUDA graph (device-side WHILE node) gives
+    bitwise the same iterate and iteration count as the host-driven loop."""
+    g = inputs.chung_lu(20000, m_target=100000, seed=3)
+    b = inputs.rhs(g.n, seed=4)
+    p = lgmod.FP64 if prec == "fp64" else lgmod.FP32_HIER
+    out = []
+    for use_graphs in (1, 0):
+        H = lgmod.Hierarchy(g, precision=p, use_graphs=use_graphs)
+        x, info = H.solve(b)
+        x2, info2 = H.solve(b)  # the second solve replays the cached graph
+        np.testing.assert_array_equal(x, x2)
+        out.append((x, info.iterations, info.relres))
+        H.close()
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    assert out[0][1] == out[1][1] and out[0][2] == out[1][2]
+
+
+def test_max_iter_and_tolerance(lgmod, inputs):
+    g = inputs.grid2d(40, 40)
+    b = inputs.rhs(g.n, seed=6)
+    H = lgmod.Hierarchy(g, max_iter=3)
+    x, info = H.solve(b, check=False)
+    assert info.status == lgmod.ERR_NOT_CONVERGED and info.iterations == 3 and info.relres > 1e-8
+    H.close()
+    H = lgmod.Hierarchy(g)
+    x1, i1 = H.solve(b, tol=1e-4)
+    x2, i2 = H.solve(b, tol=1e-10)
+    assert i1.relres <= 1e-4 and i2.relres <= 1e-10 and i2.iterations > i1.iterations
+    H.close()
+
+
+@pytest.mark.parametrize("name", ["chunglu_20k", "grid3d_8", "star_5000"])
+def test_degree_renumbering(lgmod, oracle, inputs, name):
+    """The renumbering is a permutation by non-increasing degree (ties by id),
+    and solves with and without it agree within the solve tolerance."""
+    g = GRAPHS[name](inputs)
+    H = lgmod.Hierarchy(g)
+    perm = H.permutation()
+    assert np.array_equal(np.sort(perm), np.arange(g.n))
+    deg = np.diff(g.rowptr)[perm]
+    assert np.all(deg[:-1] >= deg[1:])
+    same = deg[:-1] == deg[1:]
+    assert np.all(perm[:-1][same] < perm[1:][same])
+    b = inputs.rhs(g.n, seed=8)
+    x1, i1 = H.solve(b)
+    H.close()
+    H0 = lgmod.Hierarchy(g, reorder=0)
+    assert np.array_equal(H0.permutation(), np.arange(g.n))
+    x0, i0 = H0.solve(b)
+    H0.close()
+    assert relres(g, b, x1) <= 1e-8 and relres(g, b, x0) <= 1e-8
+    assert np.linalg.norm(x1 - x0) <= 1e-6 * np.linalg.norm(x0)
