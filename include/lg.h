@@ -278,6 +278,28 @@ int lg_aggregate(int64_t n, const int64_t* rowptr, const int32_t* col, const dou
                  int32_t iters, int32_t threshold, int32_t* agg, int64_t* nc, int8_t* state,
                  int32_t* votes, void* stream);
 
+/*
+ * lg_elim_select without allocation. Same inputs, outputs and results as
+ * lg_elim_select (is_f bit for bit, *nf on the host), for callers that may
+ * not allocate device memory during the call: code confined to a memory pool
+ * that must not grow, host callbacks or threads of an embedding runtime that
+ * forbid cudaMalloc, or loops that cannot afford an allocation's stall. It
+ * calls no cudaMalloc / cudaFree and no allocating library routine; its
+ * scratch (one 64-bit hash per vertex and a counter) lives in a fixed device
+ * array of the library, sized for at most 1048576 vertices (8 MiB held on
+ * every device that uses the library, until the process exits). Larger n
+ * returns LG_ERR_INVALID with a message in lg_last_error_detail().
+ *  - The first call on a device looks up the array's device address on that
+ *    device; make that first call before any stream capture.
+ *  - Every call shares the array: calls whose work overlaps on the GPU (two
+ *    host threads, or two streams) race and give wrong results. Serialise
+ *    them, e.g. on one stream.
+ *  - The paper has no counterpart; this is an interface variant of
+ *    lg_elim_select (Section 3.4).
+ */
+int lg_elim_select_noalloc(int64_t n, const int64_t* rowptr, const int32_t* col, int32_t max_degree,
+                           uint64_t seed, uint8_t* is_f, int64_t* nf, void* stream);
+
 /* ---- serving: continuous batching of solves over resident hierarchies ---- */
 typedef struct {
   double hbm_budget_bytes;  /* admission budget for resident hierarchies + in-flight workspaces */

@@ -12,6 +12,7 @@
 #include <cstddef>
 #include <cstdio>
 #include <stdexcept>
+#include <string>
 #include <utility>
 #include <vector>
 
@@ -28,6 +29,9 @@ struct Error {
 };
 
 [[noreturn]] inline void fail(int code, const char* what) { throw Error{code, what}; }
+
+// Detail of the last error on this host thread (lg_last_error_detail).
+extern thread_local std::string g_last_error;
 
 inline void check_cuda(cudaError_t e, const char* what) {
   if (e == cudaSuccess) return;

@@ -88,6 +88,7 @@ _SIGS = {
     "lg_vcycle": (C.c_int, [_P, _P, _P, _I32]),
     "lg_laplacian_apply": (C.c_int, [_I64, _P, _P, _P, _P, _P, _P]),
     "lg_elim_select": (C.c_int, [_I64, _P, _P, _I32, _U64, _P, _P, _P]),
+    "lg_elim_select_noalloc": (C.c_int, [_I64, _P, _P, _I32, _U64, _P, _P, _P]),
     "lg_strength": (C.c_int, [_I64, _P, _P, _P, _U64, _I32, _I32, _I32, _D, _P, _P]),
     "lg_aggregate": (C.c_int, [_I64, _P, _P, _P, _I32, _I32, _P, _P, _P, _P, _P]),
     "lg_kernel_launches": (C.c_uint64, []),
@@ -274,6 +275,14 @@ def lg_elim_select(n, rowptr, col, max_degree, seed, is_f, stream=None) -> int:
     nf = C.c_int64()
     _check(_load().lg_elim_select(int(n), _ptr(rowptr), _ptr(col), int(max_degree), int(seed), _ptr(is_f),
                                   C.byref(nf), _stream(stream)), "lg_elim_select")
+    return nf.value
+
+
+def lg_elim_select_noalloc(n, rowptr, col, max_degree, seed, is_f, stream=None) -> int:
+    """lg_elim_select with its scratch in a fixed device array (no allocation)."""
+    nf = C.c_int64()
+    _check(_load().lg_elim_select_noalloc(int(n), _ptr(rowptr), _ptr(col), int(max_degree), int(seed), _ptr(is_f),
+                                          C.byref(nf), _stream(stream)), "lg_elim_select_noalloc")
     return nf.value
 
 
