@@ -379,7 +379,7 @@ void bin_rows(RowPlanStore& ps, int64_t n, const int64_t* rowptr, int E, cudaStr
     p.cls_off[c] = off[c];
     p.blk_off[c] = blk;
     const int64_t rows = off[c + 1] - off[c];
-    const int64_t per_block = kRowThreads >> c;  // groups of 2^c lanes
+    const int64_t per_block = class_rows_per_block(c);
     blk += (int)((rows + per_block - 1) / per_block);
   }
   p.cls_off[kClasses] = off[kClasses];

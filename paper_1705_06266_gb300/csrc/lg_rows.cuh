@@ -5,9 +5,12 @@
 // over the row's entries, then calls an epilogue with (i, s_i). The plan
 // (lg_common.cuh) bins the rows by length: a row of class c is handled by one
 // aligned group of G = 2^c lanes, every lane taking about E entries, so the
-// groups of a warp finish together and each lane has its loads in flight at
-// once; the group reduces into its first lane, which applies the epilogue
-// with operands prefetched before the entry loop. Rows longer than kChunk
+// groups of a warp finish together. For G <= 8 a warp takes 32 rows, a group
+// working through G of them and a reduce-scatter handing each lane one
+// finished row, so the per-row work (finish, epilogue) runs on all lanes at
+// once (this matters for FP64, whose narrow pipe charges an instruction its
+// full warp time however few lanes are active); for G = 16, 32 the group
+// reduces into its first lane. Rows longer than kChunk
 // entries are cut into chunks, one block each; the last block of a row to
 // finish (a per-row ticket) adds the chunk partials in chunk order. Every
 // addition happens in an order fixed by the row lengths and the plan, never
@@ -23,6 +26,35 @@
 
 namespace lg {
 
+// Loads with L1 eviction hints: the CSR arrays are read once per pass and
+// should not take L1 lines from the gathered vector, whose entries (the
+// high-degree vertices especially) are re-read by many rows.
+__device__ __forceinline__ int32_t ld_stream(const int32_t* p) {
+  int32_t v;
+  asm("ld.global.nc.L1::no_allocate.b32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float ld_stream(const float* p) {
+  float v;
+  asm("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ double ld_stream(const double* p) {
+  double v;
+  asm("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float ld_keep(const float* p) {
+  float v;
+  asm("ld.global.nc.L1::evict_last.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ double ld_keep(const double* p) {
+  double v;
+  asm("ld.global.nc.L1::evict_last.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  return v;
+}
+
 // The Laplacian applied to x (Section 2.1: L = D - A, D_ii = sum_j w_ij).
 // FP32: difference form, sum_j w_ij (x_i - x_j), so L 1 = 0 holds exactly.
 // FP64: d_i x_i - sum_j w_ij x_j, one fused multiply-add per entry (FP64
@@ -30,16 +62,20 @@ namespace lg {
 template <typename T>
 struct LapTerm;
 
+// Each term type gives row(i) (a per-row value the entry loop needs),
+// acc(s, k, j, rv) (s plus the contribution of entry k with column j, as one
+// fused multiply-add where there is a product) and finish(i, rv, s) (the
+// row's result from its entry sum, evaluated once per row).
 template <>
 struct LapTerm<float> {
   const float* __restrict__ w;
   const float* __restrict__ x;
   const double* __restrict__ d;  // unused
   __device__ __forceinline__ float row(int64_t i) const { return __ldg(&x[i]); }
-  __device__ __forceinline__ float operator()(int64_t k, int32_t j, float xi) const {
-    return __ldg(&w[k]) * (xi - __ldg(&x[j]));
+  __device__ __forceinline__ float acc(float s, int64_t k, int32_t j, float xi) const {
+    return fmaf(ld_stream(&w[k]), xi - ld_keep(&x[j]), s);
   }
-  __device__ __forceinline__ float finish(float, float s) const { return s; }
+  __device__ __forceinline__ float finish(int64_t, float, float s) const { return s; }
 };
 
 template <>
@@ -47,11 +83,13 @@ struct LapTerm<double> {
   const double* __restrict__ w;
   const double* __restrict__ x;
   const double* __restrict__ d;
-  __device__ __forceinline__ double row(int64_t i) const { return __ldg(&d[i]) * __ldg(&x[i]); }
-  __device__ __forceinline__ double operator()(int64_t k, int32_t j, double) const {
-    return __ldg(&w[k]) * __ldg(&x[j]);
+  __device__ __forceinline__ double row(int64_t) const { return 0.0; }
+  __device__ __forceinline__ double acc(double s, int64_t k, int32_t j, double) const {
+    return fma(ld_stream(&w[k]), ld_keep(&x[j]), s);
   }
-  __device__ __forceinline__ double finish(double dx, double s) const { return dx - s; }
+  __device__ __forceinline__ double finish(int64_t i, double, double s) const {
+    return fma(__ldg(&d[i]), __ldg(&x[i]), -s);
+  }
 };
 
 // Plain gather-sum: sum_k v[idx_k] (restriction by aggregate member lists).
@@ -59,8 +97,8 @@ template <typename T>
 struct GatherTerm {
   const T* __restrict__ v;
   __device__ __forceinline__ T row(int64_t) const { return T(0); }
-  __device__ __forceinline__ T operator()(int64_t, int32_t j, T) const { return __ldg(&v[j]); }
-  __device__ __forceinline__ T finish(T, T s) const { return s; }
+  __device__ __forceinline__ T acc(T s, int64_t, int32_t j, T) const { return s + __ldg(&v[j]); }
+  __device__ __forceinline__ T finish(int64_t, T, T s) const { return s; }
 };
 
 // Weighted gather-sum: sum_k c_k v[idx_k] (transpose of the elimination prolongation).
@@ -69,44 +107,84 @@ struct WGatherTerm {
   const T* __restrict__ c;
   const T* __restrict__ v;
   __device__ __forceinline__ T row(int64_t) const { return T(0); }
-  __device__ __forceinline__ T operator()(int64_t k, int32_t j, T) const { return __ldg(&c[k]) * __ldg(&v[j]); }
-  __device__ __forceinline__ T finish(T, T s) const { return s; }
+  __device__ __forceinline__ T acc(T s, int64_t k, int32_t j, T) const { return fma(__ldg(&c[k]), __ldg(&v[j]), s); }
+  __device__ __forceinline__ T finish(int64_t, T, T s) const { return s; }
 };
 
-// Sum of a row's entries with G lanes, four loads in flight per lane.
+// Sum of a row's entries with G lanes: the column indices of four entries
+// per lane are loaded together, then their terms, accumulated into two
+// chains of fused multiply-adds.
 template <typename T, int G, class Term>
 __device__ __forceinline__ T row_sum(const Term& term, const int32_t* __restrict__ col, int64_t beg, int64_t end,
                                      int lane, T rv) {
   T s0 = T(0), s1 = T(0);
   int64_t k = beg + lane;
   for (; k + 3 * G < end; k += 4 * G) {
-    const int32_t j0 = __ldg(&col[k]), j1 = __ldg(&col[k + G]);
-    const int32_t j2 = __ldg(&col[k + 2 * G]), j3 = __ldg(&col[k + 3 * G]);
-    const T a0 = term(k, j0, rv), a1 = term(k + G, j1, rv);
-    const T a2 = term(k + 2 * G, j2, rv), a3 = term(k + 3 * G, j3, rv);
-    s0 += a0 + a2;
-    s1 += a1 + a3;
+    const int32_t j0 = ld_stream(&col[k]), j1 = ld_stream(&col[k + G]);
+    const int32_t j2 = ld_stream(&col[k + 2 * G]), j3 = ld_stream(&col[k + 3 * G]);
+    s0 = term.acc(s0, k, j0, rv);
+    s1 = term.acc(s1, k + G, j1, rv);
+    s0 = term.acc(s0, k + 2 * G, j2, rv);
+    s1 = term.acc(s1, k + 3 * G, j3, rv);
   }
-  for (; k < end; k += G) s0 += term(k, __ldg(&col[k]), rv);
+  for (; k < end; k += G) s0 = term.acc(s0, k, ld_stream(&col[k]), rv);
   return s0 + s1;
 }
 
-// One row of class G: group of G lanes, reduction into the group's lane 0.
-template <typename T, int G, class Term, class Epi>
-__device__ __forceinline__ void class_row(const RowPlan& plan, int c, int64_t b, const int64_t* __restrict__ rowptr,
-                                          const int32_t* __restrict__ col, const Term& term, const Epi& epi,
-                                          double* red) {
-  const int64_t idx = b * (kRowThreads / G) + threadIdx.x / G;
-  const int64_t lo = plan.cls_off[c], hi = plan.cls_off[c + 1];
-  const int lane = threadIdx.x & (G - 1);
-  if (lo + idx >= hi) return;  // the whole group leaves together
-  const int64_t row = plan.rows_by_class[lo + idx];
-  const int64_t beg = rowptr[row], end = rowptr[row + 1];
-  const auto pre = epi.pre(row);
-  const T rv = term.row(row);
-  T s = row_sum<T, G>(term, col, beg, end, lane, rv);
-  s = group_sum_first<G>(s, group_mask<G>(), lane);
-  if (lane == 0) epi(row, term.finish(rv, s), pre, red);
+// Rows of class G, R per group of G lanes (R divides G): the group works
+// through its R rows one per round, keeping one partial sum per round. A
+// recursive-halving exchange over the top log2(R) lane bits then leaves every
+// lane with a partial of one row (the round given by those bits), and a tree
+// over the remaining bits completes it in each of the G/R lanes of that
+// subgroup; the first of them finishes the row and applies the epilogue.
+// With R = G every lane finishes one row, so the per-row work (finish,
+// epilogue) runs on all lanes at once, which matters for FP64, whose narrow
+// pipe charges an instruction its full warp time however few lanes are
+// active. Rows of round j: list entries base + j (32/G) + group.
+template <typename T, int G, int R, class Term, class Epi>
+__device__ __forceinline__ void class_rows_batched(const RowPlan& plan, int c, int64_t b,
+                                                   const int64_t* __restrict__ rowptr,
+                                                   const int32_t* __restrict__ col, const Term& term,
+                                                   const Epi& epi, double* red) {
+  constexpr int kGroups = 32 / G;
+  constexpr int kSub = G / R;  // lanes that end up sharing one row
+  const int lane = threadIdx.x & 31;
+  const int grp = lane / G, gl = lane & (G - 1);
+  const int64_t base = (b * (kRowThreads / 32) + (threadIdx.x >> 5)) * (kGroups * R);
+  const int64_t lo = plan.cls_off[c], cnt = plan.cls_off[c + 1] - lo;
+  if (base >= cnt) return;  // the whole warp leaves together
+  T part[R];
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    const int64_t idx = base + j * kGroups + grp;
+    part[j] = T(0);
+    if (idx < cnt) {
+      const int64_t row = plan.rows_by_class[lo + idx];
+      part[j] = row_sum<T, G>(term, col, rowptr[row], rowptr[row + 1], gl, term.row(row));
+    }
+  }
+  if constexpr (G > 1) {
+    const unsigned mask = group_mask<G>();
+#pragma unroll
+    for (int h = G / 2, m = R; h >= kSub; h >>= 1, m >>= 1) {
+      const bool upper = (gl & h) != 0;
+#pragma unroll
+      for (int q = 0; q < m / 2; ++q) {
+        const T send = upper ? part[q] : part[q + m / 2];
+        const T keep = upper ? part[q + m / 2] : part[q];
+        part[q] = keep + __shfl_xor_sync(mask, send, h, G);
+      }
+    }
+#pragma unroll
+    for (int h = kSub / 2; h >= 1; h >>= 1) part[0] += __shfl_xor_sync(mask, part[0], h, G);
+  }
+  if (gl % kSub != 0) return;
+  const int64_t idx = base + (gl / kSub) * kGroups + grp;  // the row this subgroup owns
+  if (idx < cnt) {
+    const int64_t row = plan.rows_by_class[lo + idx];
+    const T rv = term.row(row);
+    epi(row, term.finish(row, rv, part[0]), epi.pre(row), red);
+  }
 }
 
 template <typename T, int NRED, class Term, class Epi>
@@ -147,7 +225,7 @@ k_rows(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, Term
           T tot = T(0);
           for (int32_t q = 0; q < cnt; ++q) tot += (T)__ldcg(&plan.partial[f0 + q]);
           plan.ticket[lr] = 0u;
-          epi(row, term.finish(rv, tot), epi.pre(row), red);
+          epi(row, term.finish(row, rv, tot), epi.pre(row), red);
         }
       }
     }
@@ -159,12 +237,12 @@ k_rows(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, Term
     for (int q = 1; q < kClasses; ++q) c += b >= plan.blk_off[q];
     const int64_t bb = b - plan.blk_off[c];
     switch (c) {
-      case 0: class_row<T, 1>(plan, 0, bb, rowptr, col, term, epi, red); break;
-      case 1: class_row<T, 2>(plan, 1, bb, rowptr, col, term, epi, red); break;
-      case 2: class_row<T, 4>(plan, 2, bb, rowptr, col, term, epi, red); break;
-      case 3: class_row<T, 8>(plan, 3, bb, rowptr, col, term, epi, red); break;
-      case 4: class_row<T, 16>(plan, 4, bb, rowptr, col, term, epi, red); break;
-      default: class_row<T, 32>(plan, 5, bb, rowptr, col, term, epi, red); break;
+      case 0: class_rows_batched<T, 1, 1>(plan, 0, bb, rowptr, col, term, epi, red); break;
+      case 1: class_rows_batched<T, 2, 2>(plan, 1, bb, rowptr, col, term, epi, red); break;
+      case 2: class_rows_batched<T, 4, 4>(plan, 2, bb, rowptr, col, term, epi, red); break;
+      case 3: class_rows_batched<T, 8, 8>(plan, 3, bb, rowptr, col, term, epi, red); break;
+      case 4: class_rows_batched<T, 16, kRowsPerGroup16>(plan, 4, bb, rowptr, col, term, epi, red); break;
+      default: class_rows_batched<T, 32, kRowsPerGroup32>(plan, 5, bb, rowptr, col, term, epi, red); break;
     }
   }
   if constexpr (NRED > 0) {

@@ -127,8 +127,8 @@ __global__ void k_cc_roots(int64_t n, int32_t* parent, uint8_t* is_root, int* er
 struct WeightTerm {
   const double* __restrict__ w;
   __device__ __forceinline__ double row(int64_t) const { return 0.0; }
-  __device__ __forceinline__ double operator()(int64_t k, int32_t, double) const { return w[k]; }
-  __device__ __forceinline__ double finish(double, double s) const { return s; }
+  __device__ __forceinline__ double acc(double s, int64_t k, int32_t, double) const { return s + w[k]; }
+  __device__ __forceinline__ double finish(int64_t, double, double s) const { return s; }
 };
 struct EpiDinv {
   double* d;
