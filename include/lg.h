@@ -238,6 +238,13 @@ int lg_profile(lg_handle h, int32_t enable);
 int lg_level_plan(lg_handle h, int32_t l, int64_t out[6]);
 int lg_profile_read(lg_handle h, int32_t level, lg_kernel_profile* out);
 
+/* One multi-column V-cycle on k right-hand sides at once (1 <= k <= 32): X =
+ * M F with F, X column-major n x k blocks (leading dimensions ldf, ldx >= n,
+ * host or device), the same preconditioner as lg_vcycle applied to every
+ * column, run as SpMM passes. */
+int lg_vcycle_batch(lg_handle h, int32_t k, const double* F, int64_t ldf, double* X, int64_t ldx,
+                    int32_t precision);
+
 /* ---- single steps on caller data (DEVICE pointers only, on `stream`) ----
  * These run one stage of the setup on an arbitrary graph so that each stage
  * can be checked on its own. The graph must satisfy the conventions above

@@ -37,6 +37,7 @@ Hier::~Hier() {
   // every stream-ordered buffer goes back on the handle's stream before that
   // stream is destroyed
   ws.reset();
+  wsb.reset();
   levels.clear();
   dev_err.release();
   perm.release();
@@ -216,7 +217,11 @@ int lg_solve_batch(lg_handle hh, int32_t k, const double* B, int64_t ldb, double
   lg::DBuf<double> Bd((size_t)n * k, s), Xd((size_t)n * k, s);
   for (int c = 0; c < k; ++c)
     LG_CUDA(cudaMemcpyAsync(Bd.get() + (size_t)c * n, B + (size_t)c * ldb, sizeof(double) * n, cudaMemcpyDefault, s));
-  int st = lg::pcg_solve_batch(h, *h.ws, k, Bd.get(), Xd.get(), tol, h.opts.precision, s, infos);
+  if (k > 1 && (!h.wsb || h.wsb->k < k)) {
+    h.wsb.reset();
+    h.wsb = lg::make_workspace(h, k, s);
+  }
+  int st = lg::pcg_solve_batch(h, k > 1 ? *h.wsb : *h.ws, k, Bd.get(), Xd.get(), tol, h.opts.precision, s, infos);
   for (int c = 0; c < k; ++c)
     LG_CUDA(cudaMemcpyAsync(X + (size_t)c * ldx, Xd.get() + (size_t)c * n, sizeof(double) * n, cudaMemcpyDefault, s));
   LG_CUDA(cudaStreamSynchronize(s));
@@ -371,6 +376,30 @@ int lg_profile_read(lg_handle hh, int32_t level, lg_kernel_profile* out) {
     out->bytes += p.stats[l].bytes;
     out->launches += p.stats[l].launches;
   }
+  return LG_OK;
+  LG_API_END
+}
+
+int lg_vcycle_batch(lg_handle hh, int32_t k, const double* F, int64_t ldf, double* X, int64_t ldx,
+                    int32_t precision) {
+  if (!hh || !F || !X || k < 1 || k > lg::kMaxCols || (precision != LG_FP64 && precision != LG_FP32_HIER))
+    return LG_ERR_INVALID;
+  lg::Hier& h = *H(hh);
+  const int64_t n = h.levels[0]->n;
+  if (ldf < n || ldx < n) return LG_ERR_INVALID;
+  LG_API_BEGIN
+  cudaStream_t s = h.stream;
+  if (!h.wsb || h.wsb->k < k) {
+    h.wsb.reset();
+    h.wsb = lg::make_workspace(h, k < 2 ? 2 : k, s);
+  }
+  lg::DBuf<double> Fd((size_t)n * k, s), Xd((size_t)n * k, s);
+  for (int c = 0; c < k; ++c)
+    LG_CUDA(cudaMemcpyAsync(Fd.get() + (size_t)c * n, F + (size_t)c * ldf, sizeof(double) * n, cudaMemcpyDefault, s));
+  lg::vcycle_apply_batch(h, *h.wsb, k, Fd.get(), Xd.get(), precision, s);
+  for (int c = 0; c < k; ++c)
+    LG_CUDA(cudaMemcpyAsync(X + (size_t)c * ldx, Xd.get() + (size_t)c * n, sizeof(double) * n, cudaMemcpyDefault, s));
+  LG_CUDA(cudaStreamSynchronize(s));
   return LG_OK;
   LG_API_END
 }

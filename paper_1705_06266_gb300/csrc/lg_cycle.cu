@@ -585,7 +585,7 @@ std::unique_ptr<Workspace> make_workspace(Hier& h, int k, cudaStream_t s) {
   ws->q.alloc(n0, s, c);
   ws->io.alloc(n0, s, c);
   max_grid = std::max<int64_t>(max_grid, kSMs * 8);
-  ws->partials.alloc((size_t)max_grid * 8 * k, s, c);
+  ws->partials.alloc((size_t)max_grid * (k > 1 ? 5 * kMaxCols : 8), s, c);
   ws->tickets.alloc(4, s, c);
   LG_CUDA(cudaMemsetAsync(ws->tickets.get(), 0, 4 * sizeof(unsigned), s));
   ws->scal.alloc((size_t)kNScal * k, s, c);
@@ -747,19 +747,6 @@ int pcg_solve(Hier& h, Workspace& ws, const double* b, double* x, double tol, in
     info->nnz = h.nnz0;
   }
   return status;
-}
-
-int pcg_solve_batch(Hier& h, Workspace& ws, int k, const double* B, double* X, double tol, int precision,
-                    cudaStream_t s, lg_info* infos) {
-  int worst = LG_OK;
-  const int64_t n = h.levels[0]->n;
-  for (int c = 0; c < k; ++c) {
-    lg_info inf{};
-    int st = pcg_solve(h, ws, B + (size_t)c * n, X + (size_t)c * n, tol, precision, s, &inf);
-    if (infos) infos[c] = inf;
-    if (st != LG_OK && worst == LG_OK) worst = st;
-  }
-  return worst;
 }
 
 }  // namespace lg

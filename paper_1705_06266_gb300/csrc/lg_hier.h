@@ -139,6 +139,7 @@ struct Workspace {
   double* host_scal = nullptr;         // pinned mirror of the scalars read by the host
   int64_t bytes = 0;
   Prof prof;
+  std::shared_ptr<void> batch;          // SpMM plans of multi-column solves (lg_batch.cu)
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // captured preconditioned iteration per precision
   ~Workspace();
 };
@@ -154,6 +155,7 @@ struct Hier {
   std::vector<std::unique_ptr<Level>> levels;
   std::vector<Cheb> cheb;               // per level (aggregation levels only)
   std::unique_ptr<Workspace> ws;        // default workspace of lg_solve
+  std::unique_ptr<Workspace> wsb;       // workspace of lg_solve_batch (widest batch so far)
   DBuf<int> dev_err;                    // device error word
   DBuf<int32_t> perm;                   // level-0 vertex i is the caller's vertex perm[i]
   ~Hier();
@@ -180,6 +182,7 @@ void vcycle_apply(Hier& h, Workspace& ws, const double* f, double* x, int precis
 // uses stride-1 columns of length n). Fills info.
 int pcg_solve(Hier& h, Workspace& ws, const double* b, double* x, double tol, int precision,
               cudaStream_t s, lg_info* info);
+void vcycle_apply_batch(Hier& h, Workspace& ws, int k, const double* F, double* X, int precision, cudaStream_t s);
 int pcg_solve_batch(Hier& h, Workspace& ws, int k, const double* B, double* X, double tol, int precision,
                     cudaStream_t s, lg_info* infos);
 

@@ -86,6 +86,7 @@ _SIGS = {
     "lg_coarsest_pinv": (C.c_int, [_P, _P]),
     "lg_permutation": (C.c_int, [_P, _P]),
     "lg_vcycle": (C.c_int, [_P, _P, _P, _I32]),
+    "lg_vcycle_batch": (C.c_int, [_P, _I32, _P, _I64, _P, _I64, _I32]),
     "lg_laplacian_apply": (C.c_int, [_I64, _P, _P, _P, _P, _P, _P]),
     "lg_elim_select": (C.c_int, [_I64, _P, _P, _I32, _U64, _P, _P, _P]),
     "lg_elim_select_noalloc": (C.c_int, [_I64, _P, _P, _I32, _U64, _P, _P, _P]),
@@ -383,6 +384,27 @@ class Hierarchy:
             x = np.zeros(self.n)
         info = lg_solve(self.h, b, x, tol, check=check)
         return x, info
+
+    def solve_batch(self, B, tol=1e-8, precision=None, check=True):
+        """B: [n][k] (one right-hand side per column). Returns (X [n][k], infos)."""
+        if precision is not None:
+            lg_set_precision(self.h, precision)
+        B = np.asarray(B, dtype=np.float64)
+        k = B.shape[1]
+        Bc = np.ascontiguousarray(B.T)  # column-major n x k, leading dimension n
+        Xc = np.zeros_like(Bc)
+        infos = lg_solve_batch(self.h, k, Bc, self.n, Xc, self.n, tol, check=check)
+        return np.ascontiguousarray(Xc.T), infos
+
+    def vcycle_batch(self, F, precision=FP64):
+        """F: [n][k]. One multi-column V-cycle; returns X [n][k]."""
+        F = np.asarray(F, dtype=np.float64)
+        k = F.shape[1]
+        Fc = np.ascontiguousarray(F.T)
+        Xc = np.zeros_like(Fc)
+        _check(_load().lg_vcycle_batch(self.h, int(k), _ptr(Fc), self.n, _ptr(Xc), self.n, int(precision)),
+               "lg_vcycle_batch")
+        return np.ascontiguousarray(Xc.T)
 
     def vcycle(self, f, precision=FP64):
         x = np.zeros(self.n)

@@ -313,3 +313,59 @@ def test_degree_renumbering(lgmod, oracle, inputs, name):
     H0.close()
     assert relres(g, b, x1) <= 1e-8 and relres(g, b, x0) <= 1e-8
     assert np.linalg.norm(x1 - x0) <= 1e-6 * np.linalg.norm(x0)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("k", [2, 5, 32])
+@pytest.mark.parametrize("name", ["chunglu_20k", "grid3d_8", "star_5000"])
+def test_solve_batch_matches_single(lgmod, oracle, inputs, name, k, prec):
+    """Multi-RHS solve (SpMM cycles, per-column CG scalars): every column meets
+    the tolerance and agrees with the single-RHS solve of that column."""
+    g = GRAPHS[name](inputs)
+    B = inputs.rhs(g.n, k, seed=11)
+    p = lgmod.FP64 if prec == "fp64" else lgmod.FP32_HIER
+    H = lgmod.Hierarchy(g, precision=p)
+    X, infos = H.solve_batch(B)
+    ref_pcg = oracle.Hierarchy(g)
+    for c in range(k):
+        assert infos[c].status == lgmod.OK and infos[c].relres <= 1e-8
+        assert relres(g, B[:, c], X[:, c]) <= 1e-8
+        xs, inf = H.solve(np.ascontiguousarray(B[:, c]))
+        assert abs(infos[c].iterations - inf.iterations) <= 1
+        assert np.linalg.norm(X[:, c] - xs) <= 1e-6 * np.linalg.norm(xs)
+        if c < 2:
+            xr, st, _, _ = ref_pcg.pcg(np.ascontiguousarray(B[:, c]), tol=1e-12, maxit=1000)
+            assert np.linalg.norm(X[:, c] - xr) <= 1e-6 * np.linalg.norm(xr)
+    H.close()
+
+
+def test_batch_columns_independent(lgmod, inputs):
+    g = inputs.grid2d(48, 48)
+    B = inputs.rhs(g.n, 4, seed=12)
+    B[:, 1] = 0.0      # zero right-hand side: done at once
+    B[:, 2] = 3.0      # constant: zero after the projection
+    B[:, 3] *= 1e-6    # tiny but nonzero: same relative tolerance
+    H = lgmod.Hierarchy(g)
+    X, infos = H.solve_batch(B)
+    assert [i.status for i in infos] == [lgmod.OK] * 4
+    assert infos[1].iterations == 0 and infos[2].iterations == 0
+    assert np.all(X[:, 1] == 0) and np.all(X[:, 2] == 0)
+    assert infos[0].iterations > 0 and abs(infos[3].iterations - infos[0].iterations) <= 1
+    assert relres(g, np.ascontiguousarray(B[:, 3]), X[:, 3]) <= 1e-8
+    H.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", ["chunglu_20k", "grid3d_8"])
+def test_vcycle_batch_matches_single(lgmod, inputs, name, prec):
+    """The multi-column cycle applies the same preconditioner to every column."""
+    g = GRAPHS[name](inputs)
+    F = inputs.rhs(g.n, 3, seed=13)
+    p = lgmod.FP64 if prec == "fp64" else lgmod.FP32_HIER
+    H = lgmod.Hierarchy(g)
+    X = H.vcycle_batch(F, p)
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    for c in range(3):
+        xs = H.vcycle(np.ascontiguousarray(F[:, c]), p)
+        assert np.linalg.norm(X[:, c] - xs) <= tol * np.linalg.norm(xs), c
+    H.close()
