@@ -50,6 +50,13 @@ def parse():
     ap.add_argument("--workload", default="chung_lu_1m")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-multi-rhs", action="store_true")
+    ap.add_argument("--multi-rhs-k", type=int, default=32)
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-graphs", type=int, default=64)
+    ap.add_argument("--serve-nmax", type=int, default=262144)
+    ap.add_argument("--serve-requests", type=int, default=1000)
+    ap.add_argument("--serve-load", type=float, default=0.8)
     return ap.parse_args()
 
 
@@ -188,6 +195,110 @@ def cpu_baseline(workload_name, g, b):
     }
 
 
+def multi_rhs_leg(lg, inputs, torch, dev, k):
+    """k right-hand sides solved together (FP32 hierarchy, SpMM cycles, FP64
+    outer CG) against the same k solved one after another, on the R-MAT scale
+    20 graph and the 128^3 grid. Device-resident B and X; each figure is the
+    solve's own event time."""
+    out = {}
+    for name in ("rmat_20", "grid3d_128"):
+        g = inputs.workload(name)
+        B = inputs.rhs(g.n, k, seed=3)
+        Bd = torch.from_numpy(np.ascontiguousarray(B.T)).to(dev)  # column-major n x k
+        Xd = torch.zeros_like(Bd)
+        torch.cuda.synchronize()
+        h = lg.lg_setup(g.n, g.rowptr, g.col, g.w, lg.options())
+        lg.lg_set_precision(h, lg.FP32_HIER)
+        lg.lg_solve_batch(h, k, Bd, g.n, Xd, g.n, TOL)  # warm-up (plans, workspace)
+        lg.lg_solve(h, Bd[0], Xd[0], TOL)
+        torch.cuda.synchronize()
+        infos = lg.lg_solve_batch(h, k, Bd, g.n, Xd, g.n, TOL)
+        batch_ms = infos[0].solve_ms
+        seq_ms, seq_it = 0.0, []
+        for c in range(k):
+            inf = lg.lg_solve(h, Bd[c], Xd[c], TOL)
+            seq_ms += inf.solve_ms
+            seq_it.append(inf.iterations)
+        lg.lg_destroy(h)
+        out[name] = {
+            "n": g.n, "nnz": g.nnz, "k": k,
+            "batched_ms": batch_ms, "batched_nnz_per_s": g.nnz * k / (batch_ms * 1e-3),
+            "batched_iterations_max": max(i.iterations for i in infos),
+            "batched_relres_max": max(i.relres for i in infos),
+            "sequential_ms": seq_ms, "sequential_nnz_per_s": g.nnz * k / (seq_ms * 1e-3),
+            "sequential_iterations_max": max(seq_it),
+            "speedup": seq_ms / batch_ms,
+        }
+    return out
+
+
+def serve_leg(lg, inputs, args):
+    """Continuous batching over resident hierarchies: a burst of requests
+    measures the saturation rate, then Poisson arrivals at a fraction of it
+    give the latency percentiles (submission to completion, host B and X)."""
+    graphs = inputs.serving_mix(args.serve_graphs, 1000, args.serve_nmax, seed=5)
+    hs = [lg.Hierarchy(g) for g in graphs]
+    rng = np.random.Generator(np.random.PCG64(11))
+    # one column-major block of 8 right-hand sides per graph; a request of k takes its first k
+    blocks = [np.ascontiguousarray(inputs.rhs(g.n, 8, seed=20 + q).T) for q, g in enumerate(graphs)]
+
+    def requests(count):
+        return [(int(rng.integers(0, len(graphs))), int(rng.integers(1, 9))) for _ in range(count)]
+
+    def run(reqs, rate):
+        sv = lg.lg_serve_create(lg.serve_options(slots=8, precision=lg.FP32_HIER, hbm_budget_bytes=120e9))
+        for H in hs:
+            lg.lg_serve_register(sv, H.h)
+        live, rhs, failed = {}, 0, 0
+        t0 = time.perf_counter()
+        arrival = 0.0
+        for gi, k in reqs:
+            if rate:
+                arrival += rng.exponential(1.0 / rate)
+                while time.perf_counter() - t0 < arrival:
+                    for t in list(live):
+                        done, info = lg.lg_serve_poll(sv, t)
+                        if done:
+                            failed += info.status != lg.OK
+                            del live[t]
+            X = np.empty((k, graphs[gi].n))
+            t = lg.lg_serve_submit(sv, hs[gi].h, k, blocks[gi][:k], X, TOL)
+            live[t] = X
+            rhs += k
+        while live:
+            for t in list(live):
+                done, info = lg.lg_serve_poll(sv, t)
+                if done:
+                    failed += info.status != lg.OK
+                    del live[t]
+        span = time.perf_counter() - t0
+        st = lg.lg_serve_stats(sv)
+        lg.lg_serve_destroy(sv)
+        return st, span, rhs, failed
+
+    burst = requests(max(100, args.serve_requests // 4))
+    st_b, span_b, rhs_b, fail_b = run(burst, None)
+    sat_rps = len(burst) / span_b
+    rate = args.serve_load * sat_rps
+    st, span, rhs, failed = run(requests(args.serve_requests), rate)
+    for H in hs:
+        H.close()
+    return {
+        "p50_ms": st.p50_ms, "p99_ms": st.p99_ms, "mean_ms": st.mean_ms, "max_ms": st.max_ms,
+        "solves_per_s": rhs / span, "requests_per_s": args.serve_requests / span,
+        "offered_rps": rate, "saturation_rps": sat_rps, "saturation_solves_per_s": rhs_b / span_b,
+        "saturation_p50_ms": st_b.p50_ms, "saturation_p99_ms": st_b.p99_ms,
+        "completed": int(st.completed), "failed": int(st.failed + failed + st_b.failed + fail_b),
+        "requests": args.serve_requests, "graphs": len(graphs),
+        "vertices_resident": int(sum(g.n for g in graphs)), "nnz_resident": int(sum(g.nnz for g in graphs)),
+        "resident_bytes": st.resident_bytes,
+        "config": f"{len(graphs)} resident graphs, n log-uniform in [1000, {args.serve_nmax}], type uniform over "
+                  f"2D grid / 3D grid / Chung-Lu 2.1 / R-MAT ef16; k uniform in 1..8; tol 1e-8; FP32 hierarchy; "
+                  f"8 slots; HBM budget 120 GB; Poisson arrivals at {args.serve_load} x the burst saturation "
+                  f"rate; latency = submission to completion with host B and X",
+    }
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -314,6 +425,10 @@ def main():
         lg.lg_destroy(h2)
         lg.lg_destroy(h)
 
+        # the other two workloads the metric names, after the timed region
+        multi = None if args.no_multi_rhs else multi_rhs_leg(lg, inputs, torch, dev, args.multi_rhs_k)
+        serve = None if args.no_serve else serve_leg(lg, inputs, args)
+
     setup_ms = sum(r[0].setup_ms for r in recs) / len(recs)
     solve64_ms = sum(r[1].solve_ms for r in recs) / len(recs)
     solve32_ms = sum(r[2].solve_ms for r in recs) / len(recs)
@@ -391,6 +506,10 @@ def main():
         "gpu_launches": launches,
         "wall_s_timed": wall,
     }
+    if multi is not None:
+        line["multi_rhs"] = multi
+    if serve is not None:
+        line["serve"] = serve
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, g, b)
     print(json.dumps(line), flush=True)

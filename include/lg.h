@@ -345,6 +345,12 @@ int lg_serve_submit(lg_server_t s, lg_handle h, int32_t k, const double* B, doub
  * solve_ms). A ticket can be polled done once; later polls return LG_ERR_INVALID. */
 int lg_serve_poll(lg_server_t s, uint64_t ticket, int32_t* done, lg_info* info);
 
+/* Device bytes the server reserves from its budget while a request of k
+ * right-hand sides on h runs (its solve workspace and staging). A request is
+ * admitted only when the registered hierarchies plus the requests already
+ * running plus this figure fit the budget. */
+int lg_serve_request_bytes(lg_handle h, int32_t k, double* bytes);
+
 /* Latency and throughput statistics over completed requests. */
 int lg_serve_stats(lg_server_t s, lg_serve_stats_t* st);
 

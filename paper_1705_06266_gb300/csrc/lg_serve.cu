@@ -74,7 +74,7 @@ static double workspace_bytes(const Hier& h, int k) {
     b += nv * vecs * (8.0 + 4.0);
     b += (double)(L->plan.plan.nchunks + L->mem_plan.plan.nchunks + L->pt_plan.plan.nchunks) * 8.0 * k;
   }
-  b += (double)h.levels[0]->n * k * 8.0 * 9.0;  // Krylov vectors + staging
+  b += (double)h.levels[0]->n * k * 8.0 * 11.0;  // Krylov vectors, transposes, the slot's B and X
   return b + (1 << 20);
 }
 
@@ -251,6 +251,12 @@ int lg_serve_poll(lg_server_t s, uint64_t ticket, int32_t* done, lg_info* info) 
     sv->requests.erase(it);
     delete rq;
   }
+  return LG_OK;
+}
+
+int lg_serve_request_bytes(lg_handle hh, int32_t k, double* bytes) {
+  if (!hh || !bytes || k < 1 || k > lg::kMaxCols) return LG_ERR_INVALID;
+  *bytes = lg::workspace_bytes(*reinterpret_cast<lg::Hier*>(hh), k);
   return LG_OK;
 }
 

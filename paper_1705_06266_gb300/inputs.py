@@ -24,6 +24,8 @@ from __future__ import annotations
 
 import dataclasses
 
+import math
+
 import numpy as np
 
 _M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
@@ -222,6 +224,30 @@ def rhs(n: int, k: int = 1, *, seed: int = 2) -> np.ndarray:
     b = rng.standard_normal((n, k))
     b -= b.mean(axis=0, keepdims=True)
     return np.ascontiguousarray(b[:, 0]) if k == 1 else np.ascontiguousarray(b)
+
+
+def serving_mix(count: int, nmin: int, nmax: int, *, seed: int = 5) -> list[Graph]:
+    """Graphs of a serving workload: sizes log-uniform in [nmin, nmax] vertices,
+    type uniform over 2D grid, 3D grid, Chung-Lu (exponent 2.1, 5 sampled edges
+    per vertex) and R-MAT (edge factor 16, scale rounded to the size). Sizes
+    are targets: grids round to whole sides, generated graphs keep their
+    largest component."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for q in range(count):
+        n = int(round(math.exp(rng.uniform(math.log(nmin), math.log(nmax)))))
+        kind = int(rng.integers(0, 4))
+        if kind == 0:
+            side = max(2, int(round(math.sqrt(n))))
+            out.append(grid2d(side, side))
+        elif kind == 1:
+            side = max(2, int(round(n ** (1.0 / 3.0))))
+            out.append(grid3d(side, side, side))
+        elif kind == 2:
+            out.append(chung_lu(n, m_target=5 * n, seed=1000 + q))
+        else:
+            out.append(rmat(max(6, int(round(math.log2(n)))), seed=1000 + q))
+    return out
 
 
 # The workloads named by the benchmark, with their fixed seeds.

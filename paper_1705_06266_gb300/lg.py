@@ -102,6 +102,7 @@ _SIGS = {
     "lg_serve_submit": (C.c_int, [_P, _P, _I32, _P, _P, _D, _P]),
     "lg_serve_poll": (C.c_int, [_P, _U64, _P, _P]),
     "lg_serve_stats": (C.c_int, [_P, _P]),
+    "lg_serve_request_bytes": (C.c_int, [_P, _I32, _P]),
     "lg_serve_destroy": (None, [_P]),
 }
 
@@ -338,6 +339,69 @@ def lg_serve_stats(s) -> ServeStats:
 
 def lg_serve_destroy(s):
     _load().lg_serve_destroy(s)
+
+
+def lg_serve_request_bytes(h, k: int) -> float:
+    b = C.c_double()
+    _check(_load().lg_serve_request_bytes(h, int(k), C.byref(b)), "lg_serve_request_bytes")
+    return b.value
+
+
+class Server:
+    """A continuous-batching solve server (lg_serve_*). Right-hand sides are
+    [n][k] numpy arrays; the column-major copies handed to the server are kept
+    alive here until the request is polled done."""
+
+    def __init__(self, **kw):
+        self.s = lg_serve_create(serve_options(**kw))
+        self._live = {}
+
+    def register(self, H):
+        lg_serve_register(self.s, H.h)
+
+    def submit(self, H, B, tol=1e-8) -> int:
+        B = np.asarray(B, dtype=np.float64)
+        if B.ndim == 1:
+            B = B[:, None]
+        Bc = np.ascontiguousarray(B.T)
+        Xc = np.zeros_like(Bc)
+        t = lg_serve_submit(self.s, H.h, B.shape[1], Bc, Xc, tol)
+        self._live[t] = (Bc, Xc)
+        return t
+
+    def poll(self, ticket):
+        """(X [n][k], info) once done, else (None, None)."""
+        done, info = lg_serve_poll(self.s, ticket)
+        if not done:
+            return None, None
+        _, Xc = self._live.pop(ticket)
+        return np.ascontiguousarray(Xc.T), info
+
+    def wait(self, ticket, timeout=120.0):
+        import time
+        t0 = time.monotonic()
+        while True:
+            X, info = self.poll(ticket)
+            if X is not None:
+                return X, info
+            if time.monotonic() - t0 > timeout:
+                raise TimeoutError(f"request {ticket} not done after {timeout} s")
+            time.sleep(2e-4)
+
+    def stats(self) -> ServeStats:
+        return lg_serve_stats(self.s)
+
+    def close(self):
+        if getattr(self, "s", None):
+            lg_serve_destroy(self.s)
+            self.s = None
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Hierarchy:

@@ -233,6 +233,20 @@ def test_edge_cases(lgmod, inputs):
     with pytest.raises(lgmod.LGError) as e:
         lgmod.Hierarchy(inputs.Graph(g.n, g.rowptr, badc, g.w))
     assert e.value.status == lgmod.ERR_INVALID
+    # a self-loop, a repeated column, a negative weight
+    for mutate in ("self", "dup", "neg"):
+        c2, w2 = g.col.copy(), g.w.copy()
+        r = 55  # an interior vertex with four neighbours
+        k0 = g.rowptr[r]
+        if mutate == "self":
+            c2[k0] = r
+        elif mutate == "dup":
+            c2[k0 + 1] = c2[k0]
+        else:
+            w2[k0] = -w2[k0]
+        with pytest.raises(lgmod.LGError) as e:
+            lgmod.Hierarchy(inputs.Graph(g.n, g.rowptr, c2, w2))
+        assert e.value.status == lgmod.ERR_INVALID, mutate
 
 
 def test_deterministic(lgmod, inputs):

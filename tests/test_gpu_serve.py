@@ -1,0 +1,177 @@
+"""The continuous-batching server (lg_serve_*).
+
+Requests on graphs of different sizes arrive while others are running; each
+must be admitted as slots and budget free up, overlap on the device with the
+others, and give the same result as when it runs alone. The served solves run
+the same kernels with the same launch plans whatever else is in flight and
+every reduction is in a fixed order, so "the same" is bitwise here; each
+result is also checked for a true relative residual <= 1e-8 recomputed with
+scipy.
+"""
+
+import time
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+from scipy.sparse.csgraph import laplacian
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-8
+
+GRAPHS = {
+    "grid2d_40": lambda I: I.grid2d(40, 40),
+    "grid3d_12": lambda I: I.grid3d(12, 12, 12),
+    "chunglu_30k": lambda I: I.chung_lu(30000, m_target=150000, seed=5),
+    "rmat_13": lambda I: I.rmat(13, seed=4),
+}
+
+
+def rhs2(inputs, n, k, seed):
+    return inputs.rhs(n, k, seed=seed).reshape(n, k)
+
+
+def relres_cols(g, B, X):
+    A = laplacian(sp.csr_matrix((g.w, g.col, g.rowptr), shape=(g.n, g.n)))
+    Bm = B - B.mean(axis=0)
+    return np.linalg.norm(Bm - A @ X, axis=0) / np.linalg.norm(Bm, axis=0)
+
+
+@pytest.fixture(scope="module")
+def graphs(lgmod, inputs):
+    out = {}
+    for name, make in GRAPHS.items():
+        g = make(inputs)
+        out[name] = (g, lgmod.Hierarchy(g))
+    yield out
+    for _, H in out.values():
+        H.close()
+
+
+def request_mix(graphs, inputs, count, seed):
+    rng = np.random.default_rng(seed)
+    names = list(graphs)
+    reqs = []
+    for q in range(count):
+        name = names[q % len(names)]
+        k = int(rng.integers(1, 5))
+        reqs.append((name, rhs2(inputs, graphs[name][0].n, k, 100 + q)))
+    order = rng.permutation(count)
+    return [reqs[i] for i in order]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_serve_same_alone_and_in_mix(lgmod, inputs, graphs, prec):
+    p = lgmod.FP64 if prec == "fp64" else lgmod.FP32_HIER
+    reqs = request_mix(graphs, inputs, 12, seed=7)
+
+    alone = []
+    sv = lgmod.Server(slots=1, precision=p)
+    for _, H in graphs.values():
+        sv.register(H)
+    for name, B in reqs:  # one at a time: nothing else on the device
+        t = sv.submit(graphs[name][1], B, TOL)
+        X, info = sv.wait(t)
+        assert info.status == lgmod.OK
+        alone.append(X)
+    sv.close()
+
+    sv = lgmod.Server(slots=4, precision=p)
+    for _, H in graphs.values():
+        sv.register(H)
+    tickets = [sv.submit(graphs[name][1], B, TOL) for name, B in reqs]  # all in flight together
+    mixed = [sv.wait(t) for t in tickets]
+    st = sv.stats()
+    sv.close()
+
+    assert st.completed == len(reqs) and st.failed == 0
+    for (name, B), Xa, (Xm, info) in zip(reqs, alone, mixed):
+        assert info.status == lgmod.OK
+        assert np.array_equal(Xa, Xm), name
+        assert relres_cols(graphs[name][0], B, Xm).max() <= TOL * 1.0001
+        assert np.abs(Xm.mean(axis=0)).max() <= 1e-12 * np.abs(Xm).max()
+
+
+def test_serve_short_request_overtakes_long(lgmod, inputs):
+    """A short request submitted right after a long one finishes first: it is
+    admitted into a free slot while the long one is still on the device."""
+    big = inputs.chung_lu(300000, m_target=2000000, seed=9)
+    small = inputs.grid2d(32, 32)
+    Hb, Hs = lgmod.Hierarchy(big), lgmod.Hierarchy(small)
+    sv = lgmod.Server(slots=2, precision=lgmod.FP64)
+    sv.register(Hb)
+    sv.register(Hs)
+    Bb = rhs2(inputs, big.n, 8, 1)
+    Bs = rhs2(inputs, small.n, 1, 2)
+    tb = sv.submit(Hb, Bb, TOL)
+    ts = sv.submit(Hs, Bs, TOL)
+    Xs, infs = sv.wait(ts)
+    Xb, infb = sv.wait(tb)
+    sv.close()
+    assert infs.status == lgmod.OK and infb.status == lgmod.OK
+    assert infs.solve_ms < infb.solve_ms  # latency from submission
+    assert relres_cols(small, Bs, Xs).max() <= TOL * 1.0001
+    assert relres_cols(big, Bb, Xb).max() <= TOL * 1.0001
+    Hb.close()
+    Hs.close()
+
+
+def test_serve_admission_budget(lgmod, inputs, graphs):
+    """With a budget that holds the hierarchies and one request's workspace,
+    requests run one at a time (never two in flight) and all complete."""
+    g, H = graphs["chunglu_30k"]
+    hb, _ = lgmod.lg_hier_bytes(H.h)
+    req = lgmod.lg_serve_request_bytes(H.h, 2)
+    assert req > 0
+    sv = lgmod.Server(slots=4, precision=lgmod.FP32_HIER, hbm_budget_bytes=float(hb + 1.5 * req))
+    sv.register(H)
+    assert sv.stats().resident_bytes == hb
+    Bs = [rhs2(inputs, g.n, 2, 30 + q) for q in range(6)]
+    tickets = [sv.submit(H, B, TOL) for B in Bs]
+    max_running = 0
+    results = {}
+    t0 = time.monotonic()
+    while len(results) < len(tickets) and time.monotonic() - t0 < 120:
+        max_running = max(max_running, sv.stats().running)
+        for t in tickets:
+            if t not in results:
+                X, info = sv.poll(t)
+                if X is not None:
+                    results[t] = (X, info)
+    st = sv.stats()
+    # a request that could never fit the budget is refused at submission
+    with pytest.raises(lgmod.LGError) as e:
+        sv.submit(H, inputs.rhs(g.n, 32, seed=1), TOL)
+    assert e.value.status == lgmod.ERR_NOMEM
+    sv.close()
+    assert len(results) == len(tickets)
+    assert max_running <= 1
+    assert st.completed == len(tickets) and st.failed == 0
+    assert 0 < st.p50_ms <= st.p99_ms <= st.max_ms
+    for t, B in zip(tickets, Bs):
+        X, info = results[t]
+        assert info.status == lgmod.OK
+        assert relres_cols(g, B, X).max() <= TOL * 1.0001
+
+
+def test_serve_errors(lgmod, inputs, graphs):
+    g, H = graphs["grid2d_40"]
+    sv = lgmod.Server(slots=1)
+    with pytest.raises(lgmod.LGError) as e:  # not registered
+        sv.submit(H, inputs.rhs(g.n, 1, seed=1), TOL)
+    assert e.value.status == lgmod.ERR_INVALID
+    with pytest.raises(lgmod.LGError):
+        lgmod.lg_serve_poll(sv.s, 12345)  # unknown ticket
+    sv.register(H)
+    t = sv.submit(H, inputs.rhs(g.n, 1, seed=1), TOL)
+    sv.wait(t)
+    with pytest.raises(lgmod.LGError):
+        lgmod.lg_serve_poll(sv.s, t)  # a ticket is polled done once
+    sv.close()
+    # the budget refuses a hierarchy that does not fit
+    sv = lgmod.Server(slots=1, hbm_budget_bytes=1000.0)
+    with pytest.raises(lgmod.LGError) as e:
+        sv.register(H)
+    assert e.value.status == lgmod.ERR_NOMEM
+    sv.close()
