@@ -169,10 +169,13 @@ void run_laplacian_apply(int64_t n, const int64_t* rowptr, const int32_t* col, c
                          const double* x, double* y, cudaStream_t s);
 int64_t run_elim_select(int64_t n, const int64_t* rowptr, const int32_t* col, int max_degree,
                         uint64_t seed, uint8_t* is_f, cudaStream_t s);
+// bins / dinv: the level's own (setup), or null to derive them from the CSR.
 void run_strength(int64_t n, const int64_t* rowptr, const int32_t* col, const double* w, uint64_t seed,
-                  int level, int m, int sweeps, double omega, double* S, cudaStream_t s);
+                  int level, int m, int sweeps, double omega, double* S, cudaStream_t s,
+                  const RowBins* bins = nullptr, const double* dinv = nullptr);
 int64_t run_aggregate(int64_t n, const int64_t* rowptr, const int32_t* col, const double* S, int iters,
-                      int threshold, int32_t* agg, int8_t* state, int32_t* votes, cudaStream_t s);
+                      int threshold, int32_t* agg, int8_t* state, int32_t* votes, cudaStream_t s,
+                      const RowBins* bins = nullptr);
 
 // ---- solve (lg_cycle.cu) ----
 std::unique_ptr<Workspace> make_workspace(Hier& h, int k, cudaStream_t s);

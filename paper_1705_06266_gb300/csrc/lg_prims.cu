@@ -387,6 +387,42 @@ void bin_rows(RowPlanStore& ps, int64_t n, const int64_t* rowptr, int E, cudaStr
   p.rows_by_class = ps.rows_by_class.get();
 }
 
+RowBins bins_of(const RowPlan& p, int64_t n) {
+  RowBins b;
+  b.rows = p.rows_by_class;
+  for (int c = 0; c <= kClasses; ++c) b.off[c] = p.cls_off[c];
+  b.off[kClasses + 1] = n;
+  int blk = (int)(n - p.cls_off[kClasses]);  // one block per long row
+  for (int c = kClasses - 1; c >= 0; --c) {
+    b.blk[c] = blk;
+    const int64_t per = kEachThreads >> c;
+    blk += (int)((b.off[c + 1] - b.off[c] + per - 1) / per);
+  }
+  b.grid = blk;
+  return b;
+}
+
+void make_bins(RowBinsStore& b, int64_t n, const int64_t* rowptr, cudaStream_t s) {
+  int64_t off[kClasses + 1] = {0};
+  b.rows.alloc(n, s);
+  if (n > 0) {
+    DBuf<uint64_t> key(n, s), val(n, s);
+    DBuf<int64_t> doff(kClasses + 1, s);
+    const int g = grid_for(n, 256, kSMs * 16);
+    k_plan_class<<<g, 256, 0, s>>>(n, rowptr, 4, key.get(), val.get());
+    LG_LAUNCH_CHECK();
+    radix_sort_pairs(key.get(), val.get(), n, 8, s);
+    k_plan_lists<<<g, 256, 0, s>>>(n, key.get(), val.get(), b.rows.get(), doff.get());
+    LG_LAUNCH_CHECK();
+    LG_CUDA(cudaMemcpyAsync(off, doff.get(), sizeof(off), cudaMemcpyDeviceToHost, s));
+    LG_CUDA(cudaStreamSynchronize(s));
+  }
+  RowPlan p;
+  p.rows_by_class = b.rows.get();
+  for (int c = 0; c <= kClasses; ++c) p.cls_off[c] = off[c];
+  b.bins = bins_of(p, n);
+}
+
 void build_row_plan(RowPlanStore& ps, int64_t n, int64_t nnz, const int64_t* rowptr, cudaStream_t s,
                     int64_t* counter) {
   RowPlan& p = ps.plan;

@@ -46,6 +46,28 @@ struct RowPlanStore {
   DBuf<double> partial;
   DBuf<unsigned> ticket;
 };
+// Rows of a CSR structure grouped by length for the setup passes (lg_each.cuh):
+// class c < kClasses holds rows of at most E 2^c entries (the last class: at
+// most kChunk) and is visited by groups of 2^c lanes, kEachThreads / 2^c rows
+// per block; each row longer than kChunk gets a block of its own. Blocks are
+// ordered long rows first, then classes from the longest rows down, so the
+// heaviest work starts first.
+constexpr int kEachThreads = 256;
+struct RowBins {
+  const int32_t* rows = nullptr;    // row ids class by class, long rows last
+  int64_t off[kClasses + 2] = {0};  // class c: rows[off[c], off[c+1]); long rows: [off[kClasses], off[kClasses+1])
+  int blk[kClasses] = {0};          // first block of class c
+  int grid = 0;
+};
+// The bins of a built plan (its classes and long rows).
+RowBins bins_of(const RowPlan& p, int64_t n);
+// Bins of a CSR structure without a plan (E = 4), owning the row list.
+struct RowBinsStore {
+  DBuf<int32_t> rows;
+  RowBins bins;
+};
+void make_bins(RowBinsStore& b, int64_t n, const int64_t* rowptr, cudaStream_t s);
+
 // Build the plan for a CSR structure with n rows and nnz entries (rows binned
 // with E = 4 entries per lane).
 void build_row_plan(RowPlanStore& ps, int64_t n, int64_t nnz, const int64_t* rowptr, cudaStream_t s,

@@ -12,6 +12,7 @@
 #include <tuple>
 
 #include "lg_hier.h"
+#include "lg_each.cuh"
 #include "lg_rows.cuh"
 
 namespace lg {
@@ -19,13 +20,9 @@ namespace lg {
 constexpr int kNT = 256;
 
 static inline int blocks_for(int64_t n, int per_block = kNT) { return grid_for(n, per_block, kSMs * 16); }
-static inline int warp_blocks(int64_t rows) { return grid_for(rows * 32, kNT, kSMs * 16); }
 
 #define LG_GRID_STRIDE(i, n) \
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
-#define LG_WARP_STRIDE(row, n)                                                                   \
-  for (int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; row < (n);          \
-       row += ((int64_t)gridDim.x * blockDim.x) >> 5)
 
 // Device error word bits.
 enum : int {
@@ -55,24 +52,52 @@ __device__ __forceinline__ bool find_col(const int64_t* rowptr, const int32_t* c
   return false;
 }
 
-__global__ void k_check_rows(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                             const double* __restrict__ w, int* err) {
-  const int lane = threadIdx.x & 31;
-  LG_WARP_STRIDE(i, n) {
-    int bits = 0;
-    for (int64_t k = rowptr[i] + lane; k < rowptr[i + 1]; k += 32) {
-      const int32_t j = col[k];
-      if (j < 0 || j >= n) { bits |= kErrCol; continue; }
-      if (j == i) bits |= kErrSelf;
-      if (k > rowptr[i] && col[k - 1] >= j) bits |= kErrOrder;
-      const double wk = w[k];
-      if (!(wk > 0.0) || !isfinite(wk)) bits |= kErrWeight;
+// Per-entry checks of one row: column range, no self-loop, strictly
+// increasing columns (so no duplicates), positive finite weight, and the
+// mirror entry. The mirror of (i, j) is looked up only from the end with more
+// entries (ties: larger id), by binary search in the row of the other end,
+// which keeps the searches short on power-law graphs; the looked-up entries
+// count +1 and the others -1, and a zero total (every entry either looked up
+// or the mirror of one) completes the symmetry check: the looked-up entries
+// map one-to-one onto the others, so equal counts leave no entry unmatched.
+struct FCheck {
+  int64_t n;
+  const int64_t* __restrict__ rowptr;
+  const int32_t* __restrict__ col;
+  const double* __restrict__ w;
+  int* err;
+  struct Acc {
+    long long sign;
+    int bits;
+  };
+  __device__ Acc init(int64_t, int64_t, int64_t) const { return Acc{0, 0}; }
+  __device__ void add(Acc& a, int64_t i, int64_t k) const {
+    const int32_t j = col[k];
+    if (j < 0 || j >= n) { a.bits |= kErrCol; return; }
+    if (j == i) { a.bits |= kErrSelf; return; }
+    const int64_t b = rowptr[i], di = rowptr[i + 1] - b;
+    if (k > b && col[k - 1] >= j) a.bits |= kErrOrder;
+    const double wk = w[k];
+    if (!(wk > 0.0) || !isfinite(wk)) a.bits |= kErrWeight;
+    const int64_t dj = rowptr[j + 1] - rowptr[j];
+    if (dj < di || (dj == di && j < i)) {
       int64_t pos;
-      if (!find_col(rowptr, col, j, (int32_t)i, &pos) || w[pos] != wk) bits |= kErrAsym;
+      if (!find_col(rowptr, col, j, (int32_t)i, &pos) || w[pos] != wk) a.bits |= kErrAsym;
+      a.sign += 1;
+    } else {
+      a.sign -= 1;
     }
-    if (bits) atomicOr(err, bits);
   }
-}
+  __device__ void merge(Acc& a, const Acc& o) const {
+    a.sign += o.sign;
+    a.bits |= o.bits;
+  }
+  __device__ Acc shfl(const Acc& a, int o) const { return Acc{each_shfl(a.sign, o), each_shfl(a.bits, o)}; }
+  __device__ long long finish(int64_t, const Acc& a, int64_t, int64_t) const {
+    if (a.bits) atomicOr(err, a.bits);
+    return a.sign;
+  }
+};
 
 // Connected components by union-find with lock-free hooking (the larger root
 // is hooked under the smaller one by compare-and-swap) and path halving.
@@ -93,26 +118,37 @@ __global__ void k_cc_init(int64_t n, int32_t* parent) {
   LG_GRID_STRIDE(i, n) parent[i] = (int32_t)i;
 }
 
-__global__ void k_cc_hook(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                          int32_t* parent, int* err) {
-  const int lane = threadIdx.x & 31;
-  LG_WARP_STRIDE(i, n) {
-    for (int64_t k = rowptr[i] + lane; k < rowptr[i + 1]; k += 32) {
-      const int32_t j = col[k];
-      if (j <= i) continue;
-      int32_t a = cc_find(parent, (int32_t)i, n, err), b = cc_find(parent, j, n, err);
-      int tries = 0;
-      while (a != b) {
-        const int32_t hi = a > b ? a : b, lo = a > b ? b : a;
-        const int32_t old = atomicCAS(&parent[hi], hi, lo);
-        if (old == hi) break;
-        a = cc_find(parent, old, n, err);
-        b = cc_find(parent, lo, n, err);
-        if (++tries > (1 << 20)) { atomicOr(err, kErrLoop); break; }
+// Union of the two ends of every entry (i, j), j > i.
+struct FHook {
+  int64_t n;
+  const int32_t* __restrict__ col;
+  int32_t* parent;
+  int* err;
+  struct Acc {
+    int z;
+  };
+  __device__ Acc init(int64_t, int64_t, int64_t) const { return Acc{0}; }
+  __device__ void add(Acc&, int64_t i, int64_t k) const {
+    const int32_t j = col[k];
+    if (j <= i) return;
+    int32_t a = cc_find(parent, (int32_t)i, n, err), b = cc_find(parent, j, n, err);
+    int tries = 0;
+    while (a != b) {
+      const int32_t hi = a > b ? a : b, lo = a > b ? b : a;
+      const int32_t old = atomicCAS(&parent[hi], hi, lo);
+      if (old == hi) break;
+      a = cc_find(parent, old, n, err);
+      b = cc_find(parent, lo, n, err);
+      if (++tries > (1 << 20)) {
+        atomicOr(err, kErrLoop);
+        break;
       }
     }
   }
-}
+  __device__ void merge(Acc&, const Acc&) const {}
+  __device__ Acc shfl(const Acc& a, int) const { return a; }
+  __device__ long long finish(int64_t, const Acc&, int64_t, int64_t) const { return 0; }
+};
 
 __global__ void k_cc_roots(int64_t n, int32_t* parent, uint8_t* is_root, int* err) {
   LG_GRID_STRIDE(i, n) {
@@ -204,67 +240,66 @@ __global__ void k_elim_maps(int64_t n, const uint8_t* __restrict__ is_f, const i
 // gives its kept neighbours (L_CC); an eliminated row f of degree d gives
 // the d(d-1) ordered pairs of its neighbours (the fill of
 // -L_FC^T L_FF^-1 L_FC; F is independent, so all neighbours are kept).
-__global__ void k_schur_count(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                              const uint8_t* __restrict__ is_f, int64_t* __restrict__ cnt) {
-  const int lane = threadIdx.x & 31;
-  LG_WARP_STRIDE(i, n) {
-    const int64_t b = rowptr[i], e = rowptr[i + 1];
-    int64_t c = 0;
-    if (is_f[i]) {
-      c = lane == 0 ? (e - b) * (e - b - 1) : 0;
-    } else {
-      for (int64_t k = b + lane; k < e; k += 32) c += is_f[col[k]] ? 0 : 1;
-    }
-    c = group_sum<32>(c, 0xffffffffu);
-    if (lane == 0) cnt[i] = c;
+struct FSchurCount {
+  const int32_t* __restrict__ col;
+  const uint8_t* __restrict__ is_f;
+  int64_t* __restrict__ cnt;
+  struct Acc {
+    long long c;
+  };
+  __device__ Acc init(int64_t, int64_t, int64_t) const { return Acc{0}; }
+  __device__ void add(Acc& a, int64_t, int64_t k) const { a.c += is_f[col[k]] ? 0 : 1; }
+  __device__ void merge(Acc& a, const Acc& o) const { a.c += o.c; }
+  __device__ Acc shfl(const Acc& a, int o) const { return Acc{each_shfl(a.c, o)}; }
+  __device__ long long finish(int64_t i, const Acc& a, int64_t b, int64_t e) const {
+    cnt[i] = is_f[i] ? (e - b) * (e - b - 1) : a.c;
+    return 0;
   }
-}
+};
 
 // Keys are (coarse row << cbits) | coarse col; values are FP64 bit patterns.
 // Entries are written in fine-row order, kept rows in column order, fill in
 // (first neighbour, second neighbour) order, so the sort-and-sum that follows
 // adds equal keys in a fixed order. The fill weight is w_fa w_fb / d_f with
 // d_f = sum_j w_fj summed sequentially.
-__global__ void k_schur_emit(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                             const double* __restrict__ w, const uint8_t* __restrict__ is_f,
-                             const int32_t* __restrict__ cmap, const int64_t* __restrict__ off, int cbits,
-                             uint64_t* __restrict__ keys, uint64_t* __restrict__ vals) {
-  const int lane = threadIdx.x & 31;
-  const unsigned lt = (1u << lane) - 1u;
-  LG_WARP_STRIDE(i, n) {
-    const int64_t b = rowptr[i], e = rowptr[i + 1];
-    int64_t o = off[i];
-    if (is_f[i]) {
-      const int64_t d = e - b;
-      double df = 0.0;
-      for (int64_t k = b; k < e; ++k) df += w[k];
-      for (int64_t t = lane; t < d * (d - 1); t += 32) {
-        const int64_t a = t / (d - 1), bb0 = t % (d - 1);
-        const int64_t bb = bb0 < a ? bb0 : bb0 + 1;
-        const int64_t ka = b + a, kb = b + bb;
+struct ESchur {
+  const int32_t* __restrict__ col;
+  const double* __restrict__ w;
+  const uint8_t* __restrict__ is_f;
+  const int32_t* __restrict__ cmap;
+  int cbits;
+  uint64_t* __restrict__ keys;
+  uint64_t* __restrict__ vals;
+  struct Row {
+    unsigned long long key;
+    bool f;
+  };
+  __device__ Row row(int64_t i) const {
+    const bool f = is_f[i];
+    return Row{f ? 0ull : (unsigned long long)cmap[i] << cbits, f};
+  }
+  __device__ bool special(const Row& r) const { return r.f; }
+  __device__ void emit_special(const Row&, int64_t, int64_t b, int64_t e, int64_t o) const {
+    const int64_t d = e - b;
+    double df = 0.0;
+    for (int64_t k = b; k < e; ++k) df += w[k];
+    int64_t t = 0;
+    for (int64_t ka = b; ka < e; ++ka)
+      for (int64_t kb = b; kb < e; ++kb) {
+        if (kb == ka) continue;
         keys[o + t] = ((uint64_t)cmap[col[ka]] << cbits) | (uint64_t)cmap[col[kb]];
         vals[o + t] = (uint64_t)__double_as_longlong(w[ka] * w[kb] / df);
+        ++t;
       }
-    } else {
-      const uint64_t row = (uint64_t)cmap[i] << cbits;
-      for (int64_t k0 = b; k0 < e; k0 += 32) {
-        const int64_t k = k0 + lane;
-        const bool take = k < e && !is_f[col[k]];
-        const unsigned m = __ballot_sync(0xffffffffu, take);
-        if (take) {
-          const int64_t p = o + __popc(m & lt);
-          keys[p] = row | (uint64_t)cmap[col[k]];
-          vals[p] = (uint64_t)__double_as_longlong(w[k]);
-        }
-        o += __popc(m);
-      }
-    }
+    (void)d;
   }
-}
+  __device__ bool take(const Row&, int64_t, int64_t k) const { return !is_f[col[k]]; }
+  __device__ void put(const Row& r, int64_t, int64_t k, int64_t p) const {
+    keys[p] = r.key | (uint64_t)cmap[col[k]];
+    vals[p] = (uint64_t)__double_as_longlong(w[k]);
+  }
+};
 
-// Transpose of the F rows of P: for every eliminated f and neighbour c an
-// entry keyed by c's coarse id carrying (f, slot) so the coefficient
-// w_fc / d_f can be gathered after sorting.
 __global__ void k_pt_emit(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                           const uint8_t* __restrict__ is_f, const int32_t* __restrict__ cmap,
                           const int64_t* __restrict__ off, uint64_t* __restrict__ keys, uint64_t* __restrict__ vals) {
@@ -320,75 +355,138 @@ __global__ void k_strength_init(int64_t n, int m, uint64_t seed, int level, doub
   }
 }
 
-// One damped Jacobi sweep on L y = 0 for m columns ([n][m] layout):
+// One damped Jacobi sweep on L y = 0 for M columns ([n][M] layout):
 // x_out = x - omega D^-1 L x, L x in difference form.
-__global__ void k_jacobi_m(int64_t n, int m, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                           const double* __restrict__ w, const double* __restrict__ dinv, double omega,
-                           const double* __restrict__ x, double* __restrict__ xo) {
-  const int lane = threadIdx.x & 31;
-  LG_WARP_STRIDE(i, n) {
-    double xi[kMaxVecs], s[kMaxVecs];
-    for (int k = 0; k < m; ++k) { xi[k] = x[i * m + k]; s[k] = 0.0; }
-    for (int64_t p = rowptr[i] + lane; p < rowptr[i + 1]; p += 32) {
-      const int64_t j = col[p];
-      const double wp = w[p];
-      for (int k = 0; k < m; ++k) s[k] += wp * (xi[k] - x[j * m + k]);
+template <int M>
+struct FJacobi {
+  const int32_t* __restrict__ col;
+  const double* __restrict__ w;
+  const double* __restrict__ dinv;
+  double omega;
+  const double* __restrict__ x;
+  double* __restrict__ xo;
+  struct Acc {
+    double s[M], xi[M];
+  };
+  __device__ Acc init(int64_t i, int64_t, int64_t) const {
+    Acc a;
+#pragma unroll
+    for (int q = 0; q < M; ++q) {
+      a.s[q] = 0.0;
+      a.xi[q] = x[i * M + q];
     }
-    for (int k = 0; k < m; ++k) s[k] = group_sum<32>(s[k], 0xffffffffu);
-    if (lane < m) {
-      double v = 0.0, sv = 0.0;
-      for (int k = 0; k < m; ++k) if (k == lane) { v = xi[k]; sv = s[k]; }
-      xo[i * m + lane] = v - omega * dinv[i] * sv;
-    }
+    return a;
   }
-}
+  __device__ void add(Acc& a, int64_t, int64_t k) const {
+    const int64_t j = col[k];
+    const double wk = w[k];
+#pragma unroll
+    for (int q = 0; q < M; ++q) a.s[q] += wk * (a.xi[q] - x[j * M + q]);
+  }
+  __device__ void merge(Acc& a, const Acc& o) const {
+#pragma unroll
+    for (int q = 0; q < M; ++q) a.s[q] += o.s[q];
+  }
+  __device__ Acc shfl(const Acc& a, int o) const {
+    Acc r = a;
+#pragma unroll
+    for (int q = 0; q < M; ++q) r.s[q] = each_shfl(a.s[q], o);
+    return r;
+  }
+  __device__ long long finish(int64_t i, const Acc& a, int64_t, int64_t) const {
+    const double di = dinv[i];
+#pragma unroll
+    for (int q = 0; q < M; ++q) xo[i * M + q] = a.xi[q] - omega * di * a.s[q];
+    return 0;
+  }
+};
 
 // C_ij = (x_i . x_j)^2 / (|x_i|^2 |x_j|^2), 0 when the denominator is 0; the
 // products and sums are formed the same way for (i, j) and (j, i), so C is
 // bitwise symmetric. rowmax_i = max_j C_ij.
-__device__ __forceinline__ double affinity_of(const double* xi, double xi2, const double* __restrict__ x, int64_t j,
-                                              int m) {
-  double xj2 = 0.0, xij = 0.0;
-  for (int k = 0; k < m; ++k) {
-    const double a = x[j * m + k];
-    xj2 += a * a;
-    xij += xi[k] * a;
-  }
-  const double den = xi2 * xj2;
-  return den > 0.0 ? (xij * xij) / den : 0.0;
-}
-
-__global__ void k_affinity(int64_t n, int m, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                           const double* __restrict__ x, double* __restrict__ C, double* __restrict__ rowmax) {
-  const int lane = threadIdx.x & 31;
-  LG_WARP_STRIDE(i, n) {
-    double xi[kMaxVecs];
-    double xi2 = 0.0;
-    for (int k = 0; k < m; ++k) { xi[k] = x[i * m + k]; xi2 += xi[k] * xi[k]; }
-    double mx = 0.0;
-    for (int64_t p = rowptr[i] + lane; p < rowptr[i + 1]; p += 32) {
-      const double c = affinity_of(xi, xi2, x, col[p], m);
-      C[p] = c;
-      mx = c > mx ? c : mx;
+template <int M>
+struct FAffinity {
+  const int32_t* __restrict__ col;
+  const double* __restrict__ x;
+  double* __restrict__ C;
+  double* __restrict__ rowmax;
+  struct Acc {
+    double mx, xi2, xi[M];
+  };
+  __device__ Acc init(int64_t i, int64_t, int64_t) const {
+    Acc a;
+    a.mx = 0.0;
+    a.xi2 = 0.0;
+#pragma unroll
+    for (int q = 0; q < M; ++q) {
+      a.xi[q] = x[i * M + q];
+      a.xi2 += a.xi[q] * a.xi[q];
     }
-    mx = group_max<32>(mx, 0xffffffffu);
-    if (lane == 0) rowmax[i] = mx;
+    return a;
   }
-}
+  __device__ void add(Acc& a, int64_t, int64_t k) const {
+    const int64_t j = col[k];
+    double xj2 = 0.0, xij = 0.0;
+#pragma unroll
+    for (int q = 0; q < M; ++q) {
+      const double v = x[j * M + q];
+      xj2 += v * v;
+      xij += a.xi[q] * v;
+    }
+    const double den = a.xi2 * xj2;
+    const double c = den > 0.0 ? (xij * xij) / den : 0.0;
+    C[k] = c;
+    a.mx = c > a.mx ? c : a.mx;
+  }
+  __device__ void merge(Acc& a, const Acc& o) const { a.mx = o.mx > a.mx ? o.mx : a.mx; }
+  __device__ Acc shfl(const Acc& a, int o) const {
+    Acc r = a;
+    r.mx = each_shfl(a.mx, o);
+    return r;
+  }
+  __device__ long long finish(int64_t i, const Acc& a, int64_t, int64_t) const {
+    rowmax[i] = a.mx;
+    return 0;
+  }
+};
 
 // S_ij = C_ij / max(rowmax_i, rowmax_j) (C symmetric: column max = row max).
-__global__ void k_normalize(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                            const double* __restrict__ rowmax, double* __restrict__ S) {
-  const int lane = threadIdx.x & 31;
-  LG_WARP_STRIDE(i, n) {
-    const double ri = rowmax[i];
-    for (int64_t p = rowptr[i] + lane; p < rowptr[i + 1]; p += 32) {
-      const double rj = rowmax[col[p]];
-      const double mx = ri > rj ? ri : rj;
-      S[p] = mx > 0.0 ? S[p] / mx : 0.0;
-    }
+struct FNormalize {
+  const int32_t* __restrict__ col;
+  const double* __restrict__ rowmax;
+  double* __restrict__ S;
+  struct Acc {
+    double ri;
+  };
+  __device__ Acc init(int64_t i, int64_t, int64_t) const { return Acc{rowmax[i]}; }
+  __device__ void add(Acc& a, int64_t, int64_t k) const {
+    const double rj = rowmax[col[k]];
+    const double mx = a.ri > rj ? a.ri : rj;
+    S[k] = mx > 0.0 ? S[k] / mx : 0.0;
   }
-}
+  __device__ void merge(Acc&, const Acc&) const {}
+  __device__ Acc shfl(const Acc& a, int) const { return a; }
+  __device__ long long finish(int64_t, const Acc&, int64_t, int64_t) const { return 0; }
+};
+
+// d_i = sum_j w_ij and 1/d_i (0 for an isolated vertex).
+struct FRowSum {
+  const double* __restrict__ w;
+  double* __restrict__ d;
+  double* __restrict__ dinv;
+  struct Acc {
+    double s;
+  };
+  __device__ Acc init(int64_t, int64_t, int64_t) const { return Acc{0.0}; }
+  __device__ void add(Acc& a, int64_t, int64_t k) const { a.s += w[k]; }
+  __device__ void merge(Acc& a, const Acc& o) const { a.s += o.s; }
+  __device__ Acc shfl(const Acc& a, int o) const { return Acc{each_shfl(a.s, o)}; }
+  __device__ long long finish(int64_t i, const Acc& a, int64_t, int64_t) const {
+    if (d) d[i] = a.s;
+    dinv[i] = a.s > 0.0 ? 1.0 / a.s : 0.0;
+    return 0;
+  }
+};
 
 // ---------------------------------------------------------------------------
 // Aggregation (Section 3.5, Algorithms "Aggregation", "Aggregation-Step").
@@ -409,46 +507,62 @@ __global__ void k_agg_init(int64_t n, int8_t* state, int32_t* idx, int32_t* vote
 // an Undecided vertex whose best neighbour is a Seed joins it (Decided); if
 // the best is Undecided it votes for it. Seeds and Decided vertices keep
 // their status.
-__global__ void k_agg_decide(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                             const double* __restrict__ S, double filter, const int8_t* __restrict__ state,
-                             const int32_t* __restrict__ idx, int8_t* __restrict__ nstate,
-                             int32_t* __restrict__ nidx, int32_t* __restrict__ votes) {
-  const int lane = threadIdx.x & 31;
-  LG_WARP_STRIDE(i, n) {
-    const int8_t si = state[i];
-    if (si != LG_UNDECIDED) {
-      if (lane == 0) { nstate[i] = si; nidx[i] = idx[i]; }
-      continue;
-    }
-    uint64_t hi = 0, lo = 0;  // the (Decided, -1, 0) identity sorts below every real entry
-    for (int64_t p = rowptr[i] + lane; p < rowptr[i + 1]; p += 32) {
-      const double sp = S[p];
-      if (!(sp >= filter)) continue;
-      const int32_t j = col[p];
-      const uint64_t h = ((uint64_t)state[j] << 62) | (uint64_t)__double_as_longlong(sp);
-      const uint64_t l = (uint64_t)(~(uint32_t)idx[j]);
-      if (h > hi || (h == hi && l > lo)) { hi = h; lo = l; }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const uint64_t h2 = __shfl_xor_sync(0xffffffffu, hi, o);
-      const uint64_t l2 = __shfl_xor_sync(0xffffffffu, lo, o);
-      if (h2 > hi || (h2 == hi && l2 > lo)) { hi = h2; lo = l2; }
-    }
-    if (lane == 0) {
-      const int s = (int)(hi >> 62);
-      const int32_t j = (int32_t)(~(uint32_t)lo);
-      int8_t ns = LG_UNDECIDED;
-      int32_t ni = (int32_t)i;
-      if (hi != 0) {
-        if (s == LG_SEED) { ns = LG_DECIDED; ni = j; }
-        else if (s == LG_UNDECIDED) atomicAdd(&votes[j], 1);
-      }
-      nstate[i] = ns;
-      nidx[i] = ni;
+struct FAggDecide {
+  const int32_t* __restrict__ col;
+  const double* __restrict__ S;
+  double filter;
+  const int8_t* __restrict__ state;
+  const int32_t* __restrict__ idx;
+  int8_t* __restrict__ nstate;
+  int32_t* __restrict__ nidx;
+  int32_t* __restrict__ votes;
+  struct Acc {
+    unsigned long long hi, lo;  // the (Decided, -1, 0) identity sorts below every real entry
+    int und;
+  };
+  __device__ Acc init(int64_t i, int64_t, int64_t) const { return Acc{0ull, 0ull, state[i] == LG_UNDECIDED}; }
+  __device__ void add(Acc& a, int64_t, int64_t p) const {
+    if (!a.und) return;
+    const double sp = S[p];
+    if (!(sp >= filter)) return;
+    const int32_t j = col[p];
+    const unsigned long long h = ((unsigned long long)state[j] << 62) | (unsigned long long)__double_as_longlong(sp);
+    const unsigned long long l = (unsigned long long)(~(uint32_t)idx[j]);
+    if (h > a.hi || (h == a.hi && l > a.lo)) {
+      a.hi = h;
+      a.lo = l;
     }
   }
-}
+  __device__ void merge(Acc& a, const Acc& o) const {
+    if (o.hi > a.hi || (o.hi == a.hi && o.lo > a.lo)) {
+      a.hi = o.hi;
+      a.lo = o.lo;
+    }
+  }
+  __device__ Acc shfl(const Acc& a, int o) const { return Acc{each_shfl(a.hi, o), each_shfl(a.lo, o), a.und}; }
+  __device__ long long finish(int64_t i, const Acc& a, int64_t, int64_t) const {
+    if (!a.und) {
+      nstate[i] = state[i];
+      nidx[i] = idx[i];
+      return 0;
+    }
+    const int s = (int)(a.hi >> 62);
+    const int32_t j = (int32_t)(~(uint32_t)a.lo);
+    int8_t ns = LG_UNDECIDED;
+    int32_t ni = (int32_t)i;
+    if (a.hi != 0) {
+      if (s == LG_SEED) {
+        ns = LG_DECIDED;
+        ni = j;
+      } else if (s == LG_UNDECIDED) {
+        atomicAdd(&votes[j], 1);
+      }
+    }
+    nstate[i] = ns;
+    nidx[i] = ni;
+    return 0;
+  }
+};
 
 __global__ void k_agg_promote(int64_t n, int threshold, const int32_t* __restrict__ votes, int8_t* __restrict__ state,
                               const int32_t* __restrict__ idx) {
@@ -470,47 +584,45 @@ __global__ void k_agg_number(int64_t n, const int32_t* __restrict__ idx, const i
 // Galerkin product L_c = R L P, P = R^T (Section 3.5): the coarse weight
 // between aggregates I != J sums the weights of the edges joining them.
 // ---------------------------------------------------------------------------
-__global__ void k_gal_count(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                            const int32_t* __restrict__ agg, int64_t* __restrict__ cnt) {
-  const int lane = threadIdx.x & 31;
-  LG_WARP_STRIDE(i, n) {
-    const int32_t ai = agg[i];
-    int64_t c = 0;
-    for (int64_t p = rowptr[i] + lane; p < rowptr[i + 1]; p += 32) c += agg[col[p]] != ai;
-    c = group_sum<32>(c, 0xffffffffu);
-    if (lane == 0) cnt[i] = c;
+struct FGalCount {
+  const int32_t* __restrict__ col;
+  const int32_t* __restrict__ agg;
+  int64_t* __restrict__ cnt;
+  struct Acc {
+    long long c;
+    int32_t ai;
+  };
+  __device__ Acc init(int64_t i, int64_t, int64_t) const { return Acc{0, agg[i]}; }
+  __device__ void add(Acc& a, int64_t, int64_t p) const { a.c += agg[col[p]] != a.ai; }
+  __device__ void merge(Acc& a, const Acc& o) const { a.c += o.c; }
+  __device__ Acc shfl(const Acc& a, int o) const { return Acc{each_shfl(a.c, o), a.ai}; }
+  __device__ long long finish(int64_t i, const Acc& a, int64_t, int64_t) const {
+    cnt[i] = a.c;
+    return 0;
   }
-}
+};
 
-__global__ void k_gal_emit(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                           const double* __restrict__ w, const int32_t* __restrict__ agg,
-                           const int64_t* __restrict__ off, int cbits, uint64_t* __restrict__ keys,
-                           uint64_t* __restrict__ vals) {
-  const int lane = threadIdx.x & 31;
-  const unsigned lt = (1u << lane) - 1u;
-  LG_WARP_STRIDE(i, n) {
-    const int32_t ai = agg[i];
-    const uint64_t row = (uint64_t)ai << cbits;
-    const int64_t e = rowptr[i + 1];
-    int64_t o = off[i];
-    for (int64_t k0 = rowptr[i]; k0 < e; k0 += 32) {
-      const int64_t k = k0 + lane;
-      int32_t aj = 0;
-      bool take = false;
-      if (k < e) {
-        aj = agg[col[k]];
-        take = aj != ai;
-      }
-      const unsigned m = __ballot_sync(0xffffffffu, take);
-      if (take) {
-        const int64_t p = o + __popc(m & lt);
-        keys[p] = row | (uint64_t)aj;
-        vals[p] = (uint64_t)__double_as_longlong(w[k]);
-      }
-      o += __popc(m);
-    }
+// Galerkin entries: (agg_i << cbits | agg_j, w_ij) for every stored (i, j)
+// joining two different aggregates, in row order.
+struct EGal {
+  const int32_t* __restrict__ col;
+  const double* __restrict__ w;
+  const int32_t* __restrict__ agg;
+  int cbits;
+  uint64_t* __restrict__ keys;
+  uint64_t* __restrict__ vals;
+  struct Row {
+    int32_t ai;
+  };
+  __device__ Row row(int64_t i) const { return Row{agg[i]}; }
+  __device__ bool special(const Row&) const { return false; }
+  __device__ void emit_special(const Row&, int64_t, int64_t, int64_t, int64_t) const {}
+  __device__ bool take(const Row& r, int64_t, int64_t k) const { return agg[col[k]] != r.ai; }
+  __device__ void put(const Row& r, int64_t, int64_t k, int64_t p) const {
+    keys[p] = ((uint64_t)r.ai << cbits) | (uint64_t)agg[col[k]];
+    vals[p] = (uint64_t)__double_as_longlong(w[k]);
   }
-}
+};
 
 __global__ void k_iota_u64(int64_t n, const int32_t* __restrict__ agg, uint64_t* __restrict__ keys,
                            uint64_t* __restrict__ vals) {
@@ -725,18 +837,25 @@ __global__ void k_iota_i32(int64_t n, int32_t* __restrict__ a) {
 }
 
 // Entries of the renumbered graph: (inv[i], inv[j]) for every stored (i, j).
-__global__ void k_perm_emit(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                            const double* __restrict__ w, const int32_t* __restrict__ inv, int cbits,
-                            uint64_t* __restrict__ keys, uint64_t* __restrict__ vals) {
-  const int lane = threadIdx.x & 31;
-  LG_WARP_STRIDE(i, n) {
-    const uint64_t row = (uint64_t)inv[i] << cbits;
-    for (int64_t k = rowptr[i] + lane; k < rowptr[i + 1]; k += 32) {
-      keys[k] = row | (uint64_t)inv[col[k]];
-      vals[k] = (uint64_t)__double_as_longlong(w[k]);
-    }
+struct FPermEmit {
+  const int32_t* __restrict__ col;
+  const double* __restrict__ w;
+  const int32_t* __restrict__ inv;
+  int cbits;
+  uint64_t* __restrict__ keys;
+  uint64_t* __restrict__ vals;
+  struct Acc {
+    unsigned long long row;
+  };
+  __device__ Acc init(int64_t i, int64_t, int64_t) const { return Acc{(unsigned long long)inv[i] << cbits}; }
+  __device__ void add(Acc& a, int64_t, int64_t k) const {
+    keys[k] = a.row | (uint64_t)inv[col[k]];
+    vals[k] = (uint64_t)__double_as_longlong(w[k]);
   }
-}
+  __device__ void merge(Acc&, const Acc&) const {}
+  __device__ Acc shfl(const Acc& a, int) const { return a; }
+  __device__ long long finish(int64_t, const Acc&, int64_t, int64_t) const { return 0; }
+};
 
 // ===========================================================================
 // Host side.
@@ -788,31 +907,50 @@ int64_t run_elim_select(int64_t n, const int64_t* rowptr, const int32_t* col, in
 }
 
 void run_strength(int64_t n, const int64_t* rowptr, const int32_t* col, const double* w, uint64_t seed, int level,
-                  int m, int sweeps, double omega, double* S, cudaStream_t s) {
+                  int m, int sweeps, double omega, double* S, cudaStream_t s, const RowBins* bins_in,
+                  const double* dinv_in) {
   if (m < 1 || m > kMaxVecs) fail(LG_ERR_INVALID, "strength_vecs must be 1..8");
-  RowPlanStore ps;
-  const int64_t nnz = read_i64(rowptr + n, s);
-  build_row_plan(ps, n, nnz, rowptr, s, nullptr);
-  DBuf<double> d(n, s), dinv(n, s), xa((size_t)n * m, s), xb((size_t)n * m, s), rowmax(n, s);
-  launch_rows<double, 0>(n, rowptr, col, WeightTerm{w}, ps.plan, EpiDinv{d.get(), dinv.get()}, s);
+  RowBinsStore own;
+  if (!bins_in) make_bins(own, n, rowptr, s);
+  const RowBins& bins = bins_in ? *bins_in : own.bins;
+  DBuf<double> dv, xa((size_t)n * m, s), xb((size_t)n * m, s), rowmax(n, s);
+  const double* dinv = dinv_in;
+  if (!dinv) {
+    dv.alloc(n, s);
+    each_row(FRowSum{w, nullptr, dv.get()}, rowptr, bins, s);
+    dinv = dv.get();
+  }
   k_strength_init<<<blocks_for(n), kNT, 0, s>>>(n, m, seed, level, xa.get());
   LG_LAUNCH_CHECK();
   double* x = xa.get();
   double* xo = xb.get();
-  for (int sw = 0; sw < sweeps; ++sw) {
-    k_jacobi_m<<<warp_blocks(n), kNT, 0, s>>>(n, m, rowptr, col, w, dinv.get(), omega, x, xo);
-    LG_LAUNCH_CHECK();
-    std::swap(x, xo);
+  auto sweep = [&](auto mtag) {
+    constexpr int M = decltype(mtag)::value;
+    for (int sw = 0; sw < sweeps; ++sw) {
+      each_row(FJacobi<M>{col, w, dinv, omega, x, xo}, rowptr, bins, s);
+      std::swap(x, xo);
+    }
+    each_row(FAffinity<M>{col, x, S, rowmax.get()}, rowptr, bins, s);
+  };
+  switch (m) {
+    case 1: sweep(std::integral_constant<int, 1>{}); break;
+    case 2: sweep(std::integral_constant<int, 2>{}); break;
+    case 3: sweep(std::integral_constant<int, 3>{}); break;
+    case 4: sweep(std::integral_constant<int, 4>{}); break;
+    case 5: sweep(std::integral_constant<int, 5>{}); break;
+    case 6: sweep(std::integral_constant<int, 6>{}); break;
+    case 7: sweep(std::integral_constant<int, 7>{}); break;
+    default: sweep(std::integral_constant<int, 8>{}); break;
   }
-  k_affinity<<<warp_blocks(n), kNT, 0, s>>>(n, m, rowptr, col, x, S, rowmax.get());
-  LG_LAUNCH_CHECK();
-  k_normalize<<<warp_blocks(n), kNT, 0, s>>>(n, rowptr, col, rowmax.get(), S);
-  LG_LAUNCH_CHECK();
-  LG_CUDA(cudaStreamSynchronize(s));
+  each_row(FNormalize{col, rowmax.get(), S}, rowptr, bins, s);
+  if (!bins_in) LG_CUDA(cudaStreamSynchronize(s));
 }
 
 int64_t run_aggregate(int64_t n, const int64_t* rowptr, const int32_t* col, const double* S, int iters, int threshold,
-                      int32_t* agg, int8_t* state_out, int32_t* votes_out, cudaStream_t s) {
+                      int32_t* agg, int8_t* state_out, int32_t* votes_out, cudaStream_t s, const RowBins* bins_in) {
+  RowBinsStore own;
+  if (!bins_in) make_bins(own, n, rowptr, s);
+  const RowBins& bins = bins_in ? *bins_in : own.bins;
   DBuf<int8_t> st(n, s), nst(n, s);
   DBuf<int32_t> idx(n, s), nidx(n, s), votes(n, s);
   DBuf<uint8_t> root(n, s);
@@ -823,8 +961,7 @@ int64_t run_aggregate(int64_t n, const int64_t* rowptr, const int32_t* col, cons
   int32_t *ia = idx.get(), *ib = nidx.get();
   for (int it = 1; it <= iters; ++it) {
     const double filter = std::ldexp(1.0, -it);  // 0.5^iter
-    k_agg_decide<<<warp_blocks(n), kNT, 0, s>>>(n, rowptr, col, S, filter, a, ia, b, ib, votes.get());
-    LG_LAUNCH_CHECK();
+    each_row(FAggDecide{col, S, filter, a, ia, b, ib, votes.get()}, rowptr, bins, s);
     k_agg_promote<<<blocks_for(n), kNT, 0, s>>>(n, threshold, votes.get(), b, ib);
     LG_LAUNCH_CHECK();
     std::swap(a, b);
@@ -858,17 +995,15 @@ static std::unique_ptr<Level> eliminate(Level& L, const uint8_t* is_f, int64_t n
   LG_LAUNCH_CHECK();
 
   // Schur complement entries, sorted and summed into the coarse CSR.
-  k_schur_count<<<warp_blocks(n), kNT, 0, s>>>(n, L.rowptr.get(), L.col.get(), is_f, cnt.get());
-  LG_LAUNCH_CHECK();
+  each_row(FSchurCount{L.col.get(), is_f, cnt.get()}, L.rowptr.get(), bins_of(L.plan.plan, n), s);
   exclusive_scan(cnt.get(), cnt.get(), n, s);
   const int64_t nent = read_i64(cnt.get() + n, s);
   const int cbits = bits_for(nc);
   auto C = std::make_unique<Level>();
   {
     DBuf<uint64_t> keys(nent, s), vals(nent, s);
-    k_schur_emit<<<warp_blocks(n), kNT, 0, s>>>(n, L.rowptr.get(), L.col.get(), L.w.get(), is_f, L.cmap.get(),
-                                               cnt.get(), cbits, keys.get(), vals.get());
-    LG_LAUNCH_CHECK();
+    emit_rows(ESchur{L.col.get(), L.w.get(), is_f, L.cmap.get(), cbits, keys.get(), vals.get()}, L.rowptr.get(),
+              cnt.get(), bins_of(L.plan.plan, n), s);
     CsrOut out;
     accumulate_csr(keys, vals, nent, nc, cbits, out, s, counter);
     C->n = nc;
@@ -919,15 +1054,13 @@ static std::unique_ptr<Level> galerkin(Level& L, cudaStream_t s, int64_t* counte
     build_row_plan(L.mem_plan, nc, n, L.mem_ptr.get(), s, counter);
   }
   DBuf<int64_t> cnt(n + 1, s);
-  k_gal_count<<<warp_blocks(n), kNT, 0, s>>>(n, L.rowptr.get(), L.col.get(), L.agg.get(), cnt.get());
-  LG_LAUNCH_CHECK();
+  each_row(FGalCount{L.col.get(), L.agg.get(), cnt.get()}, L.rowptr.get(), bins_of(L.plan.plan, n), s);
   exclusive_scan(cnt.get(), cnt.get(), n, s);
   const int64_t nent = read_i64(cnt.get() + n, s);
   const int cbits = bits_for(nc);
   DBuf<uint64_t> keys(nent, s), vals(nent, s);
-  k_gal_emit<<<warp_blocks(n), kNT, 0, s>>>(n, L.rowptr.get(), L.col.get(), L.w.get(), L.agg.get(), cnt.get(), cbits,
-                                           keys.get(), vals.get());
-  LG_LAUNCH_CHECK();
+  emit_rows(EGal{L.col.get(), L.w.get(), L.agg.get(), cbits, keys.get(), vals.get()}, L.rowptr.get(), cnt.get(),
+            bins_of(L.plan.plan, n), s);
   CsrOut out;
   accumulate_csr(keys, vals, nent, nc, cbits, out, s, counter);
   auto C = std::make_unique<Level>();
@@ -1096,17 +1229,22 @@ void setup_hierarchy(Hier& h, int64_t n, const int64_t* rowptr, const int32_t* c
   k_check_rowptr<<<blocks_for(n + 1), kNT, 0, s>>>(n, nnz, cur->rowptr.get(), h.dev_err.get());
   LG_LAUNCH_CHECK();
   if (read_err(h.dev_err, s)) fail(LG_ERR_INVALID, "rowptr");
-  k_check_rows<<<warp_blocks(n), kNT, 0, s>>>(n, cur->rowptr.get(), cur->col.get(), cur->w.get(), h.dev_err.get());
-  LG_LAUNCH_CHECK();
-  if (read_err(h.dev_err, s)) fail(LG_ERR_INVALID, "graph entries");
+  RowBinsStore in_bins;
+  make_bins(in_bins, n, cur->rowptr.get(), s);
+  DBuf<unsigned long long> sign(1, s);
+  LG_CUDA(cudaMemsetAsync(sign.get(), 0, sizeof(unsigned long long), s));
+  each_row(FCheck{n, cur->rowptr.get(), cur->col.get(), cur->w.get(), h.dev_err.get()}, cur->rowptr.get(),
+           in_bins.bins, s, sign.get());
+  unsigned long long sign_h = 0;
+  LG_CUDA(cudaMemcpyAsync(&sign_h, sign.get(), sizeof(sign_h), cudaMemcpyDeviceToHost, s));
+  if (read_err(h.dev_err, s) || sign_h != 0) fail(LG_ERR_INVALID, "graph entries");
   {
     DBuf<int32_t> parent(n, s);
     DBuf<uint8_t> is_root(n, s);
     DBuf<int64_t> cnt(n + 1, s);
     k_cc_init<<<blocks_for(n), kNT, 0, s>>>(n, parent.get());
     LG_LAUNCH_CHECK();
-    k_cc_hook<<<warp_blocks(n), kNT, 0, s>>>(n, cur->rowptr.get(), cur->col.get(), parent.get(), h.dev_err.get());
-    LG_LAUNCH_CHECK();
+    each_row(FHook{n, cur->col.get(), parent.get(), h.dev_err.get()}, cur->rowptr.get(), in_bins.bins, s);
     k_cc_roots<<<blocks_for(n), kNT, 0, s>>>(n, parent.get(), is_root.get(), h.dev_err.get());
     LG_LAUNCH_CHECK();
     exclusive_scan_flags(is_root.get(), cnt.get(), n, s);
@@ -1126,9 +1264,8 @@ void setup_hierarchy(Hier& h, int64_t n, const int64_t* rowptr, const int32_t* c
     LG_LAUNCH_CHECK();
     const int cbits = bits_for(n);
     DBuf<uint64_t> keys(nnz, s), vals(nnz, s);
-    k_perm_emit<<<warp_blocks(n), kNT, 0, s>>>(n, cur->rowptr.get(), cur->col.get(), cur->w.get(), inv.get(), cbits,
-                                              keys.get(), vals.get());
-    LG_LAUNCH_CHECK();
+    each_row(FPermEmit{cur->col.get(), cur->w.get(), inv.get(), cbits, keys.get(), vals.get()}, cur->rowptr.get(),
+             in_bins.bins, s);
     CsrOut out;
     accumulate_csr(keys, vals, nnz, n, cbits, out, s, counter);
     cur->rowptr = std::move(out.rowptr);
@@ -1163,11 +1300,14 @@ void setup_hierarchy(Hier& h, int64_t n, const int64_t* rowptr, const int32_t* c
     }
     const int level = (int)h.levels.size();
     DBuf<double> S(cur->nnz, s);
+    // the level's bins match those lg_strength / lg_aggregate derive for the same CSR (E = 4,
+    // before autotuning), so the strength values here are bitwise those of the single steps
+    const RowBins bins = bins_of(cur->plan.plan, cur->n);
     run_strength(cur->n, cur->rowptr.get(), cur->col.get(), cur->w.get(), o.seed, level, o.strength_vecs,
-                 o.strength_sweeps, o.jacobi_omega, S.get(), s);
+                 o.strength_sweeps, o.jacobi_omega, S.get(), s, &bins);
     cur->agg.alloc(cur->n, s, counter);
     const int64_t nc = run_aggregate(cur->n, cur->rowptr.get(), cur->col.get(), S.get(), o.agg_iters,
-                                     o.vote_threshold, cur->agg.get(), nullptr, nullptr, s);
+                                     o.vote_threshold, cur->agg.get(), nullptr, nullptr, s, &bins);
     if ((double)nc > o.stagnation_frac * (double)cur->n) {
       cur->agg.release();
       break;
