@@ -286,16 +286,13 @@ __device__ __forceinline__ bool grid_sum(double (&v)[K], double* partials, unsig
 constexpr int kRowThreads = 256;
 constexpr int kChunk = 2048;
 constexpr int kClasses = 6;
-// Rows per lane group in the two widest classes (groups of 16 and 32 lanes).
-constexpr int kRowsPerGroup16 = 1;
-constexpr int kRowsPerGroup32 = 1;
-
 // Rows one block of kRowThreads threads serves in class c (groups of 2^c
-// lanes; classes 0..3 take 2^c rows per group, so 32 rows per warp).
+// lanes; classes 0..3 take 2^c rows per group, so 32 rows per warp; the two
+// widest classes one row per group, so that every such row has its own group
+// in flight: more rows per group would serialise them and leave the gathers'
+// latency exposed).
 __host__ __device__ constexpr int64_t class_rows_per_block(int c) {
-  return c <= 3 ? kRowThreads
-         : c == 4 ? (kRowThreads / 16) * kRowsPerGroup16
-                  : (kRowThreads / 32) * kRowsPerGroup32;
+  return c <= 3 ? kRowThreads : c == 4 ? kRowThreads / 16 : kRowThreads / 32;
 }
 
 struct RowPlan {

@@ -111,24 +111,45 @@ struct WGatherTerm {
   __device__ __forceinline__ T finish(int64_t, T, T s) const { return s; }
 };
 
-// Sum of a row's entries with G lanes: the column indices of four entries
-// per lane are loaded together, then their terms, accumulated into two
-// chains of fused multiply-adds.
+// Sum of a row's entries with G lanes, lane l taking entries l, l + G, ...
+// FP64 (bound by the narrow FP64 pipe, where an instruction costs its full
+// warp slot however few lanes are active): every lane of the warp runs the
+// same number of steps (the warp's largest per-lane count), the steps past a
+// lane's own count predicated off, so rows of different lengths in one warp
+// cost the longest row's steps once, instead of an unrolled loop and a
+// remainder loop that diverge; and one accumulation chain, since a second
+// would cost an extra add per row. FP32 (bound by the latency of the
+// gathers): four entries' loads issued together per step, two chains.
 template <typename T, int G, class Term>
 __device__ __forceinline__ T row_sum(const Term& term, const int32_t* __restrict__ col, int64_t beg, int64_t end,
                                      int lane, T rv) {
-  T s0 = T(0), s1 = T(0);
-  int64_t k = beg + lane;
-  for (; k + 3 * G < end; k += 4 * G) {
-    const int32_t j0 = ld_stream(&col[k]), j1 = ld_stream(&col[k + G]);
-    const int32_t j2 = ld_stream(&col[k + 2 * G]), j3 = ld_stream(&col[k + 3 * G]);
-    s0 = term.acc(s0, k, j0, rv);
-    s1 = term.acc(s1, k + G, j1, rv);
-    s0 = term.acc(s0, k + 2 * G, j2, rv);
-    s1 = term.acc(s1, k + 3 * G, j3, rv);
+  if constexpr (sizeof(T) == 8) {
+    const int64_t k0 = beg + lane;
+    const int cnt = k0 < end ? (int)((end - k0 + G - 1) / G) : 0;
+    const int steps = __reduce_max_sync(0xffffffffu, cnt);
+    T s = T(0);
+#pragma unroll 4
+    for (int t = 0; t < steps; ++t) {
+      if (t < cnt) {
+        const int64_t k = k0 + (int64_t)t * G;
+        s = term.acc(s, k, ld_stream(&col[k]), rv);
+      }
+    }
+    return s;
+  } else {
+    T s0 = T(0), s1 = T(0);
+    int64_t k = beg + lane;
+    for (; k + 3 * G < end; k += 4 * G) {
+      const int32_t j0 = ld_stream(&col[k]), j1 = ld_stream(&col[k + G]);
+      const int32_t j2 = ld_stream(&col[k + 2 * G]), j3 = ld_stream(&col[k + 3 * G]);
+      s0 = term.acc(s0, k, j0, rv);
+      s1 = term.acc(s1, k + G, j1, rv);
+      s0 = term.acc(s0, k + 2 * G, j2, rv);
+      s1 = term.acc(s1, k + 3 * G, j3, rv);
+    }
+    for (; k < end; k += G) s0 = term.acc(s0, k, ld_stream(&col[k]), rv);
+    return s0 + s1;
   }
-  for (; k < end; k += G) s0 = term.acc(s0, k, ld_stream(&col[k]), rv);
-  return s0 + s1;
 }
 
 // Rows of class G, R per group of G lanes (R divides G): the group works
@@ -156,12 +177,16 @@ __device__ __forceinline__ void class_rows_batched(const RowPlan& plan, int c, i
   T part[R];
 #pragma unroll
   for (int j = 0; j < R; ++j) {
+    // every lane takes part (row_sum steps the whole warp together); a group
+    // past the end of the class sums an empty row
     const int64_t idx = base + j * kGroups + grp;
-    part[j] = T(0);
+    int64_t row = 0, rb = 0, re = 0;
     if (idx < cnt) {
-      const int64_t row = plan.rows_by_class[lo + idx];
-      part[j] = row_sum<T, G>(term, col, rowptr[row], rowptr[row + 1], gl, term.row(row));
+      row = plan.rows_by_class[lo + idx];
+      rb = rowptr[row];
+      re = rowptr[row + 1];
     }
+    part[j] = row_sum<T, G>(term, col, rb, re, gl, term.row(row));
   }
   if constexpr (G > 1) {
     const unsigned mask = group_mask<G>();
@@ -187,6 +212,50 @@ __device__ __forceinline__ void class_rows_batched(const RowPlan& plan, int c, i
   }
 }
 
+// FP64 rows of the two widest classes (one row per group of G = 16 or 32
+// lanes, kRowThreads / G rows per block). Completing each row by an xor tree
+// in its group and finishing it on one lane would cost about a dozen FP64
+// warp instructions per row, nearly all lanes idle. Instead the groups'
+// partial sums go to shared memory and one warp completes every row of the
+// block: kLanes = 32 / rows lanes per row each add 8 partials (full-width
+// adds), an xor tree over those kLanes lanes finishes the sum, and the
+// epilogues of the block's rows run side by side.
+template <typename T, int G, class Term, class Epi>
+__device__ __forceinline__ void class_rows_block(const RowPlan& plan, int c, int64_t b,
+                                                 const int64_t* __restrict__ rowptr,
+                                                 const int32_t* __restrict__ col, const Term& term,
+                                                 const Epi& epi, double* red) {
+  constexpr int kRows = kRowThreads / G;  // 8 or 16
+  constexpr int kLanes = 32 / kRows;      // 4 or 2 lanes complete one row
+  constexpr int kPer = G / kLanes;        // 8 partials per lane
+  __shared__ T sp[kRowThreads];
+  const int64_t lo = plan.cls_off[c], cnt = plan.cls_off[c + 1] - lo;
+  const int64_t base = b * kRows;
+  if (base >= cnt) return;  // uniform over the block
+  const int grp = threadIdx.x / G, gl = threadIdx.x & (G - 1);
+  int64_t row = 0, rb = 0, re = 0;
+  if (base + grp < cnt) {
+    row = plan.rows_by_class[lo + base + grp];
+    rb = rowptr[row];
+    re = rowptr[row + 1];
+  }
+  sp[threadIdx.x] = row_sum<T, G>(term, col, rb, re, gl, term.row(row));
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int r = threadIdx.x / kLanes, q0 = (threadIdx.x % kLanes) * kPer;
+    T s = sp[r * G + q0];
+#pragma unroll
+    for (int q = 1; q < kPer; ++q) s += sp[r * G + q0 + q];
+#pragma unroll
+    for (int o = kLanes / 2; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (q0 == 0 && base + r < cnt) {
+      const int64_t rr = plan.rows_by_class[lo + base + r];
+      const T rv = term.row(rr);
+      epi(rr, term.finish(rr, rv, s), epi.pre(rr), red);
+    }
+  }
+}
+
 template <typename T, int NRED, class Term, class Epi>
 __global__ void __launch_bounds__(kRowThreads)
 k_rows(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, Term term, RowPlan plan, Epi epi,
@@ -208,12 +277,31 @@ k_rows(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, Term
     const int64_t end = beg + kChunk < rend ? beg + kChunk : rend;
     const T rv = term.row(row);
     T s = row_sum<T, kRowThreads>(term, col, beg, end, threadIdx.x, rv);
-    s = group_sum_first<32>(s, 0xffffffffu, threadIdx.x & 31);
-    if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = s;
-    __syncthreads();
+    T t = T(0);
+    if constexpr (sizeof(T) == 8) {
+      // FP64: the 256 partials through shared memory, each lane of one warp
+      // adding 8 of them, then an xor tree (full-width adds throughout)
+      __shared__ T sp[kRowThreads];
+      sp[threadIdx.x] = s;
+      __syncthreads();
+      if (threadIdx.x < 32) {
+        constexpr int kPer = kRowThreads / 32;
+        t = sp[threadIdx.x * kPer];
+#pragma unroll
+        for (int q = 1; q < kPer; ++q) t += sp[threadIdx.x * kPer + q];
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      }
+    } else {
+      s = group_sum_first<32>(s, 0xffffffffu, threadIdx.x & 31);
+      if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = s;
+      __syncthreads();
+      if (threadIdx.x < 32) {
+        t = threadIdx.x < kRowThreads / 32 ? sred[threadIdx.x] : T(0);
+        t = group_sum_first<kRowThreads / 32>(t, 0xffffffffu, threadIdx.x);
+      }
+    }
     if (threadIdx.x < 32) {
-      T t = threadIdx.x < kRowThreads / 32 ? sred[threadIdx.x] : T(0);
-      t = group_sum_first<kRowThreads / 32>(t, 0xffffffffu, threadIdx.x);
       if (threadIdx.x == 0) {
         const int32_t lr = plan.chunk_lrow[c];
         plan.partial[c] = (double)t;
@@ -241,8 +329,14 @@ k_rows(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, Term
       case 1: class_rows_batched<T, 2, 2>(plan, 1, bb, rowptr, col, term, epi, red); break;
       case 2: class_rows_batched<T, 4, 4>(plan, 2, bb, rowptr, col, term, epi, red); break;
       case 3: class_rows_batched<T, 8, 8>(plan, 3, bb, rowptr, col, term, epi, red); break;
-      case 4: class_rows_batched<T, 16, kRowsPerGroup16>(plan, 4, bb, rowptr, col, term, epi, red); break;
-      default: class_rows_batched<T, 32, kRowsPerGroup32>(plan, 5, bb, rowptr, col, term, epi, red); break;
+      case 4:
+        if constexpr (sizeof(T) == 8) class_rows_block<T, 16>(plan, 4, bb, rowptr, col, term, epi, red);
+        else class_rows_batched<T, 16, 1>(plan, 4, bb, rowptr, col, term, epi, red);
+        break;
+      default:
+        if constexpr (sizeof(T) == 8) class_rows_block<T, 32>(plan, 5, bb, rowptr, col, term, epi, red);
+        else class_rows_batched<T, 32, 1>(plan, 5, bb, rowptr, col, term, epi, red);
+        break;
     }
   }
   if constexpr (NRED > 0) {
