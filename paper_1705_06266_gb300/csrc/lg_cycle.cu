@@ -16,6 +16,28 @@ namespace lg {
 
 constexpr int kVT = 256;
 
+// Scalars of the FP64 PCG (device array ws.scal).
+enum Scal : int {
+  kBB = 0,     // ||b_m||^2
+  kRZ = 1,     // r^T z (projected z)
+  kPQ = 2,     // p^T L p
+  kAlpha = 3,
+  kBeta = 4,
+  kMeanZ = 5,
+  kRR = 6,     // ||r||^2
+  kSumB = 7,
+  kBreak = 8,  // 1 after a breakdown
+  kZ0 = 9,     // 5 sums of the z reduction (9..13)
+  kTmp = 14,   // 2 scratch totals (14..15)
+  kIter = 16,  // iterations done
+  kDone = 17,  // 1 once the true residual met the tolerance
+  kTol2BB = 18,  // tol^2 ||b_m||^2
+  kMaxit = 19,
+  kEvery = 20,   // true-residual replacement period
+  kNeedTrue = 21,  // 1 when this iteration recomputes the true residual
+  kNScal = 24
+};
+
 #define LG_GRID_STRIDE(i, n) \
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
 
@@ -153,21 +175,49 @@ static void op_pass(Workspace& ws, int level, const OpView<T>& op, const Term& t
   if (timed) ws.prof.end(s, level, pass_bytes(op.n, op.nnz, (int)sizeof(T), streams));
 }
 
+// The PCG's reduction over the preconditioned residual z (see k_z_reduce),
+// when the kernel that produces z computes it on the way.
+struct ZSums {
+  const double* r = nullptr;   // null: no reduction
+  const double* ro = nullptr;
+  double* scal = nullptr;
+  double* partials = nullptr;
+  unsigned* ticket = nullptr;
+};
+__device__ void z_sums_finish(int64_t n, double* scal, int first);
+
 // x = P x_c + Fsmooth(f) at an elimination level: kept vertices take their
-// coarse value; an eliminated f takes (f_f + sum_c w_fc x_c) / d_f.
-template <typename T>
+// coarse value; an eliminated f takes (f_f + sum_c w_fc x_c) / d_f. At level 0
+// of a PCG iteration the same kernel also forms the sums over z = x (zs).
+template <typename T, bool kZ>
 __global__ void k_elim_prolong(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                                const T* __restrict__ w, const T* __restrict__ dinv, const int32_t* __restrict__ cmap,
-                               const T* __restrict__ f, const T* __restrict__ xc, T* __restrict__ x) {
+                               const T* __restrict__ f, const T* __restrict__ xc, T* __restrict__ x, ZSums zs) {
+  int first = 0;
+  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  if constexpr (kZ) first = zs.scal[kIter] == 0.0;
   LG_GRID_STRIDE(i, n) {
     const int32_t c = cmap[i];
+    T v;
     if (c >= 0) {
-      x[i] = xc[c];
+      v = xc[c];
     } else {
       T s = f[i];
       for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) s += w[k] * xc[cmap[col[k]]];
-      x[i] = s * dinv[i];
+      v = s * dinv[i];
     }
+    x[i] = v;
+    if constexpr (kZ) {
+      const double zi = (double)v, ri = zs.r[i], roi = first ? 0.0 : zs.ro[i];
+      acc[0] += zi;
+      acc[1] += zi * ri;
+      acc[2] += zi * roi;
+      acc[3] += ri;
+      acc[4] += roi;
+    }
+  }
+  if constexpr (kZ) {
+    if (grid_sum<kVT, 5>(acc, zs.partials, zs.ticket, zs.scal + kZ0)) z_sums_finish(n, zs.scal, first);
   }
 }
 
@@ -240,7 +290,7 @@ static void next_dir(Hier& h, Workspace& ws, int l, T** d0, const T** dinv, T* i
 // Precondition: level l's f (and d_0 = dA when l smooths) hold the input.
 // Postcondition: level l's x holds the cycle's result.
 template <typename T>
-static void cycle_level(Hier& h, Workspace& ws, int l, cudaStream_t s) {
+static void cycle_level(Hier& h, Workspace& ws, int l, cudaStream_t s, const ZSums& zs = ZSums{}) {
   const Level& L = *h.levels[l];
   LevelVecs<T>& V = vecs<T>(ws)[l];
   const int64_t n = L.n;
@@ -261,8 +311,12 @@ static void cycle_level(Hier& h, Workspace& ws, int l, cudaStream_t s) {
                       EpiElimRestrict<T>{V.f.get(), L.cfine.get(), C.f.get(), d0n, dinvn, itn}, s);
     cycle_level<T>(h, ws, l + 1, s);
     const OpView<T> op = L.op<T>();
-    k_elim_prolong<T><<<vblocks(n), kVT, 0, s>>>(n, op.rowptr, op.col, op.w, op.dinv, L.cmap.get(), V.f.get(),
-                                                C.x.get(), V.x.get());
+    if (zs.r)
+      k_elim_prolong<T, true><<<vblocks(n), kVT, 0, s>>>(n, op.rowptr, op.col, op.w, op.dinv, L.cmap.get(),
+                                                        V.f.get(), C.x.get(), V.x.get(), zs);
+    else
+      k_elim_prolong<T, false><<<vblocks(n), kVT, 0, s>>>(n, op.rowptr, op.col, op.w, op.dinv, L.cmap.get(),
+                                                         V.f.get(), C.x.get(), V.x.get(), zs);
     LG_LAUNCH_CHECK();
     return;
   }
@@ -310,8 +364,10 @@ static void cycle_level(Hier& h, Workspace& ws, int l, cudaStream_t s) {
 }
 
 // Level-0 cycle from an FP64 vector r0; result in level 0's x (precision T).
+// zs: the PCG's sums over that result, formed by the cycle's last kernel
+// when level 0 is an elimination level (returns whether it did).
 template <typename T>
-static void cycle_from(Hier& h, Workspace& ws, const double* r0, cudaStream_t s) {
+static bool cycle_from(Hier& h, Workspace& ws, const double* r0, cudaStream_t s, const ZSums& zs = ZSums{}) {
   const Level& L0 = *h.levels[0];
   LevelVecs<T>& V = vecs<T>(ws)[0];
   T* d0 = nullptr;
@@ -324,7 +380,9 @@ static void cycle_from(Hier& h, Workspace& ws, const double* r0, cudaStream_t s)
   }
   k_cycle_in<T><<<vblocks(L0.n), kVT, 0, s>>>(L0.n, r0, V.f.get(), d0, dinv, it);
   LG_LAUNCH_CHECK();
-  cycle_level<T>(h, ws, 0, s);
+  const bool fused = L0.kind == LG_LEVEL_ELIM && zs.r != nullptr;
+  cycle_level<T>(h, ws, 0, s, fused ? zs : ZSums{});
+  return fused;
 }
 
 __global__ void k_gather_perm(int64_t n, const int32_t* __restrict__ perm, const double* __restrict__ src,
@@ -357,26 +415,6 @@ void vcycle_apply(Hier& h, Workspace& ws, const double* f, double* x, int precis
 // FP64 preconditioned CG (Sections 2.3, 4). Scalars live on the device so the
 // iteration needs no host round trip except the convergence test.
 // ---------------------------------------------------------------------------
-enum Scal : int {
-  kBB = 0,     // ||b_m||^2
-  kRZ = 1,     // r^T z (projected z)
-  kPQ = 2,     // p^T L p
-  kAlpha = 3,
-  kBeta = 4,
-  kMeanZ = 5,
-  kRR = 6,     // ||r||^2
-  kSumB = 7,
-  kBreak = 8,  // 1 after a breakdown
-  kZ0 = 9,     // 5 sums of the z reduction (9..13)
-  kTmp = 14,   // 2 scratch totals (14..15)
-  kIter = 16,  // iterations done
-  kDone = 17,  // 1 once the true residual met the tolerance
-  kTol2BB = 18,  // tol^2 ||b_m||^2
-  kMaxit = 19,
-  kEvery = 20,   // true-residual replacement period
-  kNeedTrue = 21,  // 1 when this iteration recomputes the true residual
-  kNScal = 24
-};
 
 __global__ void k_sum1(int64_t n, const double* __restrict__ v, double* partials, unsigned* ticket, double* out) {
   double acc[1] = {0.0};
@@ -410,28 +448,6 @@ __global__ void k_pcg_init(int64_t n, const double* __restrict__ b, const int32_
   }
 }
 
-// After the x, r update of an iteration: count it, and ask for the true
-// residual on replacement iterations or when the recurrence residual meets
-// the tolerance.
-__global__ void k_pcg_gate(double* scal) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const double it = scal[kIter] + 1.0;
-  scal[kIter] = it;
-  const bool need = fmod(it, scal[kEvery]) == 0.0 || scal[kRR] <= scal[kTol2BB];
-  scal[kNeedTrue] = need ? 1.0 : 0.0;
-}
-
-// End of an iteration: converged once the true residual meets the tolerance;
-// stop on convergence, breakdown or max_iter. Inside the graph it sets the
-// loop condition of the WHILE node; the iteration bound always holds.
-__global__ void k_pcg_cond(double* scal, cudaGraphConditionalHandle handle, int in_graph) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const bool conv = scal[kNeedTrue] != 0.0 && scal[kRR] <= scal[kTol2BB];
-  if (conv) scal[kDone] = 1.0;
-  const bool cont = !conv && scal[kBreak] == 0.0 && scal[kIter] < scal[kMaxit];
-  if (in_graph) cudaGraphSetConditional(handle, cont ? 1u : 0u);
-}
-
 // Sums over the preconditioned residual z (precision T, mean not yet
 // removed): sum z, z.r, z.r_old, sum r, sum r_old. The last block derives the
 // projected products (z - mean(z)).v = z.v - mean(z) sum v, the Polak-Ribiere
@@ -450,19 +466,23 @@ __global__ void k_z_reduce(int64_t n, const T* __restrict__ z, const double* __r
     acc[3] += ri;
     acc[4] += roi;
   }
-  if (grid_sum<kVT, 5>(acc, partials, ticket, scal + kZ0)) {
-    const double m = scal[kZ0] / (double)n;
-    const double zr = scal[kZ0 + 1] - m * scal[kZ0 + 3];
-    const double zro = scal[kZ0 + 2] - m * scal[kZ0 + 4];
-    scal[kMeanZ] = m;
-    if (first) {
-      scal[kBeta] = 0.0;
-    } else {
-      scal[kBeta] = (zr - zro) / scal[kRZ];
-    }
-    if (!(zr > 0.0) || !isfinite(zr)) scal[kBreak] = 1.0;
-    scal[kRZ] = zr;
+  if (grid_sum<kVT, 5>(acc, partials, ticket, scal + kZ0)) z_sums_finish(n, scal, first);
+}
+
+// From the five sums: the mean of z, the projected r^T z and the
+// Polak-Ribiere beta (0 on the first iteration); breakdown on r^T z <= 0.
+__device__ void z_sums_finish(int64_t n, double* scal, int first) {
+  const double m = scal[kZ0] / (double)n;
+  const double zr = scal[kZ0 + 1] - m * scal[kZ0 + 3];
+  const double zro = scal[kZ0 + 2] - m * scal[kZ0 + 4];
+  scal[kMeanZ] = m;
+  if (first) {
+    scal[kBeta] = 0.0;
+  } else {
+    scal[kBeta] = (zr - zro) / scal[kRZ];
   }
+  if (!(zr > 0.0) || !isfinite(zr)) scal[kBreak] = 1.0;
+  scal[kRZ] = zr;
 }
 
 // p = (z - mean z) + beta p.
@@ -480,7 +500,9 @@ struct EpiQ {
   __device__ void finish(const double*) const {}
 };
 
-// p^T q; the last block sets alpha = r^T z / p^T q (0 after a breakdown).
+// p^T q; the last block sets alpha = r^T z / p^T q (0 after a breakdown). A
+// separate kernel: summing inside the q pass would put a grid-wide ticket on
+// every one of its many small blocks.
 __global__ void k_pq_dot(int64_t n, const double* __restrict__ p, const double* __restrict__ q, double* scal,
                          double* partials, unsigned* ticket) {
   double acc[1] = {0.0};
@@ -497,10 +519,14 @@ __global__ void k_pq_dot(int64_t n, const double* __restrict__ p, const double* 
   }
 }
 
-// r_old = r; x += alpha p; r -= alpha q; ||r||^2.
+// r_old = r; x += alpha p; r -= alpha q; ||r||^2. The last block counts the
+// iteration and asks for the true residual on replacement iterations or when
+// the recurrence residual meets the tolerance; without that request it also
+// sets the loop condition (inside the graph): go on unless broken down or at
+// max_iter.
 __global__ void k_xr_update(int64_t n, double* __restrict__ x, double* __restrict__ r, double* __restrict__ ro,
                             const double* __restrict__ p, const double* __restrict__ q, double* scal,
-                            double* partials, unsigned* ticket) {
+                            double* partials, unsigned* ticket, cudaGraphConditionalHandle handle, int in_graph) {
   const double a = scal[kAlpha];
   double acc[1] = {0.0};
   LG_GRID_STRIDE(i, n) {
@@ -511,7 +537,13 @@ __global__ void k_xr_update(int64_t n, double* __restrict__ x, double* __restric
     r[i] = rn;
     acc[0] += rn * rn;
   }
-  grid_sum<kVT, 1>(acc, partials, ticket, scal + kRR);
+  if (grid_sum<kVT, 1>(acc, partials, ticket, scal + kRR)) {
+    const double it = scal[kIter] + 1.0;
+    scal[kIter] = it;
+    const bool need = fmod(it, scal[kEvery]) == 0.0 || scal[kRR] <= scal[kTol2BB];
+    scal[kNeedTrue] = need ? 1.0 : 0.0;
+    if (!need && in_graph) cudaGraphSetConditional(handle, scal[kBreak] == 0.0 && it < scal[kMaxit] ? 1u : 0u);
+  }
 }
 
 // r = b_m - L x (true residual).
@@ -524,12 +556,20 @@ struct EpiTrueRes {
 };
 
 // ||r||^2 into scal[kRR]; skipped like the pass before it when gated off.
+// Inside the PCG loop (loop = 1) the last block also ends the iteration:
+// converged once this true residual meets the tolerance; the loop condition
+// (inside the graph) is to go on unless converged, broken down or at max_iter.
 __global__ void k_rr(int64_t n, const double* __restrict__ r, double* scal, double* partials, unsigned* ticket,
-                     const double* gate) {
+                     const double* gate, int loop, cudaGraphConditionalHandle handle, int in_graph) {
   if (gate && *gate == 0.0) return;
   double acc[1] = {0.0};
   LG_GRID_STRIDE(i, n) acc[0] += r[i] * r[i];
-  grid_sum<kVT, 1>(acc, partials, ticket, scal + kRR);
+  if (grid_sum<kVT, 1>(acc, partials, ticket, scal + kRR) && loop) {
+    const bool conv = scal[kRR] <= scal[kTol2BB];
+    if (conv) scal[kDone] = 1.0;
+    const bool cont = !conv && scal[kBreak] == 0.0 && scal[kIter] < scal[kMaxit];
+    if (in_graph) cudaGraphSetConditional(handle, cont ? 1u : 0u);
+  }
 }
 
 // out[perm[i]] = x[i] - mean(x): back to the caller's numbering, mean removed.
@@ -594,44 +634,48 @@ std::unique_ptr<Workspace> make_workspace(Hier& h, int k, cudaStream_t s) {
   return ws;
 }
 
-// One PCG iteration: z = M r (cycle in T), beta, p; q = L p, alpha, x, r;
-// then the gate, the gated true residual and the loop condition.
-static void true_residual(Hier& h, Workspace& ws, cudaStream_t s, const double* gate);
+// One PCG iteration: z = M r (cycle in T) with its sums, beta, p; q = L p;
+// p^T q and alpha; x, r with the true-residual request; the requested true
+// residual, which decides convergence. The loop condition is set by the
+// update kernel, or by the true residual's when it runs.
+static void true_residual(Hier& h, Workspace& ws, cudaStream_t s, const double* gate, int loop,
+                          cudaGraphConditionalHandle handle, int in_graph);
 
 template <typename T>
 static void pcg_body(Hier& h, Workspace& ws, cudaStream_t s, cudaGraphConditionalHandle handle, int in_graph) {
   const Level& L0 = *h.levels[0];
   const int64_t n = L0.n;
   double* scal = ws.scal.get();
-  cycle_from<T>(h, ws, ws.r.get(), s);
+  const ZSums zs{ws.r.get(), ws.ro.get(), scal, ws.partials.get(), ws.tickets.get()};
   const T* z = vecs<T>(ws)[0].x.get();
-  k_z_reduce<T><<<vblocks(n), kVT, 0, s>>>(n, z, ws.r.get(), ws.ro.get(), scal, ws.partials.get(), ws.tickets.get());
-  LG_LAUNCH_CHECK();
+  if (!cycle_from<T>(h, ws, ws.r.get(), s, zs)) {
+    k_z_reduce<T><<<vblocks(n), kVT, 0, s>>>(n, z, ws.r.get(), ws.ro.get(), scal, ws.partials.get(),
+                                             ws.tickets.get());
+    LG_LAUNCH_CHECK();
+  }
   k_p_update<T><<<vblocks(n), kVT, 0, s>>>(n, z, ws.p.get(), scal);
   LG_LAUNCH_CHECK();
   OpView<double> op = L0.op<double>();
   op.plan = ws.scratch[0].op.bind(op.plan);
-  op_pass<double, 0>(ws, 0, op, LapTerm<double>{op.w, ws.p.get(), op.d}, EpiQ{ws.q.get()}, 0, s);
+  op_pass<double, 0>(ws, 0, op, LapTerm<double>{op.w, ws.p.get(), op.d}, EpiQ{ws.q.get()}, 1, s);
   k_pq_dot<<<vblocks(n), kVT, 0, s>>>(n, ws.p.get(), ws.q.get(), scal, ws.partials.get(), ws.tickets.get());
   LG_LAUNCH_CHECK();
   k_xr_update<<<vblocks(n), kVT, 0, s>>>(n, ws.x.get(), ws.r.get(), ws.ro.get(), ws.p.get(), ws.q.get(), scal,
-                                        ws.partials.get(), ws.tickets.get());
+                                        ws.partials.get(), ws.tickets.get(), handle, in_graph);
   LG_LAUNCH_CHECK();
-  k_pcg_gate<<<1, 32, 0, s>>>(scal);
-  LG_LAUNCH_CHECK();
-  true_residual(h, ws, s, scal + kNeedTrue);
-  k_pcg_cond<<<1, 32, 0, s>>>(scal, handle, in_graph);
-  LG_LAUNCH_CHECK();
+  true_residual(h, ws, s, scal + kNeedTrue, 1, handle, in_graph);
 }
 
-static void true_residual(Hier& h, Workspace& ws, cudaStream_t s, const double* gate) {
+static void true_residual(Hier& h, Workspace& ws, cudaStream_t s, const double* gate, int loop,
+                          cudaGraphConditionalHandle handle, int in_graph) {
   const Level& L0 = *h.levels[0];
   OpView<double> op = L0.op<double>();
   op.plan = ws.scratch[0].op.bind(op.plan);
   double* scal = ws.scal.get();
   op_pass<double, 0>(ws, 0, op, LapTerm<double>{op.w, ws.x.get(), op.d}, EpiTrueRes{ws.bm.get(), ws.r.get()}, 2, s,
                      nullptr, nullptr, nullptr, gate);
-  k_rr<<<vblocks(L0.n), kVT, 0, s>>>(L0.n, ws.r.get(), scal, ws.partials.get(), ws.tickets.get(), gate);
+  k_rr<<<vblocks(L0.n), kVT, 0, s>>>(L0.n, ws.r.get(), scal, ws.partials.get(), ws.tickets.get(), gate, loop, handle,
+                                     in_graph);
   LG_LAUNCH_CHECK();
 }
 
@@ -721,7 +765,7 @@ int pcg_solve(Hier& h, Workspace& ws, const double* b, double* x, double tol, in
     rel = std::sqrt(hs[kRR] / bb);
   }
   if (status != LG_OK && bb > 0.0) {
-    true_residual(h, ws, s, nullptr);
+    true_residual(h, ws, s, nullptr, 0, cudaGraphConditionalHandle{}, 0);
     read_scal(ws, s);
     rel = std::sqrt(ws.host_scal[kRR] / bb);
   }
