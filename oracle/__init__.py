@@ -45,6 +45,7 @@ class Opts(C.Structure):
         ("vote_threshold", C.c_int32), ("strength_vecs", C.c_int32), ("strength_sweeps", C.c_int32),
         ("cheb_degree", C.c_int32), ("eig_iters", C.c_int32), ("max_coarse_n", C.c_int32),
         ("elim_enable", C.c_int32),
+        ("kcycle", C.c_int32),
     ]
 
 
@@ -90,6 +91,7 @@ def _load():
         "lgref_hier_level_map": (None, [_P, _I32, _P]),
         "lgref_hier_coarsest_pinv": (None, [_P, _P]),
         "lgref_vcycle": (None, [_P, _P, _P]),
+        "lgref_level_cycle": (None, [_P, C.c_int32, _P, _P, C.c_int32]),
         "lgref_pcg": (C.c_int, [_P, _P, _P, _D, _I32, _P, _P]),
         "lgref_csr_n": (_I64, [_P]),
         "lgref_csr_nnz": (_I64, [_P]),
@@ -351,6 +353,14 @@ class Hierarchy:
         f = np.ascontiguousarray(f, dtype=np.float64)
         x = np.zeros(self.n)
         _load().lgref_vcycle(self._h, _ptr(f), _ptr(x))
+        return x
+
+    def level_cycle(self, l: int, f, body_only: bool = False) -> np.ndarray:
+        """The cycle at level l from x = 0 (body_only: without that level's own
+        K-cycle acceleration)."""
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        x = np.zeros(len(f))
+        _load().lgref_level_cycle(self._h, int(l), _ptr(f), _ptr(x), 1 if body_only else 0)
         return x
 
     def pcg(self, b, tol: float = 1e-8, maxit: int = 500):

@@ -916,8 +916,72 @@ void lgref_hier_coarsest_pinv(const lgref_hier* h, double* out) {
 /* ------------------------------------------------------------------------ */
 /* Multigrid cycle (Algorithm "Multigrid cycle", gamma = 1: a V-cycle) with  */
 /* x = 0 on entry at every level (it is applied as a preconditioner).        */
+/* With the K-cycle (Section 3.7) the system of every aggregation level      */
+/* below the first is solved by two FCG iterations preconditioned by that    */
+/* level's cycle (so each such level is visited twice per visit of the one   */
+/* above: cycle index 2). Readings: the first aggregation level is left to   */
+/* the outer Krylov method, and elimination levels, exact, get no Krylov     */
+/* (Section 3.7 says so); two iterations, no residual test between them.    */
 /* ------------------------------------------------------------------------ */
+static void cycle(const lgref_hier* h, int32_t l, const double* f, double* x);
+
+static double dot(int64_t n, const double* a, const double* b);
+
+static int32_t first_agg_level(const lgref_hier* h) {
+  for (int32_t l = 0; l < h->nlev; ++l)
+    if (h->lev[l].kind == LGREF_LEVEL_AGG) return l;
+  return -1;
+}
+
+static void cycle_body(const lgref_hier* h, int32_t l, const double* f, double* x);
+
+/* Two FCG iterations on L_l x = f from x = 0, preconditioner B = the level's
+ * cycle body (Notay & Vassilevski's K-cycle with two inner iterations):
+ *   c1 = B f, v1 = L c1, rho1 = c1.v1, t1 = c1.f / rho1, r1 = f - t1 v1;
+ *   c2 = B r1, v2 = L c2, g = c2.v1, rho2 = c2.v2 - g^2 / rho1,
+ *   x = (t1 - g (c2.r1) / (rho1 rho2)) c1 + ((c2.r1) / rho2) c2,
+ * the second direction being c2 made L-orthogonal to c1. A non-positive
+ * rho1 gives x = c1, a non-positive rho2 x = t1 c1. */
+static void kcycle_solve(const lgref_hier* h, int32_t l, const double* f, double* x) {
+  const level_t* L = &h->lev[l];
+  const int64_t n = L->a.n;
+  double* c1 = (double*)xcalloc((size_t)n, sizeof(double));
+  double* c2 = (double*)xcalloc((size_t)n, sizeof(double));
+  double* v1 = (double*)xmalloc(sizeof(double) * (size_t)n);
+  double* v2 = (double*)xmalloc(sizeof(double) * (size_t)n);
+  double* r1 = (double*)xmalloc(sizeof(double) * (size_t)n);
+  cycle_body(h, l, f, c1);
+  lgref_apply_L(n, L->a.rowptr, L->a.col, L->a.w, c1, v1);
+  const double rho1 = dot(n, c1, v1);
+  if (!(rho1 > 0.0)) {
+    memcpy(x, c1, sizeof(double) * (size_t)n);
+  } else {
+    const double t1 = dot(n, c1, f) / rho1;
+    for (int64_t i = 0; i < n; ++i) r1[i] = f[i] - t1 * v1[i];
+    cycle_body(h, l, r1, c2);
+    lgref_apply_L(n, L->a.rowptr, L->a.col, L->a.w, c2, v2);
+    const double g = dot(n, c2, v1);
+    const double rho2 = dot(n, c2, v2) - g * g / rho1;
+    if (!(rho2 > 0.0)) {
+      for (int64_t i = 0; i < n; ++i) x[i] = t1 * c1[i];
+    } else {
+      const double a2 = dot(n, c2, r1);
+      const double u1 = t1 - g * a2 / (rho1 * rho2), u2 = a2 / rho2;
+      for (int64_t i = 0; i < n; ++i) x[i] = u1 * c1[i] + u2 * c2[i];
+    }
+  }
+  free(r1); free(v2); free(v1); free(c2); free(c1);
+}
+
 static void cycle(const lgref_hier* h, int32_t l, const double* f, double* x) {
+  if (h->o.kcycle && h->lev[l].kind == LGREF_LEVEL_AGG && l != first_agg_level(h)) {
+    kcycle_solve(h, l, f, x);
+    return;
+  }
+  cycle_body(h, l, f, x);
+}
+
+static void cycle_body(const lgref_hier* h, int32_t l, const double* f, double* x) {
   const level_t* L = &h->lev[l];
   int64_t n = L->a.n;
   const int64_t* rp = L->a.rowptr;
@@ -973,6 +1037,13 @@ static void cycle(const lgref_hier* h, int32_t l, const double* f, double* x) {
 }
 
 void lgref_vcycle(const lgref_hier* h, const double* f, double* x) { cycle(h, 0, f, x); }
+
+void lgref_level_cycle(const lgref_hier* h, int32_t l, const double* f, double* x, int32_t body_only) {
+  const int64_t n = h->lev[l].a.n;
+  for (int64_t i = 0; i < n; ++i) x[i] = 0.0;
+  if (body_only) cycle_body(h, l, f, x);
+  else cycle(h, l, f, x);
+}
 
 static double dot(int64_t n, const double* a, const double* b) {
   double s = 0.0;

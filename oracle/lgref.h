@@ -51,6 +51,7 @@ typedef struct {
   int32_t eig_iters;       /* 10 (Section 3.6) */
   int32_t max_coarse_n;    /* 4096: largest coarsest level for the dense solve */
   int32_t elim_enable;     /* 1 */
+  int32_t kcycle;          /* 0: V-cycle (Section 4's default); 1: K-cycle (Section 3.7) */
 } lgref_opts;
 
 void lgref_opts_default(lgref_opts* o);
@@ -115,6 +116,10 @@ void lgref_hier_level_csr(const lgref_hier* h, int32_t l, int64_t* rowptr, int32
 void lgref_hier_level_map(const lgref_hier* h, int32_t l, int32_t* map);
 void lgref_hier_coarsest_pinv(const lgref_hier* h, double* out);
 void lgref_vcycle(const lgref_hier* h, const double* f, double* x);
+/* The cycle at level l from x = 0 (what the level above applies to its
+ * restricted residual). body_only = 1 leaves out the level's own K-cycle
+ * acceleration (its coarser levels keep theirs). */
+void lgref_level_cycle(const lgref_hier* h, int32_t l, const double* f, double* x, int32_t body_only);
 int lgref_pcg(const lgref_hier* h, const double* b, double* x, double tol, int32_t maxit,
               int32_t* iters, double* relres);
 

@@ -458,3 +458,57 @@ def test_setup_errors(oracle, inputs):
         oracle.Hierarchy(inputs.Graph(g.n + 1, rp, g.col, g.w))
     with pytest.raises(RuntimeError, match="status 3"):
         oracle.Hierarchy(inputs.grid2d(30, 30), oracle.default_opts(max_levels=1, max_coarse_n=100))
+
+
+# ---------------------------------------------------------------------------
+# K-cycle (Section 3.7): two FCG iterations from x = 0 with a fixed linear
+# preconditioner B give the L-orthogonal projection of the solution onto
+# span{B f, B L B f}, x = V (V^T L V)^-1 V^T f. On a hierarchy whose second
+# aggregation level sits right above the coarsest (exact) solve, that level's
+# cycle body is linear, so the K-solve there is pinned by this closed form.
+# ---------------------------------------------------------------------------
+def _lap_dense(a):
+    n = a.n
+    A = np.zeros((n, n))
+    for i in range(n):
+        for k in range(a.rowptr[i], a.rowptr[i + 1]):
+            A[i, a.col[k]] -= a.w[k]
+            A[i, i] += a.w[k]
+    return A
+
+
+@pytest.mark.parametrize("name", ["grid24", "rand800"])
+def test_kcycle_two_fcg_steps_are_an_energy_projection(oracle, inputs, name):
+    g = inputs.grid2d(24, 24) if name == "grid24" else inputs.random_graph(800, 6, seed=3)
+    h = oracle.Hierarchy(g, oracle.default_opts(elim_enable=0, coarse_nnz=600, kcycle=1))
+    kinds = [h.level(l).kind for l in range(h.nlevels)]
+    assert kinds == [oracle.AGG, oracle.AGG, oracle.COARSEST]
+    lv = h.level(1)
+    n1 = lv.a.n
+    A = _lap_dense(lv.a)
+    B = np.column_stack([h.level_cycle(1, np.eye(n1)[j], body_only=True) for j in range(n1)])
+    f = np.random.default_rng(5).standard_normal(n1)
+    f -= f.mean()
+    V = np.column_stack([B @ f, B @ (A @ (B @ f))])
+    ref = V @ np.linalg.solve(V.T @ A @ V, V.T @ f)
+    x = h.level_cycle(1, f)
+    assert np.linalg.norm(x - ref) <= 1e-9 * np.linalg.norm(ref)
+    # the first aggregation level is left to the outer Krylov method
+    f0 = np.random.default_rng(6).standard_normal(g.n)
+    f0 -= f0.mean()
+    np.testing.assert_array_equal(h.level_cycle(0, f0), h.level_cycle(0, f0, body_only=True))
+    # with the V-cycle every level is its body
+    hv = oracle.Hierarchy(g, oracle.default_opts(elim_enable=0, coarse_nnz=600, kcycle=0))
+    np.testing.assert_array_equal(hv.level_cycle(1, f), hv.level_cycle(1, f, body_only=True))
+
+
+def test_kcycle_pcg_matches_dense(oracle, inputs):
+    g = inputs.grid2d(64, 64)
+    b = inputs.rhs(g.n, seed=2)
+    h = oracle.Hierarchy(g, oracle.default_opts(kcycle=1))
+    x, st, it, rel = h.pcg(b, tol=1e-8)
+    assert st == oracle.OK and rel <= 1e-8
+    ref = oracle.dense_solve(g, b)
+    assert np.linalg.norm(x - ref) <= 1e-6 * np.linalg.norm(ref)
+    _, _, it_v, _ = oracle.Hierarchy(g).pcg(b, tol=1e-8)
+    assert it <= it_v  # the K-cycle is the stronger preconditioner here
