@@ -101,7 +101,12 @@ typedef struct {
                                lines; solves take and return vectors in the caller's numbering.
                                0: keep the caller's numbering (the paper's random ordering, Section
                                3.3, serves a 2D distribution this library does not use) */
-  int32_t reserved;
+  int32_t kcycle;           /* 0: V-cycle (Section 4's default). 1: K-cycle (Section 3.7): every
+                               aggregation level below the first solves its system by two FCG
+                               iterations preconditioned by its own cycle (the first is accelerated
+                               by the outer iteration; elimination levels are exact). The outer
+                               iteration's Polak-Ribiere beta makes it flexible CG. Multi-column
+                               solves then run their columns one at a time. */
 } lg_options;
 
 /* Result of a setup or a solve. */

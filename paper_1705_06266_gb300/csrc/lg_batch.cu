@@ -897,6 +897,15 @@ int pcg_solve_batch(Hier& h, Workspace& ws, int k, const double* B, double* X, d
   if (k == 1) return pcg_solve(h, ws, B, X, tol, precision, s, infos);
   if (ws.k < k) fail(LG_ERR_INVALID, "workspace narrower than the batch");
   const int64_t n = h.levels[0]->n;
+  if (h.opts.kcycle) {  // the SpMM cycle is the V-cycle: K-cycle columns run one at a time
+    int worst = LG_OK;
+    for (int c = 0; c < k; ++c) {
+      const int st = pcg_solve(h, ws, B + (size_t)c * n, X + (size_t)c * n, tol, precision, s,
+                               infos ? infos + c : nullptr);
+      if (st != LG_OK && worst == LG_OK) worst = st;
+    }
+    return worst;
+  }
   const int kp = pow2_at_least(k);
   const bool f32 = precision == LG_FP32_HIER;
   k_cm_to_rm<<<bblocks(n * k), kBT, 0, s>>>(n, k, B, ws.z.get());
@@ -971,6 +980,11 @@ static void mcycle_apply(Hier& h, Workspace& ws, int k, const double* F, double*
 
 void vcycle_apply_batch(Hier& h, Workspace& ws, int k, const double* F, double* X, int precision, cudaStream_t s) {
   if (ws.k < k) fail(LG_ERR_INVALID, "workspace narrower than the batch");
+  if (h.opts.kcycle) {  // the SpMM cycle is the V-cycle: K-cycle columns one at a time
+    const int64_t n = h.levels[0]->n;
+    for (int c = 0; c < k; ++c) vcycle_apply(h, ws, F + (size_t)c * n, X + (size_t)c * n, precision, s);
+    return;
+  }
   if (precision == LG_FP32_HIER) mcycle_apply<float>(h, ws, k, F, X, s);
   else mcycle_apply<double>(h, ws, k, F, X, s);
 }

@@ -272,6 +272,87 @@ template <typename T> const T* pt_coef_of(const Level& L);
 template <> const double* pt_coef_of<double>(const Level& L) { return L.pt_coef.get(); }
 template <> const float* pt_coef_of<float>(const Level& L) { return L.pt_coef32.get(); }
 
+// ---------------------------------------------------------------------------
+// K-cycle (Section 3.7): two FCG iterations at an aggregation level, the
+// level's own cycle as the preconditioner (see kcycle_level). Sums in FP64.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct EpiKStore {  // y = L c
+  T* y;
+  __device__ __forceinline__ NoPre pre(int64_t) const { return NoPre{}; }
+  __device__ __forceinline__ void operator()(int64_t i, T s, NoPre, double*) const { y[i] = s; }
+  __device__ void finish(const double*) const {}
+};
+
+// c1 = x (kept), rho1 = c1.v1, c1.f; the last block: t1 = c1.f / rho1 (0 and
+// the flag cleared when rho1 is not positive).
+template <typename T>
+__global__ void k_kfirst(int64_t n, const T* __restrict__ x, const T* __restrict__ v1, const T* __restrict__ f,
+                         T* __restrict__ c1, double* ks, double* partials, unsigned* ticket) {
+  double acc[2] = {0.0, 0.0};
+  LG_GRID_STRIDE(i, n) {
+    const T xi = x[i];
+    c1[i] = xi;
+    acc[0] += (double)xi * (double)v1[i];
+    acc[1] += (double)xi * (double)f[i];
+  }
+  if (grid_sum<kVT, 2>(acc, partials, ticket, ks + kRho1)) {
+    const bool ok = ks[kRho1] > 0.0 && isfinite(ks[kRho1]);
+    ks[kOk1] = ok ? 1.0 : 0.0;
+    ks[kT1] = ok ? ks[kA1] / ks[kRho1] : 0.0;
+  }
+}
+
+// r1 = f - t1 v1 in place of f, and its first Chebyshev direction
+// d_0 = D^-1 r1 / theta: the input of the level's second cycle.
+template <typename T>
+__global__ void k_kres(int64_t n, T* __restrict__ f, const T* __restrict__ v1, const T* __restrict__ dinv,
+                       T inv_theta, T* __restrict__ d0, const double* ks) {
+  const T t1 = (T)ks[kT1];
+  LG_GRID_STRIDE(i, n) {
+    const T r = f[i] - t1 * v1[i];
+    f[i] = r;
+    d0[i] = r * dinv[i] * inv_theta;
+  }
+}
+
+// With x = c2: g = c2.v1, c2.v2, c2.r1; the last block forms the weights of
+// x = u1 c1 + u2 c2 (rho2 = c2.v2 - g^2 / rho1; u1 = t1 - g (c2.r1) / (rho1
+// rho2), u2 = (c2.r1) / rho2; x = c1 when rho1 was not positive, x = t1 c1
+// when rho2 is not).
+template <typename T>
+__global__ void k_ksecond(int64_t n, const T* __restrict__ x, const T* __restrict__ v1, const T* __restrict__ v2,
+                          const T* __restrict__ r1, double* ks, double* partials, unsigned* ticket) {
+  double acc[3] = {0.0, 0.0, 0.0};
+  LG_GRID_STRIDE(i, n) {
+    const double xi = (double)x[i];
+    acc[0] += xi * (double)v1[i];
+    acc[1] += xi * (double)v2[i];
+    acc[2] += xi * (double)r1[i];
+  }
+  if (grid_sum<kVT, 3>(acc, partials, ticket, ks + kG)) {
+    double u1 = 1.0, u2 = 0.0;
+    if (ks[kOk1] != 0.0) {
+      const double rho1 = ks[kRho1], t1 = ks[kT1], g = ks[kG], a2 = ks[kA2];
+      const double rho2 = ks[kB2] - g * g / rho1;
+      if (rho2 > 0.0 && isfinite(rho2)) {
+        u1 = t1 - g * a2 / (rho1 * rho2);
+        u2 = a2 / rho2;
+      } else {
+        u1 = t1;
+      }
+    }
+    ks[kU1] = u1;
+    ks[kU2] = u2;
+  }
+}
+
+template <typename T>
+__global__ void k_kcombine(int64_t n, const T* __restrict__ c1, T* __restrict__ x, const double* ks) {
+  const double u1 = ks[kU1], u2 = ks[kU2];
+  LG_GRID_STRIDE(i, n) x[i] = (T)(u1 * (double)c1[i] + u2 * (double)x[i]);
+}
+
 // Next level's d_0 target, when that level smooths.
 template <typename T>
 static void next_dir(Hier& h, Workspace& ws, int l, T** d0, const T** dinv, T* inv_theta) {
@@ -290,8 +371,16 @@ static void next_dir(Hier& h, Workspace& ws, int l, T** d0, const T** dinv, T* i
 // Precondition: level l's f (and d_0 = dA when l smooths) hold the input.
 // Postcondition: level l's x holds the cycle's result.
 template <typename T>
-static void cycle_level(Hier& h, Workspace& ws, int l, cudaStream_t s, const ZSums& zs = ZSums{}) {
+static void kcycle_level(Hier& h, Workspace& ws, int l, cudaStream_t s);
+
+template <typename T>
+static void cycle_level(Hier& h, Workspace& ws, int l, cudaStream_t s, const ZSums& zs = ZSums{},
+                        bool body = false) {
   const Level& L = *h.levels[l];
+  if (!body && h.opts.kcycle && L.kind == LG_LEVEL_AGG && l != h.first_agg) {
+    kcycle_level<T>(h, ws, l, s);
+    return;
+  }
   LevelVecs<T>& V = vecs<T>(ws)[l];
   const int64_t n = L.n;
   if (L.kind == LG_LEVEL_COARSEST) {
@@ -361,6 +450,38 @@ static void cycle_level(Hier& h, Workspace& ws, int l, cudaStream_t s, const ZSu
     k_axpy1<T><<<vblocks(n), kVT, 0, s>>>(n, V.dA.get(), V.x.get());
     LG_LAUNCH_CHECK();
   }
+}
+
+// K-cycle at aggregation level l (Section 3.7; Notay and Vassilevski's two
+// inner iterations): the level's system L_l x = f solved by two FCG
+// iterations from x = 0, preconditioned by the level's cycle body (which
+// recurses with the K-cycle below):
+//   c1 = B f, v1 = L c1, t1 = c1.f / c1.v1, r1 = f - t1 v1,
+//   c2 = B r1, v2 = L c2, x = u1 c1 + u2 c2 (k_ksecond).
+// Same pre/postconditions as cycle_level; f is overwritten by r1.
+template <typename T>
+static void kcycle_level(Hier& h, Workspace& ws, int l, cudaStream_t s) {
+  const Level& L = *h.levels[l];
+  LevelVecs<T>& V = vecs<T>(ws)[l];
+  const int64_t n = L.n;
+  OpView<T> op = L.op<T>();
+  op.plan = ws.scratch[l].op.bind(op.plan);
+  double* ks = ws.kscal.get() + (size_t)kKScal * l;
+  const int vb = vblocks(n);
+  cycle_level<T>(h, ws, l, s, ZSums{}, true);  // c1 in V.x
+  op_pass<T, 0>(ws, l, op, LapTerm<T>{op.w, V.x.get(), op.d}, EpiKStore<T>{V.kv1.get()}, 1, s);
+  k_kfirst<T><<<vb, kVT, 0, s>>>(n, V.x.get(), V.kv1.get(), V.f.get(), V.kc1.get(), ks, ws.partials.get(),
+                                 ws.tickets.get());
+  LG_LAUNCH_CHECK();
+  k_kres<T><<<vb, kVT, 0, s>>>(n, V.f.get(), V.kv1.get(), op.dinv, (T)h.cheb[l].inv_theta, V.dA.get(), ks);
+  LG_LAUNCH_CHECK();
+  cycle_level<T>(h, ws, l, s, ZSums{}, true);  // c2 in V.x
+  op_pass<T, 0>(ws, l, op, LapTerm<T>{op.w, V.x.get(), op.d}, EpiKStore<T>{V.kv2.get()}, 1, s);
+  k_ksecond<T><<<vb, kVT, 0, s>>>(n, V.x.get(), V.kv1.get(), V.kv2.get(), V.f.get(), ks, ws.partials.get(),
+                                  ws.tickets.get());
+  LG_LAUNCH_CHECK();
+  k_kcombine<T><<<vb, kVT, 0, s>>>(n, V.kc1.get(), V.x.get(), ks);
+  LG_LAUNCH_CHECK();
 }
 
 // Level-0 cycle from an FP64 vector r0; result in level 0's x (precision T).
@@ -599,6 +720,7 @@ std::unique_ptr<Workspace> make_workspace(Hier& h, int k, cudaStream_t s) {
     const size_t n = (size_t)lv.n * k;
     const bool smooth = lv.kind == LG_LEVEL_AGG;
     for (int prec = 0; prec < 2; ++prec) {
+      const bool kc = h.opts.kcycle && smooth && (int)l != h.first_agg;
       auto alloc = [&](auto& V) {
         V.f.alloc(n, s, c);
         V.x.alloc(n, s, c);
@@ -606,6 +728,11 @@ std::unique_ptr<Workspace> make_workspace(Hier& h, int k, cudaStream_t s) {
           V.r.alloc(n, s, c);
           V.dA.alloc(n, s, c);
           V.dB.alloc(n, s, c);
+        }
+        if (kc) {
+          V.kc1.alloc(n, s, c);
+          V.kv1.alloc(n, s, c);
+          V.kv2.alloc(n, s, c);
         }
       };
       if (prec == 0) alloc(ws->v64[l]); else alloc(ws->v32[l]);
@@ -628,6 +755,8 @@ std::unique_ptr<Workspace> make_workspace(Hier& h, int k, cudaStream_t s) {
   ws->partials.alloc((size_t)max_grid * (k > 1 ? 5 * kMaxCols : 8), s, c);
   ws->tickets.alloc(4, s, c);
   LG_CUDA(cudaMemsetAsync(ws->tickets.get(), 0, 4 * sizeof(unsigned), s));
+  ws->kscal.alloc((size_t)kKScal * L, s, c);
+  LG_CUDA(cudaMemsetAsync(ws->kscal.get(), 0, sizeof(double) * kKScal * L, s));
   ws->scal.alloc((size_t)kNScal * k, s, c);
   LG_CUDA(cudaMemsetAsync(ws->scal.get(), 0, sizeof(double) * kNScal * k, s));
   LG_CUDA(cudaMallocHost(&ws->host_scal, sizeof(double) * kNScal * k));

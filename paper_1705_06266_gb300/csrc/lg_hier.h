@@ -78,7 +78,11 @@ struct Cheb {
 template <typename T>
 struct LevelVecs {
   DBuf<T> f, x, r, dA, dB;
+  DBuf<T> kc1, kv1, kv2;  // K-cycle levels: the first FCG direction, L c1, L c2
 };
+
+// K-cycle scalars of one level (ws.kscal, kKScal per level).
+enum KScal : int { kRho1 = 0, kA1, kT1, kOk1, kG, kB2, kA2, kU1, kU2, kKScal = 10 };
 
 // Long-row scratch (chunk partials, per-row tickets) of one row plan, owned by
 // a workspace so that concurrent solves on one hierarchy never share it.
@@ -136,6 +140,7 @@ struct Workspace {
   DBuf<double> partials;               // grid reduction partials
   DBuf<unsigned> tickets;              // grid reduction tickets (zero between launches)
   DBuf<double> scal;                   // device scalars of the PCG (see lg_cycle.cu)
+  DBuf<double> kscal;                  // K-cycle scalars, kKScal per level
   double* host_scal = nullptr;         // pinned mirror of the scalars read by the host
   int64_t bytes = 0;
   Prof prof;
@@ -158,6 +163,7 @@ struct Hier {
   std::unique_ptr<Workspace> wsb;       // workspace of lg_solve_batch (widest batch so far)
   DBuf<int> dev_err;                    // device error word
   DBuf<int32_t> perm;                   // level-0 vertex i is the caller's vertex perm[i]
+  int first_agg = -1;                   // first aggregation level (-1: none)
   ~Hier();
 };
 

@@ -1333,6 +1333,10 @@ void setup_hierarchy(Hier& h, int64_t n, const int64_t* rowptr, const int32_t* c
     }
   }
 
+  h.first_agg = -1;
+  for (size_t l = 0; l < h.levels.size() && h.first_agg < 0; ++l)
+    if (h.levels[l]->kind == LG_LEVEL_AGG) h.first_agg = (int)l;
+
   // ---- Chebyshev constants from the eigenvalue estimates ----
   std::vector<double> lam(h.levels.size() + 1, 0.0);
   LG_CUDA(cudaMemcpyAsync(lam.data(), lam_dev.get(), sizeof(double) * h.levels.size(), cudaMemcpyDeviceToHost, s));

@@ -383,3 +383,66 @@ def test_vcycle_batch_matches_single(lgmod, inputs, name, prec):
         xs = H.vcycle(np.ascontiguousarray(F[:, c]), p)
         assert np.linalg.norm(X[:, c] - xs) <= tol * np.linalg.norm(xs), c
     H.close()
+
+
+# ---------------------------------------------------------------------------
+# K-cycle (Section 3.7): every aggregation level below the first solved by two
+# FCG iterations preconditioned by its own cycle.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("seed,n", [(4, 3000), (5, 6000)])
+def test_kcycle_matches_oracle(lgmod, oracle, inputs, seed, n):
+    """Where the oracle builds the identical hierarchy, one application of the
+    K-cycle preconditioner agrees to rounding (FP64)."""
+    g = inputs.random_graph(n, 6, seed=seed, weights="uniform")
+    H = lgmod.Hierarchy(g, reorder=0, kcycle=1)
+    R = oracle.Hierarchy(g, oracle.default_opts(kcycle=1))
+    assert H.nlevels == R.nlevels
+    kinds = [R.level(l).kind for l in range(R.nlevels)]
+    assert kinds.count(oracle.AGG) >= 2  # the K-cycle acts below the first aggregation level
+    for l in range(H.nlevels):
+        rp, cl, w, mp = H.level(l)
+        Lr = R.level(l)
+        np.testing.assert_array_equal(rp, Lr.a.rowptr)
+        np.testing.assert_array_equal(cl, Lr.a.col)
+        if mp is not None:
+            np.testing.assert_array_equal(mp, Lr.map)
+    f = inputs.rhs(g.n, seed=9)
+    xr = R.vcycle(f)
+    assert np.linalg.norm(xr - oracle.Hierarchy(g).vcycle(f)) > 1e-6 * np.linalg.norm(xr)  # differs from V
+    xg = H.vcycle(f, lgmod.FP64)
+    assert np.linalg.norm(xg - xr) <= 1e-9 * np.linalg.norm(xr)
+    x32 = H.vcycle(f, lgmod.FP32_HIER)
+    assert np.linalg.norm(x32 - xr) <= 1e-3 * np.linalg.norm(xr)
+    H.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", ["grid2d_64", "grid3d_16", "chunglu_20k"])
+def test_kcycle_solve(lgmod, oracle, inputs, name, prec):
+    g = {"grid2d_64": lambda: inputs.grid2d(64, 64), "grid3d_16": lambda: inputs.grid3d(16, 16, 16),
+         "chunglu_20k": lambda: inputs.chung_lu(20000, m_target=100000, seed=3)}[name]()
+    b = inputs.rhs(g.n, seed=2)
+    p = lgmod.FP64 if prec == "fp64" else lgmod.FP32_HIER
+    H = lgmod.Hierarchy(g, precision=p, kcycle=1)
+    x, info = H.solve(b, tol=1e-8)
+    assert info.status == lgmod.OK
+    assert relres(g, b, x) <= 1e-8
+    R = oracle.Hierarchy(g, oracle.default_opts(kcycle=1))
+    xr, st, it, _ = R.pcg(b, tol=1e-12)
+    xr -= xr.mean()
+    assert np.linalg.norm(x - x.mean() - xr) <= 1e-6 * np.linalg.norm(xr)
+    _, _, it8, _ = R.pcg(b, tol=1e-8)
+    assert abs(info.iterations - it8) <= (1 if prec == "fp64" else 3)
+    H.close()
+
+
+def test_kcycle_batch_runs_columns(lgmod, inputs):
+    g = inputs.grid3d(12, 12, 12)
+    B = inputs.rhs(g.n, 3, seed=4)
+    H = lgmod.Hierarchy(g, kcycle=1)
+    X, infos = H.solve_batch(B)
+    for c in range(3):
+        assert infos[c].status == lgmod.OK
+        xs, _ = H.solve(np.ascontiguousarray(B[:, c]))
+        np.testing.assert_array_equal(X[:, c], xs)
+    H.close()
