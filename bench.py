@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-multi-rhs", action="store_true")
     ap.add_argument("--multi-rhs-k", type=int, default=32)
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-kcycle", action="store_true")
     ap.add_argument("--serve-graphs", type=int, default=64)
     ap.add_argument("--serve-nmax", type=int, default=262144)
     ap.add_argument("--serve-requests", type=int, default=1000)
@@ -229,6 +230,34 @@ def multi_rhs_leg(lg, inputs, torch, dev, k):
             "sequential_iterations_max": max(seq_it),
             "speedup": seq_ms / batch_ms,
         }
+    return out
+
+
+def kcycle_leg(lg, inputs, torch, dev, g_main, b_main):
+    """The K-cycle (Section 3.7) beside the V-cycle: single right-hand-side
+    solves to 1e-8 from device-resident b, in both precisions, on the main
+    workload and on the 128^3 grid (where the V-cycle needs many iterations)."""
+    out = {}
+    for name, g, b in (("chung_lu_1m", g_main, b_main), ("grid3d_128", None, None)):
+        if g is None:
+            g = inputs.workload(name)
+            b = inputs.rhs(g.n, seed=2)
+        bd = torch.from_numpy(b).to(dev)
+        xd = torch.zeros_like(bd)
+        torch.cuda.synchronize()
+        row = {"n": g.n, "nnz": g.nnz}
+        for cyc in ((0, 1) if name == "grid3d_128" else (1,)):
+            h = lg.lg_setup(g.n, g.rowptr, g.col, g.w, lg.options(kcycle=cyc))
+            tag = "k" if cyc else "v"
+            for pname, prec in (("fp64", lg.FP64), ("fp32", lg.FP32_HIER)):
+                lg.lg_set_precision(h, prec)
+                lg.lg_solve(h, bd, xd, TOL)  # warm-up (graph capture)
+                inf = lg.lg_solve(h, bd, xd, TOL)
+                row[f"{tag}_{pname}_ms"] = inf.solve_ms
+                row[f"{tag}_{pname}_iterations"] = inf.iterations
+                row[f"{tag}_{pname}_nnz_per_s"] = g.nnz / (inf.solve_ms * 1e-3)
+            lg.lg_destroy(h)
+        out[name] = row
     return out
 
 
@@ -427,6 +456,7 @@ def main():
 
         # the other two workloads the metric names, after the timed region
         multi = None if args.no_multi_rhs else multi_rhs_leg(lg, inputs, torch, dev, args.multi_rhs_k)
+        kcyc = None if args.no_kcycle else kcycle_leg(lg, inputs, torch, dev, g, b)
         serve = None if args.no_serve else serve_leg(lg, inputs, args)
 
     setup_ms = sum(r[0].setup_ms for r in recs) / len(recs)
@@ -508,6 +538,8 @@ def main():
     }
     if multi is not None:
         line["multi_rhs"] = multi
+    if kcyc is not None:
+        line["kcycle"] = kcyc
     if serve is not None:
         line["serve"] = serve
     if world == 1 and not args.no_cpu_baseline:

@@ -115,6 +115,7 @@ int lg_options_default(lg_options* o) {
   o->use_graphs = 1;
   o->autotune = 1;
   o->reorder = 1;
+  o->kcycle = 0;
   return LG_OK;
 }
 
