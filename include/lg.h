@@ -351,9 +351,13 @@ int lg_serve_submit(lg_server_t s, lg_handle h, int32_t k, const double* B, doub
 int lg_serve_poll(lg_server_t s, uint64_t ticket, int32_t* done, lg_info* info);
 
 /* Device bytes the server reserves from its budget while a request of k
- * right-hand sides on h runs (its solve workspace and staging). A request is
- * admitted only when the registered hierarchies plus the requests already
- * running plus this figure fit the budget. */
+ * right-hand sides on h runs (its solve workspace, k rounded up to a power of
+ * two, and staging). A request is admitted only when the registered
+ * hierarchies plus the requests already running plus this figure fit the
+ * budget. Finished requests leave their workspaces in a pool for reuse by
+ * later requests on the same hierarchy; pooled workspaces count against the
+ * budget and are released, least recently used first, when a new request
+ * needs the room. */
 int lg_serve_request_bytes(lg_handle h, int32_t k, double* bytes);
 
 /* Latency and throughput statistics over completed requests. */

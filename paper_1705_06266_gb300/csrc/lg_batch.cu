@@ -2,17 +2,19 @@
 // columns at once (k <= 32), vectors stored row-major [n][k] so that the k
 // values of one vertex are contiguous.
 //
-// Every SpMV of the cycle becomes an SpMM pass: a warp takes one row, its 32
-// lanes split into S = 32 / KP entry slices of KP column lanes (KP = k rounded
-// up to a power of two); a slice walks every S-th entry of the row and each
-// of its lanes accumulates one column, so the k values gathered for an entry
-// are one coalesced access and every matrix entry is read once for all
-// columns. Rows longer than kChunkM entries are cut into chunks, one block
+// Every SpMV of the cycle becomes an SpMM pass over the lanes of a warp split
+// into S = 32 / KP entry slices of KP column lanes (KP = k rounded up to a
+// power of two); each lane of a slice accumulates one column, so the k values
+// gathered for an entry are one coalesced access and every matrix entry is
+// read once for all columns. Rows of at most kShortM entries take one slice
+// each (S rows per warp); longer rows take a warp, its slices walking every
+// S-th entry; rows longer than kChunkM entries are cut into chunks, one block
 // each, combined by the last block of the row in chunk order. The CG scalars
 // are per column; a column that has converged keeps its iterate (alpha = 0)
 // while the others go on.
 #include <algorithm>
 #include <cmath>
+#include <map>
 
 #include "lg_hier.h"
 #include "lg_rows.cuh"
@@ -36,7 +38,12 @@ static int pow2_at_least(int k) {
 // ---------------------------------------------------------------------------
 // Plans of the SpMM passes: rows longer than kChunkM entries in chunks.
 // ---------------------------------------------------------------------------
+constexpr int kShortM = 16;  // rows of at most this many entries take one entry slice each
+
 struct MPlan {
+  int64_t nshort = 0, nmed = 0;
+  const int32_t* short_rows = nullptr;  // rows of <= kShortM entries, ascending
+  const int32_t* med_rows = nullptr;    // rows of kShortM+1 .. kChunkM entries, ascending
   int64_t nchunks = 0;
   const int32_t* chunk_row = nullptr;
   const int64_t* chunk_beg = nullptr;
@@ -48,12 +55,20 @@ struct MPlan {
 };
 
 __global__ void k_mplan_count(int64_t n, const int64_t* __restrict__ rowptr, int64_t* __restrict__ nch,
-                              uint8_t* __restrict__ islong) {
+                              uint8_t* __restrict__ islong, uint8_t* __restrict__ isshort,
+                              uint8_t* __restrict__ ismed) {
   LG_GRID_STRIDE(i, n) {
     const int64_t deg = rowptr[i + 1] - rowptr[i];
     islong[i] = deg > kChunkM;
+    isshort[i] = deg <= kShortM;
+    ismed[i] = deg > kShortM && deg <= kChunkM;
     nch[i] = deg > kChunkM ? (deg + kChunkM - 1) / kChunkM : 0;
   }
+}
+
+__global__ void k_mplan_list(int64_t n, const uint8_t* __restrict__ flag, const int64_t* __restrict__ pos,
+                             int32_t* __restrict__ list) {
+  LG_GRID_STRIDE(i, n) if (flag[i]) list[pos[i]] = (int32_t)i;
 }
 
 __global__ void k_mplan_fill(int64_t n, const int64_t* __restrict__ rowptr, const uint8_t* __restrict__ islong,
@@ -74,24 +89,41 @@ __global__ void k_mplan_fill(int64_t n, const int64_t* __restrict__ rowptr, cons
 
 struct MPlanStore {
   MPlan plan;
+  DBuf<int32_t> short_rows, med_rows;
   DBuf<int32_t> chunk_row, chunk_lrow, lrow_first, lrow_count;
   DBuf<int64_t> chunk_beg;
   DBuf<double> partial;
   DBuf<unsigned> ticket;
   void build(int64_t n, const int64_t* rowptr, cudaStream_t s, int64_t* counter) {
-    DBuf<int64_t> nch(n + 1, s), lidx(n + 1, s);
-    DBuf<uint8_t> islong(n, s);
+    DBuf<int64_t> nch(n + 1, s), lidx(n + 1, s), sidx(n + 1, s), midx(n + 1, s);
+    DBuf<uint8_t> islong(n, s), isshort(n, s), ismed(n, s);
     const int g = grid_for(n, 256, kSMs * 16);
     if (n > 0) {
-      k_mplan_count<<<g, 256, 0, s>>>(n, rowptr, nch.get(), islong.get());
+      k_mplan_count<<<g, 256, 0, s>>>(n, rowptr, nch.get(), islong.get(), isshort.get(), ismed.get());
       LG_LAUNCH_CHECK();
     }
     exclusive_scan(nch.get(), nch.get(), n, s);
     exclusive_scan_flags(islong.get(), lidx.get(), n, s);
-    int64_t tot[2];
+    exclusive_scan_flags(isshort.get(), sidx.get(), n, s);
+    exclusive_scan_flags(ismed.get(), midx.get(), n, s);
+    int64_t tot[4];
     LG_CUDA(cudaMemcpyAsync(&tot[0], nch.get() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     LG_CUDA(cudaMemcpyAsync(&tot[1], lidx.get() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    LG_CUDA(cudaMemcpyAsync(&tot[2], sidx.get() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    LG_CUDA(cudaMemcpyAsync(&tot[3], midx.get() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     LG_CUDA(cudaStreamSynchronize(s));
+    plan.nshort = tot[2];
+    plan.nmed = tot[3];
+    short_rows.alloc(plan.nshort > 0 ? plan.nshort : 1, s, counter);
+    med_rows.alloc(plan.nmed > 0 ? plan.nmed : 1, s, counter);
+    if (n > 0) {
+      k_mplan_list<<<g, 256, 0, s>>>(n, isshort.get(), sidx.get(), short_rows.get());
+      LG_LAUNCH_CHECK();
+      k_mplan_list<<<g, 256, 0, s>>>(n, ismed.get(), midx.get(), med_rows.get());
+      LG_LAUNCH_CHECK();
+    }
+    plan.short_rows = short_rows.get();
+    plan.med_rows = med_rows.get();
     plan.nchunks = tot[0];
     const int64_t nlong = tot[1];
     chunk_row.alloc(plan.nchunks, s, counter);
@@ -178,7 +210,8 @@ struct MWGather {  // elimination restriction: sum coef_e v[j][c]
 template <typename T, int KP, class Term, class Epi>
 __global__ void __launch_bounds__(kBT)
 k_mrows(int64_t n, int k, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, Term term, MPlan plan,
-        Epi epi) {
+        Epi epi, const double* gate) {
+  if (gate && *gate == 0.0) return;  // a pass gated off does nothing (every block reads the same flag)
   constexpr int S = 32 / KP;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int c = lane & (KP - 1), slice = lane / KP;
@@ -225,10 +258,24 @@ k_mrows(int64_t n, int k, const int64_t* __restrict__ rowptr, const int32_t* __r
     }
     return;
   }
-  const int64_t row = (bid - plan.nchunks) * (kBT / 32) + warp;
-  if (row >= n) return;
+  const int64_t nshort_blk = (plan.nshort + (kBT / 32) * S - 1) / ((kBT / 32) * S);
+  if (bid < plan.nchunks + nshort_blk) {
+    // short rows: one entry slice (KP column lanes) per row, S rows per warp
+    const int64_t idx = ((bid - plan.nchunks) * (kBT / 32) + warp) * S + slice;
+    if (idx >= plan.nshort) return;
+    const int64_t row = plan.short_rows[idx];
+    const int64_t beg = rowptr[row], end = rowptr[row + 1];
+    const T rv = term.row(row, cc);
+    T s = T(0);
+    for (int64_t e = beg; e < end; ++e) s = term.acc(s, e, col[e], cc, rv);
+    if (active) epi(row, c, term.finish(row, c, rv, s));
+    return;
+  }
+  // medium rows: one warp per row, the S slices splitting its entries
+  const int64_t midx = (bid - plan.nchunks - nshort_blk) * (kBT / 32) + warp;
+  if (midx >= plan.nmed) return;
+  const int64_t row = plan.med_rows[midx];
   const int64_t beg = rowptr[row], end = rowptr[row + 1];
-  if (end - beg > kChunkM) return;  // served by the chunk blocks
   const T rv = term.row(row, cc);
   T s0 = T(0), s1 = T(0);
   int64_t e = beg + slice;
@@ -246,15 +293,18 @@ k_mrows(int64_t n, int k, const int64_t* __restrict__ rowptr, const int32_t* __r
 
 template <typename T, class Term, class Epi>
 static void launch_mrows(int kp, int64_t n, int k, const int64_t* rowptr, const int32_t* col, const Term& term,
-                         const MPlan& plan, const Epi& epi, cudaStream_t s) {
-  const int64_t grid = plan.nchunks + (n + (kBT / 32) - 1) / (kBT / 32);
+                         const MPlan& plan, const Epi& epi, cudaStream_t s, const double* gate = nullptr) {
+  const int64_t S = 32 / kp;
+  const int64_t grid = plan.nchunks + (plan.nshort + (kBT / 32) * S - 1) / ((kBT / 32) * S) +
+                       (plan.nmed + (kBT / 32) - 1) / (kBT / 32);
   if (grid <= 0) return;
+  (void)n;
   switch (kp) {
-    case 2: k_mrows<T, 2><<<(unsigned)grid, kBT, 0, s>>>(n, k, rowptr, col, term, plan, epi); break;
-    case 4: k_mrows<T, 4><<<(unsigned)grid, kBT, 0, s>>>(n, k, rowptr, col, term, plan, epi); break;
-    case 8: k_mrows<T, 8><<<(unsigned)grid, kBT, 0, s>>>(n, k, rowptr, col, term, plan, epi); break;
-    case 16: k_mrows<T, 16><<<(unsigned)grid, kBT, 0, s>>>(n, k, rowptr, col, term, plan, epi); break;
-    case 32: k_mrows<T, 32><<<(unsigned)grid, kBT, 0, s>>>(n, k, rowptr, col, term, plan, epi); break;
+    case 2: k_mrows<T, 2><<<(unsigned)grid, kBT, 0, s>>>(n, k, rowptr, col, term, plan, epi, gate); break;
+    case 4: k_mrows<T, 4><<<(unsigned)grid, kBT, 0, s>>>(n, k, rowptr, col, term, plan, epi, gate); break;
+    case 8: k_mrows<T, 8><<<(unsigned)grid, kBT, 0, s>>>(n, k, rowptr, col, term, plan, epi, gate); break;
+    case 16: k_mrows<T, 16><<<(unsigned)grid, kBT, 0, s>>>(n, k, rowptr, col, term, plan, epi, gate); break;
+    case 32: k_mrows<T, 32><<<(unsigned)grid, kBT, 0, s>>>(n, k, rowptr, col, term, plan, epi, gate); break;
     default: fail(LG_ERR_INVALID, "column block width");
   }
   LG_LAUNCH_CHECK();
@@ -426,12 +476,29 @@ __device__ __forceinline__ bool col_grid_sum(double (&v)[NV], double* partials /
   __syncthreads();
   if (!am_last) return false;
   __threadfence();
-  if (threadIdx.x < KP) {
+  // the last block adds the blocks' partials: thread t takes column t % KP and
+  // blocks t / KP, t / KP + kParts, ... (kParts = kBT / KP), then the kParts
+  // sums of each column are added in part order
+  {
+    constexpr int kParts = kBT / KP;
+    __shared__ double fin[kParts][NV][KP];
+    const int cc = threadIdx.x % KP, part = threadIdx.x / KP;
+    double t[NV];
 #pragma unroll
-    for (int q = 0; q < NV; ++q) {
-      double t = 0.0;
-      for (unsigned b = 0; b < gridDim.x; ++b) t += __ldcg(&partials[((int64_t)b * NV + q) * KP + threadIdx.x]);
-      out[q * KP + threadIdx.x] = t;
+    for (int q = 0; q < NV; ++q) t[q] = 0.0;
+    for (unsigned b = part; b < gridDim.x; b += kParts)
+#pragma unroll
+      for (int q = 0; q < NV; ++q) t[q] += __ldcg(&partials[((int64_t)b * NV + q) * KP + cc]);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) fin[part][q][cc] = t[q];
+    __syncthreads();
+    if (threadIdx.x < KP) {
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        double u = 0.0;
+        for (int pp = 0; pp < kParts; ++pp) u += fin[pp][q][threadIdx.x];
+        out[q * KP + threadIdx.x] = u;
+      }
     }
   }
   __syncthreads();
@@ -446,8 +513,11 @@ __device__ __forceinline__ bool col_grid_sum(double (&v)[NV], double* partials /
 
 // Per-column scalars, column c at scal[c * kMS + field].
 enum MScal : int {
-  mBB = 0, mRZ, mPQ, mAlpha, mBeta, mMeanZ, mRR, mSumB, mBreak, mDone, mIter, mTol2BB, mNeedTrue, mActive, kMS = 16
+  mBB = 0, mRZ, mPQ, mAlpha, mBeta, mMeanZ, mRR, mSumB, mBreak, mDone, mIter, mTol2BB, mNeedTrue, mActive, mConv,
+  kMS = 16
 };
+// Loop scalars after the k column blocks (scal + k kMS).
+enum MGlob : int { gIter = 0, gNeed, gMaxit, gEvery, kMG = 4 };
 
 template <int KP>
 __global__ void k_m_colsum(int64_t n, int k, const double* __restrict__ v, double* partials, unsigned* ticket,
@@ -464,7 +534,7 @@ template <int KP>
 __global__ void k_m_init(int64_t n, int k, const double* __restrict__ b, const int32_t* __restrict__ perm,
                          const double* __restrict__ colsum, double* __restrict__ bm, double* __restrict__ x,
                          double* __restrict__ r, double* scal, double* partials, unsigned* ticket, double* tmp,
-                         double tol) {
+                         double tol, int maxit, int every) {
   const int c = threadIdx.x & (KP - 1);
   double acc[1] = {0.0};
   if (c < k) {
@@ -488,7 +558,13 @@ __global__ void k_m_init(int64_t n, int k, const double* __restrict__ b, const i
       sc[mTol2BB] = tol * tol * tmp[q];
       sc[mNeedTrue] = 0.0;
       sc[mActive] = tmp[q] > 0.0 ? 1.0 : 0.0;
+      sc[mConv] = 0.0;
     }
+    double* gl = scal + k * kMS;
+    gl[gIter] = 0.0;
+    gl[gNeed] = 0.0;
+    gl[gMaxit] = (double)maxit;
+    gl[gEvery] = (double)every;
   }
 }
 
@@ -496,7 +572,8 @@ __global__ void k_m_init(int64_t n, int k, const double* __restrict__ b, const i
 template <typename T, int KP>
 __global__ void k_m_z_reduce(int64_t n, int k, const T* __restrict__ z, const double* __restrict__ r,
                              const double* __restrict__ ro, double* scal, double* partials, unsigned* ticket,
-                             double* tmp, int first) {
+                             double* tmp) {
+  const int first = scal[k * kMS + gIter] == 0.0;
   const int c = threadIdx.x & (KP - 1);
   double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
   if (c < k) {
@@ -563,7 +640,7 @@ __global__ void k_m_pq(int64_t n, int k, const double* __restrict__ p, const dou
 template <int KP>
 __global__ void k_m_xr(int64_t n, int k, double* __restrict__ x, double* __restrict__ r, double* __restrict__ ro,
                        const double* __restrict__ p, const double* __restrict__ q, double* scal, double* partials,
-                       unsigned* ticket, double* tmp) {
+                       unsigned* ticket, double* tmp, cudaGraphConditionalHandle handle, int in_graph) {
   const int c = threadIdx.x & (KP - 1);
   double acc[1] = {0.0};
   if (c < k) {
@@ -583,22 +660,57 @@ __global__ void k_m_xr(int64_t n, int k, double* __restrict__ x, double* __restr
     }
   }
   if (col_grid_sum<KP, 1>(acc, partials, ticket, tmp)) {
+    // count the iteration; ask for the true residuals on replacement
+    // iterations or when a live column's recurrence residual meets the
+    // tolerance; otherwise set the loop condition here (inside the graph)
+    double* gl = scal + k * kMS;
+    const double it = gl[gIter] + 1.0;
+    gl[gIter] = it;
+    bool need = fmod(it, gl[gEvery]) == 0.0, any = false;
     for (int cc = 0; cc < k; ++cc) {
       double* sc = scal + cc * kMS;
       sc[mRR] = tmp[cc];
-      if (sc[mActive] != 0.0) sc[mIter] += 1.0;
+      if (sc[mActive] != 0.0) {
+        sc[mIter] += 1.0;
+        any = true;
+        if (sc[mRR] <= sc[mTol2BB]) need = true;
+      }
     }
+    gl[gNeed] = need ? 1.0 : 0.0;
+    if (!need && in_graph) cudaGraphSetConditional(handle, any && it < gl[gMaxit] ? 1u : 0u);
   }
 }
 
+// ||r||^2 per column. Inside the loop (loop = 1, gated by the true-residual
+// request) the last block also freezes every live column whose true residual
+// meets the tolerance and sets the loop condition: go on while a column is
+// live and the iteration bound allows.
 template <int KP>
 __global__ void k_m_rr(int64_t n, int k, const double* __restrict__ r, double* scal, double* partials,
-                       unsigned* ticket, double* tmp) {
+                       unsigned* ticket, double* tmp, const double* gate, int loop, cudaGraphConditionalHandle handle,
+                       int in_graph) {
+  if (gate && *gate == 0.0) return;
   const int c = threadIdx.x & (KP - 1);
   double acc[1] = {0.0};
   if (c < k) LG_COL_STRIDE(i, n) acc[0] += r[i * k + c] * r[i * k + c];
-  if (col_grid_sum<KP, 1>(acc, partials, ticket, tmp))
+  if (col_grid_sum<KP, 1>(acc, partials, ticket, tmp)) {
     for (int cc = 0; cc < k; ++cc) scal[cc * kMS + mRR] = tmp[cc];
+    if (loop) {
+      double* gl = scal + k * kMS;
+      const double it = gl[gIter];
+      bool any = false;
+      for (int cc = 0; cc < k; ++cc) {
+        double* sc = scal + cc * kMS;
+        if (sc[mActive] != 0.0 && sc[mRR] <= sc[mTol2BB]) {
+          sc[mActive] = 0.0;
+          sc[mDone] = 1.0;
+          sc[mConv] = it;
+        }
+        if (sc[mActive] != 0.0) any = true;
+      }
+      if (in_graph) cudaGraphSetConditional(handle, any && it < gl[gMaxit] ? 1u : 0u);
+    }
+  }
 }
 
 // x columns back to the caller's numbering, column mean removed.
@@ -617,6 +729,12 @@ __global__ void k_m_out(int64_t n, int k, const double* __restrict__ x, const in
 // ---------------------------------------------------------------------------
 struct BatchState {
   std::vector<std::unique_ptr<MPlanStore>> op, mem, pt;  // per level
+  DBuf<double> tmp, colsum;                              // reduction totals of the column kernels
+  std::map<std::pair<int, int>, cudaGraphExec_t> graphs;  // captured loop per (FP32?, k)
+  ~BatchState() {
+    for (auto& g : graphs)
+      if (g.second) cudaGraphExecDestroy(g.second);
+  }
 };
 
 template <typename T> static std::vector<LevelVecs<T>>& mvecs(Workspace& ws);
@@ -698,11 +816,20 @@ static void mcycle(Hier& h, Workspace& ws, BatchState& bs, int l, int k, int kp,
   }
 }
 
+// One multi-column PCG iteration (as pcg_body in lg_cycle.cu): z = M r, the
+// per-column sums, beta and p; q = L p; alpha; x, r and the true-residual
+// request; the requested true residuals, which freeze converged columns.
+template <int KP>
+static void mtrue_res(Hier& h, Workspace& ws, BatchState& bs, int k, cudaStream_t s, const double* gate, int loop,
+                      cudaGraphConditionalHandle handle, int in_graph);
+
 template <typename T, int KP>
-static void mbody(Hier& h, Workspace& ws, BatchState& bs, int k, int first, cudaStream_t s, double* tmp) {
+static void mbody(Hier& h, Workspace& ws, BatchState& bs, int k, cudaStream_t s, cudaGraphConditionalHandle handle,
+                  int in_graph) {
   const Level& L0 = *h.levels[0];
   const int64_t n = L0.n;
   double* scal = ws.scal.get();
+  double* tmp = bs.tmp.get();
   LevelVecs<T>& V = mvecs<T>(ws)[0];
   T* d0 = nullptr;
   const T* dinv = nullptr;
@@ -718,7 +845,7 @@ static void mbody(Hier& h, Workspace& ws, BatchState& bs, int k, int first, cuda
   const T* z = V.x.get();
   const int vb = grid_for(n * KP, kBT, kSMs * 8);
   k_m_z_reduce<T, KP><<<vb, kBT, 0, s>>>(n, k, z, ws.r.get(), ws.ro.get(), scal, ws.partials.get(),
-                                         ws.tickets.get(), tmp, first);
+                                         ws.tickets.get(), tmp);
   LG_LAUNCH_CHECK();
   k_m_p_update<T><<<bblocks(n * k), kBT, 0, s>>>(n, k, z, ws.p.get(), scal);
   LG_LAUNCH_CHECK();
@@ -728,101 +855,120 @@ static void mbody(Hier& h, Workspace& ws, BatchState& bs, int k, int first, cuda
   k_m_pq<KP><<<vb, kBT, 0, s>>>(n, k, ws.p.get(), ws.q.get(), scal, ws.partials.get(), ws.tickets.get(), tmp);
   LG_LAUNCH_CHECK();
   k_m_xr<KP><<<vb, kBT, 0, s>>>(n, k, ws.x.get(), ws.r.get(), ws.ro.get(), ws.p.get(), ws.q.get(), scal,
-                                ws.partials.get(), ws.tickets.get(), tmp);
+                                ws.partials.get(), ws.tickets.get(), tmp, handle, in_graph);
   LG_LAUNCH_CHECK();
+  mtrue_res<KP>(h, ws, bs, k, s, scal + k * kMS + gNeed, 1, handle, in_graph);
 }
 
 template <int KP>
-static void mtrue_res(Hier& h, Workspace& ws, BatchState& bs, int k, cudaStream_t s, double* tmp) {
+static void mtrue_res(Hier& h, Workspace& ws, BatchState& bs, int k, cudaStream_t s, const double* gate, int loop,
+                      cudaGraphConditionalHandle handle, int in_graph) {
   const Level& L0 = *h.levels[0];
   const int64_t n = L0.n;
   const OpView<double> op = L0.op<double>();
   launch_mrows<double>(KP, n, k, op.rowptr, op.col, MLap<double>{op.w, ws.x.get(), op.d, k}, bs.op[0]->plan,
-                       MEpiTrueRes{ws.bm.get(), ws.r.get(), k}, s);
+                       MEpiTrueRes{ws.bm.get(), ws.r.get(), k}, s, gate);
   k_m_rr<KP><<<grid_for(n * KP, kBT, kSMs * 8), kBT, 0, s>>>(n, k, ws.r.get(), ws.scal.get(), ws.partials.get(),
-                                                            ws.tickets.get(), tmp);
+                                                            ws.tickets.get(), bs.tmp.get(), gate, loop, handle,
+                                                            in_graph);
   LG_LAUNCH_CHECK();
 }
 
 static BatchState& batch_state(Hier& h, Workspace& ws, cudaStream_t s);
+
+// The whole multi-column loop as one graph: a WHILE node whose body is one
+// iteration, captured once per workspace, precision and width.
+template <typename T, int KP>
+static cudaGraphExec_t mgraph(Hier& h, Workspace& ws, BatchState& bs, int k, cudaStream_t s) {
+  const auto key = std::make_pair(sizeof(T) == 4 ? 1 : 0, k);
+  auto found = bs.graphs.find(key);
+  if (found != bs.graphs.end()) return found->second;
+  cudaGraph_t g = nullptr;
+  LG_CUDA(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle handle;
+  LG_CUDA(cudaGraphConditionalHandleCreate(&handle, g, 1u, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = handle;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  LG_CUDA(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np));
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  LG_CUDA(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  try {
+    mbody<T, KP>(h, ws, bs, k, s, handle, 1);
+  } catch (...) {
+    cudaGraph_t dummy;
+    cudaStreamEndCapture(s, &dummy);
+    cudaGraphDestroy(g);
+    throw;
+  }
+  LG_CUDA(cudaStreamEndCapture(s, &body));
+  cudaGraphExec_t exec = nullptr;
+  LG_CUDA(cudaGraphInstantiate(&exec, g, 0));
+  cudaGraphDestroy(g);
+  bs.graphs[key] = exec;
+  return exec;
+}
 
 template <typename T, int KP>
 static int msolve(Hier& h, Workspace& ws, int k, const double* B, double* X, double tol, cudaStream_t s,
                   lg_info* infos) {
   const Level& L0 = *h.levels[0];
   const int64_t n = L0.n;
-  int64_t* counter = &ws.bytes;
   BatchState& bs = batch_state(h, ws, s);
-  DBuf<double> tmp(5 * KP, s), colsum(KP, s);
   double* scal = ws.scal.get();
+  double* tmp = bs.tmp.get();
+  double* colsum = bs.colsum.get();
+  const int maxit = h.opts.max_iter;
+  const int every = h.opts.residual_replace > 0 ? h.opts.residual_replace : 1 << 30;
   cudaEvent_t e0, e1;
   LG_CUDA(cudaEventCreate(&e0));
   LG_CUDA(cudaEventCreate(&e1));
   LG_CUDA(cudaEventRecord(e0, s));
   const int vb = grid_for(n * KP, kBT, kSMs * 8);
-  k_m_colsum<KP><<<vb, kBT, 0, s>>>(n, k, B, ws.partials.get(), ws.tickets.get(), colsum.get());
+  k_m_colsum<KP><<<vb, kBT, 0, s>>>(n, k, B, ws.partials.get(), ws.tickets.get(), colsum);
   LG_LAUNCH_CHECK();
-  k_m_init<KP><<<vb, kBT, 0, s>>>(n, k, B, h.perm.get(), colsum.get(), ws.bm.get(), ws.x.get(), ws.r.get(), scal,
-                                  ws.partials.get(), ws.tickets.get(), tmp.get(), tol);
+  k_m_init<KP><<<vb, kBT, 0, s>>>(n, k, B, h.perm.get(), colsum, ws.bm.get(), ws.x.get(), ws.r.get(), scal,
+                                  ws.partials.get(), ws.tickets.get(), tmp, tol, maxit, every);
   LG_LAUNCH_CHECK();
-  std::vector<double> hs((size_t)k * kMS);
+  const size_t nscal = (size_t)k * kMS + kMG;
+  std::vector<double> hs(nscal);
   auto read = [&]() {
-    LG_CUDA(cudaMemcpyAsync(hs.data(), scal, sizeof(double) * k * kMS, cudaMemcpyDeviceToHost, s));
+    LG_CUDA(cudaMemcpyAsync(hs.data(), scal, sizeof(double) * nscal, cudaMemcpyDeviceToHost, s));
     LG_CUDA(cudaStreamSynchronize(s));
   };
-  read();
-  const int maxit = h.opts.max_iter;
-  const int every = h.opts.residual_replace > 0 ? h.opts.residual_replace : 1 << 30;
-  int it = 0;
-  std::vector<int> conv_iter(k, 0);
   auto any_active = [&]() {
     for (int c = 0; c < k; ++c)
       if (hs[c * kMS + mActive] != 0.0) return true;
     return false;
   };
-  while (any_active() && it < maxit) {
-    ++it;
-    mbody<T, KP>(h, ws, bs, k, it == 1, s, tmp.get());
-    read();
-    bool need = it % every == 0;
-    for (int c = 0; c < k && !need; ++c) {
-      const double* sc = &hs[c * kMS];
-      if (sc[mActive] != 0.0 && sc[mRR] <= sc[mTol2BB]) need = true;
-    }
-    if (need) {
-      std::vector<double> rr_rec(k);
-      for (int c = 0; c < k; ++c) rr_rec[c] = hs[c * kMS + mRR];
-      mtrue_res<KP>(h, ws, bs, k, s, tmp.get());
+  read();
+  if (any_active() && maxit > 0) {
+    if (h.opts.use_graphs && !debug_sync()) {
+      LG_CUDA(cudaGraphLaunch(mgraph<T, KP>(h, ws, bs, k, s), s));
       read();
-      // a column converges when its true residual meets the tolerance; it is then frozen
-      std::vector<double> upd(hs);
-      bool changed = false;
-      for (int c = 0; c < k; ++c) {
-        double* sc = &upd[c * kMS];
-        if (sc[mActive] != 0.0 && sc[mRR] <= sc[mTol2BB]) {
-          sc[mActive] = 0.0;
-          sc[mDone] = 1.0;
-          conv_iter[c] = it;
-          changed = true;
-        }
-      }
-      if (changed) {
-        LG_CUDA(cudaMemcpyAsync(scal, upd.data(), sizeof(double) * k * kMS, cudaMemcpyHostToDevice, s));
-        hs = upd;
+    } else {
+      for (;;) {
+        mbody<T, KP>(h, ws, bs, k, s, cudaGraphConditionalHandle{}, 0);
+        read();
+        if (!any_active() || hs[k * kMS + gIter] >= maxit) break;
       }
     }
   }
+  const int it = (int)hs[k * kMS + gIter];
   // results in the caller's numbering, mean removed
-  k_m_colsum<KP><<<vb, kBT, 0, s>>>(n, k, ws.x.get(), ws.partials.get(), ws.tickets.get(), colsum.get());
+  k_m_colsum<KP><<<vb, kBT, 0, s>>>(n, k, ws.x.get(), ws.partials.get(), ws.tickets.get(), colsum);
   LG_LAUNCH_CHECK();
   bool all_done = true;
   for (int c = 0; c < k; ++c)
-    if (hs[c * kMS + mDone] == 0.0) all_done = false;
+    if (hs[c * kMS + mDone] == 0.0 && hs[c * kMS + mBB] != 0.0) all_done = false;
   if (!all_done) {
-    mtrue_res<KP>(h, ws, bs, k, s, tmp.get());
+    mtrue_res<KP>(h, ws, bs, k, s, nullptr, 0, cudaGraphConditionalHandle{}, 0);
     read();
   }
-  k_m_out<KP><<<bblocks(n * k), kBT, 0, s>>>(n, k, ws.x.get(), h.perm.get(), colsum.get(), ws.io.get());
+  k_m_out<KP><<<bblocks(n * k), kBT, 0, s>>>(n, k, ws.x.get(), h.perm.get(), colsum, ws.io.get());
   LG_LAUNCH_CHECK();
   (void)X;  // the caller transposes ws.io into X
   LG_CUDA(cudaEventRecord(e1, s));
@@ -841,7 +987,7 @@ static int msolve(Hier& h, Workspace& ws, int k, const double* B, double* X, dou
       lg_info& inf = infos[c];
       inf = lg_info{};
       inf.status = st;
-      inf.iterations = sc[mBB] == 0.0 ? 0 : (sc[mDone] != 0.0 ? conv_iter[c] : it);
+      inf.iterations = sc[mBB] == 0.0 ? 0 : (sc[mDone] != 0.0 ? (int)sc[mConv] : it);
       inf.relres = sc[mBB] > 0.0 ? std::sqrt(sc[mRR] / sc[mBB]) : 0.0;
       inf.solve_ms = ms;
       inf.levels = (int)h.levels.size();
@@ -871,6 +1017,8 @@ static BatchState& batch_state(Hier& h, Workspace& ws, cudaStream_t s) {
         st->pt[l]->build(L.nc, L.pt_ptr.get(), s, &ws.bytes);
       }
     }
+    st->tmp.alloc(5 * kMaxCols, s, &ws.bytes);
+    st->colsum.alloc(kMaxCols, s, &ws.bytes);
     ws.batch = st;
   }
   return *static_cast<BatchState*>(ws.batch.get());

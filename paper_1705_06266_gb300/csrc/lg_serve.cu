@@ -39,10 +39,19 @@ struct Request {
 
 struct Slot {
   cudaStream_t stream = nullptr;
-  Hier* cached_h = nullptr;
-  int cached_k = 0;
+  DBuf<double> Bd, Xd;  // staging of the running request (grown as needed)
+  size_t staged = 0;
+};
+
+// An idle solve workspace kept for reuse, so that a request does not pay for
+// allocations, a CUDA graph capture and SpMM plans each time its slot served
+// another graph before. Widths are powers of two.
+struct Pooled {
+  Hier* h = nullptr;
+  int k = 0;
+  double bytes = 0.0;
+  uint64_t last_use = 0;
   std::unique_ptr<Workspace> ws;
-  DBuf<double> Bd, Xd;
 };
 
 struct Server {
@@ -57,12 +66,21 @@ struct Server {
   int running = 0;
   bool stopping = false;
   std::vector<Slot> slots;
+  std::vector<Pooled> pool;  // idle workspaces
+  double pooled_bytes = 0.0;
+  uint64_t use_clock = 0;
   std::vector<std::thread> threads;
   std::vector<double> latencies_ms;
   int64_t completed = 0, failed = 0, rhs_done = 0;
   Clock::time_point created = Clock::now();
   int device = 0;
 };
+
+static int pow2_width(int k) {
+  int p = 1;
+  while (p < k) p <<= 1;
+  return p;
+}
 
 // Device bytes of a solve workspace for k columns: per-level cycle vectors in
 // both precisions, the FP64 Krylov vectors and reduction scratch.
@@ -78,14 +96,46 @@ static double workspace_bytes(const Hier& h, int k) {
   return b + (1 << 20);
 }
 
+// Under the server lock: the smallest idle workspace of h at least k wide
+// (removed from the pool), or null.
+static std::unique_ptr<Workspace> pool_take(Server* sv, Hier* h, int k) {
+  int best = -1;
+  for (int i = 0; i < (int)sv->pool.size(); ++i) {
+    const Pooled& p = sv->pool[i];
+    if (p.h == h && p.k >= k && (best < 0 || p.k < sv->pool[best].k)) best = i;
+  }
+  if (best < 0) return nullptr;
+  std::unique_ptr<Workspace> ws = std::move(sv->pool[best].ws);
+  sv->pooled_bytes -= sv->pool[best].bytes;
+  sv->pool.erase(sv->pool.begin() + best);
+  return ws;
+}
+
+// Under the server lock: move least recently used idle workspaces to `out`
+// (freed by the caller outside the lock) until `need` more bytes fit.
+static void pool_evict(Server* sv, double need, std::vector<std::unique_ptr<Workspace>>& out) {
+  while (!sv->pool.empty() &&
+         sv->resident_bytes + sv->inflight_bytes + sv->pooled_bytes + need > sv->o.hbm_budget_bytes) {
+    int lru = 0;
+    for (int i = 1; i < (int)sv->pool.size(); ++i)
+      if (sv->pool[i].last_use < sv->pool[lru].last_use) lru = i;
+    sv->pooled_bytes -= sv->pool[lru].bytes;
+    out.push_back(std::move(sv->pool[lru].ws));
+    sv->pool.erase(sv->pool.begin() + lru);
+  }
+}
+
 static void serve_worker(Server* sv, int slot_id) {
   Slot& slot = sv->slots[slot_id];
   cudaSetDevice(sv->device);
   for (;;) {
     Request* rq = nullptr;
+    std::unique_ptr<Workspace> ws;
+    std::vector<std::unique_ptr<Workspace>> evicted;
     {
       std::unique_lock<std::mutex> lk(sv->mu);
-      // admit the oldest request once it fits the budget (arrival order)
+      // admit the oldest request once it fits the budget (arrival order);
+      // idle pooled workspaces give way to it
       sv->cv_work.wait(lk, [&] {
         if (sv->queue.empty()) return sv->stopping;
         Request* head = sv->queue.front();
@@ -95,24 +145,26 @@ static void serve_worker(Server* sv, int slot_id) {
       if (sv->queue.empty() && sv->stopping) return;
       rq = sv->queue.front();
       sv->queue.pop_front();
+      ws = pool_take(sv, rq->h, rq->k);
+      if (!ws) pool_evict(sv, rq->ws_bytes, evicted);
       sv->inflight_bytes += rq->ws_bytes;
       sv->running += 1;
     }
+    evicted.clear();  // frees the evicted workspaces' device memory
     int st = LG_OK;
     lg_info worst{};
     try {
       const int64_t n = rq->h->levels[0]->n;
-      if (slot.cached_h != rq->h || slot.cached_k < rq->k || !slot.ws) {
-        slot.ws.reset();
-        slot.ws = make_workspace(*rq->h, rq->k, slot.stream);
-        slot.Bd.alloc((size_t)n * rq->k, slot.stream);
-        slot.Xd.alloc((size_t)n * rq->k, slot.stream);
-        slot.cached_h = rq->h;
-        slot.cached_k = rq->k;
+      if (!ws) ws = make_workspace(*rq->h, pow2_width(rq->k), slot.stream);
+      const size_t need = (size_t)n * rq->k;
+      if (slot.staged < need) {
+        slot.Bd.alloc(need, slot.stream);
+        slot.Xd.alloc(need, slot.stream);
+        slot.staged = need;
       }
       LG_CUDA(cudaMemcpyAsync(slot.Bd.get(), rq->B, sizeof(double) * n * rq->k, cudaMemcpyHostToDevice, slot.stream));
       std::vector<lg_info> infos(rq->k);
-      st = pcg_solve_batch(*rq->h, *slot.ws, rq->k, slot.Bd.get(), slot.Xd.get(), rq->tol, sv->o.precision,
+      st = pcg_solve_batch(*rq->h, *ws, rq->k, slot.Bd.get(), slot.Xd.get(), rq->tol, sv->o.precision,
                            slot.stream, infos.data());
       LG_CUDA(cudaMemcpyAsync(rq->X, slot.Xd.get(), sizeof(double) * n * rq->k, cudaMemcpyDeviceToHost, slot.stream));
       LG_CUDA(cudaStreamSynchronize(slot.stream));
@@ -130,6 +182,16 @@ static void serve_worker(Server* sv, int slot_id) {
     const double ms = std::chrono::duration<double, std::milli>(Clock::now() - rq->submitted).count();
     {
       std::lock_guard<std::mutex> lk(sv->mu);
+      if (ws && st == LG_OK) {  // back to the pool (the slot's stream has finished with it)
+        Pooled p;
+        p.h = rq->h;
+        p.k = ws->k;
+        p.bytes = (double)ws->bytes;
+        p.last_use = ++sv->use_clock;
+        p.ws = std::move(ws);
+        sv->pooled_bytes += p.bytes;
+        sv->pool.push_back(std::move(p));
+      }
       worst.status = st;
       worst.solve_ms = ms;
       rq->info = worst;
@@ -213,7 +275,7 @@ int lg_serve_submit(lg_server_t s, lg_handle hh, int32_t k, const double* B, dou
   rq->B = B;
   rq->X = X;
   rq->tol = tol;
-  rq->ws_bytes = lg::workspace_bytes(*h, k);
+  rq->ws_bytes = lg::workspace_bytes(*h, lg::pow2_width(k));
   rq->submitted = lg::Clock::now();
   {
     std::lock_guard<std::mutex> lk(sv->mu);
@@ -256,7 +318,7 @@ int lg_serve_poll(lg_server_t s, uint64_t ticket, int32_t* done, lg_info* info) 
 
 int lg_serve_request_bytes(lg_handle hh, int32_t k, double* bytes) {
   if (!hh || !bytes || k < 1 || k > lg::kMaxCols) return LG_ERR_INVALID;
-  *bytes = lg::workspace_bytes(*reinterpret_cast<lg::Hier*>(hh), k);
+  *bytes = lg::workspace_bytes(*reinterpret_cast<lg::Hier*>(hh), lg::pow2_width(k));
   return LG_OK;
 }
 
@@ -301,8 +363,8 @@ void lg_serve_destroy(lg_server_t s) {
   }
   sv->cv_work.notify_all();
   for (auto& t : sv->threads) t.join();
+  sv->pool.clear();  // workspaces before the streams they were made on
   for (auto& sl : sv->slots) {
-    sl.ws.reset();
     sl.Bd.release();
     sl.Xd.release();
     if (sl.stream) {
