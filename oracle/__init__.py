@@ -45,7 +45,7 @@ class Opts(C.Structure):
         ("vote_threshold", C.c_int32), ("strength_vecs", C.c_int32), ("strength_sweeps", C.c_int32),
         ("cheb_degree", C.c_int32), ("eig_iters", C.c_int32), ("max_coarse_n", C.c_int32),
         ("elim_enable", C.c_int32),
-        ("kcycle", C.c_int32),
+        ("kcycle", C.c_int32), ("elim_rounds", C.c_int32),
     ]
 
 

@@ -86,6 +86,7 @@ void lgref_opts_default(lgref_opts* o) {
   o->eig_iters = 10;
   o->max_coarse_n = 4096;
   o->elim_enable = 1;
+  o->elim_rounds = 1;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -822,23 +823,31 @@ lgref_hier* lgref_setup(int64_t n, const int64_t* rowptr, const int32_t* col, co
   int32_t maxlev = o->max_levels < LGREF_MAX_LEVELS ? o->max_levels : LGREF_MAX_LEVELS;
   for (;;) {
     if ((double)(cur.nnz + cur.n) <= o->coarse_nnz || h->nlev >= maxlev - 1) break;
-    if (o->elim_enable) {
+    /* Reading of the elimination rounds (Section 3.4 finds one round enough;
+     * more serve chain-like graphs): up to elim_rounds elimination levels in
+     * a row, each while the 5% gate passes, then aggregation. */
+    int stop = 0;
+    for (int32_t round = 0; o->elim_enable && round < o->elim_rounds; ++round) {
       uint8_t* is_f = (uint8_t*)xmalloc((size_t)cur.n);
       int64_t nf = lgref_elim_select(cur.n, cur.rowptr, cur.col, o->elim_max_degree, o->seed, is_f);
-      if ((double)nf > o->elim_min_frac * (double)cur.n) {
-        int32_t* cmap = (int32_t*)xmalloc(sizeof(int32_t) * (size_t)cur.n);
-        lgref_csr* s = lgref_schur(cur.n, cur.rowptr, cur.col, cur.w, is_f, cmap);
-        level_t* L = push_level(h, LGREF_LEVEL_ELIM, cur);
-        L->map = cmap;
-        L->nc = s->n;
-        cur = *s;
-        free(s);
+      if (!((double)nf > o->elim_min_frac * (double)cur.n)) {
         free(is_f);
-        if ((double)(cur.nnz + cur.n) <= o->coarse_nnz || h->nlev >= maxlev - 1) break;
-      } else {
-        free(is_f);
+        break;
+      }
+      int32_t* cmap = (int32_t*)xmalloc(sizeof(int32_t) * (size_t)cur.n);
+      lgref_csr* s = lgref_schur(cur.n, cur.rowptr, cur.col, cur.w, is_f, cmap);
+      level_t* L = push_level(h, LGREF_LEVEL_ELIM, cur);
+      L->map = cmap;
+      L->nc = s->n;
+      cur = *s;
+      free(s);
+      free(is_f);
+      if ((double)(cur.nnz + cur.n) <= o->coarse_nnz || h->nlev >= maxlev - 1) {
+        stop = 1;
+        break;
       }
     }
+    if (stop) break;
     double* S = (double*)xmalloc(sizeof(double) * (size_t)(cur.nnz ? cur.nnz : 1));
     lgref_strength(cur.n, cur.rowptr, cur.col, cur.w, o->seed, h->nlev, o->strength_vecs,
                    o->strength_sweeps, o->jacobi_omega, S);

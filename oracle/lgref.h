@@ -52,6 +52,7 @@ typedef struct {
   int32_t max_coarse_n;    /* 4096: largest coarsest level for the dense solve */
   int32_t elim_enable;     /* 1 */
   int32_t kcycle;          /* 0: V-cycle (Section 4's default); 1: K-cycle (Section 3.7) */
+  int32_t elim_rounds;     /* 1: elimination rounds before each aggregation (Section 3.4) */
 } lgref_opts;
 
 void lgref_opts_default(lgref_opts* o);

@@ -512,3 +512,42 @@ def test_kcycle_pcg_matches_dense(oracle, inputs):
     assert np.linalg.norm(x - ref) <= 1e-6 * np.linalg.norm(ref)
     _, _, it_v, _ = oracle.Hierarchy(g).pcg(b, tol=1e-8)
     assert it <= it_v  # the K-cycle is the stronger preconditioner here
+
+
+# ---------------------------------------------------------------------------
+# Repeated elimination rounds (Section 3.4). Elimination is exact (a Schur
+# complement), so a hierarchy made only of elimination levels above the
+# coarsest dense solve is a direct solver: one cycle gives L^+ f.
+# ---------------------------------------------------------------------------
+def test_elim_rounds_path_is_exact(oracle, inputs):
+    g = inputs.path(2000)
+    h = oracle.Hierarchy(g, oracle.default_opts(elim_rounds=20))
+    kinds = [h.level(l).kind for l in range(h.nlevels)]
+    assert kinds[-1] == oracle.COARSEST and all(k == oracle.ELIM for k in kinds[:-1])
+    f = inputs.rhs(g.n, seed=3)
+    ref = oracle.dense_solve(g, f)
+    x = h.vcycle(f)
+    # exact up to rounding: the path Laplacian's condition number is ~n^2 = 4e6, so both this and the
+    # dense reference carry errors of order 4e6 * 1e-16; an inexact cycle would be off by ~1e-1
+    assert np.linalg.norm(x - x.mean() - ref) <= 1e-8 * np.linalg.norm(ref)
+    _, st, it, rel = h.pcg(f, tol=1e-8)
+    assert st == oracle.OK and it == 1
+
+
+@pytest.mark.parametrize("name", ["grid64", "chunglu"])
+def test_elim_rounds_stop_at_the_gate(oracle, inputs, name):
+    g = inputs.grid2d(64, 64) if name == "grid64" else inputs.chung_lu(20000, m_target=100000, seed=3)
+    h = oracle.Hierarchy(g, oracle.default_opts(elim_rounds=20))
+    kinds = [h.level(l).kind for l in range(h.nlevels)]
+    for l, k in enumerate(kinds[:-1]):
+        lv = h.level(l)
+        G = inputs.Graph(lv.a.n, lv.a.rowptr, lv.a.col, lv.a.w)
+        nf = int(oracle.elim_select(G, 4, 0x5EED).sum())
+        if k == oracle.ELIM:
+            assert nf > 0.05 * lv.a.n and lv.nc == lv.a.n - nf
+        else:  # an aggregation level: the gate failed on it
+            assert nf <= 0.05 * lv.a.n
+    # one round is the default hierarchy
+    h1 = oracle.Hierarchy(g, oracle.default_opts(elim_rounds=1))
+    hd = oracle.Hierarchy(g)
+    assert [h1.level(l).a.n for l in range(h1.nlevels)] == [hd.level(l).a.n for l in range(hd.nlevels)]
