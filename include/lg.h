@@ -107,6 +107,10 @@ typedef struct {
                                by the outer iteration; elimination levels are exact). The outer
                                iteration's Polak-Ribiere beta makes it flexible CG. Multi-column
                                solves then run their columns one at a time. */
+  int32_t elim_rounds;      /* 1 (Section 3.4 finds one round enough): up to this many elimination
+                               levels in a row before each aggregation, each while more than
+                               elim_min_frac of the vertices go; more rounds serve chain-like graphs */
+  int32_t reserved;
 } lg_options;
 
 /* Result of a setup or a solve. */

@@ -116,6 +116,7 @@ int lg_options_default(lg_options* o) {
   o->autotune = 1;
   o->reorder = 1;
   o->kcycle = 0;
+  o->elim_rounds = 1;
   return LG_OK;
 }
 

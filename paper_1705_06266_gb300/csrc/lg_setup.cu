@@ -1205,6 +1205,7 @@ void setup_hierarchy(Hier& h, int64_t n, const int64_t* rowptr, const int32_t* c
   if (o.strength_vecs < 1 || o.strength_vecs > 7) fail(LG_ERR_INVALID, "strength_vecs must be 1..7");
   if (o.cheb_degree < 1 || o.cheb_degree > 8) fail(LG_ERR_INVALID, "cheb_degree must be 1..8");
   if (o.max_levels < 1) fail(LG_ERR_INVALID, "max_levels");
+  if (o.elim_rounds < 1 || o.elim_rounds > 64) fail(LG_ERR_INVALID, "elim_rounds must be 1..64");
 
   h.dev_err.alloc(1, s);
   LG_CUDA(cudaMemsetAsync(h.dev_err.get(), 0, sizeof(int), s));
@@ -1286,18 +1287,23 @@ void setup_hierarchy(Hier& h, int64_t n, const int64_t* rowptr, const int32_t* c
   };
   for (;;) {
     if (stop(*cur)) break;
-    if (o.elim_enable && o.elim_max_degree > 0) {
+    // up to elim_rounds elimination levels in a row, each while the gate passes
+    bool done = false;
+    for (int round = 0; o.elim_enable && o.elim_max_degree > 0 && round < o.elim_rounds; ++round) {
       DBuf<uint8_t> is_f(cur->n, s);
       const int64_t nf = run_elim_select(cur->n, cur->rowptr.get(), cur->col.get(), o.elim_max_degree, o.seed,
                                          is_f.get(), s);
-      if ((double)nf > o.elim_min_frac * (double)cur->n) {
-        auto next = eliminate(*cur, is_f.get(), nf, s, counter);
-        h.levels.push_back(std::move(cur));
-        cur = std::move(next);
-        prepare_operator(*cur, s, counter);
-        if (stop(*cur)) break;
+      if (!((double)nf > o.elim_min_frac * (double)cur->n)) break;
+      auto next = eliminate(*cur, is_f.get(), nf, s, counter);
+      h.levels.push_back(std::move(cur));
+      cur = std::move(next);
+      prepare_operator(*cur, s, counter);
+      if (stop(*cur)) {
+        done = true;
+        break;
       }
     }
+    if (done) break;
     const int level = (int)h.levels.size();
     DBuf<double> S(cur->nnz, s);
     // the level's bins match those lg_strength / lg_aggregate derive for the same CSR (E = 4,

@@ -36,6 +36,7 @@ class Options(C.Structure):
         ("cheb_degree", C.c_int32), ("eig_iters", C.c_int32), ("max_coarse_n", C.c_int32),
         ("residual_replace", C.c_int32), ("memory_space", C.c_int32), ("use_graphs", C.c_int32),
         ("autotune", C.c_int32), ("reorder", C.c_int32), ("kcycle", C.c_int32),
+        ("elim_rounds", C.c_int32), ("reserved", C.c_int32),
     ]
 
 

@@ -446,3 +446,50 @@ def test_kcycle_batch_runs_columns(lgmod, inputs):
         xs, _ = H.solve(np.ascontiguousarray(B[:, c]))
         np.testing.assert_array_equal(X[:, c], xs)
     H.close()
+
+
+# ---------------------------------------------------------------------------
+# Repeated elimination rounds (Section 3.4).
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("name", ["path_3000", "grid2d_20", "chunglu_20k"])
+def test_elim_rounds_hierarchy(torch_cuda, lgmod, oracle, inputs, name):
+    """With several rounds, each elimination level matches the oracle's Schur
+    complement of the GPU's previous level (reinjection), and the kinds of the
+    levels match the oracle's hierarchy."""
+    g = {"path_3000": lambda: inputs.path(3000), "grid2d_20": lambda: inputs.grid2d(20, 20),
+         "chunglu_20k": lambda: inputs.chung_lu(20000, m_target=100000, seed=3)}[name]()
+    H = lgmod.Hierarchy(g, elim_rounds=8, reorder=0)  # the oracle hashes the caller's vertex ids
+    R = oracle.Hierarchy(g, oracle.default_opts(elim_rounds=8))
+    kinds = [H.level_info(l)["kind"] for l in range(H.nlevels)]
+    assert kinds == [R.level(l).kind for l in range(R.nlevels)]
+    assert kinds.count(lgmod.LEVEL_ELIM) > (1 if name != "grid2d_20" else 0)
+    for l in range(H.nlevels - 1):
+        if kinds[l] != lgmod.LEVEL_ELIM:
+            continue
+        rp, cl, w, mp = H.level(l)
+        G = inputs.Graph(len(rp) - 1, rp, cl, w)
+        is_f = oracle.elim_select(G, 4, SEED)
+        np.testing.assert_array_equal((mp < 0).astype(np.uint8), is_f)
+        coarse, cmap = oracle.schur(G, is_f)
+        nrp, ncl, nw, _ = H.level(l + 1)
+        same_csr(nrp, ncl, nw, coarse)
+    H.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_elim_rounds_path_solve_is_direct(lgmod, oracle, inputs, prec):
+    """Only elimination levels over the dense coarsest solve: one cycle is the
+    exact solve, so PCG converges in one iteration."""
+    g = inputs.path(2000)
+    p = lgmod.FP64 if prec == "fp64" else lgmod.FP32_HIER
+    H = lgmod.Hierarchy(g, elim_rounds=20, precision=p)
+    kinds = [H.level_info(l)["kind"] for l in range(H.nlevels)]
+    assert kinds[-1] == lgmod.LEVEL_COARSEST and all(k == lgmod.LEVEL_ELIM for k in kinds[:-1])
+    b = inputs.rhs(g.n, seed=3)
+    x, info = H.solve(b, tol=1e-8)
+    assert info.status == lgmod.OK and relres(g, b, x) <= 1e-8
+    if prec == "fp64":
+        assert info.iterations == 1
+    ref = oracle.dense_solve(g, b)
+    assert np.linalg.norm(x - x.mean() - ref) <= 1e-6 * np.linalg.norm(ref)
+    H.close()
