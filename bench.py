@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--multi-rhs-k", type=int, default=32)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-kcycle", action="store_true")
+    ap.add_argument("--no-wda", action="store_true")
+    ap.add_argument("--no-ordering", action="store_true")
     ap.add_argument("--serve-graphs", type=int, default=64)
     ap.add_argument("--serve-nmax", type=int, default=262144)
     ap.add_argument("--serve-requests", type=int, default=1000)
@@ -196,6 +198,16 @@ def cpu_baseline(workload_name, g, b):
     }
 
 
+_GRAPHS = {}
+
+
+def workload(inputs, name):
+    """inputs.workload(name), generated once per run."""
+    if name not in _GRAPHS:
+        _GRAPHS[name] = inputs.workload(name)
+    return _GRAPHS[name]
+
+
 def multi_rhs_leg(lg, inputs, torch, dev, k):
     """k right-hand sides solved together (FP32 hierarchy, SpMM cycles, FP64
     outer CG) against the same k solved one after another, on the R-MAT scale
@@ -203,7 +215,7 @@ def multi_rhs_leg(lg, inputs, torch, dev, k):
     solve's own event time."""
     out = {}
     for name in ("rmat_20", "grid3d_128"):
-        g = inputs.workload(name)
+        g = workload(inputs, name)
         B = inputs.rhs(g.n, k, seed=3)
         Bd = torch.from_numpy(np.ascontiguousarray(B.T)).to(dev)  # column-major n x k
         Xd = torch.zeros_like(Bd)
@@ -240,7 +252,7 @@ def kcycle_leg(lg, inputs, torch, dev, g_main, b_main):
     out = {}
     for name, g, b in (("chung_lu_1m", g_main, b_main), ("grid3d_128", None, None)):
         if g is None:
-            g = inputs.workload(name)
+            g = workload(inputs, name)
             b = inputs.rhs(g.n, seed=2)
         bd = torch.from_numpy(b).to(dev)
         xd = torch.zeros_like(bd)
@@ -257,6 +269,67 @@ def kcycle_leg(lg, inputs, torch, dev, g_main, b_main):
                 row[f"{tag}_{pname}_iterations"] = inf.iterations
                 row[f"{tag}_{pname}_nnz_per_s"] = g.nnz / (inf.solve_ms * 1e-3)
             lg.lg_destroy(h)
+        out[name] = row
+    return out
+
+
+def wda_leg(lg, inputs, torch, dev):
+    """Work per digit of accuracy (Section 2.3.1) on a synthetic suite of the
+    paper's graph families at ~10^5 vertices, FP64 solves to 1e-8, for the
+    V-cycle, the K-cycle and the V-cycle with four elimination rounds."""
+    suite = [
+        ("grid2d_300", lambda: inputs.grid2d(300, 300)),
+        ("grid3d_45", lambda: inputs.grid3d(45, 45, 45)),
+        ("chung_lu_100k", lambda: inputs.chung_lu(100000, m_target=500000, seed=11)),
+        ("rmat_17", lambda: inputs.rmat(17, seed=11)),
+        ("random_100k", lambda: inputs.random_graph(100000, 6, seed=11)),
+        ("road_like_400", lambda: inputs.road_like(400, 400, seed=11)),
+    ]
+    configs = [("v", {}), ("k", {"kcycle": 1}), ("v_elim4", {"elim_rounds": 4})]
+    out = {"graphs": {}}
+    for name, make in suite:
+        g = make()
+        b = inputs.rhs(g.n, seed=2)
+        bd = torch.from_numpy(b).to(dev)
+        xd = torch.zeros_like(bd)
+        torch.cuda.synchronize()
+        row = {"n": g.n, "nnz": g.nnz}
+        for tag, kw in configs:
+            h = lg.lg_setup(g.n, g.rowptr, g.col, g.w, lg.options(**kw))
+            lg.lg_solve(h, bd, xd, TOL)
+            inf = lg.lg_solve(h, bd, xd, TOL)
+            row[tag] = {"iterations": inf.iterations, "work_units": inf.work_units,
+                        "wda": inf.work_units / -math.log10(max(inf.relres, 1e-300)),
+                        "solve_ms": inf.solve_ms, "levels": inf.levels}
+            lg.lg_destroy(h)
+        out["graphs"][name] = row
+    for tag, _ in configs:
+        out[f"median_wda_{tag}"] = statistics.median(r[tag]["wda"] for r in out["graphs"].values())
+    out["note"] = ("WDA = work_units / -log10(relres); work in finest-residual units counted from operator "
+                   "nonzeros (lg_info.work_units)")
+    return out
+
+
+def ordering_leg(lg, torch, dev, graphs):
+    """Vertex orderings (Section 3.3 uses a random one): the caller's, by
+    descending degree (the default) and random; setup and FP64/FP32 solves."""
+    out = {}
+    for name, g, b in graphs:
+        bd = torch.from_numpy(b).to(dev)
+        xd = torch.zeros_like(bd)
+        torch.cuda.synchronize()
+        row = {}
+        for tag, code in (("caller", 0), ("degree", 1), ("random", 2)):
+            h = lg.lg_setup(g.n, g.rowptr, g.col, g.w, lg.options(reorder=code))
+            r = {"setup_ms": lg.lg_hier_info(h).setup_ms}
+            for pname, prec in (("fp64", lg.FP64), ("fp32", lg.FP32_HIER)):
+                lg.lg_set_precision(h, prec)
+                lg.lg_solve(h, bd, xd, TOL)
+                inf = lg.lg_solve(h, bd, xd, TOL)
+                r[f"{pname}_ms"] = inf.solve_ms
+                r[f"{pname}_iterations"] = inf.iterations
+            lg.lg_destroy(h)
+            row[tag] = r
         out[name] = row
     return out
 
@@ -457,6 +530,12 @@ def main():
         # the other two workloads the metric names, after the timed region
         multi = None if args.no_multi_rhs else multi_rhs_leg(lg, inputs, torch, dev, args.multi_rhs_k)
         kcyc = None if args.no_kcycle else kcycle_leg(lg, inputs, torch, dev, g, b)
+        wda = None if args.no_wda else wda_leg(lg, inputs, torch, dev)
+        order = None
+        if not args.no_ordering:
+            g_rmat = workload(inputs, "rmat_20")
+            order = ordering_leg(lg, torch, dev, [(args.workload, g, b),
+                                                  ("rmat_20", g_rmat, inputs.rhs(g_rmat.n, seed=2))])
         serve = None if args.no_serve else serve_leg(lg, inputs, args)
 
     setup_ms = sum(r[0].setup_ms for r in recs) / len(recs)
@@ -518,6 +597,7 @@ def main():
                       "iterations": i32.iterations, "relres": i32.relres,
                       "speedup_vs_fp64": solve64_ms / solve32_ms},
         "tda_ms_per_digit": solve64_ms / -math.log10(max(i64.relres, 1e-300)),
+        "wda": i64.work_units / -math.log10(max(i64.relres, 1e-300)),
         "hierarchy_bytes": recs[-1][4][0], "workspace_bytes": recs[-1][4][1],
         "e2e": {"value": world * nnz / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * g.n,
                 "d2h_bytes_per_step": 8 * g.n, "setup_from_host_ms": setup_e2e * 1e3,
@@ -540,6 +620,10 @@ def main():
         line["multi_rhs"] = multi
     if kcyc is not None:
         line["kcycle"] = kcyc
+    if wda is not None:
+        line["wda"] = wda
+    if order is not None:
+        line["ordering"] = order
     if serve is not None:
         line["serve"] = serve
     if world == 1 and not args.no_cpu_baseline:

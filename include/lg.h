@@ -98,9 +98,10 @@ typedef struct {
                                0: a fixed rule */
   int32_t reorder;          /* 1: renumber the vertices by descending degree before the setup (ties
                                by id), so the gathered values of high-degree vertices share cache
-                               lines; solves take and return vectors in the caller's numbering.
-                               0: keep the caller's numbering (the paper's random ordering, Section
-                               3.3, serves a 2D distribution this library does not use) */
+                               lines, and the row classes are contiguous; 2: a random ordering
+                               (Section 3.3, which uses it to balance a 2D distribution; a hash of
+                               the seed and the vertex id); 0: keep the caller's numbering. Solves
+                               take and return vectors in the caller's numbering either way. */
   int32_t kcycle;           /* 0: V-cycle (Section 4's default). 1: K-cycle (Section 3.7): every
                                aggregation level below the first solves its system by two FCG
                                iterations preconditioned by its own cycle (the first is accelerated
@@ -119,7 +120,12 @@ typedef struct {
   double op_complexity;  /* sum_l nnz(L_l) / nnz(L_0), diagonals included */
   double setup_ms;       /* device time of lg_setup */
   double solve_ms;       /* device time of this solve (or batch) */
-  double work_units;     /* solve work in finest-residual units (Section 2.2, WDA numerator) */
+  double work_units;     /* solve work in finest-residual units (Section 2.3.1: WDA = work_units /
+                            -log10(relres)), counted from operator nonzeros: per iteration one
+                            level-0 operator application plus the cycle (2 deg (nnz_l + n_l) + 2 n_l
+                            per aggregation-body visit, 2 nnz_F + n_c + n_l per elimination visit,
+                            n_c^2 for the coarsest solve; a K-cycle level is two bodies plus two
+                            operator applications), in units of nnz(L_0) + n_0 */
   int64_t nnz;           /* nnz(L_0) = stored off-diagonal entries + n */
   int32_t status;        /* lg status of this result */
   int32_t iterations;    /* PCG iterations */

@@ -158,6 +158,7 @@ __device__ __forceinline__ double uniform_pm1(uint64_t seed, int stream, int lev
 
 constexpr int kStreamHash = 0;
 constexpr int kStreamLanczos = 8;
+constexpr int kStreamOrder = 9;  // the random vertex ordering (option reorder = 2)
 
 // ---------------------------------------------------------------------------
 // Reductions. Group reductions use xor butterflies inside aligned groups of

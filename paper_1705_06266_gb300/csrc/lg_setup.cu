@@ -823,6 +823,15 @@ __global__ void k_degree_keys(int64_t n, const int64_t* __restrict__ rowptr, uin
   }
 }
 
+// Keys of the random ordering (Section 3.3): a SplitMix64 value per vertex
+// (stream kStreamOrder), the vertex id breaking the (unlikely) ties.
+__global__ void k_random_keys(int64_t n, uint64_t seed, uint64_t* __restrict__ key, uint64_t* __restrict__ val) {
+  LG_GRID_STRIDE(i, n) {
+    key[i] = splitmix64(seed, rng_counter(kStreamOrder, 0, i)) >> 32;
+    val[i] = (uint64_t)i;
+  }
+}
+
 __global__ void k_perm_from_sorted(int64_t n, const uint64_t* __restrict__ val, int32_t* __restrict__ perm,
                                    int32_t* __restrict__ inv) {
   LG_GRID_STRIDE(i, n) {
@@ -1206,6 +1215,7 @@ void setup_hierarchy(Hier& h, int64_t n, const int64_t* rowptr, const int32_t* c
   if (o.cheb_degree < 1 || o.cheb_degree > 8) fail(LG_ERR_INVALID, "cheb_degree must be 1..8");
   if (o.max_levels < 1) fail(LG_ERR_INVALID, "max_levels");
   if (o.elim_rounds < 1 || o.elim_rounds > 64) fail(LG_ERR_INVALID, "elim_rounds must be 1..64");
+  if (o.reorder < 0 || o.reorder > 2) fail(LG_ERR_INVALID, "reorder must be 0, 1 or 2");
 
   h.dev_err.alloc(1, s);
   LG_CUDA(cudaMemsetAsync(h.dev_err.get(), 0, sizeof(int), s));
@@ -1258,7 +1268,10 @@ void setup_hierarchy(Hier& h, int64_t n, const int64_t* rowptr, const int32_t* c
   if (o.reorder && n > 1) {
     DBuf<uint64_t> key(n, s), val(n, s);
     DBuf<int32_t> inv(n, s);
-    k_degree_keys<<<blocks_for(n), kNT, 0, s>>>(n, cur->rowptr.get(), key.get(), val.get());
+    if (o.reorder == 2)
+      k_random_keys<<<blocks_for(n), kNT, 0, s>>>(n, o.seed, key.get(), val.get());
+    else
+      k_degree_keys<<<blocks_for(n), kNT, 0, s>>>(n, cur->rowptr.get(), key.get(), val.get());
     LG_LAUNCH_CHECK();
     radix_sort_pairs(key.get(), val.get(), n, 32, s);
     k_perm_from_sorted<<<blocks_for(n), kNT, 0, s>>>(n, val.get(), h.perm.get(), inv.get());

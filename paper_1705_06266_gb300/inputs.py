@@ -134,6 +134,18 @@ def grid3d(nx: int, ny: int, nz: int, *, weights: str = "unit", seed: int = 1) -
     return from_edges(nx * ny * nz, u, v, weights=weights, seed=seed, name=f"grid3d_{nx}x{ny}x{nz}")
 
 
+def road_like(nx: int, ny: int, *, keep: float = 0.6, seed: int = 1) -> Graph:
+    """A stand-in for road networks (long chains, low degree, large diameter):
+    the 2D grid with each edge kept with probability ``keep`` (seeded), weights
+    uniform in [0.5, 1.5), the largest component kept."""
+    idx = np.arange(nx * ny, dtype=np.int64).reshape(ny, nx)
+    u = np.concatenate([idx[:, :-1].ravel(), idx[:-1, :].ravel()])
+    v = np.concatenate([idx[:, 1:].ravel(), idx[1:, :].ravel()])
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sel = rng.random(len(u)) < keep
+    return from_edges(nx * ny, u[sel], v[sel], weights="uniform", seed=seed, name=f"road_like_{nx}x{ny}")
+
+
 def chung_lu(n: int, *, exponent: float = 2.1, dmin: float = 1.0, dmax: float = 50000.0,
              m_target: int | None = None, seed: int = 1, weights: str = "uniform",
              wlo: float = 0.5, whi: float = 1.5) -> Graph:

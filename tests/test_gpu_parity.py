@@ -493,3 +493,70 @@ def test_elim_rounds_path_solve_is_direct(lgmod, oracle, inputs, prec):
     ref = oracle.dense_solve(g, b)
     assert np.linalg.norm(x - x.mean() - ref) <= 1e-6 * np.linalg.norm(ref)
     H.close()
+
+
+# ---------------------------------------------------------------------------
+# Work units (Section 2.3.1, WDA): recomputed here from the level structure.
+# ---------------------------------------------------------------------------
+def _iteration_work(lgmod, H, kcycle, deg=2):
+    lv = [H.level_info(l) for l in range(H.nlevels)]
+    first_agg = next((l for l, d in enumerate(lv) if d["kind"] == lgmod.LEVEL_AGG), -1)
+
+    def solve(l):
+        d = lv[l]
+        A = d["nnz"] + d["n"]
+        if d["kind"] == lgmod.LEVEL_COARSEST:
+            return d["n"] ** 2
+        if d["kind"] == lgmod.LEVEL_ELIM:
+            rp, _, _, mp = H.level(l)
+            nnz_f = int(np.diff(rp)[mp < 0].sum())
+            return 2 * nnz_f + d["nc"] + d["n"] + solve(l + 1)
+        body = 2 * deg * A + 2 * d["n"] + solve(l + 1)
+        return 2 * body + 2 * A if (kcycle and l != first_agg) else body
+
+    A0 = lv[0]["nnz"] + lv[0]["n"]
+    return (A0 + solve(0)) / A0
+
+
+@pytest.mark.parametrize("kcycle", [0, 1])
+def test_work_units(lgmod, inputs, kcycle):
+    g = inputs.grid3d(16, 16, 16)
+    H = lgmod.Hierarchy(g, kcycle=kcycle)
+    b = inputs.rhs(g.n, seed=2)
+    _, info = H.solve(b)
+    w = _iteration_work(lgmod, H, kcycle)
+    assert info.work_units == pytest.approx(info.iterations * w, rel=1e-12)
+    wda = info.work_units / -np.log10(info.relres)
+    assert 1.0 < wda < 1000.0
+    X, infos = H.solve_batch(inputs.rhs(g.n, 2, seed=5))
+    for inf in infos:
+        assert inf.work_units == pytest.approx(inf.iterations * w, rel=1e-12)
+    H.close()
+
+
+@pytest.mark.parametrize("name", ["chunglu_20k", "grid3d_8", "rmat_12"])
+def test_random_ordering(lgmod, oracle, inputs, name):
+    """reorder = 2 (Section 3.3's random ordering): the permutation sorts the
+    vertices by the counter-based hash of the seed and id (recomputed here with
+    the published SplitMix64), level 0 is the graph in that numbering, and the
+    solve agrees with the oracle's solution."""
+    g = GRAPHS[name](inputs)
+    H = lgmod.Hierarchy(g, reorder=2)
+    perm = H.permutation()
+    ids = np.arange(g.n, dtype=np.uint64)
+    counter = (np.uint64(9) << np.uint64(56)) | ids
+    keys = np.array([oracle.splitmix64(SEED, int(c)) >> 32 for c in counter], dtype=np.uint64)
+    expect = np.lexsort((ids, keys))  # by key, then by id
+    np.testing.assert_array_equal(perm, expect)
+    prp, pcl, pw = renumbered(g, perm)
+    rp, cl, w, _ = H.level(0)
+    np.testing.assert_array_equal(rp, prp)
+    np.testing.assert_array_equal(cl, pcl)
+    np.testing.assert_array_equal(w, pw)
+    b = inputs.rhs(g.n, seed=8)
+    x, info = H.solve(b)
+    assert info.status == lgmod.OK and relres(g, b, x) <= 1e-8
+    xr, _, _, _ = oracle.Hierarchy(g).pcg(b, tol=1e-12)
+    xr -= xr.mean()
+    assert np.linalg.norm(x - x.mean() - xr) <= 1e-6 * np.linalg.norm(xr)
+    H.close()
