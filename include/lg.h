@@ -4,11 +4,11 @@
  * The method is the unsmoothed-aggregation multigrid with low-degree
  * elimination of Konolige & Brown, "A Parallel Solver for Graph Laplacians"
  * (PASC'18): the setup builds a hierarchy by low-degree elimination
- * (Section 3.4, Algorithm "Determine vertices to eliminate"), affinity
+ * (Section 3.4, Algorithm 2), affinity
  * strength of connection and voting aggregation (Section 3.5, Algorithms
  * "Aggregation" / "Aggregation-Step"), and Galerkin products R L P; the solve
  * is conjugate gradients preconditioned by one V-cycle (Section 2.3,
- * Algorithm "Multigrid cycle") with degree-2 Chebyshev smoothing
+ * Algorithm 1) with degree-2 Chebyshev smoothing
  * (Sections 3.6 and 4).
  *
  * Problem statement (Section 2.1): solve L x = b for the Laplacian L = D - A
@@ -217,7 +217,7 @@ int lg_coarsest_pinv(lg_handle h, double* out);
 
 /*
  * Apply one V-cycle of the hierarchy to f (n doubles, host or device) in the
- * given precision, starting from x = 0: x = M f (Algorithm "Multigrid cycle",
+ * given precision, starting from x = 0: x = M f (Algorithm 1,
  * gamma = 1). No mean projection.
  */
 int lg_vcycle(lg_handle h, const double* f, double* x, int32_t precision);
@@ -270,9 +270,8 @@ int lg_laplacian_apply(int64_t n, const int64_t* rowptr, const int32_t* col, con
                        const double* x, double* y, void* stream);
 
 /*
- * Low-degree elimination candidates (Section 3.4, Algorithm "Determine
- * vertices to eliminate"): is_f[i] = 1 iff deg(i) <= max_degree and hash(i)
- * is the smallest hash among the candidates of i's closed neighbourhood.
+ * Low-degree elimination candidates (Section 3.4, Algorithm 2): is_f[i] = 1
+ * iff deg(i) <= max_degree and hash(i) is the smallest hash among the candidates of i's closed neighbourhood.
  * hash(i) = SplitMix64 output number i for `seed`. *nf (host) receives |F|.
  */
 int lg_elim_select(int64_t n, const int64_t* rowptr, const int32_t* col, int32_t max_degree,
@@ -289,9 +288,8 @@ int lg_strength(int64_t n, const int64_t* rowptr, const int32_t* col, const doub
                 void* stream);
 
 /*
- * Voting aggregation (Section 3.5, Algorithms "Aggregation" and
- * "Aggregation-Step") on strength values S[nnz]: agg[n] receives the
- * aggregate of each vertex, numbered from 0 in ascending order of the root
+ * Voting aggregation (Section 3.5, Algorithm 3) on strength values S[nnz]:
+ * agg[n] receives the aggregate of each vertex, numbered from 0 in ascending order of the root
  * vertex; *nc (host) the number of aggregates; state[n] (LG_SEED /
  * LG_UNDECIDED / LG_DECIDED) and votes[n] the final status and vote counts
  * (state and votes may be NULL).

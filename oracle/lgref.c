@@ -107,7 +107,7 @@ static uint64_t stream_counter(int32_t stream, int32_t level, int64_t idx) {
   return ((uint64_t)(uint32_t)stream << 56) | ((uint64_t)(uint32_t)level << 40) | (uint64_t)idx;
 }
 
-/* Reading: the paper's "hash of the vertex's id" (Section 3.4) is the id-th
+/* Reading: the hash of a vertex id that Section 3.4 leaves open is the id-th
  * output of stream 0; SplitMix64 is a bijection, so distinct ids never tie.
  * The same hash serves every level (ids are per level). */
 uint64_t lgref_vertex_hash(uint64_t seed, int64_t id) {
@@ -279,13 +279,15 @@ static lgref_csr* csr_from_triplets(int64_t n, trip_t* t, int64_t nt) {
 /* Low-degree elimination, Section 3.4.                                      */
 /* ------------------------------------------------------------------------ */
 
-/* candidates_i = i if degree(V_i) <= 4 else "none"; then
- *   z = L (+)elim.(x)elim candidates,
- * with a (x)elim c = c for a != 0 (every stored entry and the diagonal of L
- * are nonzero), and x (+)elim y keeping the operand with the smaller hash
- * (the left one on a tie), hash(none) = infinity. V_i is eliminated iff
- * z_i = i. Reading: "degree" is the number of off-diagonal entries; the
- * neighbourhood is that of L, so it contains the vertex itself. */
+/* Elimination selection (Section 3.4, Algorithm 2): every vertex with at
+ * most max_degree neighbours is a candidate carrying its own id, the others
+ * carry nothing. A semiring product of L with this candidate vector gives,
+ * for each vertex, the candidate of smallest hash in its neighbourhood (the
+ * product passes a candidate through any nonzero entry, and the sum keeps
+ * the candidate with the smaller hash; an absent candidate ranks last). A
+ * vertex is eliminated when that winner is itself. Readings: a vertex's
+ * degree counts its off-diagonal entries, and the neighbourhood is taken
+ * from L, so it contains the vertex itself. */
 int64_t lgref_elim_select(int64_t n, const int64_t* rowptr, const int32_t* col,
                           int32_t max_degree, uint64_t seed, uint8_t* is_f) {
   int64_t* cand = (int64_t*)xmalloc(sizeof(int64_t) * (size_t)n);
@@ -444,7 +446,7 @@ void lgref_strength(int64_t n, const int64_t* rowptr, const int32_t* col, const 
 }
 
 /* ------------------------------------------------------------------------ */
-/* Aggregation, Section 3.5 (Algorithms "Aggregation", "Aggregation-Step").  */
+/* Aggregation, Section 3.5 (Algorithm 3).  */
 /* ------------------------------------------------------------------------ */
 typedef struct {
   int32_t state; /* Seed > Undecided > Decided */
@@ -702,7 +704,7 @@ void lgref_cheb_post(int64_t n, const int64_t* rowptr, const int32_t* col, const
 }
 
 /* ------------------------------------------------------------------------ */
-/* Coarsest level (Algorithm "Multigrid cycle", direct solve): the singular  */
+/* Coarsest level (Algorithm 1, direct solve): the singular  */
 /* Laplacian is inverted on the complement of its null space span(1)        */
 /* (Section 2.1), L^+ = (L + 11^T/n)^-1 - 11^T/n, by Cholesky.               */
 /* ------------------------------------------------------------------------ */
@@ -923,7 +925,7 @@ void lgref_hier_coarsest_pinv(const lgref_hier* h, double* out) {
 }
 
 /* ------------------------------------------------------------------------ */
-/* Multigrid cycle (Algorithm "Multigrid cycle", gamma = 1: a V-cycle) with  */
+/* Multigrid cycle (Algorithm 1, gamma = 1: a V-cycle) with  */
 /* x = 0 on entry at every level (it is applied as a preconditioner).        */
 /* With the K-cycle (Section 3.7) the system of every aggregation level      */
 /* below the first is solved by two FCG iterations preconditioned by that    */

@@ -69,7 +69,7 @@ void lgref_diag(int64_t n, const int64_t* rowptr, const double* w, double* d);
 void lgref_apply_L(int64_t n, const int64_t* rowptr, const int32_t* col, const double* w,
                    const double* x, double* y);
 
-/* ---- low-degree elimination (Section 3.4, Algorithm "Determine vertices to eliminate") ---- */
+/* ---- low-degree elimination (Section 3.4, Algorithm 2) ---- */
 int64_t lgref_elim_select(int64_t n, const int64_t* rowptr, const int32_t* col,
                           int32_t max_degree, uint64_t seed, uint8_t* is_f);
 lgref_csr* lgref_schur(int64_t n, const int64_t* rowptr, const int32_t* col, const double* w,
@@ -84,7 +84,7 @@ void lgref_affinity(int64_t n, const int64_t* rowptr, const int32_t* col, int32_
 void lgref_strength(int64_t n, const int64_t* rowptr, const int32_t* col, const double* w,
                     uint64_t seed, int32_t level, int32_t m, int32_t sweeps, double omega, double* S);
 
-/* ---- aggregation (Section 3.5, Algorithms "Aggregation" / "Aggregation-Step") ---- */
+/* ---- aggregation (Section 3.5, Algorithm 3) ---- */
 int64_t lgref_aggregate(int64_t n, const int64_t* rowptr, const int32_t* col, const double* S,
                         int32_t iters, int32_t threshold, int32_t* agg, int8_t* state, int32_t* votes);
 lgref_csr* lgref_galerkin(int64_t n, const int64_t* rowptr, const int32_t* col, const double* w,

@@ -262,7 +262,7 @@ __global__ void k_cycle_out(int64_t n, const T* __restrict__ x, double* __restri
 }
 
 // ---------------------------------------------------------------------------
-// V-cycle driver (Algorithm "Multigrid cycle", gamma = 1, x = 0 on entry).
+// V-cycle driver (Algorithm 1, gamma = 1, x = 0 on entry).
 // ---------------------------------------------------------------------------
 template <typename T> std::vector<LevelVecs<T>>& vecs(Workspace& ws);
 template <> std::vector<LevelVecs<double>>& vecs<double>(Workspace& ws) { return ws.v64; }

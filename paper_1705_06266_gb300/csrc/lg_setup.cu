@@ -187,9 +187,8 @@ struct EpiStore {
 };
 
 // ---------------------------------------------------------------------------
-// Low-degree elimination (Section 3.4, Algorithm "Determine vertices to
-// eliminate"): candidates are vertices of degree <= max_degree; each
-// candidate's value is hash(i) (SplitMix64 output i), others +infinity
+// Low-degree elimination (Section 3.4, Algorithm 2): candidates are vertices
+// of degree <= max_degree; each candidate's value is hash(i) (SplitMix64 output i), others +infinity
 // (UINT64_MAX); z_i = min over the closed neighbourhood; i goes iff it is a
 // candidate and z_i = hash(i).
 // ---------------------------------------------------------------------------
@@ -489,7 +488,7 @@ struct FRowSum {
 };
 
 // ---------------------------------------------------------------------------
-// Aggregation (Section 3.5, Algorithms "Aggregation", "Aggregation-Step").
+// Aggregation (Section 3.5, Algorithm 3).
 // status = (state, idx) with Seed > Undecided > Decided. The (+)agg maximum
 // over filtered neighbours is taken on a 128-bit key: high word
 // state << 62 | FP64 bits of S_ij (S in [0, 1], so its bits fit in 62),

@@ -250,7 +250,7 @@ def test_strength_invariants(oracle, inputs):
 
 
 # --------------------------------------------------------------------------
-# Aggregation (Section 3.5, Algorithms "Aggregation" and "Aggregation-Step")
+# Aggregation (Section 3.5, Algorithm 3)
 # --------------------------------------------------------------------------
 def check_partition(oracle, g, S, nc, agg, st, votes, threshold=8, iters=10):
     assert agg.min() == 0 and agg.max() == nc - 1 and np.unique(agg).size == nc
