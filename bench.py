@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-kcycle", action="store_true")
     ap.add_argument("--no-wda", action="store_true")
     ap.add_argument("--no-ordering", action="store_true")
+    ap.add_argument("--no-rmat26", action="store_true")
     ap.add_argument("--serve-graphs", type=int, default=64)
     ap.add_argument("--serve-nmax", type=int, default=262144)
     ap.add_argument("--serve-requests", type=int, default=1000)
@@ -334,6 +335,42 @@ def ordering_leg(lg, torch, dev, graphs):
     return out
 
 
+def rmat26_leg(lg, inputs, torch, dev):
+    """R-MAT scale 26 (edge factor 16, (a,b,c) = (.57,.19,.19), unit weights,
+    largest component), generated on the device: the FP32 hierarchy inside
+    FP64 PCG against the plain FP64 solve, 1e-8, device-resident b."""
+    try:
+        t0 = time.perf_counter()
+        n, rp, cl, w = inputs.rmat_device(26, seed=1, device=str(dev))
+        gen_s = time.perf_counter() - t0
+        nnz = int(cl.numel()) + n
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        h = lg.lg_setup(n, rp, cl, w, lg.options())
+        hb, _ = lg.lg_hier_bytes(h)
+        del rp, cl, w
+        torch.cuda.empty_cache()
+        b = torch.from_numpy(inputs.rhs(n, seed=2)).to(dev)
+        x = torch.zeros_like(b)
+        torch.cuda.synchronize()
+        out = {"n": n, "nnz": nnz, "generate_s": gen_s, "setup_ms": lg.lg_hier_info(h).setup_ms,
+               "levels": lg.lg_hier_info(h).levels, "hierarchy_bytes": hb}
+        for tag, prec in (("fp64", lg.FP64), ("fp32", lg.FP32_HIER)):
+            lg.lg_set_precision(h, prec)
+            lg.lg_solve(h, b, x, TOL)
+            inf = lg.lg_solve(h, b, x, TOL)
+            out[tag] = {"solve_ms": inf.solve_ms, "iterations": inf.iterations, "relres": inf.relres,
+                        "nnz_per_s": nnz / (inf.solve_ms * 1e-3)}
+        out["fp32_speedup"] = out["fp64"]["solve_ms"] / out["fp32"]["solve_ms"]
+        lg.lg_destroy(h)
+        del b, x
+        torch.cuda.empty_cache()
+        return out
+    except Exception as e:  # report, do not lose the rest of the line
+        torch.cuda.empty_cache()
+        return {"error": f"{type(e).__name__}: {e}"[:300]}
+
+
 def serve_leg(lg, inputs, args):
     """Continuous batching over resident hierarchies: a burst of requests
     measures the saturation rate, then Poisson arrivals at a fraction of it
@@ -531,6 +568,7 @@ def main():
         multi = None if args.no_multi_rhs else multi_rhs_leg(lg, inputs, torch, dev, args.multi_rhs_k)
         kcyc = None if args.no_kcycle else kcycle_leg(lg, inputs, torch, dev, g, b)
         wda = None if args.no_wda else wda_leg(lg, inputs, torch, dev)
+        r26 = None if args.no_rmat26 else rmat26_leg(lg, inputs, torch, dev)
         order = None
         if not args.no_ordering:
             g_rmat = workload(inputs, "rmat_20")
@@ -622,6 +660,8 @@ def main():
         line["kcycle"] = kcyc
     if wda is not None:
         line["wda"] = wda
+    if r26 is not None:
+        line["rmat26"] = r26
     if order is not None:
         line["ordering"] = order
     if serve is not None:

@@ -194,6 +194,77 @@ def rmat(scale: int, *, edge_factor: int = 16, a: float = 0.57, b: float = 0.19,
     return from_edges(n, u, v, weights=weights, seed=seed + 7, name=f"rmat_{scale}_{edge_factor}")
 
 
+def rmat_device(scale: int, *, edge_factor: int = 16, a: float = 0.57, b: float = 0.19, c: float = 0.19,
+                seed: int = 1, device: str = "cuda", chunk: int = 1 << 27):
+    """R-MAT (Chakrabarti, Zhan & Faloutsos 2004) generated on a torch device,
+    for sizes whose host-side generation would be too slow (scale 26: 2^26
+    vertices, 2^30 sampled edges). Edges are sampled in chunks from a seeded
+    torch generator (one quadrant draw per bit), symmetrised, deduplicated,
+    self-loops dropped, unit weights, and the largest connected component kept
+    (min-label propagation with pointer jumping) and renumbered in id order.
+    Returns (n, rowptr int64, col int32, w float64) on the device, rows sorted.
+    Not bitwise the same graph as rmat() at equal seeds: another generator."""
+    import torch
+
+    n = 1 << scale
+    m = edge_factor << scale
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    parts = []
+    for start in range(0, m, chunk):
+        cnt = min(chunk, m - start)
+        u = torch.zeros(cnt, dtype=torch.int64, device=device)
+        v = torch.zeros(cnt, dtype=torch.int64, device=device)
+        for bit in range(scale - 1, -1, -1):
+            r = torch.rand(cnt, generator=gen, device=device)
+            u |= (r >= a + b).to(torch.int64) << bit
+            v |= (((r >= a) & (r < a + b)) | (r >= a + b + c)).to(torch.int64) << bit
+            del r
+        lo, hi = torch.minimum(u, v), torch.maximum(u, v)
+        del u, v
+        keep = lo != hi
+        parts.append(torch.unique(lo[keep] * n + hi[keep]))
+        del lo, hi, keep
+    key = torch.unique(torch.cat(parts))
+    del parts
+    u, v = key // n, key % n
+    del key
+    # largest component: labels converge to the smallest id of each component
+    label = torch.arange(n, dtype=torch.int64, device=device)
+    while True:
+        mn = torch.minimum(label[u], label[v])
+        new = label.clone()
+        new.scatter_reduce_(0, u, mn, reduce="amin")
+        new.scatter_reduce_(0, v, mn, reduce="amin")
+        del mn
+        new = new[new]
+        new = new[new]
+        if torch.equal(new, label):
+            break
+        label = new
+    root = torch.bincount(label, minlength=n).argmax()
+    inc = label == root
+    del label, new
+    nid = torch.cumsum(inc.to(torch.int64), 0) - 1
+    keep = inc[u]  # both ends of an edge share a component
+    u, v = nid[u[keep]], nid[v[keep]]
+    nl = int(inc.sum())
+    del nid, keep, inc
+    rows = torch.cat([u, v])
+    cols = torch.cat([v, u])
+    del u, v
+    order = torch.argsort(rows * nl + cols)
+    rows, cols = rows[order], cols[order].to(torch.int32)
+    del order
+    rowptr = torch.zeros(nl + 1, dtype=torch.int64, device=device)
+    rowptr[1:] = torch.cumsum(torch.bincount(rows, minlength=nl), 0)
+    del rows
+    w = torch.ones(cols.numel(), dtype=torch.float64, device=device)
+    if str(device).startswith("cuda"):
+        torch.cuda.empty_cache()  # hand the temporaries' memory back for the solver's own allocations
+    return nl, rowptr, cols, w
+
+
 def random_graph(n: int, avg_degree: float, *, seed: int = 1, weights: str = "uniform") -> Graph:
     """Small Erdos-Renyi style graph plus a spanning path, so it is connected."""
     rng = np.random.Generator(np.random.PCG64(seed))
