@@ -4,11 +4,10 @@
  * The method is the unsmoothed-aggregation multigrid with low-degree
  * elimination of Konolige & Brown, "A Parallel Solver for Graph Laplacians"
  * (PASC'18): the setup builds a hierarchy by low-degree elimination
- * (Section 3.4, Algorithm 2), affinity
- * strength of connection and voting aggregation (Section 3.5, Algorithms
- * "Aggregation" / "Aggregation-Step"), and Galerkin products R L P; the solve
- * is conjugate gradients preconditioned by one V-cycle (Section 2.3,
- * Algorithm 1) with degree-2 Chebyshev smoothing
+ * (Section 3.4, Algorithm 2), affinity strength of connection and voting
+ * aggregation (Section 3.5, Algorithm 3), and Galerkin products R L P; the
+ * solve is conjugate gradients preconditioned by one V-cycle (Section 2.3,
+ * Algorithm 1) or K-cycle (Section 3.7) with degree-2 Chebyshev smoothing
  * (Sections 3.6 and 4).
  *
  * Problem statement (Section 2.1): solve L x = b for the Laplacian L = D - A
