@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-wda", action="store_true")
     ap.add_argument("--no-ordering", action="store_true")
     ap.add_argument("--no-rmat26", action="store_true")
+    ap.add_argument("--no-many", action="store_true")
+    ap.add_argument("--many-graphs", type=int, default=608)
     ap.add_argument("--serve-graphs", type=int, default=64)
     ap.add_argument("--serve-nmax", type=int, default=262144)
     ap.add_argument("--serve-requests", type=int, default=1000)
@@ -438,6 +440,45 @@ def serve_leg(lg, inputs, args):
     }
 
 
+def many_leg(lg, inputs, count):
+    """Many small graphs, one right-hand side each (host b and x): one
+    lg_solve_many launch against one lg_solve call per graph, on the same
+    hierarchies (FP32 hierarchy)."""
+    graphs = inputs.serving_mix(count, 500, 5000, seed=31)
+    hs = [lg.Hierarchy(g, precision=lg.FP32_HIER) for g in graphs]
+    handles = [H.h for H in hs]
+    bs = [inputs.rhs(g.n, seed=40 + q) for q, g in enumerate(graphs)]
+    xs = [np.zeros(g.n) for g in graphs]
+    lg.lg_solve_many(handles, bs, xs, TOL)  # warm-up (builds the device views)
+    packed = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        infos = lg.lg_solve_many(handles, bs, xs, TOL)
+        packed.append(time.perf_counter() - t0)
+    for H, b, x in zip(hs, bs, xs):  # warm-up (captures each handle's solve graph)
+        lg.lg_solve(H.h, b, x, TOL)
+    t0 = time.perf_counter()
+    single = [lg.lg_solve(H.h, b, x, TOL) for H, b, x in zip(hs, bs, xs)]
+    seq_s = time.perf_counter() - t0
+    for H in hs:
+        H.close()
+    p_s = sorted(packed)[1]
+    nnz = sum(g.nnz for g in graphs)
+    its = sorted(i.iterations for i in infos)
+    return {
+        "graphs": count, "solves_per_s": count / p_s, "nnz_per_s": nnz / p_s, "wall_ms": p_s * 1e3,
+        "launch_ms": infos[0].solve_ms,
+        "sequential_solves_per_s": count / seq_s, "speedup_vs_sequential": seq_s / p_s,
+        "iterations_median": its[len(its) // 2], "iterations_max": its[-1],
+        "iterations_equal_to_lg_solve": sum(a.iterations == b.iterations for a, b in zip(infos, single)),
+        "max_relres": max(i.relres for i in infos), "failed": sum(i.status != lg.OK for i in infos),
+        "vertices": int(sum(g.n for g in graphs)), "nnz": int(nnz),
+        "config": f"{count} graphs, n log-uniform in [500, 5000], type uniform over 2D grid / 3D grid / "
+                  f"Chung-Lu 2.1 / R-MAT ef16; one right-hand side each; tol 1e-8; FP32 hierarchy; host b and "
+                  f"x; wall time of the call (median of 3) against one lg_solve per graph",
+    }
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -575,6 +616,7 @@ def main():
             order = ordering_leg(lg, torch, dev, [(args.workload, g, b),
                                                   ("rmat_20", g_rmat, inputs.rhs(g_rmat.n, seed=2))])
         serve = None if args.no_serve else serve_leg(lg, inputs, args)
+        many = None if args.no_many else many_leg(lg, inputs, args.many_graphs)
 
     setup_ms = sum(r[0].setup_ms for r in recs) / len(recs)
     solve64_ms = sum(r[1].solve_ms for r in recs) / len(recs)
@@ -666,6 +708,8 @@ def main():
         line["ordering"] = order
     if serve is not None:
         line["serve"] = serve
+    if many is not None:
+        line["many_small"] = many
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, g, b)
     print(json.dumps(line), flush=True)

@@ -184,6 +184,27 @@ int lg_solve_batch(lg_handle h, int32_t k, const double* B, int64_t ldb, double*
 /* Set the V-cycle precision (LG_FP64 or LG_FP32_HIER) used by later solves. */
 int lg_set_precision(lg_handle h, int32_t precision);
 
+/*
+ * Many independent solves in one kernel launch: for g = 0 .. count-1, solve
+ * L_g x[g] = b[g] on hierarchy hs[g] exactly as lg_solve would (Section 4's
+ * PCG, each handle's own precision, cycle and max_iter), but with the whole
+ * solve of one graph run by one thread block, so that graphs of a few
+ * thousand vertices, which leave lg_solve bound by kernel-launch latency,
+ * share one launch. Results agree with lg_solve's to rounding (the order of
+ * additions in the reductions differs).
+ *   hs:    count distinct handles, all on the current device, each with
+ *          nnz(L_0) <= 2^22 and at most 64 levels; x[g] and b[g] hold that
+ *          handle's n doubles (host or device, per its memory_space) and
+ *          must not overlap other graphs' vectors.
+ *   infos: NULL or count entries (solve_ms: the whole launch).
+ * Uses each handle's default workspace: no other call may use these handles
+ * meanwhile. Returns LG_OK if every solve converged, else the first failing
+ * status in argument order. LG_ERR_INVALID for count < 1, a NULL or repeated
+ * handle or vector, tol <= 0, or a graph over the limits above.
+ */
+int lg_solve_many(int32_t count, const lg_handle* hs, const double* const* b, double* const* x, double tol,
+                  lg_info* infos);
+
 /* Hierarchy summary: levels, op_complexity, setup_ms, nnz. */
 int lg_hier_info(lg_handle h, lg_info* info);
 

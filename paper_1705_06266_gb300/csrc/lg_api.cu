@@ -1,11 +1,14 @@
 // extern "C" entry points of include/lg.h: argument checks, pointer-space
 // detection, handle lifecycle, and the mapping of library errors to status
 // codes. No entry point lets an exception or a CUDA error escape.
+#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "lg_hier.h"
 
@@ -38,6 +41,7 @@ Hier::~Hier() {
   // stream is destroyed
   ws.reset();
   wsb.reset();
+  many.reset();
   levels.clear();
   dev_err.release();
   perm.release();
@@ -228,6 +232,33 @@ int lg_solve_batch(lg_handle hh, int32_t k, const double* B, int64_t ldb, double
     LG_CUDA(cudaMemcpyAsync(X + (size_t)c * ldx, Xd.get() + (size_t)c * n, sizeof(double) * n, cudaMemcpyDefault, s));
   LG_CUDA(cudaStreamSynchronize(s));
   return st;
+  LG_API_END
+}
+
+int lg_solve_many(int32_t count, const lg_handle* hs, const double* const* b, double* const* x, double tol,
+                  lg_info* infos) {
+  if (count < 1 || !hs || !b || !x || !(tol > 0.0)) return LG_ERR_INVALID;
+  std::vector<lg::Hier*> v((size_t)count);
+  for (int g = 0; g < count; ++g) {
+    v[g] = H(hs[g]);
+    if (!v[g] || !b[g] || !x[g]) return LG_ERR_INVALID;
+    if (v[g]->nnz0 > lg::kManyMaxNnz || (int)v[g]->levels.size() > lg::kManyMaxLevels) return LG_ERR_INVALID;
+  }
+  {
+    std::vector<lg::Hier*> sorted(v);
+    std::sort(sorted.begin(), sorted.end());
+    if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end()) return LG_ERR_INVALID;
+  }
+  LG_API_BEGIN
+  int dev = 0;
+  LG_CUDA(cudaGetDevice(&dev));
+  std::unique_ptr<bool[]> bd(new bool[count]), xd(new bool[count]);
+  for (int g = 0; g < count; ++g) {
+    if (v[g]->device != dev) return LG_ERR_INVALID;
+    bd[g] = lg::is_device_ptr(b[g], v[g]->opts.memory_space);
+    xd[g] = lg::is_device_ptr(x[g], v[g]->opts.memory_space);
+  }
+  return lg::solve_many(count, v.data(), b, x, bd.get(), xd.get(), tol, infos);
   LG_API_END
 }
 

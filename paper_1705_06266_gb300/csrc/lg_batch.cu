@@ -529,11 +529,12 @@ __global__ void k_m_colsum(int64_t n, int k, const double* __restrict__ v, doubl
 }
 
 // b_m = b - mean(b) per column (b in the caller's numbering, gathered);
-// x = 0; r = b_m; column scalars initialised.
+// x = 0; r = b_m; p = 0 (see k_pcg_init); column scalars initialised.
 template <int KP>
 __global__ void k_m_init(int64_t n, int k, const double* __restrict__ b, const int32_t* __restrict__ perm,
                          const double* __restrict__ colsum, double* __restrict__ bm, double* __restrict__ x,
-                         double* __restrict__ r, double* scal, double* partials, unsigned* ticket, double* tmp,
+                         double* __restrict__ r, double* __restrict__ p, double* scal, double* partials,
+                         unsigned* ticket, double* tmp,
                          double tol, int maxit, int every) {
   const int c = threadIdx.x & (KP - 1);
   double acc[1] = {0.0};
@@ -544,6 +545,7 @@ __global__ void k_m_init(int64_t n, int k, const double* __restrict__ b, const i
       bm[i * k + c] = v;
       r[i * k + c] = v;
       x[i * k + c] = 0.0;
+      p[i * k + c] = 0.0;
       acc[0] += v * v;
     }
   }
@@ -930,8 +932,8 @@ static int msolve(Hier& h, Workspace& ws, int k, const double* B, double* X, dou
   const int vb = grid_for(n * KP, kBT, kSMs * 8);
   k_m_colsum<KP><<<vb, kBT, 0, s>>>(n, k, B, ws.partials.get(), ws.tickets.get(), colsum);
   LG_LAUNCH_CHECK();
-  k_m_init<KP><<<vb, kBT, 0, s>>>(n, k, B, h.perm.get(), colsum, ws.bm.get(), ws.x.get(), ws.r.get(), scal,
-                                  ws.partials.get(), ws.tickets.get(), tmp, tol, maxit, every);
+  k_m_init<KP><<<vb, kBT, 0, s>>>(n, k, B, h.perm.get(), colsum, ws.bm.get(), ws.x.get(), ws.r.get(), ws.p.get(),
+                                  scal, ws.partials.get(), ws.tickets.get(), tmp, tol, maxit, every);
   LG_LAUNCH_CHECK();
   const size_t nscal = (size_t)k * kMS + kMG;
   std::vector<double> hs(nscal);

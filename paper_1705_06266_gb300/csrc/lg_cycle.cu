@@ -544,10 +544,12 @@ __global__ void k_sum1(int64_t n, const double* __restrict__ v, double* partials
 }
 
 // b_m = b - mean(b) (b in the caller's numbering, gathered into level-0
-// order); x = 0; r = b_m; ||b_m||^2; loop control scalars.
+// order); x = 0; r = b_m; p = 0 (the first update takes beta = 0, and 0 times
+// whatever a reused buffer held could be NaN); ||b_m||^2; loop control scalars.
 __global__ void k_pcg_init(int64_t n, const double* __restrict__ b, const int32_t* __restrict__ perm,
-                           double* __restrict__ bm, double* __restrict__ x, double* __restrict__ r, double* scal,
-                           double* partials, unsigned* ticket, double tol, int maxit, int every) {
+                           double* __restrict__ bm, double* __restrict__ x, double* __restrict__ r,
+                           double* __restrict__ p, double* scal, double* partials, unsigned* ticket, double tol,
+                           int maxit, int every) {
   const double mean = scal[kSumB] / (double)n;
   double acc[1] = {0.0};
   LG_GRID_STRIDE(i, n) {
@@ -555,6 +557,7 @@ __global__ void k_pcg_init(int64_t n, const double* __restrict__ b, const int32_
     bm[i] = v;
     r[i] = v;
     x[i] = 0.0;
+    p[i] = 0.0;
     acc[0] += v * v;
   }
   if (grid_sum<kVT, 1>(acc, partials, ticket, scal + kBB)) {
@@ -888,7 +891,7 @@ int pcg_solve(Hier& h, Workspace& ws, const double* b, double* x, double tol, in
   const int every = h.opts.residual_replace > 0 ? h.opts.residual_replace : 1 << 30;
   k_sum1<<<vblocks(n), kVT, 0, s>>>(n, b, ws.partials.get(), ws.tickets.get(), scal + kSumB);
   LG_LAUNCH_CHECK();
-  k_pcg_init<<<vblocks(n), kVT, 0, s>>>(n, b, h.perm.get(), ws.bm.get(), ws.x.get(), ws.r.get(), scal,
+  k_pcg_init<<<vblocks(n), kVT, 0, s>>>(n, b, h.perm.get(), ws.bm.get(), ws.x.get(), ws.r.get(), ws.p.get(), scal,
                                         ws.partials.get(), ws.tickets.get(), tol, maxit, every);
   LG_LAUNCH_CHECK();
   read_scal(ws, s);

@@ -164,6 +164,7 @@ struct Hier {
   DBuf<int> dev_err;                    // device error word
   DBuf<int32_t> perm;                   // level-0 vertex i is the caller's vertex perm[i]
   int first_agg = -1;                   // first aggregation level (-1: none)
+  std::shared_ptr<void> many;           // device views of the levels for lg_solve_many (lg_many.cu)
   ~Hier();
 };
 
@@ -196,5 +197,13 @@ void vcycle_apply_batch(Hier& h, Workspace& ws, int k, const double* F, double* 
 double iteration_work(const Hier& h);
 int pcg_solve_batch(Hier& h, Workspace& ws, int k, const double* B, double* X, double tol, int precision,
                     cudaStream_t s, lg_info* infos);
+
+// ---- many small solves in one launch (lg_many.cu) ----
+constexpr int64_t kManyMaxNnz = int64_t(1) << 22;  // largest nnz(L_0) one block solves
+constexpr int kManyMaxLevels = 64;
+// hs: distinct handles on one device; b / x: each graph's vectors in the
+// caller's numbering, device memory where b_dev / x_dev say so, else host.
+int solve_many(int count, Hier* const* hs, const double* const* b, double* const* x, const bool* b_dev,
+               const bool* x_dev, double tol, lg_info* infos);
 
 }  // namespace lg

@@ -1,0 +1,751 @@
+// Many independent small solves in one launch (Section 4's PCG with the
+// V-cycle of Algorithm 1, or the K-cycle of Section 3.7).
+//
+// A graph of a few thousand vertices leaves the multi-kernel solve of
+// lg_cycle.cu launch-bound: every level of every cycle costs several kernel
+// launches of a few microseconds each, whatever the level's size. Here one
+// thread block runs the whole solve of one graph: every row pass, vector
+// update and dot product of the PCG and of the cycle is a loop over the
+// block's threads, separated by block barriers, so a solve costs one block
+// for its duration and no launch at all. The launch takes one block per graph
+// (largest graphs first), so thousands of graphs share one launch and the
+// hardware schedules blocks onto the 152 SMs as earlier ones finish.
+//
+// Each graph uses its own hierarchy and the vectors of its handle's default
+// workspace. The arithmetic is that of lg_cycle.cu step for step; only the
+// order of additions inside a row sum and a dot product differs (the group
+// and block reductions here versus the grid-wide ones there), so a result
+// agrees with lg_solve's to rounding and takes the same number of iterations
+// but for a residual within rounding of the tolerance.
+//
+// Vectors written inside the launch are read back with plain loads after a
+// block barrier (which makes one thread's global stores visible to the
+// block); only the hierarchy's arrays, constant for the whole launch, go
+// through the read-only path.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "lg_hier.h"
+
+namespace lg {
+
+constexpr int kMT = 256;  // threads of the block that solves one graph
+
+template <typename T>
+struct MVecs {
+  T *f, *x, *r, *a, *b, *kc1, *kv1, *kv2;  // a, b: the two Chebyshev direction buffers
+};
+
+// One CSR structure with its rows grouped by length (the plan's class
+// lists): rows off[c] .. off[c+1] of `rows` have at most E 2^c entries
+// (class 5: at most kChunk), rows off[kClasses] .. n are longer.
+struct MRows {
+  int64_t n = 0;
+  const int64_t* ptr = nullptr;
+  const int32_t* idx = nullptr;
+  const int32_t* rows = nullptr;
+  int64_t off[kClasses + 1] = {};
+};
+
+struct MLevel {
+  int kind = 0;
+  int64_t n = 0, nc = 0;
+  MRows op, mem, pt;
+  const double *w = nullptr, *d = nullptr, *dinv = nullptr;
+  const float *w32 = nullptr, *dinv32 = nullptr;
+  const int32_t *agg = nullptr, *cmap = nullptr, *cfine = nullptr;
+  const double* pt_coef = nullptr;
+  const float* pt_coef32 = nullptr;
+  const double* pinv = nullptr;
+  double inv_theta = 0.0, c1[8] = {0}, c2[8] = {0};
+  MVecs<double> v64{};
+  MVecs<float> v32{};
+  double* ks = nullptr;  // K-cycle scalars of the level (kKScal)
+};
+
+struct MGraph {
+  const MLevel* lv;
+  int nlevels, first_agg, kcycle, deg, fp32, maxit, every;
+  double tol;
+  const int32_t* perm;  // level-0 vertex i is the caller's vertex perm[i]
+  const double* b;      // caller's numbering
+  double* out;          // caller's numbering, mean removed
+  double *bm, *x, *r, *ro, *p, *q;
+  double* res;          // iterations, status, relative residual
+};
+
+// Device views of a hierarchy's levels, built once per handle.
+struct ManyDesc {
+  DBuf<MLevel> levels;
+};
+
+// ---------------------------------------------------------------------------
+// Block primitives.
+// ---------------------------------------------------------------------------
+struct MShared {
+  double red[8 * (kMT / 32) + 8];
+  int ph[kManyMaxLevels];  // cycle phase per level (see m_cycle)
+};
+
+// Sum of K values over the block, returned to every thread.
+template <int K>
+__device__ __forceinline__ void m_sum(double (&v)[K], MShared& sm) {
+  block_sum<kMT, K>(v, sm.red);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) sm.red[8 * (kMT / 32) + k] = v[k];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = sm.red[8 * (kMT / 32) + k];
+  __syncthreads();
+}
+
+#define LG_BLOCK_LOOP(i, n) for (int64_t i = threadIdx.x; i < (n); i += kMT)
+
+// Rows of class c, one aligned group of G lanes per row: s = the row's sum of
+// term.acc over its entries, then epi(row, term.fin(row, rv, s)).
+template <typename A, int G, class Term, class Epi>
+__device__ __forceinline__ void m_class(const MRows& R, int c, const Term& term, const Epi& epi) {
+  const int64_t lo = R.off[c], cnt = R.off[c + 1] - lo;
+  const int grp = threadIdx.x / G, gl = threadIdx.x & (G - 1);
+  const unsigned mask = group_mask<G>();
+  for (int64_t base = 0; base < cnt; base += kMT / G) {
+    const int64_t q = base + grp;
+    A s = A(0), rv = A(0);
+    int64_t row = 0;
+    if (q < cnt) {
+      row = __ldg(&R.rows[lo + q]);
+      rv = term.row(row);
+      const int64_t e = __ldg(&R.ptr[row + 1]);
+      for (int64_t k = __ldg(&R.ptr[row]) + gl; k < e; k += G) s = term.acc(s, k, __ldg(&R.idx[k]), rv);
+    }
+    if constexpr (G > 1) s = group_sum<G>(s, mask);
+    if (gl == 0 && q < cnt) epi(row, term.fin(row, rv, s));
+  }
+}
+
+// A row pass over every row of R, then a barrier. Rows longer than kChunk
+// entries take the whole block each. Not inlined: a call per pass costs
+// nothing next to the pass, and the kernel compiles in a fraction of the time.
+template <typename A, class Term, class Epi>
+__device__ __noinline__ void m_pass(const MRows& R, const Term& term, const Epi& epi, MShared& sm) {
+  m_class<A, 1>(R, 0, term, epi);
+  m_class<A, 2>(R, 1, term, epi);
+  m_class<A, 4>(R, 2, term, epi);
+  m_class<A, 8>(R, 3, term, epi);
+  m_class<A, 16>(R, 4, term, epi);
+  m_class<A, 32>(R, 5, term, epi);
+  for (int64_t q = R.off[kClasses]; q < R.n; ++q) {
+    const int64_t row = __ldg(&R.rows[q]);
+    const A rv = term.row(row);
+    A s = A(0);
+    const int64_t e = __ldg(&R.ptr[row + 1]);
+    for (int64_t k = __ldg(&R.ptr[row]) + threadIdx.x; k < e; k += kMT) s = term.acc(s, k, __ldg(&R.idx[k]), rv);
+    double v[1] = {(double)s};
+    m_sum<1>(v, sm);
+    if (threadIdx.x == 0) epi(row, term.fin(row, rv, (A)v[0]));
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Row terms (the forms of lg_rows.cuh, with plain loads of the vector).
+// ---------------------------------------------------------------------------
+template <typename T>
+struct MLap;
+
+template <>
+struct MLap<float> {  // difference form: sum_j w_ij (x_i - x_j)
+  const float* w;
+  const float* x;
+  __device__ __forceinline__ float row(int64_t i) const { return x[i]; }
+  __device__ __forceinline__ float acc(float s, int64_t k, int32_t j, float xi) const {
+    return fmaf(__ldg(&w[k]), xi - x[j], s);
+  }
+  __device__ __forceinline__ float fin(int64_t, float, float s) const { return s; }
+};
+
+template <>
+struct MLap<double> {  // d_i x_i - sum_j w_ij x_j
+  const double* w;
+  const double* x;
+  const double* d;
+  __device__ __forceinline__ double row(int64_t) const { return 0.0; }
+  __device__ __forceinline__ double acc(double s, int64_t k, int32_t j, double) const {
+    return fma(__ldg(&w[k]), x[j], s);
+  }
+  __device__ __forceinline__ double fin(int64_t i, double, double s) const { return fma(__ldg(&d[i]), x[i], -s); }
+};
+
+template <typename T>
+__device__ __forceinline__ MLap<T> m_lap(const MLevel& L, const T* x);
+template <>
+__device__ __forceinline__ MLap<float> m_lap<float>(const MLevel& L, const float* x) {
+  return MLap<float>{L.w32, x};
+}
+template <>
+__device__ __forceinline__ MLap<double> m_lap<double>(const MLevel& L, const double* x) {
+  return MLap<double>{L.w, x, L.d};
+}
+
+template <typename T>
+struct MGather {  // sum_k v[idx_k]
+  const T* v;
+  __device__ __forceinline__ T row(int64_t) const { return T(0); }
+  __device__ __forceinline__ T acc(T s, int64_t, int32_t j, T) const { return s + v[j]; }
+  __device__ __forceinline__ T fin(int64_t, T, T s) const { return s; }
+};
+
+template <typename T>
+struct MWGather {  // sum_k c_k v[idx_k]
+  const T* c;
+  const T* v;
+  __device__ __forceinline__ T row(int64_t) const { return T(0); }
+  __device__ __forceinline__ T acc(T s, int64_t k, int32_t j, T) const { return fma(__ldg(&c[k]), v[j], s); }
+  __device__ __forceinline__ T fin(int64_t, T, T s) const { return s; }
+};
+
+template <typename T> __device__ __forceinline__ const MVecs<T>& m_vecs(const MLevel& L);
+template <> __device__ __forceinline__ const MVecs<double>& m_vecs<double>(const MLevel& L) { return L.v64; }
+template <> __device__ __forceinline__ const MVecs<float>& m_vecs<float>(const MLevel& L) { return L.v32; }
+template <typename T> __device__ __forceinline__ const T* m_dinv(const MLevel& L);
+template <> __device__ __forceinline__ const double* m_dinv<double>(const MLevel& L) { return L.dinv; }
+template <> __device__ __forceinline__ const float* m_dinv<float>(const MLevel& L) { return L.dinv32; }
+template <typename T> __device__ __forceinline__ const T* m_wop(const MLevel& L);
+template <> __device__ __forceinline__ const double* m_wop<double>(const MLevel& L) { return L.w; }
+template <> __device__ __forceinline__ const float* m_wop<float>(const MLevel& L) { return L.w32; }
+template <typename T> __device__ __forceinline__ const T* m_ptc(const MLevel& L);
+template <> __device__ __forceinline__ const double* m_ptc<double>(const MLevel& L) { return L.pt_coef; }
+template <> __device__ __forceinline__ const float* m_ptc<float>(const MLevel& L) { return L.pt_coef32; }
+
+// ---------------------------------------------------------------------------
+// Cycle steps of one level (the kernels of lg_cycle.cu as block loops).
+// ---------------------------------------------------------------------------
+
+// One Chebyshev step on D^-1 L (Section 3.6) over gathered g = d_{s-1}:
+// r_s = rin - L g, d_s = c1 g + c2 D^-1 r_s (when gn), x = [x +] g [+ d_s]
+// (when upd: mode 1 sets, mode 2 adds).
+template <typename T>
+__device__ void m_cheb(const MLevel& L, const T* g, const T* rin, T* rout, T* gn, T* x, int upd, int mode, int add_d,
+                       T c1, T c2, MShared& sm) {
+  const T* dinv = m_dinv<T>(L);
+  m_pass<T>(L.op, m_lap<T>(L, g), [&](int64_t i, T s) {
+    const T r = rin[i] - s;
+    rout[i] = r;
+    T d = T(0);
+    if (gn) {
+      d = c1 * g[i] + c2 * __ldg(&dinv[i]) * r;
+      gn[i] = d;
+    }
+    if (upd) x[i] = (mode == 2 ? x[i] : T(0)) + g[i] + (add_d ? d : T(0));
+  }, sm);
+}
+
+// The next level's first Chebyshev direction target, when that level smooths.
+template <typename T>
+__device__ __forceinline__ void m_next_dir(const MGraph& G, int l, T** d0, const T** dinv, T* it) {
+  const MLevel& N = G.lv[l + 1];
+  if (N.kind == LG_LEVEL_AGG) {
+    *d0 = m_vecs<T>(N).a;
+    *dinv = m_dinv<T>(N);
+    *it = (T)N.inv_theta;
+  } else {
+    *d0 = nullptr;
+    *dinv = nullptr;
+    *it = T(0);
+  }
+}
+
+// Going down through level l: pre-smoothing and restriction (aggregation
+// level), restriction (elimination level). Leaves the coarse input in l+1.
+template <typename T>
+__device__ void m_down(const MGraph& G, int l, MShared& sm) {
+  const MLevel& L = G.lv[l];
+  const MVecs<T>& V = m_vecs<T>(L);
+  const MVecs<T>& C = m_vecs<T>(G.lv[l + 1]);
+  T* d0n;
+  const T* dinvn;
+  T itn;
+  m_next_dir<T>(G, l, &d0n, &dinvn, &itn);
+  if (L.kind == LG_LEVEL_ELIM) {  // (P^T f)_c = f_c + sum_f (w_fc / d_f) f_f
+    m_pass<T>(L.pt, MWGather<T>{m_ptc<T>(L), V.f}, [&](int64_t c, T s) {
+      const T v = V.f[__ldg(&L.cfine[c])] + s;
+      C.f[c] = v;
+      if (d0n) d0n[c] = v * __ldg(&dinvn[c]) * itn;
+    }, sm);
+    return;
+  }
+  const int deg = G.deg;
+  T* g = V.a;
+  T* gn = V.b;
+  const T* rin = V.f;
+  for (int st = 1; st < deg; ++st) {  // pre-smoothing from x = 0
+    m_cheb<T>(L, g, rin, V.r, gn, V.x, 1, st == 1 ? 1 : 2, st == deg - 1, (T)L.c1[st], (T)L.c2[st], sm);
+    rin = V.r;
+    T* t = g;
+    g = gn;
+    gn = t;
+  }
+  // residual of the pre-smoothed x (for degree 1 also x = d_0)
+  m_cheb<T>(L, g, rin, V.r, nullptr, V.x, deg == 1, 1, 0, T(0), T(0), sm);
+  m_pass<T>(L.mem, MGather<T>{V.r}, [&](int64_t I, T s) {  // r_c = R r
+    C.f[I] = s;
+    if (d0n) d0n[I] = s * __ldg(&dinvn[I]) * itn;
+  }, sm);
+}
+
+// Coming back up through level l: prolongation and post-smoothing.
+template <typename T>
+__device__ void m_up(const MGraph& G, int l, MShared& sm) {
+  const MLevel& L = G.lv[l];
+  const MVecs<T>& V = m_vecs<T>(L);
+  const T* xc = m_vecs<T>(G.lv[l + 1]).x;
+  if (L.kind == LG_LEVEL_ELIM) {
+    // kept vertices take their coarse value; eliminated f: (f_f + sum_c w_fc x_c) / d_f
+    const T* w = m_wop<T>(L);
+    const T* dinv = m_dinv<T>(L);
+    LG_BLOCK_LOOP(i, L.n) {
+      const int32_t c = __ldg(&L.cmap[i]);
+      T v;
+      if (c >= 0) {
+        v = xc[c];
+      } else {
+        T s = V.f[i];
+        const int64_t e = __ldg(&L.op.ptr[i + 1]);
+        for (int64_t k = __ldg(&L.op.ptr[i]); k < e; ++k) s += __ldg(&w[k]) * xc[__ldg(&L.cmap[__ldg(&L.op.idx[k])])];
+        v = s * __ldg(&dinv[i]);
+      }
+      V.x[i] = v;
+    }
+    __syncthreads();
+    return;
+  }
+  LG_BLOCK_LOOP(i, L.n) V.x[i] += xc[__ldg(&L.agg[i])];  // x += P x_c
+  __syncthreads();
+  const int deg = G.deg;
+  // r_0 = f - L x, d_0 = D^-1 r_0 / theta
+  m_cheb<T>(L, V.x, V.f, V.r, V.a, nullptr, 0, 0, 0, T(0), (T)L.inv_theta, sm);
+  T* g = V.a;
+  T* gn = V.b;
+  for (int st = 1; st < deg; ++st) {
+    m_cheb<T>(L, g, V.r, V.r, gn, V.x, 1, 2, st == deg - 1, (T)L.c1[st], (T)L.c2[st], sm);
+    T* t = g;
+    g = gn;
+    gn = t;
+  }
+  if (deg == 1) {
+    LG_BLOCK_LOOP(i, L.n) V.x[i] += V.a[i];
+    __syncthreads();
+  }
+}
+
+// Coarsest level: x = L_c^+ f with the FP64 pseudo-inverse, a warp per row.
+template <typename T>
+__device__ void m_coarse(const MLevel& L) {
+  const MVecs<T>& V = m_vecs<T>(L);
+  const int lane = threadIdx.x & 31;
+  const int64_t n = L.n;
+  for (int64_t i = threadIdx.x >> 5; i < n; i += kMT / 32) {
+    double s = 0.0;
+    for (int64_t j = lane; j < n; j += 32) s += __ldg(&L.pinv[i * n + j]) * (double)V.f[j];
+    s = group_sum<32>(s, 0xffffffffu);
+    if (lane == 0) V.x[i] = (T)s;
+  }
+  __syncthreads();
+}
+
+// v = L x (the K-cycle's products).
+template <typename T>
+__device__ void m_apply(const MLevel& L, const T* x, T* v, MShared& sm) {
+  m_pass<T>(L.op, m_lap<T>(L, x), [&](int64_t i, T s) { v[i] = s; }, sm);
+}
+
+// K-cycle, after the first body: c1 = x, v1 = L c1, t1 = c1.f / c1.v1,
+// r1 = f - t1 v1 in place of f, and its direction d_0 = D^-1 r1 / theta.
+template <typename T>
+__device__ void m_kfirst(const MLevel& L, MShared& sm) {
+  const MVecs<T>& V = m_vecs<T>(L);
+  m_apply<T>(L, V.x, V.kv1, sm);
+  double acc[2] = {0.0, 0.0};
+  LG_BLOCK_LOOP(i, L.n) {
+    const T xi = V.x[i];
+    V.kc1[i] = xi;
+    acc[0] += (double)xi * (double)V.kv1[i];
+    acc[1] += (double)xi * (double)V.f[i];
+  }
+  m_sum<2>(acc, sm);
+  const bool ok = acc[0] > 0.0 && isfinite(acc[0]);
+  const double t1 = ok ? acc[1] / acc[0] : 0.0;
+  if (threadIdx.x == 0) {
+    L.ks[kRho1] = acc[0];
+    L.ks[kOk1] = ok ? 1.0 : 0.0;
+    L.ks[kT1] = t1;
+  }
+  const T tt = (T)t1, it = (T)L.inv_theta;
+  const T* dinv = m_dinv<T>(L);
+  LG_BLOCK_LOOP(i, L.n) {
+    const T r = V.f[i] - tt * V.kv1[i];
+    V.f[i] = r;
+    V.a[i] = r * __ldg(&dinv[i]) * it;
+  }
+  __syncthreads();
+}
+
+// K-cycle, after the second body: x = u1 c1 + u2 c2 with c2 = x (see k_ksecond).
+template <typename T>
+__device__ void m_ksecond(const MLevel& L, MShared& sm) {
+  const MVecs<T>& V = m_vecs<T>(L);
+  m_apply<T>(L, V.x, V.kv2, sm);
+  double acc[3] = {0.0, 0.0, 0.0};
+  LG_BLOCK_LOOP(i, L.n) {
+    const double xi = (double)V.x[i];
+    acc[0] += xi * (double)V.kv1[i];
+    acc[1] += xi * (double)V.kv2[i];
+    acc[2] += xi * (double)V.f[i];
+  }
+  m_sum<3>(acc, sm);
+  double u1 = 1.0, u2 = 0.0;
+  if (L.ks[kOk1] != 0.0) {
+    const double rho1 = L.ks[kRho1], t1 = L.ks[kT1], g = acc[0], a2 = acc[2];
+    const double rho2 = acc[1] - g * g / rho1;
+    if (rho2 > 0.0 && isfinite(rho2)) {
+      u1 = t1 - g * a2 / (rho1 * rho2);
+      u2 = a2 / rho2;
+    } else {
+      u1 = t1;
+    }
+  }
+  LG_BLOCK_LOOP(i, L.n) V.x[i] = (T)(u1 * (double)V.kc1[i] + u2 * (double)V.x[i]);
+  __syncthreads();
+}
+
+// The cycle from level 0 (input in level 0's f, and its d_0 when level 0
+// smooths; result in level 0's x), as a loop over levels with a phase per
+// level instead of recursion: phase 0 enters the level (going down), phase 1
+// returns to it from the coarser level after the first (or only) coarse
+// visit, phase 2 after a K-cycle level's second.
+template <typename T>
+__device__ void m_cycle(const MGraph& G, MShared& sm) {
+  int l = 0;
+  if (threadIdx.x == 0) sm.ph[0] = 0;
+  __syncthreads();
+  while (l >= 0) {
+    const MLevel& L = G.lv[l];
+    if (L.kind == LG_LEVEL_COARSEST) {
+      m_coarse<T>(L);
+      --l;
+      continue;
+    }
+    const bool K = G.kcycle && L.kind == LG_LEVEL_AGG && l != G.first_agg;
+    const int ph = sm.ph[l];
+    __syncthreads();  // every thread has read the phase before it changes
+    if (ph == 0) {
+      m_down<T>(G, l, sm);
+    } else {
+      m_up<T>(G, l, sm);
+      if (ph == 1 && K) {
+        m_kfirst<T>(L, sm);
+        m_down<T>(G, l, sm);
+      } else {
+        if (K) m_ksecond<T>(L, sm);
+        --l;
+        continue;
+      }
+    }
+    if (threadIdx.x == 0) {
+      sm.ph[l] = ph + 1;
+      sm.ph[l + 1] = 0;
+    }
+    __syncthreads();
+    ++l;
+  }
+}
+
+// r = b_m - L x and ||r||^2.
+__device__ double m_true_res(const MGraph& G, MShared& sm) {
+  const MLevel& L0 = G.lv[0];
+  m_pass<double>(L0.op, MLap<double>{L0.w, G.x, L0.d}, [&](int64_t i, double s) { G.r[i] = G.bm[i] - s; }, sm);
+  double acc[1] = {0.0};
+  LG_BLOCK_LOOP(i, L0.n) acc[0] += G.r[i] * G.r[i];
+  m_sum<1>(acc, sm);
+  return acc[0];
+}
+
+// The PCG of one graph (FP64, Polak-Ribiere beta, true residual every
+// `every` iterations and to confirm convergence), as pcg_solve runs it.
+template <typename T>
+__device__ void m_pcg(const MGraph& G, MShared& sm) {
+  const MLevel& L0 = G.lv[0];
+  const int64_t n = L0.n;
+  double acc[1] = {0.0};
+  LG_BLOCK_LOOP(i, n) acc[0] += G.b[i];
+  m_sum<1>(acc, sm);
+  const double mean = acc[0] / (double)n;
+  acc[0] = 0.0;
+  LG_BLOCK_LOOP(i, n) {
+    const double v = G.b[__ldg(&G.perm[i])] - mean;
+    G.bm[i] = v;
+    G.r[i] = v;
+    G.x[i] = 0.0;
+    G.p[i] = 0.0;
+    acc[0] += v * v;
+  }
+  m_sum<1>(acc, sm);
+  const double bb = acc[0], tol2bb = G.tol * G.tol * bb;
+  double rr = bb, rz = 0.0;
+  int it = 0, done = 0, brk = 0;
+  const MVecs<T>& V0 = m_vecs<T>(L0);
+  const T* dinv0 = m_dinv<T>(L0);
+  const bool smooth0 = L0.kind == LG_LEVEL_AGG;
+  const T it0 = (T)L0.inv_theta;
+  if (bb > 0.0) {
+    while (it < G.maxit) {
+      // z = M r
+      LG_BLOCK_LOOP(i, n) {
+        const T v = (T)G.r[i];
+        V0.f[i] = v;
+        if (smooth0) V0.a[i] = v * __ldg(&dinv0[i]) * it0;
+      }
+      __syncthreads();
+      m_cycle<T>(G, sm);
+      // sums over z (mean not removed), beta, r^T z
+      const int first = it == 0;
+      double zs[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+      LG_BLOCK_LOOP(i, n) {
+        const double zi = (double)V0.x[i], ri = G.r[i], roi = first ? 0.0 : G.ro[i];
+        zs[0] += zi;
+        zs[1] += zi * ri;
+        zs[2] += zi * roi;
+        zs[3] += ri;
+        zs[4] += roi;
+      }
+      m_sum<5>(zs, sm);
+      const double m = zs[0] / (double)n;
+      const double zr = zs[1] - m * zs[3], zro = zs[2] - m * zs[4];
+      const double beta = first ? 0.0 : (zr - zro) / rz;
+      if (!(zr > 0.0) || !isfinite(zr)) brk = 1;
+      rz = zr;
+      LG_BLOCK_LOOP(i, n) G.p[i] = ((double)V0.x[i] - m) + beta * G.p[i];
+      __syncthreads();
+      // q = L p, alpha
+      m_pass<double>(L0.op, MLap<double>{L0.w, G.p, L0.d}, [&](int64_t i, double s) { G.q[i] = s; }, sm);
+      acc[0] = 0.0;
+      LG_BLOCK_LOOP(i, n) acc[0] += G.p[i] * G.q[i];
+      m_sum<1>(acc, sm);
+      const double pq = acc[0];
+      double alpha = 0.0;
+      if (!(pq > 0.0) || !isfinite(pq) || brk) brk = 1;
+      else alpha = rz / pq;
+      // x, r
+      acc[0] = 0.0;
+      LG_BLOCK_LOOP(i, n) {
+        const double ri = G.r[i];
+        G.ro[i] = ri;
+        G.x[i] += alpha * G.p[i];
+        const double rn = ri - alpha * G.q[i];
+        G.r[i] = rn;
+        acc[0] += rn * rn;
+      }
+      m_sum<1>(acc, sm);
+      rr = acc[0];
+      ++it;
+      if (it % G.every == 0 || rr <= tol2bb) {
+        rr = m_true_res(G, sm);
+        if (rr <= tol2bb) done = 1;
+      }
+      if (done || brk) break;
+    }
+  }
+  int status = LG_OK;
+  double rel = 0.0;
+  if (bb > 0.0) {
+    status = done ? LG_OK : brk ? LG_ERR_BREAKDOWN : LG_ERR_NOT_CONVERGED;
+    if (status != LG_OK) rr = m_true_res(G, sm);
+    rel = sqrt(rr / bb);
+  }
+  // x with its mean removed, in the caller's numbering
+  acc[0] = 0.0;
+  LG_BLOCK_LOOP(i, n) acc[0] += G.x[i];
+  m_sum<1>(acc, sm);
+  const double mx = acc[0] / (double)n;
+  LG_BLOCK_LOOP(i, n) G.out[__ldg(&G.perm[i])] = G.x[i] - mx;
+  if (threadIdx.x == 0) {
+    G.res[0] = (double)it;
+    G.res[1] = (double)status;
+    G.res[2] = rel;
+  }
+}
+
+__global__ void __launch_bounds__(kMT) k_solve_many(const MGraph* __restrict__ graphs) {
+  __shared__ MShared sm;
+  const MGraph G = graphs[blockIdx.x];
+  if (G.fp32) m_pcg<float>(G, sm);
+  else m_pcg<double>(G, sm);
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+// ---------------------------------------------------------------------------
+static MRows rows_of(int64_t n, const int64_t* ptr, const int32_t* idx, const RowPlan& p) {
+  MRows r;
+  r.n = n;
+  r.ptr = ptr;
+  r.idx = idx;
+  r.rows = p.rows_by_class;
+  for (int c = 0; c <= kClasses; ++c) r.off[c] = p.cls_off[c];
+  return r;
+}
+
+// On the handle's own stream: the views live (and are freed) with the handle.
+static const MLevel* many_levels(Hier& h) {
+  if (h.many) return static_cast<ManyDesc*>(h.many.get())->levels.get();
+  cudaStream_t s = h.stream;
+  const size_t nl = h.levels.size();
+  std::vector<MLevel> hv(nl);
+  Workspace& ws = *h.ws;
+  for (size_t l = 0; l < nl; ++l) {
+    const Level& L = *h.levels[l];
+    MLevel& m = hv[l];
+    m.kind = L.kind;
+    m.n = L.n;
+    m.nc = L.nc;
+    m.op = rows_of(L.n, L.rowptr.get(), L.col.get(), L.plan.plan);
+    m.w = L.w.get();
+    m.d = L.d.get();
+    m.dinv = L.dinv.get();
+    m.w32 = L.w32.get();
+    m.dinv32 = L.dinv32.get();
+    if (L.kind == LG_LEVEL_AGG) {
+      m.mem = rows_of(L.nc, L.mem_ptr.get(), L.mem.get(), L.mem_plan.plan);
+      m.agg = L.agg.get();
+      const Cheb& c = h.cheb[l];
+      m.inv_theta = c.inv_theta;
+      for (int q = 0; q < 8; ++q) {
+        m.c1[q] = c.c1[q];
+        m.c2[q] = c.c2[q];
+      }
+    }
+    if (L.kind == LG_LEVEL_ELIM) {
+      m.pt = rows_of(L.nc, L.pt_ptr.get(), L.pt_f.get(), L.pt_plan.plan);
+      m.cmap = L.cmap.get();
+      m.cfine = L.cfine.get();
+      m.pt_coef = L.pt_coef.get();
+      m.pt_coef32 = L.pt_coef32.get();
+    }
+    if (L.kind == LG_LEVEL_COARSEST) m.pinv = L.pinv.get();
+    const LevelVecs<double>& a = ws.v64[l];
+    const LevelVecs<float>& b = ws.v32[l];
+    m.v64 = MVecs<double>{a.f.get(), a.x.get(), a.r.get(), a.dA.get(), a.dB.get(),
+                          a.kc1.get(), a.kv1.get(), a.kv2.get()};
+    m.v32 = MVecs<float>{b.f.get(), b.x.get(), b.r.get(), b.dA.get(), b.dB.get(),
+                         b.kc1.get(), b.kv1.get(), b.kv2.get()};
+    m.ks = ws.kscal.get() + (size_t)kKScal * l;
+  }
+  auto d = std::make_shared<ManyDesc>();
+  d->levels.alloc(nl, s, &h.bytes);
+  LG_CUDA(cudaMemcpyAsync(d->levels.get(), hv.data(), sizeof(MLevel) * nl, cudaMemcpyHostToDevice, s));
+  LG_CUDA(cudaStreamSynchronize(s));  // hv goes out of scope
+  h.many = d;
+  return d->levels.get();
+}
+
+int solve_many(int count, Hier* const* hs, const double* const* b, double* const* x, const bool* b_dev,
+               const bool* x_dev, double tol, lg_info* infos) {
+  cudaStream_t s = hs[0]->stream;
+  // run after whatever the other handles' streams hold
+  std::vector<cudaEvent_t> evs;
+  for (int g = 1; g < count; ++g) {
+    if (hs[g]->stream == s) continue;
+    cudaEvent_t e;
+    LG_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    evs.push_back(e);
+    LG_CUDA(cudaEventRecord(e, hs[g]->stream));
+    LG_CUDA(cudaStreamWaitEvent(s, e, 0));
+  }
+  // largest graphs first, so that the launch does not end on a long tail
+  std::vector<int> order(count);
+  for (int g = 0; g < count; ++g) order[g] = g;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int c) { return hs[a]->nnz0 > hs[c]->nnz0; });
+  std::vector<MGraph> hg(count);
+  DBuf<double> res((size_t)3 * count, s);
+  for (int q = 0; q < count; ++q) {
+    const int g = order[q];
+    Hier& h = *hs[g];
+    Workspace& ws = *h.ws;
+    const int64_t n = h.levels[0]->n;
+    MGraph& G = hg[q];
+    G.lv = many_levels(h);
+    G.nlevels = (int)h.levels.size();
+    G.first_agg = h.first_agg;
+    G.kcycle = h.opts.kcycle;
+    G.deg = h.opts.cheb_degree;
+    G.fp32 = h.opts.precision == LG_FP32_HIER;
+    G.maxit = h.opts.max_iter;
+    G.every = h.opts.residual_replace > 0 ? h.opts.residual_replace : 1 << 30;
+    G.tol = tol;
+    G.perm = h.perm.get();
+    if (b_dev[g]) {
+      G.b = b[g];
+    } else {
+      LG_CUDA(cudaMemcpyAsync(ws.io.get(), b[g], sizeof(double) * n, cudaMemcpyHostToDevice, s));
+      G.b = ws.io.get();
+    }
+    // the output goes through io when it is host memory (b has been read by then)
+    G.out = x_dev[g] ? x[g] : ws.io.get();
+    G.bm = ws.bm.get();
+    G.x = ws.x.get();
+    G.r = ws.r.get();
+    G.ro = ws.ro.get();
+    G.p = ws.p.get();
+    G.q = ws.q.get();
+    G.res = res.get() + (size_t)3 * g;
+  }
+  DBuf<MGraph> dg(count, s);
+  LG_CUDA(cudaMemcpyAsync(dg.get(), hg.data(), sizeof(MGraph) * count, cudaMemcpyHostToDevice, s));
+  cudaEvent_t e0, e1;
+  LG_CUDA(cudaEventCreate(&e0));
+  LG_CUDA(cudaEventCreate(&e1));
+  LG_CUDA(cudaEventRecord(e0, s));
+  k_solve_many<<<count, kMT, 0, s>>>(dg.get());
+  LG_LAUNCH_CHECK();
+  LG_CUDA(cudaEventRecord(e1, s));
+  for (int g = 0; g < count; ++g) {
+    if (x_dev[g]) continue;
+    LG_CUDA(cudaMemcpyAsync(x[g], hs[g]->ws->io.get(), sizeof(double) * hs[g]->levels[0]->n,
+                            cudaMemcpyDeviceToHost, s));
+  }
+  std::vector<double> hres((size_t)3 * count);
+  LG_CUDA(cudaMemcpyAsync(hres.data(), res.get(), sizeof(double) * 3 * count, cudaMemcpyDeviceToHost, s));
+  LG_CUDA(cudaStreamSynchronize(s));
+  float ms = 0.f;
+  LG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (auto e : evs) cudaEventDestroy(e);
+  int first_bad = LG_OK;
+  for (int g = 0; g < count; ++g) {
+    const Hier& h = *hs[g];
+    const int it = (int)hres[3 * g], st = (int)hres[3 * g + 1];
+    if (st != LG_OK && first_bad == LG_OK) first_bad = st;
+    if (!infos) continue;
+    lg_info& inf = infos[g];
+    inf = lg_info{};
+    inf.status = st;
+    inf.iterations = it;
+    inf.relres = hres[3 * g + 2];
+    inf.solve_ms = ms;
+    inf.work_units = it * iteration_work(h);
+    inf.levels = (int)h.levels.size();
+    inf.setup_ms = h.setup_ms;
+    inf.nnz = h.nnz0;
+    double oc = 0.0;
+    for (auto& L : h.levels) oc += (double)(L->nnz + L->n);
+    inf.op_complexity = oc / (double)h.nnz0;
+  }
+  return first_bad;
+}
+
+}  // namespace lg

@@ -97,6 +97,7 @@ _SIGS = {
     "lg_profile": (C.c_int, [_P, _I32]),
     "lg_profile_read": (C.c_int, [_P, _I32, _P]),
     "lg_level_plan": (C.c_int, [_P, _I32, _P]),
+    "lg_solve_many": (C.c_int, [_I32, _P, _P, _P, _D, _P]),
     "lg_serve_options_default": (C.c_int, [_P]),
     "lg_serve_create": (C.c_int, [_P, _P]),
     "lg_serve_register": (C.c_int, [_P, _P]),
@@ -188,6 +189,32 @@ def lg_solve_batch(h, k, B, ldb, X, ldx, tol: float = 1e-8, check: bool = True):
     if check and st != OK:
         raise LGError(st, "lg_solve_batch")
     return list(infos)
+
+
+def lg_solve_many(hs, bs, xs, tol: float = 1e-8, check: bool = True):
+    """hs: handles; bs / xs: one vector per handle (numpy or torch CUDA)."""
+    count = len(hs)
+
+    def addr(p):
+        return p.value if isinstance(p, C.c_void_p) else p
+
+    H = (C.c_void_p * count)(*[addr(h) for h in hs])
+    B = (C.c_void_p * count)(*[addr(_ptr(b)) for b in bs])
+    X = (C.c_void_p * count)(*[addr(_ptr(x)) for x in xs])
+    infos = (Info * count)()
+    st = _load().lg_solve_many(int(count), H, B, X, float(tol), infos)
+    if check and st != OK:
+        raise LGError(st, "lg_solve_many")
+    return list(infos)
+
+
+def solve_many(hierarchies, bs, tol: float = 1e-8, check: bool = True):
+    """Solve one right-hand side on each of several hierarchies in one launch
+    (lg_solve_many). Returns (xs, infos)."""
+    bs = [np.ascontiguousarray(b, dtype=np.float64) for b in bs]
+    xs = [np.zeros(H.n) for H in hierarchies]
+    infos = lg_solve_many([H.h for H in hierarchies], bs, xs, tol, check=check)
+    return xs, infos
 
 
 def lg_set_precision(h, precision: int):

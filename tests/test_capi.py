@@ -48,6 +48,9 @@ def test_bad_arguments_rejected_without_gpu_work(lgmod):
     h = C.c_void_p()
     assert lib.lg_setup(0, None, None, None, None, C.byref(h)) == lgmod.ERR_INVALID
     assert lib.lg_solve(None, None, None, 1e-8, None) == lgmod.ERR_INVALID
+    assert lib.lg_solve_many(0, None, None, None, 1e-8, None) == lgmod.ERR_INVALID
+    one = (C.c_void_p * 1)(None)
+    assert lib.lg_solve_many(1, one, one, one, 1e-8, None) == lgmod.ERR_INVALID  # a NULL handle
 
 
 def test_oracle_and_cuda_path_share_no_code():
