@@ -24,13 +24,19 @@
 // through the read-only path.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "lg_hier.h"
 
 namespace lg {
 
-constexpr int kMT = 256;  // threads of the block that solves one graph
+// Threads of the block that solves one graph. A solve is a chain of
+// dependent passes, so a graph's time falls with the threads that share each
+// pass; 512 threads at 64 registers (two blocks per SM) measured fastest
+// against 256 and 1024.
+constexpr int kMT = 512;
 
 template <typename T>
 struct MVecs {
@@ -105,24 +111,38 @@ __device__ __forceinline__ void m_sum(double (&v)[K], MShared& sm) {
 #define LG_BLOCK_LOOP(i, n) for (int64_t i = threadIdx.x; i < (n); i += kMT)
 
 // Rows of class c, one aligned group of G lanes per row: s = the row's sum of
-// term.acc over its entries, then epi(row, term.fin(row, rv, s)).
+// term.acc over its entries, then epi(row, term.fin(row, rv, s)). A group
+// takes two rows per step, their loads interleaved, so that each lane has
+// two independent chains of gathers in flight.
 template <typename A, int G, class Term, class Epi>
 __device__ __forceinline__ void m_class(const MRows& R, int c, const Term& term, const Epi& epi) {
   const int64_t lo = R.off[c], cnt = R.off[c + 1] - lo;
   const int grp = threadIdx.x / G, gl = threadIdx.x & (G - 1);
   const unsigned mask = group_mask<G>();
-  for (int64_t base = 0; base < cnt; base += kMT / G) {
-    const int64_t q = base + grp;
-    A s = A(0), rv = A(0);
-    int64_t row = 0;
-    if (q < cnt) {
-      row = __ldg(&R.rows[lo + q]);
-      rv = term.row(row);
-      const int64_t e = __ldg(&R.ptr[row + 1]);
-      for (int64_t k = __ldg(&R.ptr[row]) + gl; k < e; k += G) s = term.acc(s, k, __ldg(&R.idx[k]), rv);
+  constexpr int kStep = kMT / G;
+  for (int64_t base = 0; base < cnt; base += 2 * kStep) {
+    const int64_t q0 = base + grp, q1 = q0 + kStep;
+    A s0 = A(0), s1 = A(0), rv0 = A(0), rv1 = A(0);
+    int64_t row0 = 0, row1 = 0, b0 = 0, e0 = 0, b1 = 0, e1 = 0;
+    if (q0 < cnt) row0 = __ldg(&R.rows[lo + q0]);
+    if (q1 < cnt) row1 = __ldg(&R.rows[lo + q1]);
+    if (q0 < cnt) { b0 = __ldg(&R.ptr[row0]) + gl; e0 = __ldg(&R.ptr[row0 + 1]); rv0 = term.row(row0); }
+    if (q1 < cnt) { b1 = __ldg(&R.ptr[row1]) + gl; e1 = __ldg(&R.ptr[row1 + 1]); rv1 = term.row(row1); }
+    for (;;) {
+      const bool v0 = b0 < e0, v1 = b1 < e1;
+      if (!v0 && !v1) break;
+      const int32_t j0 = v0 ? __ldg(&R.idx[b0]) : 0, j1 = v1 ? __ldg(&R.idx[b1]) : 0;
+      if (v0) s0 = term.acc(s0, b0, j0, rv0);
+      if (v1) s1 = term.acc(s1, b1, j1, rv1);
+      b0 += G;
+      b1 += G;
     }
-    if constexpr (G > 1) s = group_sum<G>(s, mask);
-    if (gl == 0 && q < cnt) epi(row, term.fin(row, rv, s));
+    if constexpr (G > 1) {
+      s0 = group_sum<G>(s0, mask);
+      s1 = group_sum<G>(s1, mask);
+    }
+    if (gl == 0 && q0 < cnt) epi(row0, term.fin(row0, rv0, s0));
+    if (gl == 0 && q1 < cnt) epi(row1, term.fin(row1, rv1, s1));
   }
 }
 
@@ -578,7 +598,7 @@ __device__ void m_pcg(const MGraph& G, MShared& sm) {
   }
 }
 
-__global__ void __launch_bounds__(kMT) k_solve_many(const MGraph* __restrict__ graphs) {
+__global__ void __launch_bounds__(kMT, 2) k_solve_many(const MGraph* __restrict__ graphs) {
   __shared__ MShared sm;
   const MGraph G = graphs[blockIdx.x];
   if (G.fp32) m_pcg<float>(G, sm);
@@ -651,6 +671,16 @@ static const MLevel* many_levels(Hier& h) {
   return d->levels.get();
 }
 
+// Pinned host staging of a call (descriptors, results and the host-memory
+// vectors), so that a call makes one copy each way however many graphs it
+// holds. Grown on demand; calls take it one at a time.
+struct PinnedStage {
+  std::mutex m;
+  unsigned char* p = nullptr;
+  size_t cap = 0;
+};
+static PinnedStage g_pin;
+
 int solve_many(int count, Hier* const* hs, const double* const* b, double* const* x, const bool* b_dev,
                const bool* x_dev, double tol, lg_info* infos) {
   cudaStream_t s = hs[0]->stream;
@@ -664,19 +694,51 @@ int solve_many(int count, Hier* const* hs, const double* const* b, double* const
     LG_CUDA(cudaEventRecord(e, hs[g]->stream));
     LG_CUDA(cudaStreamWaitEvent(s, e, 0));
   }
+  // staging layout: count descriptors, 3 results per graph, then one
+  // stretch of n doubles per graph with a host b or x (the kernel reads b
+  // there at the start and writes x there at the end)
+  std::vector<int64_t> off(count, -1);
+  size_t nvec = 0;
+  for (int g = 0; g < count; ++g) {
+    if (b_dev[g] && x_dev[g]) continue;
+    off[g] = (int64_t)nvec;
+    nvec += (size_t)hs[g]->levels[0]->n;
+  }
+  const size_t desc_bytes = sizeof(MGraph) * count, res_bytes = sizeof(double) * 3 * count;
+  const size_t total = desc_bytes + res_bytes + sizeof(double) * nvec;
+  std::lock_guard<std::mutex> lock(g_pin.m);
+  // on every exit, error paths included, the copies that read or write the
+  // pinned buffer finish before the next call may take it
+  struct SyncOnExit {
+    cudaStream_t s;
+    ~SyncOnExit() {
+      if (cudaStreamSynchronize(s) != cudaSuccess) cudaGetLastError();
+    }
+  } sync_on_exit{s};
+  if (g_pin.cap < total) {
+    if (g_pin.p) cudaFreeHost(g_pin.p);  // every earlier call has finished with it
+    g_pin.p = nullptr;
+    g_pin.cap = 0;
+    LG_CUDA(cudaMallocHost(&g_pin.p, total + total / 4));
+    g_pin.cap = total + total / 4;
+  }
+  DBuf<unsigned char> dst(total, s);
+  MGraph* hg = reinterpret_cast<MGraph*>(g_pin.p);
+  double* hres = reinterpret_cast<double*>(g_pin.p + desc_bytes);
+  double* hvec = reinterpret_cast<double*>(g_pin.p + desc_bytes + res_bytes);
+  double* dres = reinterpret_cast<double*>(dst.get() + desc_bytes);
+  double* dvec = reinterpret_cast<double*>(dst.get() + desc_bytes + res_bytes);
   // largest graphs first, so that the launch does not end on a long tail
   std::vector<int> order(count);
   for (int g = 0; g < count; ++g) order[g] = g;
   std::stable_sort(order.begin(), order.end(),
                    [&](int a, int c) { return hs[a]->nnz0 > hs[c]->nnz0; });
-  std::vector<MGraph> hg(count);
-  DBuf<double> res((size_t)3 * count, s);
   for (int q = 0; q < count; ++q) {
     const int g = order[q];
     Hier& h = *hs[g];
     Workspace& ws = *h.ws;
     const int64_t n = h.levels[0]->n;
-    MGraph& G = hg[q];
+    MGraph G;
     G.lv = many_levels(h);
     G.nlevels = (int)h.levels.size();
     G.first_agg = h.first_agg;
@@ -690,36 +752,31 @@ int solve_many(int count, Hier* const* hs, const double* const* b, double* const
     if (b_dev[g]) {
       G.b = b[g];
     } else {
-      LG_CUDA(cudaMemcpyAsync(ws.io.get(), b[g], sizeof(double) * n, cudaMemcpyHostToDevice, s));
-      G.b = ws.io.get();
+      std::memcpy(hvec + off[g], b[g], sizeof(double) * n);
+      G.b = dvec + off[g];
     }
-    // the output goes through io when it is host memory (b has been read by then)
-    G.out = x_dev[g] ? x[g] : ws.io.get();
+    G.out = x_dev[g] ? x[g] : dvec + off[g];
     G.bm = ws.bm.get();
     G.x = ws.x.get();
     G.r = ws.r.get();
     G.ro = ws.ro.get();
     G.p = ws.p.get();
     G.q = ws.q.get();
-    G.res = res.get() + (size_t)3 * g;
+    G.res = dres + (size_t)3 * g;
+    hg[q] = G;
   }
-  DBuf<MGraph> dg(count, s);
-  LG_CUDA(cudaMemcpyAsync(dg.get(), hg.data(), sizeof(MGraph) * count, cudaMemcpyHostToDevice, s));
+  LG_CUDA(cudaMemcpyAsync(dst.get(), g_pin.p, total, cudaMemcpyHostToDevice, s));
   cudaEvent_t e0, e1;
   LG_CUDA(cudaEventCreate(&e0));
   LG_CUDA(cudaEventCreate(&e1));
   LG_CUDA(cudaEventRecord(e0, s));
-  k_solve_many<<<count, kMT, 0, s>>>(dg.get());
+  k_solve_many<<<count, kMT, 0, s>>>(reinterpret_cast<const MGraph*>(dst.get()));
   LG_LAUNCH_CHECK();
   LG_CUDA(cudaEventRecord(e1, s));
-  for (int g = 0; g < count; ++g) {
-    if (x_dev[g]) continue;
-    LG_CUDA(cudaMemcpyAsync(x[g], hs[g]->ws->io.get(), sizeof(double) * hs[g]->levels[0]->n,
-                            cudaMemcpyDeviceToHost, s));
-  }
-  std::vector<double> hres((size_t)3 * count);
-  LG_CUDA(cudaMemcpyAsync(hres.data(), res.get(), sizeof(double) * 3 * count, cudaMemcpyDeviceToHost, s));
+  LG_CUDA(cudaMemcpyAsync(hres, dres, total - desc_bytes, cudaMemcpyDeviceToHost, s));
   LG_CUDA(cudaStreamSynchronize(s));
+  for (int g = 0; g < count; ++g)
+    if (!x_dev[g]) std::memcpy(x[g], hvec + off[g], sizeof(double) * hs[g]->levels[0]->n);
   float ms = 0.f;
   LG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
   cudaEventDestroy(e0);
