@@ -248,10 +248,10 @@ template <> __device__ __forceinline__ const float* m_ptc<float>(const MLevel& L
 // r_s = rin - L g, d_s = c1 g + c2 D^-1 r_s (when gn), x = [x +] g [+ d_s]
 // (when upd: mode 1 sets, mode 2 adds).
 template <typename T>
-__device__ void m_cheb(const MLevel& L, const T* g, const T* rin, T* rout, T* gn, T* x, int upd, int mode, int add_d,
-                       T c1, T c2, MShared& sm) {
+__device__ __noinline__ void m_cheb(const MLevel& L, const T* g, const T* rin, T* rout, T* gn, T* x, int upd,
+                                    int mode, int add_d, T c1, T c2, MShared& sm) {
   const T* dinv = m_dinv<T>(L);
-  m_pass<T>(L.op, m_lap<T>(L, g), [&](int64_t i, T s) {
+  m_pass<T>(L.op, m_lap<T>(L, g), [=](int64_t i, T s) {
     const T r = rin[i] - s;
     rout[i] = r;
     T d = T(0);
@@ -278,6 +278,29 @@ __device__ __forceinline__ void m_next_dir(const MGraph& G, int l, T** d0, const
   }
 }
 
+// Elimination restriction (P^T f)_c = f_c + sum_f (w_fc / d_f) f_f, and the
+// next level's d_0 when it smooths.
+template <typename T>
+__device__ __noinline__ void m_restrict_elim(const MLevel& L, const T* f, T* fc, T* d0n, const T* dinvn, T itn,
+                                             MShared& sm) {
+  const int32_t* cfine = L.cfine;
+  m_pass<T>(L.pt, MWGather<T>{m_ptc<T>(L), f}, [=](int64_t c, T s) {
+    const T v = f[__ldg(&cfine[c])] + s;
+    fc[c] = v;
+    if (d0n) d0n[c] = v * __ldg(&dinvn[c]) * itn;
+  }, sm);
+}
+
+// Aggregation restriction r_c = R r, and the next level's d_0 when it smooths.
+template <typename T>
+__device__ __noinline__ void m_restrict_agg(const MLevel& L, const T* r, T* fc, T* d0n, const T* dinvn, T itn,
+                                            MShared& sm) {
+  m_pass<T>(L.mem, MGather<T>{r}, [=](int64_t I, T s) {
+    fc[I] = s;
+    if (d0n) d0n[I] = s * __ldg(&dinvn[I]) * itn;
+  }, sm);
+}
+
 // Going down through level l: pre-smoothing and restriction (aggregation
 // level), restriction (elimination level). Leaves the coarse input in l+1.
 template <typename T>
@@ -289,12 +312,8 @@ __device__ void m_down(const MGraph& G, int l, MShared& sm) {
   const T* dinvn;
   T itn;
   m_next_dir<T>(G, l, &d0n, &dinvn, &itn);
-  if (L.kind == LG_LEVEL_ELIM) {  // (P^T f)_c = f_c + sum_f (w_fc / d_f) f_f
-    m_pass<T>(L.pt, MWGather<T>{m_ptc<T>(L), V.f}, [&](int64_t c, T s) {
-      const T v = V.f[__ldg(&L.cfine[c])] + s;
-      C.f[c] = v;
-      if (d0n) d0n[c] = v * __ldg(&dinvn[c]) * itn;
-    }, sm);
+  if (L.kind == LG_LEVEL_ELIM) {
+    m_restrict_elim<T>(L, V.f, C.f, d0n, dinvn, itn, sm);
     return;
   }
   const int deg = G.deg;
@@ -310,10 +329,7 @@ __device__ void m_down(const MGraph& G, int l, MShared& sm) {
   }
   // residual of the pre-smoothed x (for degree 1 also x = d_0)
   m_cheb<T>(L, g, rin, V.r, nullptr, V.x, deg == 1, 1, 0, T(0), T(0), sm);
-  m_pass<T>(L.mem, MGather<T>{V.r}, [&](int64_t I, T s) {  // r_c = R r
-    C.f[I] = s;
-    if (d0n) d0n[I] = s * __ldg(&dinvn[I]) * itn;
-  }, sm);
+  m_restrict_agg<T>(L, V.r, C.f, d0n, dinvn, itn, sm);
 }
 
 // Coming back up through level l: prolongation and post-smoothing.
@@ -376,10 +392,10 @@ __device__ void m_coarse(const MLevel& L) {
   __syncthreads();
 }
 
-// v = L x (the K-cycle's products).
+// v = L x (the K-cycle's products, and q = L p of the PCG).
 template <typename T>
-__device__ void m_apply(const MLevel& L, const T* x, T* v, MShared& sm) {
-  m_pass<T>(L.op, m_lap<T>(L, x), [&](int64_t i, T s) { v[i] = s; }, sm);
+__device__ __noinline__ void m_apply(const MLevel& L, const T* x, T* v, MShared& sm) {
+  m_pass<T>(L.op, m_lap<T>(L, x), [=](int64_t i, T s) { v[i] = s; }, sm);
 }
 
 // K-cycle, after the first body: c1 = x, v1 = L c1, t1 = c1.f / c1.v1,
@@ -484,11 +500,11 @@ __device__ void m_cycle(const MGraph& G, MShared& sm) {
 }
 
 // r = b_m - L x and ||r||^2.
-__device__ double m_true_res(const MGraph& G, MShared& sm) {
-  const MLevel& L0 = G.lv[0];
-  m_pass<double>(L0.op, MLap<double>{L0.w, G.x, L0.d}, [&](int64_t i, double s) { G.r[i] = G.bm[i] - s; }, sm);
+__device__ __noinline__ double m_true_res(const MLevel& L0, const double* bm, const double* x, double* r,
+                                          MShared& sm) {
+  m_pass<double>(L0.op, MLap<double>{L0.w, x, L0.d}, [=](int64_t i, double s) { r[i] = bm[i] - s; }, sm);
   double acc[1] = {0.0};
-  LG_BLOCK_LOOP(i, L0.n) acc[0] += G.r[i] * G.r[i];
+  LG_BLOCK_LOOP(i, L0.n) acc[0] += r[i] * r[i];
   m_sum<1>(acc, sm);
   return acc[0];
 }
@@ -550,7 +566,7 @@ __device__ void m_pcg(const MGraph& G, MShared& sm) {
       LG_BLOCK_LOOP(i, n) G.p[i] = ((double)V0.x[i] - m) + beta * G.p[i];
       __syncthreads();
       // q = L p, alpha
-      m_pass<double>(L0.op, MLap<double>{L0.w, G.p, L0.d}, [&](int64_t i, double s) { G.q[i] = s; }, sm);
+      m_apply<double>(L0, G.p, G.q, sm);
       acc[0] = 0.0;
       LG_BLOCK_LOOP(i, n) acc[0] += G.p[i] * G.q[i];
       m_sum<1>(acc, sm);
@@ -572,7 +588,7 @@ __device__ void m_pcg(const MGraph& G, MShared& sm) {
       rr = acc[0];
       ++it;
       if (it % G.every == 0 || rr <= tol2bb) {
-        rr = m_true_res(G, sm);
+        rr = m_true_res(L0, G.bm, G.x, G.r, sm);
         if (rr <= tol2bb) done = 1;
       }
       if (done || brk) break;
@@ -582,7 +598,7 @@ __device__ void m_pcg(const MGraph& G, MShared& sm) {
   double rel = 0.0;
   if (bb > 0.0) {
     status = done ? LG_OK : brk ? LG_ERR_BREAKDOWN : LG_ERR_NOT_CONVERGED;
-    if (status != LG_OK) rr = m_true_res(G, sm);
+    if (status != LG_OK) rr = m_true_res(L0, G.bm, G.x, G.r, sm);
     rel = sqrt(rr / bb);
   }
   // x with its mean removed, in the caller's numbering
