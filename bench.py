@@ -38,6 +38,7 @@ UNIT = "nnz/s"
 TOL = 1e-8
 L2_BYTES = 129 * 2 ** 20
 FALLBACK_HBM_GBS = 6800.0
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e nominal, for the fraction of nominal
 
 
 
@@ -420,23 +421,32 @@ def serve_leg(lg, inputs, args):
     burst = requests(max(100, args.serve_requests // 4))
     st_b, span_b, rhs_b, fail_b = run(burst, None)
     sat_rps = len(burst) / span_b
-    rate = args.serve_load * sat_rps
-    st, span, rhs, failed = run(requests(args.serve_requests), rate)
+    loads = {}
+    for load in sorted({0.5, args.serve_load, 0.95}):
+        rate = load * sat_rps
+        st, span, rhs, failed = run(requests(args.serve_requests), rate)
+        loads[load] = (rate, st, span, rhs, failed)
     for H in hs:
         H.close()
+    rate, st, span, rhs, failed = loads[args.serve_load]
     return {
         "p50_ms": st.p50_ms, "p99_ms": st.p99_ms, "mean_ms": st.mean_ms, "max_ms": st.max_ms,
         "solves_per_s": rhs / span, "requests_per_s": args.serve_requests / span,
         "offered_rps": rate, "saturation_rps": sat_rps, "saturation_solves_per_s": rhs_b / span_b,
         "saturation_p50_ms": st_b.p50_ms, "saturation_p99_ms": st_b.p99_ms,
-        "completed": int(st.completed), "failed": int(st.failed + failed + st_b.failed + fail_b),
+        "by_load": {f"{ld:g}": {"offered_rps": v[0], "p50_ms": v[1].p50_ms, "p99_ms": v[1].p99_ms,
+                                "solves_per_s": v[3] / v[2], "failed": int(v[1].failed + v[4])}
+                    for ld, v in loads.items()},
+        "completed": int(st.completed),
+        "failed": int(sum(v[1].failed + v[4] for v in loads.values()) + st_b.failed + fail_b),
         "requests": args.serve_requests, "graphs": len(graphs),
         "vertices_resident": int(sum(g.n for g in graphs)), "nnz_resident": int(sum(g.nnz for g in graphs)),
         "resident_bytes": st.resident_bytes,
         "config": f"{len(graphs)} resident graphs, n log-uniform in [1000, {args.serve_nmax}], type uniform over "
                   f"2D grid / 3D grid / Chung-Lu 2.1 / R-MAT ef16; k uniform in 1..8; tol 1e-8; FP32 hierarchy; "
-                  f"8 slots; HBM budget 120 GB; Poisson arrivals at {args.serve_load} x the burst saturation "
-                  f"rate; latency = submission to completion with host B and X",
+                  f"8 slots; HBM budget 120 GB; Poisson arrivals at 0.5, {args.serve_load} (headline) and 0.95 x "
+                  f"the burst saturation rate, {args.serve_requests} requests each; latency = submission to "
+                  f"completion with host B and X",
     }
 
 
@@ -540,8 +550,9 @@ def main():
         opts = lg.options(stream=stream.cuda_stream)
 
         def per_level(h, nlev):
+            """Per level: the Laplacian passes, then the W = L P passes (profile slots nlev + l)."""
             out = []
-            for l in range(nlev):
+            for l in range(2 * nlev):
                 p = lg.lg_profile_read(h, l)
                 out.append((p.total_ms, p.bytes, p.launches))
             return out
@@ -605,6 +616,18 @@ def main():
         lg.lg_destroy(h2)
         lg.lg_destroy(h)
 
+        # the same solves with post-smoothing from f - L x instead of the W = L P pass
+        h0 = lg.lg_setup(g.n, rp, cl, w, lg.options(stream=stream.cuda_stream, lp_residual=0))
+        direct = {}
+        for tag, prec, x in (("fp64", lg.FP64, x64), ("fp32", lg.FP32_HIER, x32)):
+            lg.lg_set_precision(h0, prec)
+            ms = []
+            for _ in range(3):
+                flush.fill_(2.0)
+                ms.append(lg.lg_solve(h0, bd, x, TOL).solve_ms)
+            direct[tag] = sorted(ms)[1]
+        lg.lg_destroy(h0)
+
         # the other two workloads the metric names, after the timed region
         multi = None if args.no_multi_rhs else multi_rhs_leg(lg, inputs, torch, dev, args.multi_rhs_k)
         kcyc = None if args.no_kcycle else kcycle_leg(lg, inputs, torch, dev, g, b)
@@ -628,10 +651,10 @@ def main():
     value = world * nnz / (solve64_ms * 1e-3)
 
     # roofline of the dominant kernel: the operator row pass of the level with the most device time
-    nlev = len(recs[0][3])
+    nlev = len(recs[0][3]) // 2
     tot = [[0.0, 0.0, 0] for _ in range(nlev)]
     for r in recs:
-        for l, (ms, by, la) in enumerate(r[3]):
+        for l, (ms, by, la) in enumerate(r[3][:nlev]):
             tot[l][0] += ms
             tot[l][1] += by
             tot[l][2] += la
@@ -640,8 +663,9 @@ def main():
     peak, peak_kind = measured_peak()
     achieved = d_bytes / (d_ms * 1e-3) / 1e9 if d_ms > 0 else 0.0
     traffic, _ = ncu_traffic(args.workload)
-    all_ms = sum(t[0] for t in tot)
-    all_bytes = sum(t[1] for t in tot)
+    wpass = [[sum(r[3][nlev + l][q] for r in recs) for q in range(3)] for l in range(nlev)]
+    all_ms = sum(t[0] for t in tot) + sum(t[0] for t in wpass)
+    all_bytes = sum(t[1] for t in tot) + sum(t[1] for t in wpass)
     i64, i32 = recs[-1][1], recs[-1][2]
     # per-level operator-pass table, both precisions (ms per solve, GB/s)
     levels = []
@@ -654,6 +678,11 @@ def main():
             row[f"{tag}_ms_per_solve"] = ms
             row[f"{tag}_launches_per_solve"] = la
             row[f"{tag}_gbs"] = by / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+            wms = sum(r[idx][nlev + l][0] for r in recs) / len(recs)
+            wby = sum(r[idx][nlev + l][1] for r in recs) / len(recs)
+            if wms > 0:
+                row[f"{tag}_w_pass_ms_per_solve"] = wms
+                row[f"{tag}_w_pass_gbs"] = wby / (wms * 1e-3) / 1e9
         levels.append(row)
 
     if rank != 0:
@@ -673,6 +702,10 @@ def main():
         "iterations": i64.iterations, "relres": i64.relres, "levels": i64.levels,
         "op_complexity": recs[-1][0].op_complexity,
         "setup_inclusive_nnz_per_s": world * nnz / ((setup_ms + solve64_ms) * 1e-3),
+        "lp_residual": {"fp64_solve_ms": solve64_ms, "fp64_solve_ms_without": direct["fp64"],
+                        "fp32_solve_ms": solve32_ms, "fp32_solve_ms_without": direct["fp32"],
+                        "note": "post-smoothing started by one pass over W = L P (default) against a pass "
+                                "over L from f - L x (lp_residual = 0, median of 3 solves)"},
         "fp32_hier": {"value": world * nnz / (solve32_ms * 1e-3), "solve_ms": solve32_ms,
                       "iterations": i32.iterations, "relres": i32.relres,
                       "speedup_vs_fp64": solve64_ms / solve32_ms},
@@ -684,6 +717,10 @@ def main():
                 "note": "lg_solve with pinned host b and x: H2D of b, solve, D2H of x inside the timed call"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
+                     "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
+                     "whole_solve_frac": (all_bytes / len(recs)) / (solve64_ms * 1e-3) / 1e9 / peak,
+                     "whole_solve_note": "algorithmic bytes of every operator pass of one FP64 solve (per-pass "
+                                         "events) over the event-free FP64 solve time; vector kernels not counted",
                      "kernel": f"k_rows<double, LapTerm, *> operator passes of level {dom} "
                                f"(n={recs[-1][0].nnz}) in the timed FP64 solves".replace(
                                    f"(n={recs[-1][0].nnz})", f"({tot[dom][2] // len(recs)} per solve)"),

@@ -110,7 +110,13 @@ typedef struct {
   int32_t elim_rounds;      /* 1 (Section 3.4 finds one round enough): up to this many elimination
                                levels in a row before each aggregation, each while more than
                                elim_min_frac of the vertices go; more rounds serve chain-like graphs */
-  int32_t reserved;
+  int32_t lp_residual;      /* 1: each aggregation level of at least 4096 vertices also stores
+                               W = L P off the own aggregate
+                               (n x n_c, row i: sum of w_ij over the neighbours j in aggregate a),
+                               and lg_solve's cycle starts post-smoothing (Section 3.6) from
+                               r_0 = r_pre - L P x_c, r_pre the pre-smoothing residual, which
+                               equals f - L (x + P x_c) and gathers from the short coarse vector;
+                               the prolongation x += P x_c joins that pass. 0: r_0 = f - L x. */
 } lg_options;
 
 /* Result of a setup or a solve. */
@@ -181,6 +187,10 @@ int lg_solve(lg_handle h, const double* b, double* x, double tol, lg_info* info)
 int lg_solve_batch(lg_handle h, int32_t k, const double* B, int64_t ldb, double* X, int64_t ldx,
                    double tol, lg_info* infos);
 
+/* Stored entries of level l's W = L P operator (see lp_residual); 0 when the
+ * level has none (elimination and coarsest levels, or lp_residual = 0). */
+int lg_level_lp_nnz(lg_handle h, int32_t l, int64_t* nnz);
+
 /* Set the V-cycle precision (LG_FP64 or LG_FP32_HIER) used by later solves. */
 int lg_set_precision(lg_handle h, int32_t precision);
 
@@ -249,13 +259,15 @@ uint64_t lg_kernel_launches(void);
 
 /* Per-kernel timing of the operator passes: the row passes that apply a
  * level's Laplacian (the PCG product and true residual on level 0, the
- * Chebyshev steps of every aggregation level). When enabled on a handle,
- * each such launch of lg_solve is bracketed by CUDA events on the handle's
- * stream. lg_profile_read returns, for one level (or every level with
- * level = -1), the launches, their summed device time and their summed
- * algorithmic bytes (compulsory traffic: the CSR arrays once, the gathered
- * vector once, each epilogue vector stream once). lg_profile also clears the
- * counters. */
+ * Chebyshev steps of every aggregation level) and, counted apart, the passes
+ * over W = L P that start post-smoothing (see lp_residual). When enabled on a
+ * handle, each such launch of lg_solve is bracketed by CUDA events on the
+ * handle's stream. lg_profile_read returns, for the Laplacian passes of one
+ * level l (level = l), the W passes of level l (level = nlevels + l), or all
+ * of them (level = -1), the launches, their summed device time and their
+ * summed algorithmic bytes (compulsory traffic: the CSR arrays once, the
+ * gathered vector once, each epilogue vector stream once). lg_profile also
+ * clears the counters. */
 typedef struct {
   double total_ms;         /* summed event-measured device time of those launches */
   double bytes;            /* summed algorithmic bytes */

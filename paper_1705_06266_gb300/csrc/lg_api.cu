@@ -121,6 +121,7 @@ int lg_options_default(lg_options* o) {
   o->reorder = 1;
   o->kcycle = 0;
   o->elim_rounds = 1;
+  o->lp_residual = 1;
   return LG_OK;
 }
 
@@ -380,6 +381,14 @@ int lg_profile(lg_handle hh, int32_t enable) {
   LG_API_END
 }
 
+int lg_level_lp_nnz(lg_handle hh, int32_t l, int64_t* nnz) {
+  if (!hh || !nnz) return LG_ERR_INVALID;
+  lg::Hier& h = *H(hh);
+  if (l < 0 || l >= (int32_t)h.levels.size()) return LG_ERR_INVALID;
+  *nnz = h.levels[l]->lp_nnz;
+  return LG_OK;
+}
+
 int lg_level_plan(lg_handle hh, int32_t l, int64_t out[6]) {
   if (!hh || !out) return LG_ERR_INVALID;
   lg::Hier& h = *H(hh);
@@ -398,7 +407,7 @@ int lg_profile_read(lg_handle hh, int32_t level, lg_kernel_profile* out) {
   if (!hh || !out) return LG_ERR_INVALID;
   LG_API_BEGIN
   lg::Hier& h = *H(hh);
-  if (level < -1 || level >= (int32_t)h.levels.size()) return LG_ERR_INVALID;
+  if (level < -1 || level >= 2 * (int32_t)h.levels.size()) return LG_ERR_INVALID;
   LG_CUDA(cudaStreamSynchronize(h.stream));
   lg::Prof& p = h.ws->prof;
   p.collect();

@@ -992,7 +992,7 @@ static int msolve(Hier& h, Workspace& ws, int k, const double* B, double* X, dou
       inf.iterations = sc[mBB] == 0.0 ? 0 : (sc[mDone] != 0.0 ? (int)sc[mConv] : it);
       inf.relres = sc[mBB] > 0.0 ? std::sqrt(sc[mRR] / sc[mBB]) : 0.0;
       inf.solve_ms = ms;
-      inf.work_units = inf.iterations * iteration_work(h);
+      inf.work_units = inf.iterations * iteration_work(h, false);
       inf.levels = (int)h.levels.size();
       inf.setup_ms = h.setup_ms;
       inf.nnz = h.nnz0;

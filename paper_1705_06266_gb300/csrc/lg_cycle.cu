@@ -152,6 +152,76 @@ struct EpiElimRestrict {
   __device__ void finish(const double*) const {}
 };
 
+// (L P x_c)_i over W = L P off the own aggregate (Level::lp):
+// sum_a W_ia (x_c[agg_i] - x_c[a]). FP32 in that difference form, as LapTerm;
+// FP64 as d^W_i x_c[agg_i] - sum_a W_ia x_c[a], d^W the row sums of W. The
+// gathered x_c is the coarse level's, short enough to stay in L1.
+template <typename T>
+struct LpTerm;
+
+template <>
+struct LpTerm<float> {
+  const float* __restrict__ w;
+  const float* __restrict__ xc;
+  const int32_t* __restrict__ agg;
+  __device__ __forceinline__ float row(int64_t i) const { return ld_keep(&xc[__ldg(&agg[i])]); }
+  __device__ __forceinline__ float acc(float s, int64_t k, int32_t a, float xa) const {
+    return fmaf(ld_stream(&w[k]), xa - ld_keep(&xc[a]), s);
+  }
+  __device__ __forceinline__ float finish(int64_t, float, float s) const { return s; }
+};
+
+template <>
+struct LpTerm<double> {
+  const double* __restrict__ w;
+  const double* __restrict__ xc;
+  const int32_t* __restrict__ agg;
+  const double* __restrict__ d;
+  __device__ __forceinline__ double row(int64_t) const { return 0.0; }
+  __device__ __forceinline__ double acc(double s, int64_t k, int32_t a, double) const {
+    return fma(ld_stream(&w[k]), ld_keep(&xc[a]), s);
+  }
+  __device__ __forceinline__ double finish(int64_t i, double, double s) const {
+    return fma(__ldg(&d[i]), ld_keep(&xc[__ldg(&agg[i])]), -s);
+  }
+};
+
+template <typename T>
+static LpTerm<T> lp_term(const OpView<T>& w, const T* xc, const int32_t* agg);
+template <>
+LpTerm<float> lp_term<float>(const OpView<float>& w, const float* xc, const int32_t* agg) {
+  return LpTerm<float>{w.w, xc, agg};
+}
+template <>
+LpTerm<double> lp_term<double>(const OpView<double>& w, const double* xc, const int32_t* agg) {
+  return LpTerm<double>{w.w, xc, agg, w.d};
+}
+
+// Start of post-smoothing after the coarse correction (Section 3.6), in one
+// pass over W given s = (L P x_c)_i: x += P x_c; r_0 = r_pre - s (r_pre, the
+// pre-smoothing residual f - L x, is still in r); d_0 = D^-1 r_0 / theta.
+template <typename T>
+struct EpiPost {
+  T* r;
+  T* x;
+  const T* xc;
+  const int32_t* agg;
+  const T* dinv;
+  T* d0;
+  T inv_theta;
+  struct Pre {
+    T r, x, xa, dv;
+  };
+  __device__ __forceinline__ Pre pre(int64_t i) const { return Pre{r[i], x[i], xc[agg[i]], dinv[i]}; }
+  __device__ __forceinline__ void operator()(int64_t i, T s, const Pre& p, double*) const {
+    const T r0 = p.r - s;
+    r[i] = r0;
+    d0[i] = inv_theta * p.dv * r0;
+    x[i] = p.x + p.xa;
+  }
+  __device__ void finish(const double*) const {}
+};
+
 // Algorithmic bytes of one row pass over an operator with elements of size t:
 // the CSR arrays once, the gathered vector once, and `streams` further
 // length-n vector streams (reads or writes) of the epilogue.
@@ -432,9 +502,17 @@ static void cycle_level(Hier& h, Workspace& ws, int l, cudaStream_t s, const ZSu
   launch_rows<T, 0>(L.nc, L.mem_ptr.get(), L.mem.get(), GatherTerm<T>{V.r.get()}, sc.mem.bind(L.mem_plan.plan),
                     EpiRestrict<T>{C.f.get(), d0n, dinvn, itn}, s);
   cycle_level<T>(h, ws, l + 1, s);
-  k_agg_prolong<T><<<vblocks(n), kVT, 0, s>>>(n, L.agg.get(), C.x.get(), V.x.get());
-  LG_LAUNCH_CHECK();
-  {  // post-smoothing from x: r_0 = f - L x, d_0 = D^-1 r_0 / theta
+  if (L.lp_nnz > 0) {
+    // x += P x_c, r_0 = r_pre - L P x_c, d_0 = D^-1 r_0 / theta: one pass over W
+    OpView<T> lp = L.lp<T>();
+    lp.plan = sc.lp.bind(lp.plan);
+    op_pass<T, 0>(ws, (int)h.levels.size() + l, lp, lp_term<T>(lp, C.x.get(), L.agg.get()),
+                  EpiPost<T>{V.r.get(), V.x.get(), C.x.get(), L.agg.get(), op.dinv, V.dA.get(), (T)ch.inv_theta}, 7,
+                  s);
+  } else {
+    k_agg_prolong<T><<<vblocks(n), kVT, 0, s>>>(n, L.agg.get(), C.x.get(), V.x.get());
+    LG_LAUNCH_CHECK();
+    // post-smoothing from x: r_0 = f - L x, d_0 = D^-1 r_0 / theta
     const EpiCheb<T> e{V.x.get(), V.f.get(), V.r.get(), op.dinv, V.dA.get(), nullptr, 0, 0, T(0), (T)ch.inv_theta};
     op_pass<T, 0>(ws, l, op, LapTerm<T>{op.w, V.x.get(), op.d}, e, cheb_streams(e), s);
   }
@@ -743,6 +821,7 @@ std::unique_ptr<Workspace> make_workspace(Hier& h, int k, cudaStream_t s) {
     max_grid = std::max<int64_t>(max_grid, lv.plan.plan.grid());
     ws->scratch[l].op.make(lv.plan.plan, k, s, c);
     if (lv.kind == LG_LEVEL_AGG) ws->scratch[l].mem.make(lv.mem_plan.plan, k, s, c);
+    if (lv.lp_nnz > 0) ws->scratch[l].lp.make(lv.lp_plan.plan, k, s, c);
     if (lv.kind == LG_LEVEL_ELIM) ws->scratch[l].pt.make(lv.pt_plan.plan, k, s, c);
   }
   const size_t n0 = (size_t)h.levels[0]->n * k;
@@ -857,25 +936,27 @@ static cudaGraphExec_t pcg_graph(Hier& h, Workspace& ws, cudaStream_t s) {
 // flops / flops of a finest residual, approximated by operator nonzeros). An
 // operator application on level l costs A_l = nnz_off + n. Per iteration:
 // A_0 for q = L p, plus the cycle from level 0, where an aggregation body costs
-// 2 deg A_l (pre- and post-smoothing passes) + 2 n_l (restriction,
-// prolongation) + its coarse solve; a K-cycle level two bodies + 2 A_l; an
-// elimination level 2 nnz_F + n_c + n_l (restriction and prolongation through
-// the F rows' entries) + its coarse solve; the coarsest level n_c^2.
-static double solve_work(const Hier& h, int l) {
+// 2 deg A_l (pre- and post-smoothing passes; with W = L P in use, one of them
+// costs nnz(W) + n_l instead) + 2 n_l (restriction, prolongation) + its
+// coarse solve; a K-cycle level two bodies + 2 A_l; an elimination level
+// 2 nnz_F + n_c + n_l (restriction and prolongation through the F rows'
+// entries) + its coarse solve; the coarsest level n_c^2.
+static double solve_work(const Hier& h, int l, bool lp) {
   const Level& L = *h.levels[l];
   const double A = (double)(L.nnz + L.n);
   if (L.kind == LG_LEVEL_COARSEST) return (double)L.n * (double)L.n;
   if (L.kind == LG_LEVEL_ELIM)
-    return 2.0 * (double)L.pt_f.size() + (double)L.nc + (double)L.n + solve_work(h, l + 1);
-  const double body = 2.0 * h.opts.cheb_degree * A + 2.0 * (double)L.n + solve_work(h, l + 1);
+    return 2.0 * (double)L.pt_f.size() + (double)L.nc + (double)L.n + solve_work(h, l + 1, lp);
+  double body = 2.0 * h.opts.cheb_degree * A + 2.0 * (double)L.n + solve_work(h, l + 1, lp);
+  if (lp && L.lp_nnz > 0) body += (double)(L.lp_nnz + L.n) - A;
   if (h.opts.kcycle && l != h.first_agg) return 2.0 * body + 2.0 * A;
   return body;
 }
 
-double iteration_work(const Hier& h) {
+double iteration_work(const Hier& h, bool lp) {
   const Level& L0 = *h.levels[0];
   const double A0 = (double)(L0.nnz + L0.n);
-  return (A0 + solve_work(h, 0)) / A0;
+  return (A0 + solve_work(h, 0, lp)) / A0;
 }
 
 int pcg_solve(Hier& h, Workspace& ws, const double* b, double* x, double tol, int precision, cudaStream_t s,
@@ -943,7 +1024,7 @@ int pcg_solve(Hier& h, Workspace& ws, const double* b, double* x, double tol, in
     info->iterations = it;
     info->relres = rel;
     info->solve_ms = ms;
-    info->work_units = it * iteration_work(h);
+    info->work_units = it * iteration_work(h, true);
     info->levels = (int)h.levels.size();
     info->setup_ms = h.setup_ms;
     info->nnz = h.nnz0;

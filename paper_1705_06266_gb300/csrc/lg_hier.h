@@ -7,7 +7,9 @@
 //    row sum of w (Section 2.1), so L 1 = 0 holds in the difference form.
 //  - AGG level: agg[n] (vertex -> aggregate) and the member CSR of R
 //    (mem_ptr[nc+1], mem[n], members in ascending vertex order) for a
-//    deterministic restriction r_c = R r.
+//    deterministic restriction r_c = R r; with lp_residual also W = L P off
+//    the own aggregate (lp_ptr[n+1], lp_col = aggregate ids, lp_w, and the
+//    row sums lp_d), so that (L P x_c)_i = sum_a W_ia (x_c[agg_i] - x_c[a]).
 //  - ELIM level: cmap[n] (kept vertex -> coarse id, eliminated -> -1),
 //    cfine[nc] (coarse id -> kept vertex) and the transpose of the
 //    elimination prolongation's F rows per kept vertex (pt_ptr, pt_f,
@@ -46,6 +48,12 @@ struct Level {
   DBuf<int32_t> agg, mem;
   DBuf<int64_t> mem_ptr;
   RowPlanStore mem_plan;
+  int64_t lp_nnz = 0;  // W = L P (0: not built)
+  DBuf<int64_t> lp_ptr;
+  DBuf<int32_t> lp_col;
+  DBuf<double> lp_w, lp_d;
+  DBuf<float> lp_w32;
+  RowPlanStore lp_plan;
   // elimination
   int64_t nf = 0;
   DBuf<int32_t> cmap, cfine, pt_f;
@@ -57,6 +65,7 @@ struct Level {
   DBuf<double> pinv;
 
   template <typename T> OpView<T> op() const;
+  template <typename T> OpView<T> lp() const;
 };
 
 template <> inline OpView<double> Level::op<double>() const {
@@ -64,6 +73,13 @@ template <> inline OpView<double> Level::op<double>() const {
 }
 template <> inline OpView<float> Level::op<float>() const {
   return OpView<float>{n, nnz, rowptr.get(), col.get(), w32.get(), dinv32.get(), d.get(), plan.plan};
+}
+// W = L P as an operator view: its rows' entries, and lp_d in place of d.
+template <> inline OpView<double> Level::lp<double>() const {
+  return OpView<double>{n, lp_nnz, lp_ptr.get(), lp_col.get(), lp_w.get(), dinv.get(), lp_d.get(), lp_plan.plan};
+}
+template <> inline OpView<float> Level::lp<float>() const {
+  return OpView<float>{n, lp_nnz, lp_ptr.get(), lp_col.get(), lp_w32.get(), dinv32.get(), lp_d.get(), lp_plan.plan};
 }
 
 // Chebyshev constants of one aggregation level (Section 3.6): the interval
@@ -102,7 +118,7 @@ struct PlanScratch {
 };
 
 struct LevelScratch {
-  PlanScratch op, mem, pt;
+  PlanScratch op, mem, pt, lp;
 };
 
 struct Hier;
@@ -193,8 +209,11 @@ void vcycle_apply(Hier& h, Workspace& ws, const double* f, double* x, int precis
 int pcg_solve(Hier& h, Workspace& ws, const double* b, double* x, double tol, int precision,
               cudaStream_t s, lg_info* info);
 void vcycle_apply_batch(Hier& h, Workspace& ws, int k, const double* F, double* X, int precision, cudaStream_t s);
-// Work of one PCG iteration in finest-residual units (lg_info.work_units / iterations).
-double iteration_work(const Hier& h);
+// Work of one PCG iteration in finest-residual units (lg_info.work_units /
+// iterations); lp: whether the cycle runs the W = L P post-smoothing pass
+// (lg_solve's cycle does where W was built; the multi-column and packed
+// cycles do not).
+double iteration_work(const Hier& h, bool lp);
 int pcg_solve_batch(Hier& h, Workspace& ws, int k, const double* B, double* X, double tol, int precision,
                     cudaStream_t s, lg_info* infos);
 

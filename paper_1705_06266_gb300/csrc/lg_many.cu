@@ -810,7 +810,7 @@ int solve_many(int count, Hier* const* hs, const double* const* b, double* const
     inf.iterations = it;
     inf.relres = hres[3 * g + 2];
     inf.solve_ms = ms;
-    inf.work_units = it * iteration_work(h);
+    inf.work_units = it * iteration_work(h, false);
     inf.levels = (int)h.levels.size();
     inf.setup_ms = h.setup_ms;
     inf.nnz = h.nnz0;

@@ -623,6 +623,31 @@ struct EGal {
   }
 };
 
+// Entries of W = L P off the own aggregate: (i << cbits | agg_j, w_ij) for
+// every stored (i, j) with agg_j != agg_i, in row order. Summed over equal
+// keys they give W_ia = sum of w_ij over i's neighbours j in aggregate a, so
+// that (L P x_c)_i = sum_a W_ia (x_c[agg_i] - x_c[a]): P's columns are the
+// aggregates' indicator vectors and L's rows sum to zero.
+struct ELp {
+  const int32_t* __restrict__ col;
+  const double* __restrict__ w;
+  const int32_t* __restrict__ agg;
+  int cbits;
+  uint64_t* __restrict__ keys;
+  uint64_t* __restrict__ vals;
+  struct Row {
+    int32_t ai;
+  };
+  __device__ Row row(int64_t i) const { return Row{agg[i]}; }
+  __device__ bool special(const Row&) const { return false; }
+  __device__ void emit_special(const Row&, int64_t, int64_t, int64_t, int64_t) const {}
+  __device__ bool take(const Row& r, int64_t, int64_t k) const { return agg[col[k]] != r.ai; }
+  __device__ void put(const Row&, int64_t i, int64_t k, int64_t p) const {
+    keys[p] = ((uint64_t)i << cbits) | (uint64_t)agg[col[k]];
+    vals[p] = (uint64_t)__double_as_longlong(w[k]);
+  }
+};
+
 __global__ void k_iota_u64(int64_t n, const int32_t* __restrict__ agg, uint64_t* __restrict__ keys,
                            uint64_t* __restrict__ vals) {
   LG_GRID_STRIDE(i, n) {
@@ -1044,8 +1069,12 @@ static std::unique_ptr<Level> eliminate(Level& L, const uint8_t* is_f, int64_t n
   return C;
 }
 
-// Aggregation stage products: member CSR of R and the Galerkin level.
-static std::unique_ptr<Level> galerkin(Level& L, cudaStream_t s, int64_t* counter) {
+// Smallest aggregation level that gets W = L P (see galerkin).
+constexpr int64_t kLpMinRows = 4096;
+
+// Aggregation stage products: member CSR of R, the Galerkin level, and
+// W = L P when `lp` (levels of at least kLpMinRows vertices).
+static std::unique_ptr<Level> galerkin(Level& L, bool lp, cudaStream_t s, int64_t* counter) {
   const int64_t n = L.n, nc = L.nc;
   // member lists, ascending vertex order inside each aggregate (stable sort by aggregate)
   {
@@ -1066,17 +1095,43 @@ static std::unique_ptr<Level> galerkin(Level& L, cudaStream_t s, int64_t* counte
   exclusive_scan(cnt.get(), cnt.get(), n, s);
   const int64_t nent = read_i64(cnt.get() + n, s);
   const int cbits = bits_for(nc);
-  DBuf<uint64_t> keys(nent, s), vals(nent, s);
-  emit_rows(EGal{L.col.get(), L.w.get(), L.agg.get(), cbits, keys.get(), vals.get()}, L.rowptr.get(), cnt.get(),
-            bins_of(L.plan.plan, n), s);
-  CsrOut out;
-  accumulate_csr(keys, vals, nent, nc, cbits, out, s, counter);
   auto C = std::make_unique<Level>();
-  C->n = nc;
-  C->nnz = out.nnz;
-  C->rowptr = std::move(out.rowptr);
-  C->col = std::move(out.col);
-  C->w = std::move(out.w);
+  {
+    DBuf<uint64_t> keys(nent, s), vals(nent, s);
+    emit_rows(EGal{L.col.get(), L.w.get(), L.agg.get(), cbits, keys.get(), vals.get()}, L.rowptr.get(), cnt.get(),
+              bins_of(L.plan.plan, n), s);
+    CsrOut out;
+    accumulate_csr(keys, vals, nent, nc, cbits, out, s, counter);
+    C->n = nc;
+    C->nnz = out.nnz;
+    C->rowptr = std::move(out.rowptr);
+    C->col = std::move(out.col);
+    C->w = std::move(out.w);
+  }
+  // W = L P: the same entries keyed by fine row (accumulate_csr sorts them),
+  // once the Galerkin product's scratch is back. Not for levels of a few
+  // thousand vertices, whose passes are launch-bound: W saves nothing there.
+  if (lp && n >= kLpMinRows) {
+    DBuf<uint64_t> lkeys(nent, s), lvals(nent, s);
+    emit_rows(ELp{L.col.get(), L.w.get(), L.agg.get(), cbits, lkeys.get(), lvals.get()}, L.rowptr.get(), cnt.get(),
+              bins_of(L.plan.plan, n), s);
+    CsrOut lo;
+    accumulate_csr(lkeys, lvals, nent, n, cbits, lo, s, counter);
+    L.lp_nnz = lo.nnz;
+    L.lp_ptr = std::move(lo.rowptr);
+    L.lp_col = std::move(lo.col);
+    L.lp_w = std::move(lo.w);
+    build_row_plan(L.lp_plan, n, L.lp_nnz, L.lp_ptr.get(), s, counter);
+    L.lp_d.alloc(n, s, counter);
+    DBuf<double> unused(n, s);
+    launch_rows<double, 0>(n, L.lp_ptr.get(), L.lp_col.get(), WeightTerm{L.lp_w.get()}, L.lp_plan.plan,
+                           EpiDinv{L.lp_d.get(), unused.get()}, s);
+    if (L.lp_nnz > 0) {
+      L.lp_w32.alloc(L.lp_nnz, s, counter);
+      k_to_f32<<<blocks_for(L.lp_nnz), kNT, 0, s>>>(L.lp_nnz, L.lp_w.get(), L.lp_w32.get());
+      LG_LAUNCH_CHECK();
+    }
+  }
   return C;
 }
 
@@ -1334,7 +1389,7 @@ void setup_hierarchy(Hier& h, int64_t n, const int64_t* rowptr, const int32_t* c
     cur->nc = nc;
     lanczos(*cur, o, level, lam_dev.get() + level, s);
     lam_level.push_back(level);
-    auto next = galerkin(*cur, s, counter);
+    auto next = galerkin(*cur, o.lp_residual != 0, s, counter);
     h.levels.push_back(std::move(cur));
     cur = std::move(next);
     prepare_operator(*cur, s, counter);

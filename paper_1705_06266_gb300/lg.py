@@ -36,7 +36,7 @@ class Options(C.Structure):
         ("cheb_degree", C.c_int32), ("eig_iters", C.c_int32), ("max_coarse_n", C.c_int32),
         ("residual_replace", C.c_int32), ("memory_space", C.c_int32), ("use_graphs", C.c_int32),
         ("autotune", C.c_int32), ("reorder", C.c_int32), ("kcycle", C.c_int32),
-        ("elim_rounds", C.c_int32), ("reserved", C.c_int32),
+        ("elim_rounds", C.c_int32), ("lp_residual", C.c_int32),
     ]
 
 
@@ -98,6 +98,7 @@ _SIGS = {
     "lg_profile_read": (C.c_int, [_P, _I32, _P]),
     "lg_level_plan": (C.c_int, [_P, _I32, _P]),
     "lg_solve_many": (C.c_int, [_I32, _P, _P, _P, _D, _P]),
+    "lg_level_lp_nnz": (C.c_int, [_P, _I32, _P]),
     "lg_serve_options_default": (C.c_int, [_P]),
     "lg_serve_create": (C.c_int, [_P, _P]),
     "lg_serve_register": (C.c_int, [_P, _P]),
@@ -462,6 +463,11 @@ class Hierarchy:
 
     def level_info(self, l):
         return lg_level_info(self.h, l)
+
+    def level_lp_nnz(self, l) -> int:
+        v = C.c_int64()
+        _check(_load().lg_level_lp_nnz(self.h, int(l), C.byref(v)), "lg_level_lp_nnz")
+        return v.value
 
     def level(self, l):
         return lg_level_copy(self.h, l)

@@ -38,6 +38,7 @@ def test_options_defaults_match_paper(lgmod):
     assert o.agg_iters == 10 and o.vote_threshold == 8 and o.strength_vecs == 4 and o.strength_sweeps == 3
     assert o.cheb_degree == 2 and o.cheb_lo == 0.3 and o.cheb_hi == 1.1 and o.eig_iters == 10
     assert o.kcycle == 0 and o.elim_rounds == 1  # V-cycle, one elimination round (Sections 3.4, 4)
+    assert o.lp_residual == 1
     assert lgmod.lib().lg_error_string(0) == b"ok"
 
 

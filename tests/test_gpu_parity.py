@@ -202,6 +202,30 @@ def test_vcycle_fp64_matches_oracle_cycle(lgmod, oracle, inputs):
     H.close()
 
 
+def test_vcycle_with_w_pass_matches_oracle_cycle(lgmod, oracle, inputs):
+    """As above on a graph large enough for the W = L P post-smoothing pass
+    (the oracle computes r_0 = f - L x directly)."""
+    g = inputs.random_graph(9000, 6, seed=6, weights="uniform")
+    H = lgmod.Hierarchy(g, reorder=0)
+    R = oracle.Hierarchy(g)
+    assert H.nlevels == R.nlevels
+    for l in range(H.nlevels):
+        rp, cl, w, mp = H.level(l)
+        Lr = R.level(l)
+        np.testing.assert_array_equal(rp, Lr.a.rowptr)
+        np.testing.assert_array_equal(cl, Lr.a.col)
+        if mp is not None:
+            np.testing.assert_array_equal(mp, Lr.map)
+    assert sum(H.level_lp_nnz(l) for l in range(H.nlevels)) > 0
+    f = inputs.rhs(g.n, seed=9)
+    xg = H.vcycle(f, lgmod.FP64)
+    xr = R.vcycle(f)
+    assert np.linalg.norm(xg - xr) <= 1e-11 * np.linalg.norm(xr)
+    x32 = H.vcycle(f, lgmod.FP32_HIER)
+    assert np.linalg.norm(x32 - xr) <= 1e-4 * np.linalg.norm(xr)
+    H.close()
+
+
 def test_edge_cases(lgmod, inputs):
     one = inputs.Graph(1, np.array([0, 0]), np.zeros(0, np.int32), np.zeros(0))
     H = lgmod.Hierarchy(one)
@@ -498,7 +522,9 @@ def test_elim_rounds_path_solve_is_direct(lgmod, oracle, inputs, prec):
 # ---------------------------------------------------------------------------
 # Work units (Section 2.3.1, WDA): recomputed here from the level structure.
 # ---------------------------------------------------------------------------
-def _iteration_work(lgmod, H, kcycle, deg=2):
+def _iteration_work(lgmod, H, kcycle, deg=2, lp=True):
+    """lp: the cycle starts post-smoothing with the W = L P pass (lg_solve's
+    cycle), whose cost is nnz(W) + n in place of one Laplacian pass."""
     lv = [H.level_info(l) for l in range(H.nlevels)]
     first_agg = next((l for l, d in enumerate(lv) if d["kind"] == lgmod.LEVEL_AGG), -1)
 
@@ -512,6 +538,9 @@ def _iteration_work(lgmod, H, kcycle, deg=2):
             nnz_f = int(np.diff(rp)[mp < 0].sum())
             return 2 * nnz_f + d["nc"] + d["n"] + solve(l + 1)
         body = 2 * deg * A + 2 * d["n"] + solve(l + 1)
+        w = H.level_lp_nnz(l)
+        if lp and w > 0:
+            body += w + d["n"] - A
         return 2 * body + 2 * A if (kcycle and l != first_agg) else body
 
     A0 = lv[0]["nnz"] + lv[0]["n"]
@@ -528,9 +557,11 @@ def test_work_units(lgmod, inputs, kcycle):
     assert info.work_units == pytest.approx(info.iterations * w, rel=1e-12)
     wda = info.work_units / -np.log10(info.relres)
     assert 1.0 < wda < 1000.0
+    # the multi-column V-cycle has no W pass; K-cycle batches run lg_solve's cycle per column
+    wb = w if kcycle else _iteration_work(lgmod, H, kcycle, lp=False)
     X, infos = H.solve_batch(inputs.rhs(g.n, 2, seed=5))
     for inf in infos:
-        assert inf.work_units == pytest.approx(inf.iterations * w, rel=1e-12)
+        assert inf.work_units == pytest.approx(inf.iterations * wb, rel=1e-12)
     H.close()
 
 
@@ -560,3 +591,49 @@ def test_random_ordering(lgmod, oracle, inputs, name):
     xr -= xr.mean()
     assert np.linalg.norm(x - x.mean() - xr) <= 1e-6 * np.linalg.norm(xr)
     H.close()
+
+
+LP_GRAPHS = {
+    "chunglu_20k": GRAPHS["chunglu_20k"],
+    "grid3d_16": lambda I: I.grid3d(16, 16, 16),
+    "random_8k": lambda I: I.random_graph(8000, 5, seed=5),
+}
+
+
+@pytest.mark.parametrize("name", list(LP_GRAPHS))
+def test_lp_residual(lgmod, inputs, name):
+    """Post-smoothing from r_0 = r_pre - (L P) x_c (lp_residual = 1) against
+    r_0 = f - L x (lp_residual = 0): W = L P has one entry per (row, other
+    aggregate among the row's neighbours) (counted here with numpy), the FP64
+    cycles agree to rounding, and both solves converge in the same number of
+    iterations. (test_vcycle_fp64_matches_oracle_cycle checks the default,
+    W-based, cycle against the oracle's.)"""
+    g = LP_GRAPHS[name](inputs)
+    H1 = lgmod.Hierarchy(g, lp_residual=1)
+    H0 = lgmod.Hierarchy(g, lp_residual=0)
+    assert H1.nlevels == H0.nlevels
+    built = 0
+    for l in range(H1.nlevels):
+        d = H1.level_info(l)
+        assert H0.level_lp_nnz(l) == 0
+        if d["kind"] != lgmod.LEVEL_AGG or d["n"] < 4096:  # W only on aggregation levels of >= 4096 vertices
+            assert H1.level_lp_nnz(l) == 0
+            continue
+        rp, cl, _, agg = H1.level(l)
+        rows = np.repeat(np.arange(len(rp) - 1), np.diff(rp))
+        off = agg[cl] != agg[rows]
+        pairs = np.unique(rows[off].astype(np.int64) * (int(agg.max()) + 1) + agg[cl][off])
+        assert H1.level_lp_nnz(l) == pairs.size
+        built += pairs.size > 0
+    assert built > 0
+    f = inputs.rhs(g.n, seed=12)
+    x1 = H1.vcycle(f, lgmod.FP64)
+    x0 = H0.vcycle(f, lgmod.FP64)
+    assert np.linalg.norm(x1 - x0) <= 1e-11 * np.linalg.norm(x0)
+    for prec in (lgmod.FP64, lgmod.FP32_HIER):
+        _, i1 = H1.solve(f, precision=prec)
+        _, i0 = H0.solve(f, precision=prec)
+        assert i1.status == lgmod.OK and i0.status == lgmod.OK
+        assert abs(i1.iterations - i0.iterations) <= 1
+    H1.close()
+    H0.close()
