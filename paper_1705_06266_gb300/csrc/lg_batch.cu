@@ -192,6 +192,41 @@ struct MGather {  // restriction by member lists: sum v[j][c]
   __device__ __forceinline__ T finish(int64_t, int, T, T s) const { return s; }
 };
 
+// (L P x_c)[i][c] over W = L P off the own aggregate (Level::lp; see LpTerm
+// in lg_cycle.cu): FP32 sum_a W_ia (x_c[agg_i][c] - x_c[a][c]); FP64
+// d^W_i x_c[agg_i][c] - sum_a W_ia x_c[a][c].
+template <typename T>
+struct MLp;
+
+template <>
+struct MLp<float> {
+  const float* __restrict__ w;
+  const float* __restrict__ xc;
+  const int32_t* __restrict__ agg;
+  int k;
+  __device__ __forceinline__ float row(int64_t i, int c) const { return __ldg(&xc[(int64_t)agg[i] * k + c]); }
+  __device__ __forceinline__ float acc(float s, int64_t e, int32_t a, int c, float xa) const {
+    return fmaf(w[e], xa - __ldg(&xc[(int64_t)a * k + c]), s);
+  }
+  __device__ __forceinline__ float finish(int64_t, int, float, float s) const { return s; }
+};
+
+template <>
+struct MLp<double> {
+  const double* __restrict__ w;
+  const double* __restrict__ xc;
+  const int32_t* __restrict__ agg;
+  const double* __restrict__ d;
+  int k;
+  __device__ __forceinline__ double row(int64_t, int) const { return 0.0; }
+  __device__ __forceinline__ double acc(double s, int64_t e, int32_t a, int c, double) const {
+    return fma(w[e], __ldg(&xc[(int64_t)a * k + c]), s);
+  }
+  __device__ __forceinline__ double finish(int64_t i, int c, double, double s) const {
+    return fma(d[i], __ldg(&xc[(int64_t)agg[i] * k + c]), -s);
+  }
+};
+
 template <typename T>
 struct MWGather {  // elimination restriction: sum coef_e v[j][c]
   const T* __restrict__ coef;
@@ -362,6 +397,27 @@ struct MEpiElimRestrict {
     const T v = f[(int64_t)cfine[cr] * k + c] + s;
     fc[cr * k + c] = v;
     if (d0) d0[cr * k + c] = v * dinvc[cr] * inv_theta;
+  }
+};
+
+// Start of post-smoothing over W (see EpiPost in lg_cycle.cu): x += P x_c,
+// r_0 = r_pre - (L P x_c), d_0 = D^-1 r_0 / theta.
+template <typename T>
+struct MEpiPost {
+  T* r;
+  T* x;
+  const T* xc;
+  const int32_t* agg;
+  const T* dinv;
+  T* d0;
+  T inv_theta;
+  int k;
+  __device__ __forceinline__ void operator()(int64_t i, int c, T s) const {
+    const int64_t e = i * k + c;
+    const T r0 = r[e] - s;
+    r[e] = r0;
+    d0[e] = inv_theta * dinv[i] * r0;
+    x[e] = x[e] + xc[(int64_t)agg[i] * k + c];
   }
 };
 
@@ -730,7 +786,7 @@ __global__ void k_m_out(int64_t n, int k, const double* __restrict__ x, const in
 // Driver.
 // ---------------------------------------------------------------------------
 struct BatchState {
-  std::vector<std::unique_ptr<MPlanStore>> op, mem, pt;  // per level
+  std::vector<std::unique_ptr<MPlanStore>> op, mem, pt, lp;  // per level
   DBuf<double> tmp, colsum;                              // reduction totals of the column kernels
   std::map<std::pair<int, int>, cudaGraphExec_t> graphs;  // captured loop per (FP32?, k)
   ~BatchState() {
@@ -745,6 +801,17 @@ template <> std::vector<LevelVecs<float>>& mvecs<float>(Workspace& ws) { return 
 template <typename T> static const T* mpt_coef(const Level& L);
 template <> const double* mpt_coef<double>(const Level& L) { return L.pt_coef.get(); }
 template <> const float* mpt_coef<float>(const Level& L) { return L.pt_coef32.get(); }
+
+template <typename T>
+static MLp<T> mlp_term(const OpView<T>& w, const T* xc, const int32_t* agg, int k);
+template <>
+MLp<float> mlp_term<float>(const OpView<float>& w, const float* xc, const int32_t* agg, int k) {
+  return MLp<float>{w.w, xc, agg, k};
+}
+template <>
+MLp<double> mlp_term<double>(const OpView<double>& w, const double* xc, const int32_t* agg, int k) {
+  return MLp<double>{w.w, xc, agg, w.d, k};
+}
 
 template <typename T>
 static void mcycle(Hier& h, Workspace& ws, BatchState& bs, int l, int k, int kp, cudaStream_t s) {
@@ -797,12 +864,19 @@ static void mcycle(Hier& h, Workspace& ws, BatchState& bs, int l, int k, int kp,
   launch_mrows<T>(kp, L.nc, k, L.mem_ptr.get(), L.mem.get(), MGather<T>{V.r.get(), k}, bs.mem[l]->plan,
                   MEpiRestrict<T>{C.f.get(), d0n, dinvn, itn, k}, s);
   mcycle<T>(h, ws, bs, l + 1, k, kp, s);
-  k_m_agg_prolong<T><<<bblocks(n * k), kBT, 0, s>>>(n, k, L.agg.get(), C.x.get(), V.x.get());
-  LG_LAUNCH_CHECK();
-  launch_mrows<T>(kp, n, k, op.rowptr, op.col, MLap<T>{op.w, V.x.get(), op.d, k}, P,
-                  MEpiCheb<T>{V.x.get(), V.f.get(), V.r.get(), op.dinv, V.dA.get(), nullptr, 0, 0, k, T(0),
-                              (T)ch.inv_theta},
-                  s);
+  if (L.lp_nnz > 0) {  // x += P x_c, r_0 = r_pre - L P x_c, d_0: one pass over W
+    const OpView<T> lp = L.lp<T>();
+    launch_mrows<T>(kp, n, k, lp.rowptr, lp.col, mlp_term<T>(lp, C.x.get(), L.agg.get(), k), bs.lp[l]->plan,
+                    MEpiPost<T>{V.r.get(), V.x.get(), C.x.get(), L.agg.get(), op.dinv, V.dA.get(), (T)ch.inv_theta, k},
+                    s);
+  } else {
+    k_m_agg_prolong<T><<<bblocks(n * k), kBT, 0, s>>>(n, k, L.agg.get(), C.x.get(), V.x.get());
+    LG_LAUNCH_CHECK();
+    launch_mrows<T>(kp, n, k, op.rowptr, op.col, MLap<T>{op.w, V.x.get(), op.d, k}, P,
+                    MEpiCheb<T>{V.x.get(), V.f.get(), V.r.get(), op.dinv, V.dA.get(), nullptr, 0, 0, k, T(0),
+                                (T)ch.inv_theta},
+                    s);
+  }
   g = V.dA.get();
   gn = V.dB.get();
   for (int st = 1; st < deg; ++st) {
@@ -992,7 +1066,7 @@ static int msolve(Hier& h, Workspace& ws, int k, const double* B, double* X, dou
       inf.iterations = sc[mBB] == 0.0 ? 0 : (sc[mDone] != 0.0 ? (int)sc[mConv] : it);
       inf.relres = sc[mBB] > 0.0 ? std::sqrt(sc[mRR] / sc[mBB]) : 0.0;
       inf.solve_ms = ms;
-      inf.work_units = inf.iterations * iteration_work(h, false);
+      inf.work_units = inf.iterations * iteration_work(h);
       inf.levels = (int)h.levels.size();
       inf.setup_ms = h.setup_ms;
       inf.nnz = h.nnz0;
@@ -1007,6 +1081,7 @@ static BatchState& batch_state(Hier& h, Workspace& ws, cudaStream_t s) {
     st->op.resize(h.levels.size());
     st->mem.resize(h.levels.size());
     st->pt.resize(h.levels.size());
+    st->lp.resize(h.levels.size());
     for (size_t l = 0; l < h.levels.size(); ++l) {
       const Level& L = *h.levels[l];
       st->op[l] = std::make_unique<MPlanStore>();
@@ -1018,6 +1093,10 @@ static BatchState& batch_state(Hier& h, Workspace& ws, cudaStream_t s) {
       if (L.kind == LG_LEVEL_ELIM) {
         st->pt[l] = std::make_unique<MPlanStore>();
         st->pt[l]->build(L.nc, L.pt_ptr.get(), s, &ws.bytes);
+      }
+      if (L.lp_nnz > 0) {
+        st->lp[l] = std::make_unique<MPlanStore>();
+        st->lp[l]->build(L.n, L.lp_ptr.get(), s, &ws.bytes);
       }
     }
     st->tmp.alloc(5 * kMaxCols, s, &ws.bytes);

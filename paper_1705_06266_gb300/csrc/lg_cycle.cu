@@ -936,27 +936,27 @@ static cudaGraphExec_t pcg_graph(Hier& h, Workspace& ws, cudaStream_t s) {
 // flops / flops of a finest residual, approximated by operator nonzeros). An
 // operator application on level l costs A_l = nnz_off + n. Per iteration:
 // A_0 for q = L p, plus the cycle from level 0, where an aggregation body costs
-// 2 deg A_l (pre- and post-smoothing passes; with W = L P in use, one of them
-// costs nnz(W) + n_l instead) + 2 n_l (restriction, prolongation) + its
+// 2 deg A_l (pre- and post-smoothing passes; where the level has W = L P, one
+// of them costs nnz(W) + n_l instead) + 2 n_l (restriction, prolongation) + its
 // coarse solve; a K-cycle level two bodies + 2 A_l; an elimination level
 // 2 nnz_F + n_c + n_l (restriction and prolongation through the F rows'
 // entries) + its coarse solve; the coarsest level n_c^2.
-static double solve_work(const Hier& h, int l, bool lp) {
+static double solve_work(const Hier& h, int l) {
   const Level& L = *h.levels[l];
   const double A = (double)(L.nnz + L.n);
   if (L.kind == LG_LEVEL_COARSEST) return (double)L.n * (double)L.n;
   if (L.kind == LG_LEVEL_ELIM)
-    return 2.0 * (double)L.pt_f.size() + (double)L.nc + (double)L.n + solve_work(h, l + 1, lp);
-  double body = 2.0 * h.opts.cheb_degree * A + 2.0 * (double)L.n + solve_work(h, l + 1, lp);
-  if (lp && L.lp_nnz > 0) body += (double)(L.lp_nnz + L.n) - A;
+    return 2.0 * (double)L.pt_f.size() + (double)L.nc + (double)L.n + solve_work(h, l + 1);
+  double body = 2.0 * h.opts.cheb_degree * A + 2.0 * (double)L.n + solve_work(h, l + 1);
+  if (L.lp_nnz > 0) body += (double)(L.lp_nnz + L.n) - A;
   if (h.opts.kcycle && l != h.first_agg) return 2.0 * body + 2.0 * A;
   return body;
 }
 
-double iteration_work(const Hier& h, bool lp) {
+double iteration_work(const Hier& h) {
   const Level& L0 = *h.levels[0];
   const double A0 = (double)(L0.nnz + L0.n);
-  return (A0 + solve_work(h, 0, lp)) / A0;
+  return (A0 + solve_work(h, 0)) / A0;
 }
 
 int pcg_solve(Hier& h, Workspace& ws, const double* b, double* x, double tol, int precision, cudaStream_t s,
@@ -1024,7 +1024,7 @@ int pcg_solve(Hier& h, Workspace& ws, const double* b, double* x, double tol, in
     info->iterations = it;
     info->relres = rel;
     info->solve_ms = ms;
-    info->work_units = it * iteration_work(h, true);
+    info->work_units = it * iteration_work(h);
     info->levels = (int)h.levels.size();
     info->setup_ms = h.setup_ms;
     info->nnz = h.nnz0;

@@ -209,11 +209,8 @@ void vcycle_apply(Hier& h, Workspace& ws, const double* f, double* x, int precis
 int pcg_solve(Hier& h, Workspace& ws, const double* b, double* x, double tol, int precision,
               cudaStream_t s, lg_info* info);
 void vcycle_apply_batch(Hier& h, Workspace& ws, int k, const double* F, double* X, int precision, cudaStream_t s);
-// Work of one PCG iteration in finest-residual units (lg_info.work_units /
-// iterations); lp: whether the cycle runs the W = L P post-smoothing pass
-// (lg_solve's cycle does where W was built; the multi-column and packed
-// cycles do not).
-double iteration_work(const Hier& h, bool lp);
+// Work of one PCG iteration in finest-residual units (lg_info.work_units / iterations).
+double iteration_work(const Hier& h);
 int pcg_solve_batch(Hier& h, Workspace& ws, int k, const double* B, double* X, double tol, int precision,
                     cudaStream_t s, lg_info* infos);
 

@@ -12,7 +12,8 @@
 // hardware schedules blocks onto the 152 SMs as earlier ones finish.
 //
 // Each graph uses its own hierarchy and the vectors of its handle's default
-// workspace. The arithmetic is that of lg_cycle.cu step for step; only the
+// workspace. The arithmetic is that of lg_cycle.cu step for step (the
+// post-smoothing pass over W = L P included, where the level has it); only the
 // order of additions inside a row sum and a dot product differs (the group
 // and block reductions here versus the grid-wide ones there), so a result
 // agrees with lg_solve's to rounding and takes the same number of iterations
@@ -57,7 +58,9 @@ struct MRows {
 struct MLevel {
   int kind = 0;
   int64_t n = 0, nc = 0;
-  MRows op, mem, pt;
+  MRows op, mem, pt, lp;  // lp: W = L P (lp.n = 0 when the level has none)
+  const double *lp_w = nullptr, *lp_d = nullptr;
+  const float* lp_w32 = nullptr;
   const double *w = nullptr, *d = nullptr, *dinv = nullptr;
   const float *w32 = nullptr, *dinv32 = nullptr;
   const int32_t *agg = nullptr, *cmap = nullptr, *cfine = nullptr;
@@ -210,6 +213,48 @@ __device__ __forceinline__ MLap<double> m_lap<double>(const MLevel& L, const dou
   return MLap<double>{L.w, x, L.d};
 }
 
+// (L P x_c)_i over W = L P off the own aggregate (the forms of LpTerm).
+template <typename T>
+struct MLpT;
+
+template <>
+struct MLpT<float> {
+  const float* w;
+  const float* xc;
+  const int32_t* agg;
+  __device__ __forceinline__ float row(int64_t i) const { return xc[__ldg(&agg[i])]; }
+  __device__ __forceinline__ float acc(float s, int64_t k, int32_t a, float xa) const {
+    return fmaf(__ldg(&w[k]), xa - xc[a], s);
+  }
+  __device__ __forceinline__ float fin(int64_t, float, float s) const { return s; }
+};
+
+template <>
+struct MLpT<double> {
+  const double* w;
+  const double* xc;
+  const int32_t* agg;
+  const double* d;
+  __device__ __forceinline__ double row(int64_t) const { return 0.0; }
+  __device__ __forceinline__ double acc(double s, int64_t k, int32_t a, double) const {
+    return fma(__ldg(&w[k]), xc[a], s);
+  }
+  __device__ __forceinline__ double fin(int64_t i, double, double s) const {
+    return fma(__ldg(&d[i]), xc[__ldg(&agg[i])], -s);
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ MLpT<T> m_lpt(const MLevel& L, const T* xc);
+template <>
+__device__ __forceinline__ MLpT<float> m_lpt<float>(const MLevel& L, const float* xc) {
+  return MLpT<float>{L.lp_w32, xc, L.agg};
+}
+template <>
+__device__ __forceinline__ MLpT<double> m_lpt<double>(const MLevel& L, const double* xc) {
+  return MLpT<double>{L.lp_w, xc, L.agg, L.lp_d};
+}
+
 template <typename T>
 struct MGather {  // sum_k v[idx_k]
   const T* v;
@@ -332,6 +377,21 @@ __device__ void m_down(const MGraph& G, int l, MShared& sm) {
   m_restrict_agg<T>(L, V.r, C.f, d0n, dinvn, itn, sm);
 }
 
+// Start of post-smoothing over W (see EpiPost in lg_cycle.cu): x += P x_c,
+// r_0 = r_pre - (L P x_c), d_0 = D^-1 r_0 / theta, in one pass.
+template <typename T>
+__device__ __noinline__ void m_post_w(const MLevel& L, T* x, T* r, T* d0, const T* xc, MShared& sm) {
+  const T* dinv = m_dinv<T>(L);
+  const int32_t* agg = L.agg;
+  const T it = (T)L.inv_theta;
+  m_pass<T>(L.lp, m_lpt<T>(L, xc), [=](int64_t i, T s) {
+    const T r0 = r[i] - s;
+    r[i] = r0;
+    d0[i] = it * __ldg(&dinv[i]) * r0;
+    x[i] = x[i] + xc[__ldg(&agg[i])];
+  }, sm);
+}
+
 // Coming back up through level l: prolongation and post-smoothing.
 template <typename T>
 __device__ void m_up(const MGraph& G, int l, MShared& sm) {
@@ -358,11 +418,15 @@ __device__ void m_up(const MGraph& G, int l, MShared& sm) {
     __syncthreads();
     return;
   }
-  LG_BLOCK_LOOP(i, L.n) V.x[i] += xc[__ldg(&L.agg[i])];  // x += P x_c
-  __syncthreads();
   const int deg = G.deg;
-  // r_0 = f - L x, d_0 = D^-1 r_0 / theta
-  m_cheb<T>(L, V.x, V.f, V.r, V.a, nullptr, 0, 0, 0, T(0), (T)L.inv_theta, sm);
+  if (L.lp.n > 0) {  // x += P x_c, r_0 = r_pre - L P x_c, d_0 over W
+    m_post_w<T>(L, V.x, V.r, V.a, xc, sm);
+  } else {
+    LG_BLOCK_LOOP(i, L.n) V.x[i] += xc[__ldg(&L.agg[i])];  // x += P x_c
+    __syncthreads();
+    // r_0 = f - L x, d_0 = D^-1 r_0 / theta
+    m_cheb<T>(L, V.x, V.f, V.r, V.a, nullptr, 0, 0, 0, T(0), (T)L.inv_theta, sm);
+  }
   T* g = V.a;
   T* gn = V.b;
   for (int st = 1; st < deg; ++st) {
@@ -656,6 +720,12 @@ static const MLevel* many_levels(Hier& h) {
     if (L.kind == LG_LEVEL_AGG) {
       m.mem = rows_of(L.nc, L.mem_ptr.get(), L.mem.get(), L.mem_plan.plan);
       m.agg = L.agg.get();
+      if (L.lp_nnz > 0) {
+        m.lp = rows_of(L.n, L.lp_ptr.get(), L.lp_col.get(), L.lp_plan.plan);
+        m.lp_w = L.lp_w.get();
+        m.lp_d = L.lp_d.get();
+        m.lp_w32 = L.lp_w32.get();
+      }
       const Cheb& c = h.cheb[l];
       m.inv_theta = c.inv_theta;
       for (int q = 0; q < 8; ++q) {
@@ -810,7 +880,7 @@ int solve_many(int count, Hier* const* hs, const double* const* b, double* const
     inf.iterations = it;
     inf.relres = hres[3 * g + 2];
     inf.solve_ms = ms;
-    inf.work_units = it * iteration_work(h, false);
+    inf.work_units = it * iteration_work(h);
     inf.levels = (int)h.levels.size();
     inf.setup_ms = h.setup_ms;
     inf.nnz = h.nnz0;

@@ -522,9 +522,9 @@ def test_elim_rounds_path_solve_is_direct(lgmod, oracle, inputs, prec):
 # ---------------------------------------------------------------------------
 # Work units (Section 2.3.1, WDA): recomputed here from the level structure.
 # ---------------------------------------------------------------------------
-def _iteration_work(lgmod, H, kcycle, deg=2, lp=True):
-    """lp: the cycle starts post-smoothing with the W = L P pass (lg_solve's
-    cycle), whose cost is nnz(W) + n in place of one Laplacian pass."""
+def _iteration_work(lgmod, H, kcycle, deg=2):
+    """A level with W = L P starts post-smoothing with a pass over W, whose
+    cost is nnz(W) + n in place of one Laplacian pass."""
     lv = [H.level_info(l) for l in range(H.nlevels)]
     first_agg = next((l for l, d in enumerate(lv) if d["kind"] == lgmod.LEVEL_AGG), -1)
 
@@ -539,7 +539,7 @@ def _iteration_work(lgmod, H, kcycle, deg=2, lp=True):
             return 2 * nnz_f + d["nc"] + d["n"] + solve(l + 1)
         body = 2 * deg * A + 2 * d["n"] + solve(l + 1)
         w = H.level_lp_nnz(l)
-        if lp and w > 0:
+        if w > 0:
             body += w + d["n"] - A
         return 2 * body + 2 * A if (kcycle and l != first_agg) else body
 
@@ -557,11 +557,9 @@ def test_work_units(lgmod, inputs, kcycle):
     assert info.work_units == pytest.approx(info.iterations * w, rel=1e-12)
     wda = info.work_units / -np.log10(info.relres)
     assert 1.0 < wda < 1000.0
-    # the multi-column V-cycle has no W pass; K-cycle batches run lg_solve's cycle per column
-    wb = w if kcycle else _iteration_work(lgmod, H, kcycle, lp=False)
     X, infos = H.solve_batch(inputs.rhs(g.n, 2, seed=5))
     for inf in infos:
-        assert inf.work_units == pytest.approx(inf.iterations * wb, rel=1e-12)
+        assert inf.work_units == pytest.approx(inf.iterations * w, rel=1e-12)
     H.close()
 
 
