@@ -73,6 +73,49 @@ def test_many_mixed_options_in_one_launch(lgmod, oracle, inputs):
         H.close()
 
 
+def fuzz_graphs(inputs, count=60, seed=77):
+    """Small graphs of six shapes, sizes and weights drawn from one seed."""
+    rng = np.random.default_rng(seed)
+    gs = []
+    for q in range(count):
+        n = int(rng.integers(8, 2500))
+        kind = q % 6
+        if kind == 0:
+            g = inputs.random_graph(n, float(rng.uniform(2.5, 12.0)), seed=q + 1)
+        elif kind == 1:
+            g = inputs.chung_lu(max(n, 60), m_target=5 * max(n, 60), seed=q + 1)
+        elif kind == 2:
+            side = max(2, int(np.sqrt(n)))
+            g = inputs.grid2d(side, side + int(rng.integers(0, 5)), weights="uniform", seed=q + 1)
+        elif kind == 3:
+            g = inputs.path(n, weights="uniform", seed=q + 1)
+        elif kind == 4:
+            g = inputs.star(max(n // 4, 3), weights="uniform", seed=q + 1)
+        else:
+            g = inputs.cycle(n, weights="uniform", seed=q + 1)
+        gs.append(g)
+    return gs
+
+
+def test_fuzz_small_graphs_against_the_oracle(lgmod, oracle, inputs):
+    """Sixty seeded small graphs (random, power-law, grids, paths, stars,
+    cycles; unit and spread weights), both cycle precisions, solved in one
+    packed launch: each solution against the oracle's dense solve. Solved to
+    1e-10 so that the error bound kappa * relres stays below 1e-6 on the
+    grids (kappa about 2.4e3 at 50 x 54)."""
+    gs = fuzz_graphs(inputs)
+    Hs = [lgmod.Hierarchy(g, precision=lgmod.FP32_HIER if q % 2 else lgmod.FP64) for q, g in enumerate(gs)]
+    bs = [inputs.rhs(g.n, seed=500 + q) for q, g in enumerate(gs)]
+    xs, infos = lgmod.solve_many(Hs, bs, tol=1e-10)
+    for q, (g, b, x, info) in enumerate(zip(gs, bs, xs, infos)):
+        assert info.status == lgmod.OK, (q, g.name)
+        assert relres(g, b, x) <= 1e-10 * 1.0001, (q, g.name)
+        ref = oracle.dense_solve(g, b)
+        assert np.linalg.norm(x - ref) <= 1e-6 * np.linalg.norm(ref), (q, g.name)
+    for H in Hs:
+        H.close()
+
+
 def test_many_device_vectors(lgmod, inputs, torch_cuda):
     torch = torch_cuda
     gs = inputs.serving_mix(6, 300, 3000, seed=8)

@@ -326,6 +326,32 @@ def test_galerkin_dense_and_energy(oracle, inputs):
     assert u @ Lc_u == pytest.approx(Pu @ oracle.apply_L(g, Pu), rel=1e-12)
 
 
+def test_post_smoothing_residual_through_w(oracle, inputs):
+    """The identity behind the W = L P pass that starts post-smoothing (the
+    CUDA cycle's reading of Section 3.6): after the coarse correction
+    x = x_pre + P x_c, r_0 = f - L x equals r_pre - (L P) x_c, and
+    (L P x_c)_i = sum_a W_ia (x_c[agg_i] - x_c[a]) with W_ia the weight from i
+    into aggregate a != agg_i (the rows of L sum to zero, so the own aggregate
+    drops out). Checked with numpy against dense products on the oracle's
+    aggregates."""
+    g = inputs.random_graph(500, 6, seed=13)
+    S = oracle.strength(g, SEED, 0)
+    nc, agg, _, _ = oracle.aggregate(g, S)
+    L = dense_lap(g)
+    P = np.zeros((g.n, nc))
+    P[np.arange(g.n), agg] = 1.0
+    rows = np.repeat(np.arange(g.n), np.diff(g.rowptr))
+    off = agg[g.col] != agg[rows]
+    W = sp.csr_matrix((g.w[off], (rows[off], agg[g.col][off])), shape=(g.n, nc))  # equal keys summed
+    assert W.nnz == len(set(zip(rows[off].tolist(), agg[g.col][off].tolist())))
+    rng = np.random.default_rng(4)
+    xc, xpre, f = rng.standard_normal(nc), rng.standard_normal(g.n), rng.standard_normal(g.n)
+    lp_xc = np.asarray(W.sum(axis=1)).ravel() * xc[agg] - W @ xc
+    np.testing.assert_allclose(lp_xc, L @ P @ xc, rtol=1e-12, atol=1e-12)
+    r_pre = f - L @ xpre
+    np.testing.assert_allclose(r_pre - lp_xc, f - L @ (xpre + P @ xc), rtol=1e-11, atol=1e-11)
+
+
 # --------------------------------------------------------------------------
 # Eigenvalue estimate and Chebyshev smoothing (Section 3.6)
 # --------------------------------------------------------------------------
