@@ -208,7 +208,10 @@ int lg_set_precision(lg_handle h, int32_t precision);
  *          must not overlap other graphs' vectors.
  *   infos: NULL or count entries (solve_ms: the whole launch).
  * Uses each handle's default workspace: no other call may use these handles
- * meanwhile. Returns LG_OK if every solve converged, else the first failing
+ * meanwhile. Host vectors pass through one pinned staging buffer of the
+ * process (grown on demand, kept until exit), so concurrent calls from
+ * several threads run one after another. Returns LG_OK if every solve
+ * converged, else the first failing
  * status in argument order. LG_ERR_INVALID for count < 1, a NULL or repeated
  * handle or vector, tol <= 0, or a graph over the limits above.
  */

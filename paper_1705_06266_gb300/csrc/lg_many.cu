@@ -759,7 +759,9 @@ static const MLevel* many_levels(Hier& h) {
 
 // Pinned host staging of a call (descriptors, results and the host-memory
 // vectors), so that a call makes one copy each way however many graphs it
-// holds. Grown on demand; calls take it one at a time.
+// holds. Grown on demand and kept until the process exits (freeing pinned
+// memory from a static destructor could run after the CUDA runtime has shut
+// down); calls take it one at a time.
 struct PinnedStage {
   std::mutex m;
   unsigned char* p = nullptr;
