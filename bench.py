@@ -236,9 +236,11 @@ def multi_rhs_leg(lg, inputs, torch, dev, k):
             inf = lg.lg_solve(h, Bd[c], Xd[c], TOL)
             seq_ms += inf.solve_ms
             seq_it.append(inf.iterations)
+        levels = [lg.lg_level_info(h, l) for l in range(lg.lg_hier_info(h).levels)]
         lg.lg_destroy(h)
         out[name] = {
             "n": g.n, "nnz": g.nnz, "k": k,
+            "levels": [{q: lv[q] for q in ("kind", "n", "nnz", "nc")} for lv in levels],
             "batched_ms": batch_ms, "batched_nnz_per_s": g.nnz * k / (batch_ms * 1e-3),
             "batched_iterations_max": max(i.iterations for i in infos),
             "batched_relres_max": max(i.relres for i in infos),
