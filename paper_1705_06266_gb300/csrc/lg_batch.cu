@@ -783,7 +783,7 @@ __global__ void k_m_out(int64_t n, int k, const double* __restrict__ x, const in
 }
 
 // ---------------------------------------------------------------------------
-// Driver.
+// Host side: plans, the multi-column cycle and PCG loop.
 // ---------------------------------------------------------------------------
 struct BatchState {
   std::vector<std::unique_ptr<MPlanStore>> op, mem, pt, lp;  // per level
