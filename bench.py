@@ -19,6 +19,7 @@ bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import datetime
 import hashlib
 import json
 import math
@@ -78,7 +79,10 @@ def dist_init():
         backend = "nccl" if torch.cuda.is_available() else "gloo"
         if backend == "nccl":
             torch.cuda.set_device(local)
-        dist.init_process_group(backend=backend)
+        # a replica that fails ends the others' next barrier with an error
+        # after this long instead of holding every GPU of the job
+        timeout = datetime.timedelta(seconds=float(os.environ.get("BENCH_PG_TIMEOUT_S", "600")))
+        dist.init_process_group(backend=backend, timeout=timeout)
     return world, rank, local
 
 
