@@ -187,6 +187,23 @@ int lg_solve(lg_handle h, const double* b, double* x, double tol, lg_info* info)
 int lg_solve_batch(lg_handle h, int32_t k, const double* B, int64_t ldb, double* X, int64_t ldx,
                    double tol, lg_info* infos);
 
+/*
+ * Save and load a hierarchy. lg_save writes h's hierarchy to the file `path`
+ * (created or truncated): every level's arrays, the row-binning choices, the
+ * Chebyshev constants, the vertex order and the setup options, in host byte
+ * order, so that a hierarchy can leave the device and come back without its
+ * setup. lg_load builds a new handle from such a file; solves on it return
+ * the same results, bit for bit, as on the saved handle. opts (may be NULL)
+ * gives the new handle's stream and memory_space; every other option comes
+ * from the file.
+ * Errors: LG_ERR_INVALID for a NULL argument, a file that cannot be opened,
+ * written or read, or one that is not a complete hierarchy file of this
+ * format (a wrong header is found before any device work); LG_ERR_NOMEM and
+ * LG_ERR_CUDA as for lg_setup.
+ */
+int lg_save(lg_handle h, const char* path);
+int lg_load(const char* path, const lg_options* opts, lg_handle* out);
+
 /* Stored entries of level l's W = L P operator (see lp_residual); 0 when the
  * level has none (elimination and coarsest levels, or lp_residual = 0). */
 int lg_level_lp_nnz(lg_handle h, int32_t l, int64_t* nnz);

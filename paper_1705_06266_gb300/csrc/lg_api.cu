@@ -149,6 +149,7 @@ int lg_setup(int64_t n, const int64_t* rowptr, const int32_t* col, const double*
   lg::Hier* h = nullptr;
   LG_API_BEGIN
   h = new lg::Hier();
+  lg::NvtxRange range("lg_setup");
   if (opts) h->opts = *opts; else lg_options_default(&h->opts);
   LG_CUDA(cudaGetDevice(&h->device));
   if (h->opts.stream) {
@@ -175,6 +176,38 @@ int lg_setup(int64_t n, const int64_t* rowptr, const int32_t* col, const double*
   }
 }
 
+int lg_save(lg_handle hh, const char* path) {
+  if (!hh || !path) return LG_ERR_INVALID;
+  LG_API_BEGIN
+  lg::save_hierarchy(*reinterpret_cast<lg::Hier*>(hh), path);
+  return LG_OK;
+  LG_API_END
+}
+
+int lg_load(const char* path, const lg_options* opts, lg_handle* out) {
+  if (!out) return LG_ERR_INVALID;
+  *out = nullptr;
+  if (!path) return LG_ERR_INVALID;
+  lg::Hier* h = nullptr;
+  try {
+    h = new lg::Hier();
+    lg::load_hierarchy(*h, path, opts);
+    *out = reinterpret_cast<lg_handle>(h);
+    return LG_OK;
+  } catch (const lg::Error& e) {
+    delete h;
+    return lg::handle_error(e);
+  } catch (const std::bad_alloc&) {
+    delete h;
+    lg::g_last_error = "host allocation";
+    return LG_ERR_NOMEM;
+  } catch (...) {
+    delete h;
+    lg::g_last_error = "unexpected exception";
+    return LG_ERR_CUDA;
+  }
+}
+
 void lg_destroy(lg_handle hh) {
   try {
     delete reinterpret_cast<lg::Hier*>(hh);
@@ -193,6 +226,7 @@ int lg_set_precision(lg_handle hh, int32_t precision) {
 int lg_solve(lg_handle hh, const double* b, double* x, double tol, lg_info* info) {
   if (!hh || !b || !x || !(tol > 0.0)) return LG_ERR_INVALID;
   LG_API_BEGIN
+  lg::NvtxRange range("lg_solve");
   lg::Hier& h = *H(hh);
   cudaStream_t s = h.stream;
   const int64_t n = h.levels[0]->n;
@@ -220,6 +254,7 @@ int lg_solve_batch(lg_handle hh, int32_t k, const double* B, int64_t ldb, double
   const int64_t n = h.levels[0]->n;
   if (ldb < n || ldx < n) return LG_ERR_INVALID;
   LG_API_BEGIN
+  lg::NvtxRange range("lg_solve_batch");
   cudaStream_t s = h.stream;
   lg::DBuf<double> Bd((size_t)n * k, s), Xd((size_t)n * k, s);
   for (int c = 0; c < k; ++c)
@@ -251,6 +286,7 @@ int lg_solve_many(int32_t count, const lg_handle* hs, const double* const* b, do
     if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end()) return LG_ERR_INVALID;
   }
   LG_API_BEGIN
+  lg::NvtxRange range("lg_solve_many");
   int dev = 0;
   LG_CUDA(cudaGetDevice(&dev));
   std::unique_ptr<bool[]> bd(new bool[count]), xd(new bool[count]);

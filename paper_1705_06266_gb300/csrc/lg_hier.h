@@ -17,12 +17,23 @@
 //  - COARSEST: the dense FP64 pseudo-inverse, n x n row-major.
 #pragma once
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <memory>
 #include <vector>
 
 #include "lg_prims.h"
 
 namespace lg {
+
+// A named NVTX range for the life of the object: the phases of a setup or a
+// solve on a profiler's timeline (nothing happens without a profiler).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 template <typename T>
 struct OpView {
@@ -213,6 +224,13 @@ void vcycle_apply_batch(Hier& h, Workspace& ws, int k, const double* F, double* 
 double iteration_work(const Hier& h);
 int pcg_solve_batch(Hier& h, Workspace& ws, int k, const double* B, double* X, double tol, int precision,
                     cudaStream_t s, lg_info* infos);
+
+// ---- save and load (lg_io.cu) ----
+void save_hierarchy(const Hier& h, const char* path);
+// Fills a fresh Hier from a file written by save_hierarchy; opts (may be
+// null) gives the stream and memory space. The header is checked before any
+// CUDA call.
+void load_hierarchy(Hier& h, const char* path, const lg_options* opts);
 
 // ---- many small solves in one launch (lg_many.cu) ----
 constexpr int64_t kManyMaxNnz = int64_t(1) << 22;  // largest nnz(L_0) one block solves

@@ -1357,6 +1357,7 @@ void setup_hierarchy(Hier& h, int64_t n, const int64_t* rowptr, const int32_t* c
     // up to elim_rounds elimination levels in a row, each while the gate passes
     bool done = false;
     for (int round = 0; o.elim_enable && o.elim_max_degree > 0 && round < o.elim_rounds; ++round) {
+      NvtxRange range("lg elimination level");
       DBuf<uint8_t> is_f(cur->n, s);
       const int64_t nf = run_elim_select(cur->n, cur->rowptr.get(), cur->col.get(), o.elim_max_degree, o.seed,
                                          is_f.get(), s);
@@ -1371,6 +1372,7 @@ void setup_hierarchy(Hier& h, int64_t n, const int64_t* rowptr, const int32_t* c
       }
     }
     if (done) break;
+    NvtxRange range("lg aggregation level");
     const int level = (int)h.levels.size();
     DBuf<double> S(cur->nnz, s);
     // the level's bins match those lg_strength / lg_aggregate derive for the same CSR (E = 4,
@@ -1395,11 +1397,15 @@ void setup_hierarchy(Hier& h, int64_t n, const int64_t* rowptr, const int32_t* c
     prepare_operator(*cur, s, counter);
   }
   if (cur->n > o.max_coarse_n) fail(LG_ERR_SETUP, "coarsest level too large for the dense solve");
-  coarsest_pinv(*cur, h.dev_err.get(), s, counter);
+  {
+    NvtxRange range("lg coarsest pseudo-inverse");
+    coarsest_pinv(*cur, h.dev_err.get(), s, counter);
+  }
   h.levels.push_back(std::move(cur));
   for (auto& L : h.levels) make_f32(*L, s, counter);
   if (read_err(h.dev_err, s)) fail(LG_ERR_SETUP, "coarsest pseudo-inverse failed");
   if (o.autotune) {
+    NvtxRange range("lg row-binning tuner");
     for (auto& L : h.levels) {
       if (L->nnz < 20000) continue;
       tune_level(*L, s);

@@ -99,6 +99,8 @@ _SIGS = {
     "lg_level_plan": (C.c_int, [_P, _I32, _P]),
     "lg_solve_many": (C.c_int, [_I32, _P, _P, _P, _D, _P]),
     "lg_level_lp_nnz": (C.c_int, [_P, _I32, _P]),
+    "lg_save": (C.c_int, [_P, C.c_char_p]),
+    "lg_load": (C.c_int, [C.c_char_p, _P, _P]),
     "lg_serve_options_default": (C.c_int, [_P]),
     "lg_serve_create": (C.c_int, [_P, _P]),
     "lg_serve_register": (C.c_int, [_P, _P]),
@@ -447,6 +449,22 @@ class Hierarchy:
         if getattr(self, "h", None):
             lg_destroy(self.h)
             self.h = None
+
+    def save(self, path: str):
+        """Write the hierarchy to a file (lg_save)."""
+        _check(_load().lg_save(self.h, os.fsencode(path)), "lg_save")
+
+    @classmethod
+    def load(cls, path: str, opts: Options | None = None, **kw):
+        """A hierarchy read back from a file written by save (lg_load); opts
+        or keyword options give only the stream and memory space."""
+        self = cls.__new__(cls)
+        self.opts = opts if opts is not None else options(**kw)
+        h = C.c_void_p()
+        _check(_load().lg_load(os.fsencode(path), C.byref(self.opts), C.byref(h)), "lg_load")
+        self.h = h
+        self.n = int(lg_level_info(h, 0)["n"])
+        return self
 
     def __del__(self):
         try:

@@ -52,6 +52,20 @@ def test_bad_arguments_rejected_without_gpu_work(lgmod):
     assert lib.lg_solve_many(0, None, None, None, 1e-8, None) == lgmod.ERR_INVALID
     one = (C.c_void_p * 1)(None)
     assert lib.lg_solve_many(1, one, one, one, 1e-8, None) == lgmod.ERR_INVALID  # a NULL handle
+    assert lib.lg_save(None, b"/nonexistent/x") == lgmod.ERR_INVALID
+    assert lib.lg_load(None, None, C.byref(h)) == lgmod.ERR_INVALID
+
+
+def test_load_refuses_other_files_before_device_work(lgmod, tmp_path):
+    import ctypes as C
+
+    lib = lgmod.lib()
+    h = C.c_void_p()
+    assert lib.lg_load(str(tmp_path / "missing.lgh").encode(), None, C.byref(h)) == lgmod.ERR_INVALID
+    junk = tmp_path / "junk.lgh"
+    junk.write_bytes(b"not a hierarchy file at all" * 10)
+    assert lib.lg_load(str(junk).encode(), None, C.byref(h)) == lgmod.ERR_INVALID
+    assert not h.value
 
 
 def test_oracle_and_cuda_path_share_no_code():

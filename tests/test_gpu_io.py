@@ -1,0 +1,74 @@
+"""Save and load of a hierarchy (lg_save / lg_load): the loaded handle has
+the same levels, plans, vertex order and coarsest pseudo-inverse, and its
+solves (FP64 and FP32 hierarchy, single, multi-column and packed) return the
+same bits; damaged files are refused."""
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    "chunglu_20k": (lambda I: I.chung_lu(20000, m_target=100000, seed=3), {}),
+    "grid3d_16_kcycle": (lambda I: I.grid3d(16, 16, 16), {"kcycle": 1}),
+    "road_elim4": (lambda I: I.road_like(60, 60, seed=4), {"elim_rounds": 4}),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_save_load_round_trip(lgmod, inputs, tmp_path, name):
+    make, kw = CASES[name]
+    g = make(inputs)
+    H = lgmod.Hierarchy(g, **kw)
+    path = str(tmp_path / "h.lgh")
+    H.save(path)
+    H2 = lgmod.Hierarchy.load(path)
+    assert H2.nlevels == H.nlevels and H2.n == H.n
+    for l in range(H.nlevels):
+        assert H2.level_info(l) == H.level_info(l)
+        assert H2.level_lp_nnz(l) == H.level_lp_nnz(l)
+        assert lgmod.lg_level_plan(H2.h, l) == lgmod.lg_level_plan(H.h, l)
+        for a, b in zip(H.level(l), H2.level(l)):
+            if a is None:
+                assert b is None
+            else:
+                np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(H2.permutation(), H.permutation())
+    nc = H.level_info(H.nlevels - 1)["n"]
+    np.testing.assert_array_equal(lgmod.lg_coarsest_pinv(H2.h, nc), lgmod.lg_coarsest_pinv(H.h, nc))
+    assert H2.info().setup_ms == H.info().setup_ms
+    b = inputs.rhs(g.n, seed=3)
+    for prec in (lgmod.FP64, lgmod.FP32_HIER):
+        x1, i1 = H.solve(b, precision=prec)
+        x2, i2 = H2.solve(b, precision=prec)
+        assert i1.status == lgmod.OK and i2.iterations == i1.iterations and i2.relres == i1.relres
+        np.testing.assert_array_equal(x2, x1)
+    B = inputs.rhs(g.n, 4, seed=5)
+    X1, _ = H.solve_batch(B)
+    X2, _ = H2.solve_batch(B)
+    np.testing.assert_array_equal(X2, X1)
+    xs, infos = lgmod.solve_many([H2], [b])
+    assert infos[0].status == lgmod.OK
+    H.close()
+    H2.close()
+
+
+def test_damaged_files_refused(lgmod, inputs, tmp_path):
+    g = inputs.grid2d(40, 40)
+    H = lgmod.Hierarchy(g)
+    path = tmp_path / "h.lgh"
+    H.save(str(path))
+    data = path.read_bytes()
+    for cut in (len(data) // 2, len(data) - 1):
+        bad = tmp_path / f"cut{cut}.lgh"
+        bad.write_bytes(data[:cut])
+        with pytest.raises(lgmod.LGError) as e:
+            lgmod.Hierarchy.load(str(bad))
+        assert e.value.status == lgmod.ERR_INVALID
+    longer = tmp_path / "longer.lgh"
+    longer.write_bytes(data + b"\0")
+    with pytest.raises(lgmod.LGError) as e:
+        lgmod.Hierarchy.load(str(longer))
+    assert e.value.status == lgmod.ERR_INVALID
+    x1, _ = H.solve(inputs.rhs(g.n, seed=1))  # the saved handle is untouched
+    H.close()
