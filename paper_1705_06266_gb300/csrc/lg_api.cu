@@ -2,6 +2,7 @@
 // detection, handle lifecycle, and the mapping of library errors to status
 // codes. No entry point lets an exception or a CUDA error escape.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -58,6 +59,40 @@ static bool is_device_ptr(const void* p, int memory_space) {
     return false;
   }
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// One JSON line per setup and per solved right-hand side, appended to the
+// file named by the environment variable LG_LOG (nothing when it is unset).
+static std::mutex g_log_mu;
+
+static bool log_on() {
+  const char* p = std::getenv("LG_LOG");
+  return p && *p;
+}
+
+static void log_line(const char* line) {
+  const char* path = std::getenv("LG_LOG");
+  if (!path || !*path) return;
+  std::lock_guard<std::mutex> lk(g_log_mu);
+  if (FILE* f = std::fopen(path, "a")) {
+    std::fputs(line, f);
+    std::fputc('\n', f);
+    std::fclose(f);
+  }
+}
+
+static void log_solve(const char* call, int index, const lg_info& inf) {
+  char wda[40] = "null";  // work units per digit of residual reduction (Section 2.3.1)
+  if (inf.relres > 0.0 && inf.relres < 1.0 && std::isfinite(inf.relres))
+    std::snprintf(wda, sizeof(wda), "%.9g", inf.work_units / -std::log10(inf.relres));
+  char line[640];
+  std::snprintf(line, sizeof(line),
+                "{\"call\": \"%s\", \"index\": %d, \"status\": %d, \"iterations\": %d, \"relres\": %.17g, "
+                "\"solve_ms\": %.9g, \"setup_ms\": %.9g, \"work_units\": %.9g, \"wda\": %s, \"levels\": %d, "
+                "\"nnz\": %lld, \"op_complexity\": %.9g}",
+                call, index, inf.status, inf.iterations, std::isfinite(inf.relres) ? inf.relres : -1.0, inf.solve_ms,
+                inf.setup_ms, inf.work_units, wda, inf.levels, (long long)inf.nnz, inf.op_complexity);
+  log_line(line);
 }
 
 static int handle_error(const Error& e) {
@@ -161,6 +196,14 @@ int lg_setup(int64_t n, const int64_t* rowptr, const int32_t* col, const double*
   lg::setup_hierarchy(*h, n, rowptr, col, w);
   h->ws = lg::make_workspace(*h, 1, h->stream);
   LG_CUDA(cudaStreamSynchronize(h->stream));
+  if (lg::log_on()) {
+    char line[256];
+    std::snprintf(line, sizeof(line),
+                  "{\"call\": \"lg_setup\", \"n\": %lld, \"nnz\": %lld, \"levels\": %d, \"setup_ms\": %.9g, "
+                  "\"hierarchy_bytes\": %lld}",
+                  (long long)n, (long long)h->nnz0, (int)h->levels.size(), h->setup_ms, (long long)h->bytes);
+    lg::log_line(line);
+  }
   *out = reinterpret_cast<lg_handle>(h);
   h = nullptr;
   return LG_OK;
@@ -243,6 +286,7 @@ int lg_solve(lg_handle hh, const double* b, double* x, double tol, lg_info* info
   for (auto& L : h.levels) inf.op_complexity += (double)(L->nnz + L->n);
   inf.op_complexity /= (double)h.nnz0;
   if (info) *info = inf;
+  if (lg::log_on()) lg::log_solve("lg_solve", 0, inf);
   return st;
   LG_API_END
 }
@@ -263,10 +307,18 @@ int lg_solve_batch(lg_handle hh, int32_t k, const double* B, int64_t ldb, double
     h.wsb.reset();
     h.wsb = lg::make_workspace(h, k, s);
   }
-  int st = lg::pcg_solve_batch(h, k > 1 ? *h.wsb : *h.ws, k, Bd.get(), Xd.get(), tol, h.opts.precision, s, infos);
+  std::vector<lg_info> own;
+  lg_info* out = infos;
+  if (!out && lg::log_on()) {
+    own.resize((size_t)k);
+    out = own.data();
+  }
+  int st = lg::pcg_solve_batch(h, k > 1 ? *h.wsb : *h.ws, k, Bd.get(), Xd.get(), tol, h.opts.precision, s, out);
   for (int c = 0; c < k; ++c)
     LG_CUDA(cudaMemcpyAsync(X + (size_t)c * ldx, Xd.get() + (size_t)c * n, sizeof(double) * n, cudaMemcpyDefault, s));
   LG_CUDA(cudaStreamSynchronize(s));
+  if (out && lg::log_on())
+    for (int c = 0; c < k; ++c) lg::log_solve("lg_solve_batch", c, out[c]);
   return st;
   LG_API_END
 }
@@ -295,7 +347,16 @@ int lg_solve_many(int32_t count, const lg_handle* hs, const double* const* b, do
     bd[g] = lg::is_device_ptr(b[g], v[g]->opts.memory_space);
     xd[g] = lg::is_device_ptr(x[g], v[g]->opts.memory_space);
   }
-  return lg::solve_many(count, v.data(), b, x, bd.get(), xd.get(), tol, infos);
+  std::vector<lg_info> own;
+  lg_info* out = infos;
+  if (!out && lg::log_on()) {
+    own.resize((size_t)count);
+    out = own.data();
+  }
+  const int st = lg::solve_many(count, v.data(), b, x, bd.get(), xd.get(), tol, out);
+  if (out && lg::log_on())
+    for (int g = 0; g < count; ++g) lg::log_solve("lg_solve_many", g, out[g]);
+  return st;
   LG_API_END
 }
 

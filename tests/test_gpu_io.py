@@ -72,3 +72,32 @@ def test_damaged_files_refused(lgmod, inputs, tmp_path):
     assert e.value.status == lgmod.ERR_INVALID
     x1, _ = H.solve(inputs.rhs(g.n, seed=1))  # the saved handle is untouched
     H.close()
+
+
+def test_solve_log(lgmod, inputs, tmp_path, monkeypatch):
+    """With LG_LOG set, every setup and every solved right-hand side appends
+    one JSON line with the figures the call returned."""
+    import json
+
+    log = tmp_path / "solves.jsonl"
+    monkeypatch.setenv("LG_LOG", str(log))
+    g = inputs.grid2d(30, 30)
+    H = lgmod.Hierarchy(g)
+    b = inputs.rhs(g.n, seed=1)
+    _, info = H.solve(b)
+    _, binfos = H.solve_batch(inputs.rhs(g.n, 2, seed=2))
+    H2 = lgmod.Hierarchy(inputs.grid2d(20, 20))
+    _, minfos = lgmod.solve_many([H, H2], [b, inputs.rhs(400, seed=3)])
+    monkeypatch.delenv("LG_LOG")
+    H.solve(b)  # not logged
+    lines = [json.loads(s) for s in log.read_text().splitlines()]
+    assert [x["call"] for x in lines] == ["lg_setup", "lg_solve", "lg_solve_batch", "lg_solve_batch", "lg_setup",
+                                          "lg_solve_many", "lg_solve_many"]
+    assert lines[0]["n"] == g.n and lines[0]["levels"] == H.nlevels
+    for line, inf in zip(lines[1:4] + lines[5:], [info] + binfos + minfos):
+        assert line["status"] == inf.status == lgmod.OK
+        assert line["iterations"] == inf.iterations and line["relres"] == inf.relres
+        assert line["wda"] == pytest.approx(inf.work_units / -np.log10(inf.relres), rel=1e-6)
+    assert [x["index"] for x in lines[5:]] == [0, 1]
+    H.close()
+    H2.close()
