@@ -119,6 +119,10 @@ typedef struct {
                                the prolongation x += P x_c joins that pass. 0: r_0 = f - L x. */
 } lg_options;
 
+/* Logging: with the environment variable LG_LOG naming a file, lg_setup and
+ * every right-hand side solved by lg_solve, lg_solve_batch or lg_solve_many
+ * append one JSON line to it (the figures of lg_info, and WDA). */
+
 /* Result of a setup or a solve. */
 typedef struct {
   double relres;         /* ||b - L x||_2 / ||b||_2 of the returned x, recomputed in FP64 */
