@@ -26,6 +26,7 @@ namespace {
 
 constexpr char kMagic[8] = {'L', 'G', 'H', 'I', 'E', 'R', 'F', '1'};
 constexpr uint32_t kVersion = 1;
+constexpr size_t kStageBytes = size_t(64) << 20;  // host staging of one array at a time
 
 struct File {
   FILE* f = nullptr;
@@ -43,15 +44,18 @@ struct Writer {
   void val(const T& v) {
     raw(&v, sizeof(T));
   }
-  // count values of a device array
+  // count values of a device array, through a bounded host buffer
   template <typename T>
   void arr(const DBuf<T>& b, size_t count, cudaStream_t s) {
     val<uint64_t>(count);
-    if (!count) return;
-    std::vector<T> h(count);
-    LG_CUDA(cudaMemcpyAsync(h.data(), b.get(), sizeof(T) * count, cudaMemcpyDeviceToHost, s));
-    LG_CUDA(cudaStreamSynchronize(s));
-    raw(h.data(), sizeof(T) * count);
+    const size_t step = kStageBytes / sizeof(T);
+    std::vector<T> h(count < step ? count : step);
+    for (size_t at = 0; at < count; at += step) {
+      const size_t m = count - at < step ? count - at : step;
+      LG_CUDA(cudaMemcpyAsync(h.data(), b.get() + at, sizeof(T) * m, cudaMemcpyDeviceToHost, s));
+      LG_CUDA(cudaStreamSynchronize(s));
+      raw(h.data(), sizeof(T) * m);
+    }
   }
 };
 
@@ -66,17 +70,22 @@ struct Reader {
     raw(&v, sizeof(T));
     return v;
   }
-  // a device array of exactly `expect` values (an empty one for 0)
+  // a device array of exactly `expect` values (an empty one for 0), through
+  // a bounded host buffer
   template <typename T>
   void arr(DBuf<T>& b, int64_t expect, cudaStream_t s, int64_t* counter) {
     const uint64_t count = val<uint64_t>();
     if (expect < 0 || count != (uint64_t)expect) fail(LG_ERR_INVALID, "hierarchy file: array size mismatch");
     if (!count) return;
-    std::vector<T> h(count);
-    raw(h.data(), sizeof(T) * count);
     b.alloc(count, s, counter);
-    LG_CUDA(cudaMemcpyAsync(b.get(), h.data(), sizeof(T) * count, cudaMemcpyHostToDevice, s));
-    LG_CUDA(cudaStreamSynchronize(s));  // h goes out of scope
+    const size_t step = kStageBytes / sizeof(T);
+    std::vector<T> h(count < step ? count : step);
+    for (size_t at = 0; at < count; at += step) {
+      const size_t m = count - at < step ? count - at : step;
+      raw(h.data(), sizeof(T) * m);
+      LG_CUDA(cudaMemcpyAsync(b.get() + at, h.data(), sizeof(T) * m, cudaMemcpyHostToDevice, s));
+      LG_CUDA(cudaStreamSynchronize(s));  // h is refilled next
+    }
   }
 };
 
