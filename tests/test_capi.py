@@ -66,6 +66,24 @@ def test_load_refuses_other_files_before_device_work(lgmod, tmp_path):
     junk.write_bytes(b"not a hierarchy file at all" * 10)
     assert lib.lg_load(str(junk).encode(), None, C.byref(h)) == lgmod.ERR_INVALID
     assert not h.value
+    # the right magic with a wrong version, options layout or level count
+    import struct
+
+    magic = b"LGHIERF1"
+    opts_size = C.sizeof(lgmod.Options)
+    good_opts = bytes(opts_size)
+    cases = [
+        magic + struct.pack("<II", 2, opts_size),                                   # version
+        magic + struct.pack("<II", 1, opts_size + 8),                               # options layout
+        magic + struct.pack("<II", 1, opts_size) + good_opts + struct.pack("<iqqdi", 0, 10, 50, 1.0, -1),  # no levels
+        magic + struct.pack("<II", 1, opts_size) + good_opts + struct.pack("<iqqdi", 3, 0, 50, 1.0, -1),   # n = 0
+        magic + struct.pack("<II", 1, opts_size) + good_opts,                       # truncated header
+    ]
+    for q, data in enumerate(cases):
+        bad = tmp_path / f"bad{q}.lgh"
+        bad.write_bytes(data)
+        assert lib.lg_load(str(bad).encode(), None, C.byref(h)) == lgmod.ERR_INVALID, q
+        assert not h.value
 
 
 def test_oracle_and_cuda_path_share_no_code():
