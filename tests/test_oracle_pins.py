@@ -577,3 +577,31 @@ def test_elim_rounds_stop_at_the_gate(oracle, inputs, name):
     h1 = oracle.Hierarchy(g, oracle.default_opts(elim_rounds=1))
     hd = oracle.Hierarchy(g)
     assert [h1.level(l).a.n for l in range(h1.nlevels)] == [hd.level(l).a.n for l in range(hd.nlevels)]
+
+
+def test_setup_is_a_function_of_the_graph_and_the_seed(oracle, inputs):
+    """Two setups of one graph with one seed give the same hierarchy, bit for
+    bit (every random choice comes from the counter-based streams); another
+    seed changes the random choices (elimination hashes, test vectors)."""
+    g = inputs.chung_lu(3000, m_target=15000, seed=11)
+
+    def levels(seed):
+        o = oracle.default_opts()
+        o.seed = seed
+        H = oracle.Hierarchy(g, o)
+        out = []
+        for l in range(H.nlevels):
+            L = H.level(l)
+            out.append((L.kind, L.a.rowptr.copy(), L.a.col.copy(), L.a.w.copy(),
+                        None if L.map is None else L.map.copy(), L.lam))
+        return out
+
+    a, b, c = levels(0x5EED), levels(0x5EED), levels(12345)
+    assert len(a) == len(b)
+    for x, y in zip(a, b):
+        assert x[0] == y[0] and x[5] == y[5]
+        for p, q in zip(x[1:5], y[1:5]):
+            assert (p is None and q is None) or np.array_equal(p, q)
+    differs = len(a) != len(c) or any(
+        x[4] is not None and y[4] is not None and not np.array_equal(x[4], y[4]) for x, y in zip(a, c))
+    assert differs
