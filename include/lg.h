@@ -321,7 +321,11 @@ int lg_vcycle_batch(lg_handle h, int32_t k, const double* F, int64_t ldf, double
  * can be checked on its own. The graph must satisfy the conventions above
  * (not re-validated). They synchronise `stream` before returning. */
 
-/* y = L x (difference form: y_i = sum_j w_ij (x_i - x_j), Section 2.1). */
+/* y = L x (Section 2.1) in FP64, in the standard form the FP64 passes of the
+ * solve use: y_i = d_i x_i - sum_j w_ij x_j with d_i = sum_j w_ij computed
+ * from w first. (The FP32 passes of an FP32-hierarchy solve use the
+ * difference form sum_j w_ij (x_i - x_j) instead; both equal (L x)_i in
+ * exact arithmetic.) */
 int lg_laplacian_apply(int64_t n, const int64_t* rowptr, const int32_t* col, const double* w,
                        const double* x, double* y, void* stream);
 
@@ -365,8 +369,11 @@ int lg_aggregate(int64_t n, const int64_t* rowptr, const int32_t* col, const dou
  * array of the library, sized for at most 1048576 vertices (8 MiB held on
  * every device that uses the library, until the process exits). Larger n
  * returns LG_ERR_INVALID with a message in lg_last_error_detail().
+ *  - The call reads the count back and synchronises `stream` before it
+ *    returns, so it cannot be captured into a CUDA graph.
  *  - The first call on a device looks up the array's device address on that
- *    device; make that first call before any stream capture.
+ *    device. `stream` must belong to the current device (a stream of another
+ *    device returns LG_ERR_INVALID).
  *  - Every call shares the array: calls whose work overlaps on the GPU (two
  *    host threads, or two streams) race and give wrong results. Serialise
  *    them, e.g. on one stream.

@@ -337,6 +337,34 @@ int lg_solve_many(int32_t count, const lg_handle* hs, const double* const* b, do
     std::sort(sorted.begin(), sorted.end());
     if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end()) return LG_ERR_INVALID;
   }
+  {
+    // the outputs x[g] (n_g doubles each) must not overlap one another nor
+    // another graph's input b[g']: the packed kernel writes every x while
+    // other blocks read their b. Inputs may share memory with each other
+    // (they are only read), and a graph's own b may be its x.
+    struct Span {
+      uintptr_t beg, end;
+      int g;
+      bool operator<(const Span& o) const { return beg < o.beg; }
+    };
+    std::vector<Span> xs((size_t)count);
+    for (int g = 0; g < count; ++g) {
+      const uintptr_t a = reinterpret_cast<uintptr_t>(x[g]);
+      xs[g] = Span{a, a + sizeof(double) * (uintptr_t)v[g]->levels[0]->n, g};
+    }
+    std::sort(xs.begin(), xs.end());
+    for (int g = 1; g < count; ++g)
+      if (xs[g].beg < xs[g - 1].end) return LG_ERR_INVALID;
+    for (int g = 0; g < count; ++g) {
+      const uintptr_t a = reinterpret_cast<uintptr_t>(b[g]);
+      const uintptr_t e = a + sizeof(double) * (uintptr_t)v[g]->levels[0]->n;
+      // x spans are disjoint and sorted, so their ends ascend too: walk the
+      // ones that end after a and start before e
+      auto it = std::upper_bound(xs.begin(), xs.end(), a, [](uintptr_t p, const Span& sp) { return p < sp.end; });
+      for (; it != xs.end() && it->beg < e; ++it)
+        if (it->g != g) return LG_ERR_INVALID;
+    }
+  }
   LG_API_BEGIN
   lg::NvtxRange range("lg_solve_many");
   int dev = 0;

@@ -89,13 +89,53 @@ struct Reader {
   }
 };
 
-// Entries of a CSR whose row pointer is on the device (its last value).
-int64_t last_of(const DBuf<int64_t>& rowptr, int64_t rows, cudaStream_t s) {
-  int64_t v = 0;
-  LG_CUDA(cudaMemcpyAsync(&v, rowptr.get() + rows, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  LG_CUDA(cudaStreamSynchronize(s));
-  return v;
+// Range checks of what a file gives: a damaged or hostile file must be
+// refused before any kernel indexes with its arrays. The checks compare
+// values only (each thread reads its own element and the next pointer), so
+// they cannot themselves reach outside the arrays.
+#define LG_IO_STRIDE(i, n) \
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
+
+__global__ void k_io_check_ptr(int64_t rows, int64_t total, const int64_t* __restrict__ p, int* bad) {
+  LG_IO_STRIDE(i, rows + 1) {
+    const int64_t v = p[i];
+    if (v < 0 || v > total || (i == 0 && v != 0) || (i == rows && v != total) || (i < rows && p[i + 1] < v))
+      atomicOr(bad, 1);
+  }
 }
+
+__global__ void k_io_check_range(int64_t count, const int32_t* __restrict__ a, int64_t lo, int64_t hi, int* bad) {
+  LG_IO_STRIDE(i, count) {
+    const int64_t v = a[i];
+    if (v < lo || v >= hi) atomicOr(bad, 1);
+  }
+}
+
+struct Checker {
+  cudaStream_t s;
+  DBuf<int> bad;
+  explicit Checker(cudaStream_t st) : s(st), bad(1, st) {
+    LG_CUDA(cudaMemsetAsync(bad.get(), 0, sizeof(int), s));
+  }
+  // rowptr of `rows` rows: 0 first, `total` last, non-decreasing
+  void ptr(const DBuf<int64_t>& p, int64_t rows, int64_t total) {
+    k_io_check_ptr<<<grid_for(rows + 1, 256, kSMs * 8), 256, 0, s>>>(rows, total, p.get(), bad.get());
+    LG_LAUNCH_CHECK();
+  }
+  // every value in [lo, hi)
+  void range(const DBuf<int32_t>& a, int64_t count, int64_t lo, int64_t hi) {
+    if (count <= 0) return;
+    k_io_check_range<<<grid_for(count, 256, kSMs * 8), 256, 0, s>>>(count, a.get(), lo, hi, bad.get());
+    LG_LAUNCH_CHECK();
+  }
+  // fails with LG_ERR_INVALID if any check so far found a bad value
+  void require(const char* what) {
+    int v = 0;
+    LG_CUDA(cudaMemcpyAsync(&v, bad.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+    LG_CUDA(cudaStreamSynchronize(s));
+    if (v) fail(LG_ERR_INVALID, what);
+  }
+};
 
 // A plan over (rows, entries, rowptr) binned with E entries per lane, as the
 // setup built it (build_row_plan bins with E = 4, the tuner may re-bin).
@@ -212,6 +252,9 @@ void load_hierarchy(Hier& h, const char* path, const lg_options* call_opts) {
   h.dev_err.alloc(1, s);
   LG_CUDA(cudaMemsetAsync(h.dev_err.get(), 0, sizeof(int), s));
   r.arr(h.perm, n0, s, counter);
+  Checker check(s);
+  check.range(h.perm, n0, 0, n0);
+  check.require("hierarchy file: vertex order out of range");
   h.cheb.assign((size_t)nl, Cheb{});
   int64_t expect_n = n0;
   for (int32_t l = 0; l < nl; ++l) {
@@ -236,13 +279,18 @@ void load_hierarchy(Hier& h, const char* path, const lg_options* call_opts) {
     r.arr(L->dinv, L->n, s, counter);
     r.arr(L->w32, L->nnz, s, counter);
     r.arr(L->dinv32, L->n, s, counter);
-    if (last_of(L->rowptr, L->n, s) != L->nnz) fail(LG_ERR_INVALID, "hierarchy file: row pointer");
+    check.ptr(L->rowptr, L->n, L->nnz);
+    check.range(L->col, L->nnz, 0, L->n);
+    check.require("hierarchy file: operator row pointer or column out of range");
     plan_with(L->plan, L->n, L->nnz, L->rowptr.get(), E, s, counter);
     if (L->kind == LG_LEVEL_AGG) {
       r.arr(L->agg, L->n, s, counter);
       r.arr(L->mem_ptr, L->nc + 1, s, counter);
       r.arr(L->mem, L->n, s, counter);
-      if (last_of(L->mem_ptr, L->nc, s) != L->n) fail(LG_ERR_INVALID, "hierarchy file: member lists");
+      check.range(L->agg, L->n, 0, L->nc);
+      check.ptr(L->mem_ptr, L->nc, L->n);
+      check.range(L->mem, L->n, 0, L->n);
+      check.require("hierarchy file: aggregates or member lists out of range");
       plan_with(L->mem_plan, L->nc, L->n, L->mem_ptr.get(), r.val<int32_t>(), s, counter);
       const int64_t lpn = r.val<int64_t>();
       if (lpn < 0 || lpn > L->nnz) fail(LG_ERR_INVALID, "hierarchy file: W size");
@@ -253,7 +301,9 @@ void load_hierarchy(Hier& h, const char* path, const lg_options* call_opts) {
         r.arr(L->lp_w, lpn, s, counter);
         r.arr(L->lp_w32, lpn, s, counter);
         r.arr(L->lp_d, L->n, s, counter);
-        if (last_of(L->lp_ptr, L->n, s) != lpn) fail(LG_ERR_INVALID, "hierarchy file: W row pointer");
+        check.ptr(L->lp_ptr, L->n, lpn);
+        check.range(L->lp_col, lpn, 0, L->nc);
+        check.require("hierarchy file: W row pointer or aggregate id out of range");
         plan_with(L->lp_plan, L->n, lpn, L->lp_ptr.get(), r.val<int32_t>(), s, counter);
       }
     } else if (L->kind == LG_LEVEL_ELIM) {
@@ -261,11 +311,15 @@ void load_hierarchy(Hier& h, const char* path, const lg_options* call_opts) {
       r.arr(L->cfine, L->nc, s, counter);
       r.arr(L->pt_ptr, L->nc + 1, s, counter);
       const int64_t npt = r.val<int64_t>();
-      if (npt < 0 || npt > L->nnz || last_of(L->pt_ptr, L->nc, s) != npt)
-        fail(LG_ERR_INVALID, "hierarchy file: elimination rows");
+      if (npt < 0 || npt > L->nnz) fail(LG_ERR_INVALID, "hierarchy file: elimination rows");
       r.arr(L->pt_f, npt, s, counter);
       r.arr(L->pt_coef, npt, s, counter);
       r.arr(L->pt_coef32, npt, s, counter);
+      check.range(L->cmap, L->n, -1, L->nc);
+      check.range(L->cfine, L->nc, 0, L->n);
+      check.ptr(L->pt_ptr, L->nc, npt);
+      check.range(L->pt_f, npt, 0, L->n);
+      check.require("hierarchy file: elimination maps out of range");
       plan_with(L->pt_plan, L->nc, npt, L->pt_ptr.get(), r.val<int32_t>(), s, counter);
     } else {
       if (L->n > h.opts.max_coarse_n && L->n > 4096) fail(LG_ERR_INVALID, "hierarchy file: coarsest size");

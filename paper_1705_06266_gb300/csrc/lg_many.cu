@@ -772,13 +772,23 @@ static PinnedStage g_pin;
 int solve_many(int count, Hier* const* hs, const double* const* b, double* const* x, const bool* b_dev,
                const bool* x_dev, double tol, lg_info* infos) {
   cudaStream_t s = hs[0]->stream;
+  // every event of the call is destroyed on every exit, error paths included
+  struct Events {
+    std::vector<cudaEvent_t> v;
+    cudaEvent_t make(unsigned flags) {
+      cudaEvent_t e = nullptr;
+      LG_CUDA(cudaEventCreateWithFlags(&e, flags));
+      v.push_back(e);
+      return e;
+    }
+    ~Events() {
+      for (auto e : v) cudaEventDestroy(e);
+    }
+  } events;
   // run after whatever the other handles' streams hold
-  std::vector<cudaEvent_t> evs;
   for (int g = 1; g < count; ++g) {
     if (hs[g]->stream == s) continue;
-    cudaEvent_t e;
-    LG_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    evs.push_back(e);
+    cudaEvent_t e = events.make(cudaEventDisableTiming);
     LG_CUDA(cudaEventRecord(e, hs[g]->stream));
     LG_CUDA(cudaStreamWaitEvent(s, e, 0));
   }
@@ -854,9 +864,7 @@ int solve_many(int count, Hier* const* hs, const double* const* b, double* const
     hg[q] = G;
   }
   LG_CUDA(cudaMemcpyAsync(dst.get(), g_pin.p, total, cudaMemcpyHostToDevice, s));
-  cudaEvent_t e0, e1;
-  LG_CUDA(cudaEventCreate(&e0));
-  LG_CUDA(cudaEventCreate(&e1));
+  cudaEvent_t e0 = events.make(cudaEventDefault), e1 = events.make(cudaEventDefault);
   LG_CUDA(cudaEventRecord(e0, s));
   k_solve_many<<<count, kMT, 0, s>>>(reinterpret_cast<const MGraph*>(dst.get()));
   LG_LAUNCH_CHECK();
@@ -867,9 +875,6 @@ int solve_many(int count, Hier* const* hs, const double* const* b, double* const
     if (!x_dev[g]) std::memcpy(x[g], hvec + off[g], sizeof(double) * hs[g]->levels[0]->n);
   float ms = 0.f;
   LG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  for (auto e : evs) cudaEventDestroy(e);
   int first_bad = LG_OK;
   for (int g = 0; g < count; ++g) {
     const Hier& h = *hs[g];

@@ -95,8 +95,19 @@ extern "C" int lg_elim_select_noalloc(int64_t n, const int64_t* rowptr, const in
     return LG_ERR_INVALID;
   }
   try {
-    const lg::NoAllocAddrs a = lg::noalloc_addrs();
     cudaStream_t s = (cudaStream_t)stream;
+    if (s) {
+      // the scratch address is the current device's: a stream of another
+      // device would run the kernels against the wrong device's array
+      int cur = 0, sdev = 0;
+      LG_CUDA(cudaGetDevice(&cur));
+      LG_CUDA(cudaStreamGetDevice(s, &sdev));
+      if (sdev != cur) {
+        lg::g_last_error = "lg_elim_select_noalloc: stream belongs to another device than the current one";
+        return LG_ERR_INVALID;
+      }
+    }
+    const lg::NoAllocAddrs a = lg::noalloc_addrs();
     const int blocks = lg::grid_for(n, 256, lg::kSMs * 8);
     lg::k_na_hash<<<blocks, 256, 0, s>>>(n, rowptr, max_degree, seed, a.hash, a.count);
     LG_LAUNCH_CHECK();

@@ -101,3 +101,73 @@ def test_solve_log(lgmod, inputs, tmp_path, monkeypatch):
     assert [x["index"] for x in lines[5:]] == [0, 1]
     H.close()
     H2.close()
+
+
+def _level0_offsets(lgmod, data, n0):
+    """Byte offsets of level 0's col values and, on an aggregation level, its
+    agg values in a hierarchy file (the layout lg_save writes: header, vertex
+    order, then the level's sizes and arrays, each array a uint64 count
+    followed by its values). Each count is checked on the way, so a layout
+    misread fails here rather than corrupting the wrong bytes."""
+    import ctypes
+
+    def u64(at):
+        return int(np.frombuffer(data, dtype=np.uint64, count=1, offset=at)[0])
+
+    at = 8 + 4 + 4 + ctypes.sizeof(lgmod.Options) + 4 + 8 + 8 + 8 + 4
+    assert u64(at) == n0
+    at += 8 + 4 * n0                       # vertex order
+    kind = int(np.frombuffer(data, dtype=np.int32, count=1, offset=at)[0])
+    n, nnz, nc = (int(v) for v in np.frombuffer(data, dtype=np.int64, count=3, offset=at + 4))
+    at += 4 + 5 * 8 + 4                    # kind, n, nnz, nc, nf, lambda, binning
+    assert n == n0 and u64(at) == n + 1
+    at += 8 + 8 * (n + 1)                  # rowptr
+    rowptr_at = at - 8 * (n + 1)
+    assert u64(at) == nnz
+    col_at = at + 8
+    at += 8 + 4 * nnz
+    for count, size in ((nnz, 8), (n, 8), (n, 8), (nnz, 4), (n, 4)):  # w, d, dinv, w32, dinv32
+        assert u64(at) == count
+        at += 8 + size * count
+    agg_at = None
+    if kind == lgmod.LEVEL_AGG:
+        assert u64(at) == n
+        agg_at = at + 8
+    return rowptr_at, col_at, agg_at, n, nc
+
+
+def test_out_of_range_indices_refused(lgmod, inputs, tmp_path):
+    """A file whose sizes agree but whose index values point outside their
+    arrays (a flipped byte in a column, an aggregate id, a row pointer) is
+    refused with LG_ERR_INVALID before any solve could index with it. The
+    checks only compare values, so the damaged arrays are never used to
+    address memory."""
+    g = inputs.grid3d(20, 20, 20)  # level 0 is an aggregation level (elimination gated out)
+    H = lgmod.Hierarchy(g)
+    assert H.level_info(0)["kind"] == lgmod.LEVEL_AGG
+    path = tmp_path / "h.lgh"
+    H.save(str(path))
+    data = path.read_bytes()
+    rowptr_at, col_at, agg_at, n, nc = _level0_offsets(lgmod, data, g.n)
+    assert agg_at is not None
+    damages = {
+        "col": (col_at + 4 * 5, np.int32(n + 7)),
+        "col_negative": (col_at + 4 * 11, np.int32(-3)),
+        "agg": (agg_at + 4 * 3, np.int32(nc + 1)),
+        "rowptr_decreasing": (rowptr_at + 8 * 2, np.int64(0)),
+    }
+    good = lgmod.Hierarchy.load(str(path))  # the undamaged file still loads
+    good.close()
+    for name, (at, val) in damages.items():
+        buf = bytearray(data)
+        raw = val.tobytes()
+        buf[at:at + len(raw)] = raw
+        bad = tmp_path / f"{name}.lgh"
+        bad.write_bytes(bytes(buf))
+        with pytest.raises(lgmod.LGError) as e:
+            lgmod.Hierarchy.load(str(bad))
+        assert e.value.status == lgmod.ERR_INVALID, name
+        assert "out of range" in str(e.value), name
+    x, info = H.solve(inputs.rhs(g.n, seed=1))
+    assert info.status == lgmod.OK
+    H.close()

@@ -605,3 +605,117 @@ def test_setup_is_a_function_of_the_graph_and_the_seed(oracle, inputs):
     differs = len(a) != len(c) or any(
         x[4] is not None and y[4] is not None and not np.array_equal(x[4], y[4]) for x, y in zip(a, c))
     assert differs
+
+
+# ---------------------------------------------------------------------------
+# The composition of the cycle (Algorithm 1 with Sections 3.4-3.6), pinned
+# against a dense two-grid operator assembled here in numpy from its parts:
+# the degree-2 Chebyshev smoother as a matrix polynomial (numpy's Chebyshev
+# basis), R = P^T from the aggregates, the dense Galerkin product P^T L P and
+# numpy's pseudo-inverse of it. Only the aggregates and the eigenvalue
+# estimate come from the oracle (both pinned on their own above).
+# ---------------------------------------------------------------------------
+def _cheb_smoother(L, lam, lo=0.3, hi=1.1, degree=2):
+    """S with x = S f the Chebyshev smoother from x = 0 on D^-1 L over
+    [lo lam, hi lam]: the error after `degree` steps is r(D^-1 L) e with
+    r(t) = T_k((theta - t) / delta) / T_k(theta / delta), so the iterate is
+    s(D^-1 L) D^-1 f with s(t) = (1 - r(t)) / t, a polynomial since r(0) = 1."""
+    from numpy.polynomial import Chebyshev, Polynomial
+
+    a, b = lo * lam, hi * lam
+    theta, delta = (b + a) / 2, (b - a) / 2
+    Tk = Chebyshev.basis(degree).convert(kind=Polynomial)
+    u = Polynomial([theta / delta, -1.0 / delta])          # t -> (theta - t) / delta
+    r = Tk(u) / Tk(theta / delta)
+    s, rem = divmod(Polynomial([1.0]) - r, Polynomial([0.0, 1.0]))
+    assert np.allclose(rem.coef, 0.0, atol=1e-12 * np.abs(r.coef).max())
+    Dinv = np.diag(1.0 / np.diag(L))
+    A = Dinv @ L
+    S = np.zeros_like(L)
+    Ak = np.eye(L.shape[0])
+    for c in s.coef:
+        S += c * Ak
+        Ak = Ak @ A
+    return S @ Dinv
+
+
+def _agg_two_grid(L, agg, nc, lam, coarse):
+    """x = M f for one aggregation level over a coarse solve `coarse`:
+    pre-smooth, restrict the residual by R = P^T, coarse solve, prolong,
+    post-smooth from the current x."""
+    n = L.shape[0]
+    P = np.zeros((n, nc))
+    P[np.arange(n), agg] = 1.0
+    S = _cheb_smoother(L, lam)
+
+    def M(f):
+        x = S @ f
+        xc = coarse(P.T @ (f - L @ x))
+        x = x + P @ xc
+        return x + S @ (f - L @ x)
+
+    return M, P
+
+
+def _pinv_solve(Lc):
+    # the Laplacian of a connected graph has one zero eigenvalue; rounding
+    # leaves it at ~1e-16 of the largest, so the cut-off drops it explicitly
+    Lp = np.linalg.pinv(Lc, rcond=1e-10, hermitian=True)
+    return lambda fc: Lp @ fc
+
+
+@pytest.mark.parametrize("name", ["grid2d_16", "random_150_weighted"])
+def test_vcycle_equals_dense_two_grid(oracle, inputs, name):
+    g = inputs.grid2d(16, 16) if name == "grid2d_16" else inputs.random_graph(150, 6, seed=21, weights="uniform")
+    h = oracle.Hierarchy(g, oracle.default_opts(elim_enable=0))
+    assert [h.level(l).kind for l in range(h.nlevels)] == [oracle.AGG, oracle.COARSEST]
+    lv = h.level(0)
+    L = dense_lap(g)
+    P = np.zeros((g.n, lv.nc))
+    P[np.arange(g.n), lv.map] = 1.0
+    M, _ = _agg_two_grid(L, lv.map, lv.nc, lv.lam, _pinv_solve(P.T @ L @ P))
+    rng = np.random.default_rng(7)
+    for _ in range(3):
+        f = rng.standard_normal(g.n)
+        f -= f.mean()
+        want = M(f)
+        got = h.vcycle(f)
+        assert np.linalg.norm(got - want) <= 1e-12 * np.linalg.norm(want)
+
+
+def test_vcycle_equals_dense_three_level(oracle, inputs):
+    """An elimination level over an aggregation level over the coarsest: the
+    elimination level's additive form x = Fsmooth(f) + P_e M_agg(P_e^T f)
+    (Section 3.4) with P_e = [L_FF^-1 A_FC ; I] built densely from the
+    eliminated set, the coarse operator as the dense Schur complement."""
+    g = inputs.grid2d(24, 24)  # every vertex a candidate: level 0 eliminates ~1/5
+    h = oracle.Hierarchy(g)
+    kinds = [h.level(l).kind for l in range(h.nlevels)]
+    assert kinds == [oracle.ELIM, oracle.AGG, oracle.COARSEST]
+    L = dense_lap(g)
+    e = h.level(0)
+    F = np.flatnonzero(e.map < 0)
+    C = np.flatnonzero(e.map >= 0)
+    assert np.array_equal(e.map[C], np.arange(len(C)))  # kept vertices numbered in order
+    Pe = np.zeros((g.n, len(C)))
+    Pe[C, e.map[C]] = 1.0
+    dF = np.diag(L)[F]
+    Pe[F] = -L[np.ix_(F, C)] / dF[:, None]
+    Lc = Pe.T @ L @ Pe                                  # = the Schur complement (F independent)
+    a = h.level(1)
+    Pa = np.zeros((len(C), a.nc))
+    Pa[np.arange(len(C)), a.map] = 1.0
+    Magg, _ = _agg_two_grid(Lc, a.map, a.nc, a.lam, _pinv_solve(Pa.T @ Lc @ Pa))
+
+    def M(f):
+        x = Pe @ Magg(Pe.T @ f)
+        x[F] += f[F] / dF
+        return x
+
+    rng = np.random.default_rng(8)
+    for _ in range(3):
+        f = rng.standard_normal(g.n)
+        f -= f.mean()
+        want = M(f)
+        got = h.vcycle(f)
+        assert np.linalg.norm(got - want) <= 1e-12 * np.linalg.norm(want)

@@ -5,7 +5,8 @@ It exists for callers that must not allocate device memory during a call
 cudaMalloc, loops that cannot take an allocation's stall). Its scratch lives
 in a fixed device array shared by all calls, so this file is collected last
 and checks two calls in a row: the second must not see the first one's
-leftovers. Results must equal lg_elim_select bit for bit (integer work).
+leftovers. Results must equal lg_elim_select and the oracle's selection
+(Section 3.4, Algorithm 2) bit for bit (integer work).
 """
 
 import numpy as np
@@ -20,7 +21,7 @@ def dev(torch, a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def test_noalloc_matches_allocating_selection_twice(torch_cuda, lgmod, inputs):
+def test_noalloc_matches_allocating_selection_twice(torch_cuda, lgmod, oracle, inputs):
     torch = torch_cuda
     graphs = [inputs.chung_lu(200000, m_target=1000000, seed=5), inputs.grid2d(300, 300)]
     for g in graphs:  # two calls in a row on different graphs share the scratch
@@ -33,6 +34,9 @@ def test_noalloc_matches_allocating_selection_twice(torch_cuda, lgmod, inputs):
         assert torch.equal(out, ref)
         nf2 = lgmod.lg_elim_select_noalloc(g.n, rp, cl, 4, SEED, out)
         assert nf2 == nf_ref and torch.equal(out, ref)
+        want = oracle.elim_select(g, 4, SEED).astype(np.uint8)
+        np.testing.assert_array_equal(out.cpu().numpy(), want)
+        assert nf == int(want.sum())
 
 
 def test_noalloc_rejects_too_large(torch_cuda, lgmod, inputs):
