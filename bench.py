@@ -1,16 +1,19 @@
 #!/usr/bin/env python
 """Benchmark: nnz/s to a 1e-8 relative residual on one GB300 per rank.
 
-Workload (default): Chung-Lu power-law graph, 1M vertices, expected degrees
-Pareto(2.1) truncated to [1, 50000], 10M sampled edges, weights U[0.5, 1.5],
-largest component kept. A step is one pass of the whole path on that graph:
-hierarchy setup (elimination, strength, aggregation, Galerkin, eigenvalue
-estimates, coarsest pseudo-inverse), then one PCG solve with the FP64 V-cycle
-and one with the FP32 hierarchy, each to ||b - L x|| / ||b|| <= 1e-8 in FP64.
+Workload (default): R-MAT scale 26, edge factor 16 (2^30 sampled edges),
+(a, b, c, d) = (.57, .19, .19, .05), symmetrised, deduplicated, unit weights,
+largest component kept (n = 32.8M, nnz(L) = 2.1e9), generated on the device.
+A step is one pass of the whole path on that graph: hierarchy setup
+(elimination, strength, aggregation, Galerkin, eigenvalue estimates, coarsest
+pseudo-inverse), then one PCG solve with the FP64 V-cycle and one with the
+FP32 hierarchy inside FP64 PCG, each to ||b - L x|| / ||b|| <= 1e-8 in FP64.
 
 value = nnz(L_0) / T_solve(FP64), whole job (summed over ranks, each rank
 solving its own replica; timings are the max over ranks). The FP32-hierarchy
-solve, setup time and setup-inclusive throughput are reported beside it.
+solve, setup time, setup-inclusive throughput and each result's error against
+a 1e-12 solve are reported beside it; the 1M-vertex Chung-Lu graph and the
+64 x 64 grid run as secondary legs with errors against the oracle.
 
 --impl reference times the FP64 oracle on the host cores instead, on a
 bounded sample of the same workload.
@@ -49,7 +52,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["lg", "reference"], default="lg")
-    ap.add_argument("--workload", default="chung_lu_1m")
+    ap.add_argument("--workload", default="rmat_26")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-multi-rhs", action="store_true")
@@ -58,7 +61,7 @@ def parse():
     ap.add_argument("--no-kcycle", action="store_true")
     ap.add_argument("--no-wda", action="store_true")
     ap.add_argument("--no-ordering", action="store_true")
-    ap.add_argument("--no-rmat26", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true")
     ap.add_argument("--no-many", action="store_true")
     ap.add_argument("--many-graphs", type=int, default=608)
     ap.add_argument("--serve-graphs", type=int, default=64)
@@ -185,9 +188,25 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(workload_name, g, b):
+# The bounded sample the oracle is timed on for the R-MAT scale-26 workload:
+# an R-MAT graph of the same recipe (edge factor 16, (a, b, c) = (.57, .19,
+# .19), symmetrised, deduplicated, unit weights, largest component) at scale
+# 20, generated with torch on the host so that both arms time the same graph.
+SAMPLE_SCALE = 20
+
+
+def rmat_sample():
+    import torch
+
+    from paper_1705_06266_gb300 import inputs
+
+    n, rp, cl, w = inputs.rmat_device(SAMPLE_SCALE, seed=1, device="cpu")
+    return inputs.Graph(n, rp.numpy(), cl.numpy(), w.numpy(), name=f"rmat_{SAMPLE_SCALE}_16_host_torch")
+
+
+def cpu_baseline(workload_name, g, b, note=""):
     """The oracle as it stands, single-threaded, on a bounded sample of the
-    workload: the same graph and right-hand side, one solve."""
+    workload: its setup untimed, one FP64 PCG solve to 1e-8 timed."""
     import oracle
 
     oracle.build()
@@ -199,11 +218,20 @@ def cpu_baseline(workload_name, g, b):
     t_solve = time.perf_counter() - t0
     return {
         "value": g.nnz / t_solve, "unit": UNIT, "cores": 1, "kind": "oracle",
-        "sample": f"{workload_name} (n={g.n}, nnz(L)={g.nnz}), one right-hand side: oracle setup "
+        "sample": f"{note}{g.name} (n={g.n}, nnz(L)={g.nnz}), one right-hand side: oracle setup "
                   f"{t_setup:.1f} s untimed, one FP64 PCG solve to 1e-8 timed ({it} iterations, "
                   f"relres {rel:.2e})",
         "solve_s": t_solve, "setup_s": t_setup,
     }
+
+
+def rel_err(x, ref):
+    """Relative 2-norm error of x against ref, both with their means removed
+    (the solution of a Laplacian system is unique up to a constant)."""
+    x = np.asarray(x, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    d = (x - x.mean()) - (ref - ref.mean())
+    return float(np.linalg.norm(d) / np.linalg.norm(ref - ref.mean()))
 
 
 _GRAPHS = {}
@@ -255,15 +283,15 @@ def multi_rhs_leg(lg, inputs, torch, dev, k):
     return out
 
 
-def kcycle_leg(lg, inputs, torch, dev, g_main, b_main):
+def kcycle_leg(lg, inputs, torch, dev):
     """The K-cycle (Section 3.7) beside the V-cycle: single right-hand-side
-    solves to 1e-8 from device-resident b, in both precisions, on the main
-    workload and on the 128^3 grid (where the V-cycle needs many iterations)."""
+    solves to 1e-8 from device-resident b, in both precisions, on the 1M
+    Chung-Lu graph and on the 128^3 grid (where the V-cycle needs many
+    iterations)."""
     out = {}
-    for name, g, b in (("chung_lu_1m", g_main, b_main), ("grid3d_128", None, None)):
-        if g is None:
-            g = workload(inputs, name)
-            b = inputs.rhs(g.n, seed=2)
+    for name in ("chung_lu_1m", "grid3d_128"):
+        g = workload(inputs, name)
+        b = inputs.rhs(g.n, seed=2)
         bd = torch.from_numpy(b).to(dev)
         xd = torch.zeros_like(bd)
         torch.cuda.synchronize()
@@ -344,40 +372,54 @@ def ordering_leg(lg, torch, dev, graphs):
     return out
 
 
-def rmat26_leg(lg, inputs, torch, dev):
-    """R-MAT scale 26 (edge factor 16, (a,b,c) = (.57,.19,.19), unit weights,
-    largest component), generated on the device: the FP32 hierarchy inside
-    FP64 PCG against the plain FP64 solve, 1e-8, device-resident b."""
-    try:
-        t0 = time.perf_counter()
-        n, rp, cl, w = inputs.rmat_device(26, seed=1, device=str(dev))
-        gen_s = time.perf_counter() - t0
-        nnz = int(cl.numel()) + n
-        torch.cuda.synchronize()
-        torch.cuda.empty_cache()
-        h = lg.lg_setup(n, rp, cl, w, lg.options())
-        hb, _ = lg.lg_hier_bytes(h)
-        del rp, cl, w
-        torch.cuda.empty_cache()
-        b = torch.from_numpy(inputs.rhs(n, seed=2)).to(dev)
-        x = torch.zeros_like(b)
-        torch.cuda.synchronize()
-        out = {"n": n, "nnz": nnz, "generate_s": gen_s, "setup_ms": lg.lg_hier_info(h).setup_ms,
-               "levels": lg.lg_hier_info(h).levels, "hierarchy_bytes": hb}
-        for tag, prec in (("fp64", lg.FP64), ("fp32", lg.FP32_HIER)):
-            lg.lg_set_precision(h, prec)
-            lg.lg_solve(h, b, x, TOL)
-            inf = lg.lg_solve(h, b, x, TOL)
-            out[tag] = {"solve_ms": inf.solve_ms, "iterations": inf.iterations, "relres": inf.relres,
-                        "nnz_per_s": nnz / (inf.solve_ms * 1e-3)}
-        out["fp32_speedup"] = out["fp64"]["solve_ms"] / out["fp32"]["solve_ms"]
+def secondary_leg(lg, inputs, torch, dev, name, flush, oracle_ref):
+    """Another configuration of the metric: setup, then FP64 and FP32-hierarchy
+    solves to 1e-8 from device-resident b (median of 3, L2 flushed before
+    each), with each result's error against the oracle's solution: the dense
+    direct solve on the 64 x 64 grid, the oracle's own PCG to 1e-12 on larger
+    graphs."""
+    g = workload(inputs, name)
+    b = inputs.rhs(g.n, seed=2)
+    rp, cl, w = (torch.from_numpy(a).to(dev) for a in (g.rowptr, g.col, g.w))
+    bd = torch.from_numpy(b).to(dev)
+    xd = torch.zeros_like(bd)
+    torch.cuda.synchronize()
+    out = {"n": g.n, "nnz": g.nnz}
+    setups = []
+    for _ in range(3):
+        flush.fill_(1.0)
+        h = lg.lg_setup(g.n, rp, cl, w, lg.options())
+        setups.append(lg.lg_hier_info(h).setup_ms)
         lg.lg_destroy(h)
-        del b, x
-        torch.cuda.empty_cache()
-        return out
-    except Exception as e:  # report, do not lose the rest of the line
-        torch.cuda.empty_cache()
-        return {"error": f"{type(e).__name__}: {e}"[:300]}
+    out["setup_ms"] = sorted(setups)[1]
+    h = lg.lg_setup(g.n, rp, cl, w, lg.options())
+    xs = {}
+    for tag, prec in (("fp64", lg.FP64), ("fp32", lg.FP32_HIER)):
+        lg.lg_set_precision(h, prec)
+        lg.lg_solve(h, bd, xd, TOL)  # warm-up (graph capture)
+        runs = []
+        for _ in range(3):
+            flush.fill_(2.0)
+            runs.append(lg.lg_solve(h, bd, xd, TOL))
+        inf = sorted(runs, key=lambda i: i.solve_ms)[1]
+        xs[tag] = xd.cpu().numpy()
+        out[tag] = {"solve_ms": inf.solve_ms, "iterations": inf.iterations, "relres": inf.relres,
+                    "nnz_per_s": g.nnz / (inf.solve_ms * 1e-3)}
+    out["fp32_speedup"] = out["fp64"]["solve_ms"] / out["fp32"]["solve_ms"]
+    lg.lg_destroy(h)
+    if oracle_ref:
+        import oracle
+
+        oracle.build()
+        if g.n <= 4096:
+            ref = oracle.dense_solve(g, b)
+            out["x_reference"] = "oracle dense direct solve (pinv of L)"
+        else:
+            ref, st, it, rel = oracle.Hierarchy(g).pcg(b, tol=1e-12, maxit=1000)
+            out["x_reference"] = f"oracle FP64 PCG to 1e-12 ({it} iterations, relres {rel:.1e})"
+        for tag in xs:
+            out[tag]["x_err_vs_oracle"] = rel_err(xs[tag], ref)
+    return out
 
 
 def serve_leg(lg, inputs, args):
@@ -496,13 +538,23 @@ def many_leg(lg, inputs, count):
 
 
 def run_reference(args, world, rank):
+    """The oracle as it stands on the host cores, on a bounded sample of the
+    workload (each step one FP64 PCG solve to 1e-8, the oracle's setup
+    untimed); under torchrun only rank 0 runs it."""
     if rank != 0:
         return
     import oracle
     from paper_1705_06266_gb300 import inputs
 
     oracle.build()
-    g = inputs.workload(args.workload)
+    if args.workload == "rmat_26":
+        g = rmat_sample()
+        note = (f"R-MAT scale {SAMPLE_SCALE} of the scale-26 recipe (edge factor 16, a=.57 b=.19 c=.19, "
+                f"symmetrised, deduplicated, unit weights, largest component; torch on the host) as the "
+                f"bounded sample: ")
+    else:
+        g = inputs.workload(args.workload)
+        note = ""
     b = inputs.rhs(g.n, seed=2)
     h = oracle.Hierarchy(g)
     times = []
@@ -521,11 +573,34 @@ def run_reference(args, world, rank):
         "config": {"workload": args.workload, "rhs": 1, "tol": TOL, "precision": "fp64",
                    "parallelism": "replicas"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{args.workload} (n={g.n}, nnz(L)={g.nnz}); each step one FP64 PCG solve "
+                         "sample": f"{note}{g.name} (n={g.n}, nnz(L)={g.nnz}); each step one FP64 PCG solve "
                                    f"to 1e-8 ({it} iterations) on one host core, oracle setup untimed"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def load_main(args, inputs, torch, dev):
+    """The main workload on the device: (description, n, nnz, rowptr, col, w,
+    host b, host graph or None). R-MAT scale 26 is generated on the device
+    (host generation of 2^30 sampled edges would not fit the bench's time)."""
+    if args.workload == "rmat_26":
+        t0 = time.perf_counter()
+        n, rp, cl, w = inputs.rmat_device(26, seed=1, device=str(dev))
+        torch.cuda.synchronize()
+        gen_s = time.perf_counter() - t0
+        desc = {"graph": "rmat_26_16", "generate_s": gen_s,
+                "recipe": "R-MAT scale 26, edge factor 16 (2^30 sampled edges), a=.57 b=.19 c=.19 d=.05, "
+                          "symmetrised, deduplicated, self-loops dropped, unit weights, largest component "
+                          "kept; generated on the device (seed 1)"}
+        g = None
+    else:
+        g = workload(inputs, args.workload)
+        n = g.n
+        rp, cl, w = (torch.from_numpy(a).to(dev) for a in (g.rowptr, g.col, g.w))
+        desc = {"graph": g.name}
+    nnz = int(cl.numel()) + n
+    return desc, n, nnz, rp, cl, w, inputs.rhs(n, seed=2), g
 
 
 def main():
@@ -542,17 +617,14 @@ def main():
     _build.build()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    g = inputs.workload(args.workload)
-    b = inputs.rhs(g.n, seed=2)
+    desc, n, nnz, rp, cl, w, b, g_host = load_main(args, inputs, torch, dev)
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
     with torch.cuda.stream(stream):
-        rp = torch.from_numpy(g.rowptr).to(dev)
-        cl = torch.from_numpy(g.col).to(dev)
-        w = torch.from_numpy(g.w).to(dev)
         bd = torch.from_numpy(b).to(dev)
-        x64 = torch.zeros(g.n, dtype=torch.float64, device=dev)
-        x32 = torch.zeros(g.n, dtype=torch.float64, device=dev)
+        x64 = torch.zeros(n, dtype=torch.float64, device=dev)
+        x32 = torch.zeros(n, dtype=torch.float64, device=dev)
         opts = lg.options(stream=stream.cuda_stream)
 
         def per_level(h, nlev):
@@ -565,14 +637,14 @@ def main():
 
         def step(profile):
             flush.fill_(1.0)
-            h = lg.lg_setup(g.n, rp, cl, w, opts)
+            h = lg.lg_setup(n, rp, cl, w, opts)
             hi = lg.lg_hier_info(h)
             res = {}
             for tag, prec, x in (("fp64", lg.FP64, x64), ("fp32", lg.FP32_HIER, x32)):
                 lg.lg_set_precision(h, prec)
                 flush.fill_(2.0)
                 res[tag] = lg.lg_solve(h, bd, x, TOL)  # graph-driven, unprofiled: the timed solve
-                if profile:  # the same solve again with every operator pass bracketed by events
+                if profile and tag == "fp64":  # the same solve again with every operator pass bracketed by events
                     lg.lg_profile(h, True)
                     flush.fill_(3.0)
                     lg.lg_solve(h, bd, x, TOL)
@@ -581,7 +653,7 @@ def main():
             nb = lg.lg_hier_bytes(h)
             lv = [dict(lg.lg_level_info(h, l), **lg.lg_level_plan(h, l)) for l in range(hi.levels)]
             lg.lg_destroy(h)
-            return hi, res["fp64"], res["fp32"], res.get("fp64_prof"), nb, res.get("fp32_prof"), lv
+            return hi, res["fp64"], res["fp32"], res.get("fp64_prof"), nb, lv
 
         for _ in range(args.warmup):
             step(False)
@@ -604,26 +676,52 @@ def main():
         launches = lg.lg_kernel_launches() - launches0
         step_ms = ev0.elapsed_time(ev1) / args.steps
 
+        # After the timed region, on one more (bitwise identical) hierarchy:
+        # the FP32 per-level pass table, each result's error against an FP64
+        # solve to 1e-12, and the end-to-end solves from host buffers.
+        h = lg.lg_setup(n, rp, cl, w, opts)
+        nlev = lg.lg_hier_info(h).levels
+        lg.lg_set_precision(h, lg.FP32_HIER)
+        lg.lg_profile(h, True)
+        flush.fill_(3.0)
+        lg.lg_solve(h, bd, x32, TOL)
+        prof32 = per_level(h, nlev)
+        lg.lg_profile(h, False)
+        lg.lg_solve(h, bd, x32, TOL)
+        lg.lg_set_precision(h, lg.FP64)
+        lg.lg_solve(h, bd, x64, TOL)
+        xref = torch.zeros_like(x64)
+        ref_info = lg.lg_solve(h, bd, xref, 1e-12, check=False)
+        errs = {"fp64": rel_err(x64.cpu().numpy(), xref.cpu().numpy()),
+                "fp32": rel_err(x32.cpu().numpy(), xref.cpu().numpy())}
+        del xref
+
         # end to end through the C ABI with host buffers (pinned), per step:
-        # H2D of b, the solve, D2H of x, all inside the timed call.
-        h = lg.lg_setup(g.n, g.rowptr, g.col, g.w, lg.options())
+        # H2D of b, the solve, D2H of x, all inside the timed call
         bh = torch.from_numpy(b).pin_memory()
-        xh = torch.zeros(g.n, dtype=torch.float64).pin_memory()
+        xh = torch.zeros(n, dtype=torch.float64).pin_memory()
         bnp, xnp = bh.numpy(), xh.numpy()
-        lg.lg_solve(h, bnp, xnp, TOL)
-        e2e_t = []
-        for _ in range(args.e2e_steps):
-            t1 = time.perf_counter()
+        e2e = {}
+        for tag, prec in (("fp64", lg.FP64), ("fp32", lg.FP32_HIER)):
+            lg.lg_set_precision(h, prec)
             lg.lg_solve(h, bnp, xnp, TOL)
-            e2e_t.append(time.perf_counter() - t1)
-        t1 = time.perf_counter()
-        h2 = lg.lg_setup(g.n, g.rowptr, g.col, g.w, lg.options())
-        setup_e2e = time.perf_counter() - t1
-        lg.lg_destroy(h2)
+            ts = []
+            for _ in range(args.e2e_steps):
+                t1 = time.perf_counter()
+                lg.lg_solve(h, bnp, xnp, TOL)
+                ts.append(time.perf_counter() - t1)
+            e2e[tag] = sum(ts) / len(ts)
         lg.lg_destroy(h)
+        del bh, xh
+        setup_e2e = None
+        if g_host is not None:
+            t1 = time.perf_counter()
+            h2 = lg.lg_setup(g_host.n, g_host.rowptr, g_host.col, g_host.w, lg.options())
+            setup_e2e = time.perf_counter() - t1
+            lg.lg_destroy(h2)
 
         # the same solves with post-smoothing from f - L x instead of the W = L P pass
-        h0 = lg.lg_setup(g.n, rp, cl, w, lg.options(stream=stream.cuda_stream, lp_residual=0))
+        h0 = lg.lg_setup(n, rp, cl, w, lg.options(stream=stream.cuda_stream, lp_residual=0))
         direct = {}
         for tag, prec, x in (("fp64", lg.FP64, x64), ("fp32", lg.FP32_HIER, x32)):
             lg.lg_set_precision(h0, prec)
@@ -633,27 +731,37 @@ def main():
                 ms.append(lg.lg_solve(h0, bd, x, TOL).solve_ms)
             direct[tag] = sorted(ms)[1]
         lg.lg_destroy(h0)
+        stream.synchronize()
+    del rp, cl, w, bd, x64, x32
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
 
-        # the other two workloads the metric names, after the timed region
-        multi = None if args.no_multi_rhs else multi_rhs_leg(lg, inputs, torch, dev, args.multi_rhs_k)
-        kcyc = None if args.no_kcycle else kcycle_leg(lg, inputs, torch, dev, g, b)
-        wda = None if args.no_wda else wda_leg(lg, inputs, torch, dev)
-        r26 = None if args.no_rmat26 else rmat26_leg(lg, inputs, torch, dev)
-        order = None
-        if not args.no_ordering:
-            g_rmat = workload(inputs, "rmat_20")
-            order = ordering_leg(lg, torch, dev, [(args.workload, g, b),
-                                                  ("rmat_20", g_rmat, inputs.rhs(g_rmat.n, seed=2))])
-        serve = None if args.no_serve else serve_leg(lg, inputs, args)
-        many = None if args.no_many else many_leg(lg, inputs, args.many_graphs)
+    # the other configurations the metric names, after the timed region
+    oracle_ref = world == 1 and not args.no_cpu_baseline
+    second = {}
+    if not args.no_secondary:
+        for name in ("chung_lu_1m", "grid2d_64"):
+            if name != args.workload:
+                second[name] = secondary_leg(lg, inputs, torch, dev, name, flush, oracle_ref)
+    multi = None if args.no_multi_rhs else multi_rhs_leg(lg, inputs, torch, dev, args.multi_rhs_k)
+    kcyc = None if args.no_kcycle else kcycle_leg(lg, inputs, torch, dev)
+    wda = None if args.no_wda else wda_leg(lg, inputs, torch, dev)
+    order = None
+    if not args.no_ordering:
+        graphs = []
+        for name in ("chung_lu_1m", "rmat_20"):
+            gg = workload(inputs, name)
+            graphs.append((name, gg, inputs.rhs(gg.n, seed=2)))
+        order = ordering_leg(lg, torch, dev, graphs)
+    serve = None if args.no_serve else serve_leg(lg, inputs, args)
+    many = None if args.no_many else many_leg(lg, inputs, args.many_graphs)
+    del flush
 
     setup_ms = sum(r[0].setup_ms for r in recs) / len(recs)
     solve64_ms = sum(r[1].solve_ms for r in recs) / len(recs)
     solve32_ms = sum(r[2].solve_ms for r in recs) / len(recs)
-    e2e_s = sum(e2e_t) / len(e2e_t)
-    mx = allreduce_max([step_ms, setup_ms, solve64_ms, solve32_ms, e2e_s], world)
-    step_ms, setup_ms, solve64_ms, solve32_ms, e2e_s = mx
-    nnz = g.nnz
+    mx = allreduce_max([step_ms, setup_ms, solve64_ms, solve32_ms, e2e["fp64"], e2e["fp32"]], world)
+    step_ms, setup_ms, solve64_ms, solve32_ms, e2e64_s, e2e32_s = mx
     value = world * nnz / (solve64_ms * 1e-3)
 
     # roofline of the dominant kernel: the operator row pass of the level with the most device time
@@ -676,19 +784,26 @@ def main():
     # per-level operator-pass table, both precisions (ms per solve, GB/s)
     levels = []
     for l in range(nlev):
-        row = dict(recs[-1][6][l])
-        for tag, idx in (("fp64", 3), ("fp32", 5)):
-            ms = sum(r[idx][l][0] for r in recs) / len(recs)
-            by = sum(r[idx][l][1] for r in recs) / len(recs)
-            la = sum(r[idx][l][2] for r in recs) / len(recs)
-            row[f"{tag}_ms_per_solve"] = ms
-            row[f"{tag}_launches_per_solve"] = la
-            row[f"{tag}_gbs"] = by / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
-            wms = sum(r[idx][nlev + l][0] for r in recs) / len(recs)
-            wby = sum(r[idx][nlev + l][1] for r in recs) / len(recs)
-            if wms > 0:
-                row[f"{tag}_w_pass_ms_per_solve"] = wms
-                row[f"{tag}_w_pass_gbs"] = wby / (wms * 1e-3) / 1e9
+        row = dict(recs[-1][5][l])
+        ms = sum(r[3][l][0] for r in recs) / len(recs)
+        by = sum(r[3][l][1] for r in recs) / len(recs)
+        la = sum(r[3][l][2] for r in recs) / len(recs)
+        row["fp64_ms_per_solve"] = ms
+        row["fp64_launches_per_solve"] = la
+        row["fp64_gbs"] = by / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+        wms = sum(r[3][nlev + l][0] for r in recs) / len(recs)
+        wby = sum(r[3][nlev + l][1] for r in recs) / len(recs)
+        if wms > 0:
+            row["fp64_w_pass_ms_per_solve"] = wms
+            row["fp64_w_pass_gbs"] = wby / (wms * 1e-3) / 1e9
+        ms, by, la = prof32[l]
+        row["fp32_ms_per_solve"] = ms
+        row["fp32_launches_per_solve"] = la
+        row["fp32_gbs"] = by / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+        wms, wby, _ = prof32[nlev + l]
+        if wms > 0:
+            row["fp32_w_pass_ms_per_solve"] = wms
+            row["fp32_w_pass_gbs"] = wby / (wms * 1e-3) / 1e9
         levels.append(row)
 
     if rank != 0:
@@ -697,13 +812,12 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "graph": g.name, "n": g.n, "nnz": nnz, "rhs": 1, "tol": TOL,
-                   "precision": "fp64 (FP32-hierarchy solve reported in fp32_hier)",
-                   "step": "setup; FP64 solve; FP64 solve with per-pass events; FP32-hier solve; "
-                           "FP32-hier solve with per-pass events (value and fp32_hier from the solves "
-                           "without events)",
-                   "l2": "flushed (512 MiB write) before setup and before each solve",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "config": dict({"workload": args.workload, "n": n, "nnz": nnz, "rhs": 1, "tol": TOL,
+                        "precision": "fp64 (FP32-hierarchy solve reported in fp32_hier)",
+                        "step": "setup; FP64 solve; FP64 solve with per-pass events; FP32-hier solve "
+                                "(value and fp32_hier from the solves without events)",
+                        "l2": "flushed (512 MiB write) before setup and before each solve",
+                        "parallelism": "replicas" if world > 1 else "single GPU"}, **desc),
         "solve_ms": solve64_ms, "setup_ms": setup_ms,
         "iterations": i64.iterations, "relres": i64.relres, "levels": i64.levels,
         "op_complexity": recs[-1][0].op_complexity,
@@ -714,12 +828,16 @@ def main():
                                 "over L from f - L x (lp_residual = 0, median of 3 solves)"},
         "fp32_hier": {"value": world * nnz / (solve32_ms * 1e-3), "solve_ms": solve32_ms,
                       "iterations": i32.iterations, "relres": i32.relres,
-                      "speedup_vs_fp64": solve64_ms / solve32_ms},
+                      "speedup_vs_fp64": solve64_ms / solve32_ms, "x_err": errs["fp32"]},
+        "x_err": {"fp64": errs["fp64"], "fp32": errs["fp32"],
+                  "reference": f"FP64 solve of the same hierarchy to 1e-12 ({ref_info.iterations} iterations, "
+                               f"relres {ref_info.relres:.1e}); relative 2-norm error of the mean-removed x"},
         "tda_ms_per_digit": solve64_ms / -math.log10(max(i64.relres, 1e-300)),
         "wda": i64.work_units / -math.log10(max(i64.relres, 1e-300)),
         "hierarchy_bytes": recs[-1][4][0], "workspace_bytes": recs[-1][4][1],
-        "e2e": {"value": world * nnz / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * g.n,
-                "d2h_bytes_per_step": 8 * g.n, "setup_from_host_ms": setup_e2e * 1e3,
+        "e2e": {"value": world * nnz / e2e64_s, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
+                "d2h_bytes_per_step": 8 * n, "fp32_hier_value": world * nnz / e2e32_s,
+                "setup_from_host_ms": None if setup_e2e is None else setup_e2e * 1e3,
                 "note": "lg_solve with pinned host b and x: H2D of b, solve, D2H of x inside the timed call"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
@@ -728,8 +846,7 @@ def main():
                      "whole_solve_note": "algorithmic bytes of every operator pass of one FP64 solve (per-pass "
                                          "events) over the event-free FP64 solve time; vector kernels not counted",
                      "kernel": f"k_rows<double, LapTerm, *> operator passes of level {dom} "
-                               f"(n={recs[-1][0].nnz}) in the timed FP64 solves".replace(
-                                   f"(n={recs[-1][0].nnz})", f"({tot[dom][2] // len(recs)} per solve)"),
+                               f"({tot[dom][2] // len(recs)} per solve) in the timed FP64 solves",
                      "launches": d_launch, "avg_launch_us": d_ms * 1e3 / max(d_launch, 1),
                      "bytes_per_launch": d_bytes / max(d_launch, 1), "peak_kind": peak_kind,
                      "share_of_solve": d_ms / (solve64_ms * len(recs)),
@@ -739,22 +856,19 @@ def main():
         "gpu_launches": launches,
         "wall_s_timed": wall,
     }
-    if multi is not None:
-        line["multi_rhs"] = multi
-    if kcyc is not None:
-        line["kcycle"] = kcyc
-    if wda is not None:
-        line["wda"] = wda
-    if r26 is not None:
-        line["rmat26"] = r26
-    if order is not None:
-        line["ordering"] = order
-    if serve is not None:
-        line["serve"] = serve
-    if many is not None:
-        line["many_small"] = many
+    for key, val in (("secondary", second), ("multi_rhs", multi), ("kcycle", kcyc), ("wda", wda),
+                     ("ordering", order), ("serve", serve), ("many_small", many)):
+        if val:
+            line[key] = val
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.workload, g, b)
+        if args.workload == "rmat_26":
+            gs = rmat_sample()
+            line["cpu_baseline"] = cpu_baseline(
+                args.workload, gs, inputs.rhs(gs.n, seed=2),
+                note=f"R-MAT scale {SAMPLE_SCALE} of the scale-26 recipe (torch on the host) as the bounded "
+                     f"sample: ")
+        else:
+            line["cpu_baseline"] = cpu_baseline(args.workload, g_host, b)
     print(json.dumps(line), flush=True)
 
 

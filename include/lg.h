@@ -276,6 +276,19 @@ int lg_coarsest_pinv(lg_handle h, double* out);
  */
 int lg_vcycle(lg_handle h, const double* f, double* x, int32_t precision);
 
+/*
+ * y = L_l x for level l (0 = finest; not the coarsest) of the hierarchy, in the
+ * level's own vertex numbering (lg_level_copy gives its CSR), with the row
+ * plan the cycle uses: the operator pass of Section 3.6's smoother on its
+ * own, for measuring or profiling one level. precision LG_FP64: x, y are
+ * DEVICE doubles (standard form d_i x_i - sum_j w_ij x_j); LG_FP32_HIER:
+ * DEVICE floats (difference form sum_j w_ij (x_i - x_j)), n_l values each.
+ * Uses the handle's default workspace (no concurrent lg_solve on the handle)
+ * and synchronises the handle's stream. LG_ERR_INVALID for a bad level or a
+ * precision whose weights the handle does not hold.
+ */
+int lg_level_apply(lg_handle h, int32_t level, int32_t precision, const void* x, void* y);
+
 /* ---- instrumentation ---- */
 
 /* Kernels the library has launched in this process so far. */

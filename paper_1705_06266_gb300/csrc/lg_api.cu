@@ -193,16 +193,24 @@ int lg_setup(int64_t n, const int64_t* rowptr, const int32_t* col, const double*
     LG_CUDA(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
     h->own_stream = true;
   }
+  h->time_stages = lg::log_on();
   lg::setup_hierarchy(*h, n, rowptr, col, w);
   h->ws = lg::make_workspace(*h, 1, h->stream);
   LG_CUDA(cudaStreamSynchronize(h->stream));
   if (lg::log_on()) {
-    char line[256];
-    std::snprintf(line, sizeof(line),
+    std::string stages = "{";
+    for (const auto& st : h->setup_stages) {
+      char item[96];
+      std::snprintf(item, sizeof(item), "%s\"%s\": %.6g", stages.size() > 1 ? ", " : "", st.first.c_str(), st.second);
+      stages += item;
+    }
+    stages += "}";
+    char head[256];
+    std::snprintf(head, sizeof(head),
                   "{\"call\": \"lg_setup\", \"n\": %lld, \"nnz\": %lld, \"levels\": %d, \"setup_ms\": %.9g, "
-                  "\"hierarchy_bytes\": %lld}",
+                  "\"hierarchy_bytes\": %lld, \"stages_ms\": ",
                   (long long)n, (long long)h->nnz0, (int)h->levels.size(), h->setup_ms, (long long)h->bytes);
-    lg::log_line(line);
+    lg::log_line((std::string(head) + stages + "}").c_str());
   }
   *out = reinterpret_cast<lg_handle>(h);
   h = nullptr;
@@ -487,6 +495,21 @@ int lg_vcycle(lg_handle hh, const double* f, double* x, int32_t precision) {
   lg::vcycle_apply(h, *h.ws, fp, xp, precision, s);
   if (!xdev) LG_CUDA(cudaMemcpyAsync(x, xp, sizeof(double) * n, cudaMemcpyDefault, s));
   LG_CUDA(cudaStreamSynchronize(s));
+  return LG_OK;
+  LG_API_END
+}
+
+int lg_level_apply(lg_handle hh, int32_t level, int32_t precision, const void* x, void* y) {
+  if (!hh || !x || !y || (precision != LG_FP64 && precision != LG_FP32_HIER)) return LG_ERR_INVALID;
+  lg::Hier& h = *H(hh);
+  if (level < 0 || level >= (int)h.levels.size() || h.levels[level]->kind == LG_LEVEL_COARSEST) return LG_ERR_INVALID;
+  if (precision == LG_FP32_HIER ? !h.levels[level]->w32.get() && h.levels[level]->nnz > 0
+                                : !h.levels[level]->w.get() && h.levels[level]->nnz > 0)
+    return LG_ERR_INVALID;
+  LG_API_BEGIN
+  lg::NvtxRange range("lg_level_apply");
+  lg::level_apply(h, level, precision, x, y, h.stream);
+  LG_CUDA(cudaStreamSynchronize(h.stream));
   return LG_OK;
   LG_API_END
 }

@@ -594,6 +594,32 @@ __global__ void k_scatter_perm(int64_t n, const int32_t* __restrict__ perm, cons
   LG_GRID_STRIDE(i, n) dst[perm[i]] = src[i];
 }
 
+// y = L_l x on level l's operator, with the row plan the cycle uses (the
+// tuned binning, the default workspace's long-row scratch); x and y are
+// device vectors of the level's n values in its own numbering.
+template <typename T>
+struct EpiY {
+  T* y;
+  __device__ __forceinline__ NoPre pre(int64_t) const { return NoPre{}; }
+  __device__ __forceinline__ void operator()(int64_t i, T s, NoPre, double*) const { y[i] = s; }
+  __device__ void finish(const double*) const {}
+};
+
+template <typename T>
+static void level_apply_t(Hier& h, int l, const T* x, T* y, cudaStream_t s) {
+  const Level& L = *h.levels[l];
+  OpView<T> op = L.op<T>();
+  op.plan = h.ws->scratch[l].op.bind(op.plan);
+  launch_rows<T, 0>(op.n, op.rowptr, op.col, LapTerm<T>{op.w, x, op.d}, op.plan, EpiY<T>{y}, s);
+}
+
+void level_apply(Hier& h, int l, int precision, const void* x, void* y, cudaStream_t s) {
+  if (precision == LG_FP32_HIER)
+    level_apply_t<float>(h, l, static_cast<const float*>(x), static_cast<float*>(y), s);
+  else
+    level_apply_t<double>(h, l, static_cast<const double*>(x), static_cast<double*>(y), s);
+}
+
 void vcycle_apply(Hier& h, Workspace& ws, const double* f, double* x, int precision, cudaStream_t s) {
   const int64_t n = h.levels[0]->n;
   k_gather_perm<<<vblocks(n), kVT, 0, s>>>(n, h.perm.get(), f, ws.z.get());

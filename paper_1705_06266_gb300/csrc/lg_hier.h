@@ -19,7 +19,10 @@
 
 #include <nvtx3/nvToolsExt.h>
 
+#include <algorithm>
 #include <memory>
+#include <string>
+#include <utility>
 #include <vector>
 
 #include "lg_prims.h"
@@ -176,6 +179,43 @@ struct Workspace {
   ~Workspace();
 };
 
+// Device time of the setup's stages, for the solve log: events recorded on
+// the setup stream at stage boundaries (only while `on`), each interval
+// charged to the stage named by its closing mark and summed over levels.
+struct StageClock {
+  bool on = false;
+  cudaStream_t s = nullptr;
+  std::vector<std::pair<const char*, cudaEvent_t>> marks;
+  void mark(const char* name) {
+    if (!on) return;
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess || cudaEventRecord(e, s) != cudaSuccess) {
+      cudaGetLastError();
+      if (e) cudaEventDestroy(e);
+      return;
+    }
+    marks.emplace_back(name, e);
+  }
+  // after the stream has been synchronised: (stage, ms) in first-seen order
+  std::vector<std::pair<std::string, double>> collect() {
+    std::vector<std::pair<std::string, double>> out;
+    for (size_t i = 1; i < marks.size(); ++i) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, marks[i - 1].second, marks[i].second) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      auto it = std::find_if(out.begin(), out.end(), [&](const auto& p) { return p.first == marks[i].first; });
+      if (it == out.end()) out.emplace_back(marks[i].first, (double)ms);
+      else it->second += ms;
+    }
+    return out;
+  }
+  ~StageClock() {
+    for (auto& m : marks) cudaEventDestroy(m.second);
+  }
+};
+
 struct Hier {
   lg_options opts;
   cudaStream_t stream = nullptr;
@@ -192,6 +232,8 @@ struct Hier {
   DBuf<int32_t> perm;                   // level-0 vertex i is the caller's vertex perm[i]
   int first_agg = -1;                   // first aggregation level (-1: none)
   std::shared_ptr<void> many;           // device views of the levels for lg_solve_many (lg_many.cu)
+  bool time_stages = false;             // record setup_stages (set before the setup)
+  std::vector<std::pair<std::string, double>> setup_stages;  // device ms per setup stage
   ~Hier();
 };
 
@@ -213,6 +255,9 @@ int64_t run_aggregate(int64_t n, const int64_t* rowptr, const int32_t* col, cons
 
 // ---- solve (lg_cycle.cu) ----
 std::unique_ptr<Workspace> make_workspace(Hier& h, int k, cudaStream_t s);
+// y = L_l x on level l with the cycle's row plan (T = double for LG_FP64,
+// float for LG_FP32_HIER; device vectors in the level's numbering).
+void level_apply(Hier& h, int l, int precision, const void* x, void* y, cudaStream_t s);
 // x = M f on the device (FP64 in and out), starting from x = 0.
 void vcycle_apply(Hier& h, Workspace& ws, const double* f, double* x, int precision, cudaStream_t s);
 // PCG on device vectors b, x (n doubles each, column c of a k-wide block

@@ -747,7 +747,9 @@ __global__ void k_lz_next(int64_t n, int k, const Lanczos* lz, const double* __r
   }
 }
 
-__device__ int sturm_count_dev(int m, const double* a, const double* b, double x) {
+// Number of eigenvalues of the symmetric tridiagonal matrix (diagonal a[0..m),
+// off-diagonal b[0..m-1)) below x, by the signs of the LDL^T pivots (Sturm).
+static int sturm_count(int m, const double* a, const double* b, double x) {
   int count = 0;
   double q = 1.0;
   for (int i = 0; i < m; ++i) {
@@ -759,23 +761,28 @@ __device__ int sturm_count_dev(int m, const double* a, const double* b, double x
   return count;
 }
 
-__global__ void k_lz_ritz(const Lanczos* lz, double* out) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const int m = lz->m;
-  const double* a = lz->alpha;
-  const double* b = lz->beta;
+// Largest eigenvalue of the Lanczos tridiagonal (the Ritz value), by
+// bisection between Gershgorin bounds until the interval stops shrinking.
+// It runs on the host once per level at the end of the setup, on the alpha
+// and beta the device recursion left: a dozen scalars, a few microseconds,
+// where a one-thread kernel spent a quarter of a millisecond.
+static double ritz_max(const Lanczos& lz) {
+  const int m = lz.m;
+  const double* a = lz.alpha;
+  const double* b = lz.beta;
+  if (m < 1) return 0.0;
   double lo = a[0], hi = a[0];
   for (int i = 0; i < m; ++i) {
-    const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i < m - 1 ? fabs(b[i]) : 0.0);
-    lo = fmin(lo, a[i] - r);
-    hi = fmax(hi, a[i] + r);
+    const double r = (i > 0 ? std::fabs(b[i - 1]) : 0.0) + (i < m - 1 ? std::fabs(b[i]) : 0.0);
+    lo = std::fmin(lo, a[i] - r);
+    hi = std::fmax(hi, a[i] + r);
   }
   for (int it = 0; it < 200; ++it) {
     const double mid = 0.5 * (lo + hi);
     if (mid <= lo || mid >= hi) break;
-    if (sturm_count_dev(m, a, b, mid) == m) hi = mid; else lo = mid;
+    if (sturm_count(m, a, b, mid) == m) hi = mid; else lo = mid;
   }
-  *out = hi;
+  return hi;
 }
 
 // ---------------------------------------------------------------------------
@@ -1074,7 +1081,7 @@ constexpr int64_t kLpMinRows = 4096;
 
 // Aggregation stage products: member CSR of R, the Galerkin level, and
 // W = L P when `lp` (levels of at least kLpMinRows vertices).
-static std::unique_ptr<Level> galerkin(Level& L, bool lp, cudaStream_t s, int64_t* counter) {
+static std::unique_ptr<Level> galerkin(Level& L, bool lp, cudaStream_t s, int64_t* counter, StageClock& clk) {
   const int64_t n = L.n, nc = L.nc;
   // member lists, ascending vertex order inside each aggregate (stable sort by aggregate)
   {
@@ -1090,6 +1097,7 @@ static std::unique_ptr<Level> galerkin(Level& L, bool lp, cudaStream_t s, int64_
     LG_LAUNCH_CHECK();
     build_row_plan(L.mem_plan, nc, n, L.mem_ptr.get(), s, counter);
   }
+  clk.mark("member_lists");
   DBuf<int64_t> cnt(n + 1, s);
   each_row(FGalCount{L.col.get(), L.agg.get(), cnt.get()}, L.rowptr.get(), bins_of(L.plan.plan, n), s);
   exclusive_scan(cnt.get(), cnt.get(), n, s);
@@ -1108,6 +1116,7 @@ static std::unique_ptr<Level> galerkin(Level& L, bool lp, cudaStream_t s, int64_
     C->col = std::move(out.col);
     C->w = std::move(out.w);
   }
+  clk.mark("galerkin");
   // W = L P: the same entries keyed by fine row (accumulate_csr sorts them),
   // once the Galerkin product's scratch is back. Not for levels of a few
   // thousand vertices, whose passes are launch-bound: W saves nothing there.
@@ -1131,37 +1140,36 @@ static std::unique_ptr<Level> galerkin(Level& L, bool lp, cudaStream_t s, int64_
       k_to_f32<<<blocks_for(L.lp_nnz), kNT, 0, s>>>(L.lp_nnz, L.lp_w.get(), L.lp_w32.get());
       LG_LAUNCH_CHECK();
     }
+    clk.mark("w_lp");
   }
   return C;
 }
 
-static void lanczos(Level& L, const lg_options& o, int level, double* lam_dev, cudaStream_t s) {
+static void lanczos(Level& L, const lg_options& o, int level, Lanczos* lz_level, cudaStream_t s) {
   const int64_t n = L.n;
   const int iters = std::min(o.eig_iters, 64);
   DBuf<double> v(n, s), vp(n, s), u(n, s), t(n, s), sdinv(n, s);
   const int nb = blocks_for(n);
   DBuf<double> partials((size_t)nb, s);
   DBuf<unsigned> ticket(1, s);
-  DBuf<Lanczos> lz(1, s);
+  Lanczos* lz = lz_level;
   LG_CUDA(cudaMemsetAsync(ticket.get(), 0, sizeof(unsigned), s));
   k_lz_start<<<nb, kNT, 0, s>>>(n, o.seed, level, L.dinv.get(), v.get(), sdinv.get(), partials.get(), ticket.get(),
-                                lz.get());
+                                lz);
   LG_LAUNCH_CHECK();
-  k_lz_scale<<<nb, kNT, 0, s>>>(n, lz.get(), v.get(), sdinv.get(), t.get(), vp.get());
+  k_lz_scale<<<nb, kNT, 0, s>>>(n, lz, v.get(), sdinv.get(), t.get(), vp.get());
   LG_LAUNCH_CHECK();
   for (int k = 0; k < iters; ++k) {
     // stopped iterations leave alpha[k] untouched; only the first m entries are used
     launch_rows<double, 0>(n, L.rowptr.get(), L.col.get(), LapTerm<double>{L.w.get(), t.get(), L.d.get()}, L.plan.plan,
                            EpiLanczos{sdinv.get(), u.get()}, s);
-    k_lz_alpha<<<nb, kNT, 0, s>>>(n, k, lz.get(), v.get(), u.get(), partials.get(), ticket.get());
+    k_lz_alpha<<<nb, kNT, 0, s>>>(n, k, lz, v.get(), u.get(), partials.get(), ticket.get());
     LG_LAUNCH_CHECK();
-    k_lz_orth<<<nb, kNT, 0, s>>>(n, k, lz.get(), u.get(), v.get(), vp.get(), partials.get(), ticket.get());
+    k_lz_orth<<<nb, kNT, 0, s>>>(n, k, lz, u.get(), v.get(), vp.get(), partials.get(), ticket.get());
     LG_LAUNCH_CHECK();
-    k_lz_next<<<nb, kNT, 0, s>>>(n, k, lz.get(), u.get(), v.get(), vp.get(), sdinv.get(), t.get());
+    k_lz_next<<<nb, kNT, 0, s>>>(n, k, lz, u.get(), v.get(), vp.get(), sdinv.get(), t.get());
     LG_LAUNCH_CHECK();
   }
-  k_lz_ritz<<<1, 32, 0, s>>>(lz.get(), lam_dev);
-  LG_LAUNCH_CHECK();
 }
 
 static void coarsest_pinv(Level& L, int* err, cudaStream_t s, int64_t* counter) {
@@ -1277,6 +1285,10 @@ void setup_hierarchy(Hier& h, int64_t n, const int64_t* rowptr, const int32_t* c
   LG_CUDA(cudaEventCreate(&e0));
   LG_CUDA(cudaEventCreate(&e1));
   LG_CUDA(cudaEventRecord(e0, s));
+  StageClock clk;
+  clk.on = h.time_stages;
+  clk.s = s;
+  clk.mark("start");
 
   // ---- level 0: copy the input and check the contract ----
   const int64_t nnz = read_i64(rowptr + n, s);
@@ -1317,6 +1329,7 @@ void setup_hierarchy(Hier& h, int64_t n, const int64_t* rowptr, const int32_t* c
     if (read_err(h.dev_err, s)) fail(LG_ERR_TIMEOUT, "connected components did not settle");
     if (ncomp != 1) fail(LG_ERR_DISCONNECTED, "graph is not connected");
   }
+  clk.mark("validate");
   h.nnz0 = nnz + n;
   h.perm.alloc(n, s, counter);
   if (o.reorder && n > 1) {
@@ -1343,11 +1356,12 @@ void setup_hierarchy(Hier& h, int64_t n, const int64_t* rowptr, const int32_t* c
     k_iota_i32<<<blocks_for(n), kNT, 0, s>>>(n, h.perm.get());
     LG_LAUNCH_CHECK();
   }
+  clk.mark("reorder");
   prepare_operator(*cur, s, counter);
+  clk.mark("operator_plans");
 
   // ---- coarsening loop ----
-  std::vector<double> lam_host;
-  DBuf<double> lam_dev(o.max_levels + 1, s);
+  DBuf<Lanczos> lz_dev(o.max_levels + 1, s);  // each aggregation level's Lanczos recursion
   std::vector<int> lam_level;
   auto stop = [&](const Level& L) {
     return (double)(L.nnz + L.n) <= o.coarse_nnz || (int)h.levels.size() >= o.max_levels - 1;
@@ -1361,11 +1375,14 @@ void setup_hierarchy(Hier& h, int64_t n, const int64_t* rowptr, const int32_t* c
       DBuf<uint8_t> is_f(cur->n, s);
       const int64_t nf = run_elim_select(cur->n, cur->rowptr.get(), cur->col.get(), o.elim_max_degree, o.seed,
                                          is_f.get(), s);
+      clk.mark("elim_select");
       if (!((double)nf > o.elim_min_frac * (double)cur->n)) break;
       auto next = eliminate(*cur, is_f.get(), nf, s, counter);
+      clk.mark("elim_schur");
       h.levels.push_back(std::move(cur));
       cur = std::move(next);
       prepare_operator(*cur, s, counter);
+      clk.mark("operator_plans");
       if (stop(*cur)) {
         done = true;
         break;
@@ -1380,29 +1397,35 @@ void setup_hierarchy(Hier& h, int64_t n, const int64_t* rowptr, const int32_t* c
     const RowBins bins = bins_of(cur->plan.plan, cur->n);
     run_strength(cur->n, cur->rowptr.get(), cur->col.get(), cur->w.get(), o.seed, level, o.strength_vecs,
                  o.strength_sweeps, o.jacobi_omega, S.get(), s, &bins);
+    clk.mark("strength");
     cur->agg.alloc(cur->n, s, counter);
     const int64_t nc = run_aggregate(cur->n, cur->rowptr.get(), cur->col.get(), S.get(), o.agg_iters,
                                      o.vote_threshold, cur->agg.get(), nullptr, nullptr, s, &bins);
+    clk.mark("aggregate");
     if ((double)nc > o.stagnation_frac * (double)cur->n) {
       cur->agg.release();
       break;
     }
     cur->kind = LG_LEVEL_AGG;
     cur->nc = nc;
-    lanczos(*cur, o, level, lam_dev.get() + level, s);
+    lanczos(*cur, o, level, lz_dev.get() + level, s);
+    clk.mark("lanczos");
     lam_level.push_back(level);
-    auto next = galerkin(*cur, o.lp_residual != 0, s, counter);
+    auto next = galerkin(*cur, o.lp_residual != 0, s, counter, clk);
     h.levels.push_back(std::move(cur));
     cur = std::move(next);
     prepare_operator(*cur, s, counter);
+    clk.mark("operator_plans");
   }
   if (cur->n > o.max_coarse_n) fail(LG_ERR_SETUP, "coarsest level too large for the dense solve");
   {
     NvtxRange range("lg coarsest pseudo-inverse");
     coarsest_pinv(*cur, h.dev_err.get(), s, counter);
   }
+  clk.mark("coarsest_pinv");
   h.levels.push_back(std::move(cur));
   for (auto& L : h.levels) make_f32(*L, s, counter);
+  clk.mark("fp32_copies");
   if (read_err(h.dev_err, s)) fail(LG_ERR_SETUP, "coarsest pseudo-inverse failed");
   if (o.autotune) {
     NvtxRange range("lg row-binning tuner");
@@ -1411,25 +1434,27 @@ void setup_hierarchy(Hier& h, int64_t n, const int64_t* rowptr, const int32_t* c
       tune_level(*L, s);
     }
   }
+  clk.mark("autotune");
 
   h.first_agg = -1;
   for (size_t l = 0; l < h.levels.size() && h.first_agg < 0; ++l)
     if (h.levels[l]->kind == LG_LEVEL_AGG) h.first_agg = (int)l;
 
   // ---- Chebyshev constants from the eigenvalue estimates ----
-  std::vector<double> lam(h.levels.size() + 1, 0.0);
-  LG_CUDA(cudaMemcpyAsync(lam.data(), lam_dev.get(), sizeof(double) * h.levels.size(), cudaMemcpyDeviceToHost, s));
+  std::vector<Lanczos> lz(h.levels.size());
+  LG_CUDA(cudaMemcpyAsync(lz.data(), lz_dev.get(), sizeof(Lanczos) * h.levels.size(), cudaMemcpyDeviceToHost, s));
   LG_CUDA(cudaEventRecord(e1, s));
   LG_CUDA(cudaStreamSynchronize(s));
   float ms = 0.f;
   LG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
   h.setup_ms = ms;
+  h.setup_stages = clk.collect();
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   h.cheb.assign(h.levels.size(), Cheb{});
   for (int l : lam_level) {
     Level& L = *h.levels[l];
-    L.lambda = lam[l];
+    L.lambda = ritz_max(lz[l]);
     const double a = o.cheb_lo * L.lambda, b = o.cheb_hi * L.lambda;
     const double theta = 0.5 * (b + a), delta = 0.5 * (b - a);
     const double sigma = theta / delta;

@@ -93,6 +93,7 @@ _SIGS = {
     "lg_elim_select_noalloc": (C.c_int, [_I64, _P, _P, _I32, _U64, _P, _P, _P]),
     "lg_strength": (C.c_int, [_I64, _P, _P, _P, _U64, _I32, _I32, _I32, _D, _P, _P]),
     "lg_aggregate": (C.c_int, [_I64, _P, _P, _P, _I32, _I32, _P, _P, _P, _P, _P]),
+    "lg_level_apply": (C.c_int, [_P, _I32, _I32, _P, _P]),
     "lg_kernel_launches": (C.c_uint64, []),
     "lg_profile": (C.c_int, [_P, _I32]),
     "lg_profile_read": (C.c_int, [_P, _I32, _P]),
@@ -272,6 +273,11 @@ def lg_vcycle(h, f, x, precision: int = FP64):
 
 def lg_kernel_launches() -> int:
     return int(_load().lg_kernel_launches())
+
+
+def lg_level_apply(h, level: int, precision: int, x, y):
+    """y = L_level x on the device (float64 tensors for FP64, float32 for FP32_HIER)."""
+    _check(_load().lg_level_apply(h, int(level), int(precision), _ptr(x), _ptr(y)), "lg_level_apply")
 
 
 def lg_profile(h, enable: bool):

@@ -53,7 +53,10 @@ def test_no_sampler_gives_an_empty_record():
 def test_peak_and_traffic_lookups():
     peak, kind = bench.measured_peak()
     assert peak > 0 and kind in ("measured", "fallback")
-    traffic, h = bench.ncu_traffic("chung_lu_1m")
-    assert h == bench.kernel_source_hash()
-    assert traffic is None or traffic > 1e8  # bytes of one level-1 pass when the summary matches the sources
-    assert bench.ncu_traffic("no_such_workload")[0] is None
+    for name in ("chung_lu_1m", "rmat_26"):
+        traffic, h = bench.ncu_traffic(name)
+        if h == bench.kernel_source_hash():
+            assert traffic is not None and traffic > 1e8  # bytes of one pass of the dominant level
+        else:
+            assert traffic is None  # no summary, or one taken on other sources: not reported
+    assert bench.ncu_traffic("no_such_workload") == (None, None)

@@ -54,6 +54,35 @@ def test_laplacian_apply(torch_cuda, lgmod, oracle, inputs, name):
     assert np.all(np.abs(y.cpu().numpy() - ref) <= 1e-12 * scale)
 
 
+@pytest.mark.parametrize("name", ["chunglu_20k", "star_5000", "rmat_12"])
+def test_level_apply_matches_oracle(torch_cuda, lgmod, oracle, inputs, name):
+    """lg_level_apply on every non-coarsest level (the cycle's tuned plans,
+    chunked long rows included) against the oracle's L x on that level's CSR:
+    FP64 within a few ulps of the row scale, FP32 within its own rounding
+    (2^-24 per term, O(degree) terms, the difference form's x_i - x_j)."""
+    torch = torch_cuda
+    g = GRAPHS[name](inputs)
+    H = lgmod.Hierarchy(g)
+    rng = np.random.default_rng(4)
+    for l in range(H.nlevels - 1):
+        rp, cl, w, _ = H.level(l)
+        G = inputs.Graph(len(rp) - 1, rp, cl, w)
+        x = rng.standard_normal(G.n)
+        ref = oracle.apply_L(G, x)
+        scale = np.abs(w).max(initial=0.0) * np.abs(x).max() * np.diff(rp).clip(1)
+        y = torch.zeros(G.n, dtype=torch.float64, device="cuda")
+        lgmod.lg_level_apply(H.h, l, lgmod.FP64, dev(torch, x), y)
+        assert np.all(np.abs(y.cpu().numpy() - ref) <= 1e-12 * scale), l
+        x32 = x.astype(np.float32)
+        ref32 = oracle.apply_L(G, x32.astype(np.float64))
+        y32 = torch.zeros(G.n, dtype=torch.float32, device="cuda")
+        lgmod.lg_level_apply(H.h, l, lgmod.FP32_HIER, dev(torch, x32), y32)
+        assert np.all(np.abs(y32.cpu().numpy() - ref32) <= 2e-6 * scale), l
+    with pytest.raises(lgmod.LGError):
+        lgmod.lg_level_apply(H.h, H.nlevels - 1, lgmod.FP64, y, y)  # the coarsest has no row pass
+    H.close()
+
+
 @pytest.mark.parametrize("name", list(GRAPHS))
 def test_elim_select_bit_exact(torch_cuda, lgmod, oracle, inputs, name):
     torch = torch_cuda
