@@ -117,6 +117,15 @@ typedef struct {
                                r_0 = r_pre - L P x_c, r_pre the pre-smoothing residual, which
                                equals f - L (x + P x_c) and gathers from the short coarse vector;
                                the prolongation x += P x_c joins that pass. 0: r_0 = f - L x. */
+  int32_t fp32_only;        /* 0. 1 (with precision LG_FP32_HIER at setup): once the hierarchy is
+                               built, release what an FP32-hierarchy solve never reads: the FP64
+                               weights, row sums and W = L P weights of every level but the finest
+                               operator (the outer FP64 PCG applies L_0 in FP64), the FP64
+                               elimination coefficients, and the kept vertices' rows of elimination
+                               levels below the finest. The handle then serves FP32-hierarchy solves
+                               only: lg_set_precision(LG_FP64), FP64 lg_vcycle / lg_vcycle_batch /
+                               lg_level_apply, lg_level_copy of a released level, lg_save, and
+                               registration with an FP64 server return LG_ERR_INVALID. */
 } lg_options;
 
 /* Logging: with the environment variable LG_LOG naming a file, lg_setup and
@@ -317,9 +326,12 @@ int lg_profile(lg_handle h, int32_t enable);
 /* Launch plan of level l's operator passes: out[0] = entries per lane E of
  * the row binning (a row of class c, E 2^(c-1) < deg <= E 2^c, is served by
  * 2^c lanes), out[1] = rows served by groups of 1..16 lanes, out[2] = rows
- * served by a whole warp, out[3] = rows cut into chunks, out[4] = chunks,
- * out[5] = blocks of one pass. */
-int lg_level_plan(lg_handle h, int32_t l, int64_t out[6]);
+ * served by a whole warp, out[3] = long rows (above 2048 entries), out[4] =
+ * their chunks, out[5] = blocks of one pass served by chunks, out[6] = tiles
+ * of the column-segmented long-row pass (0: the long rows go by chunks; else
+ * they go column-segmented, with the gathered vector staged in shared memory,
+ * in passes that reduce nothing across the grid). */
+int lg_level_plan(lg_handle h, int32_t l, int64_t out[7]);
 int lg_profile_read(lg_handle h, int32_t level, lg_kernel_profile* out);
 
 /* One multi-column V-cycle on k right-hand sides at once (1 <= k <= 32): X =

@@ -229,6 +229,10 @@ int lg_setup(int64_t n, const int64_t* rowptr, const int32_t* col, const double*
 
 int lg_save(lg_handle hh, const char* path) {
   if (!hh || !path) return LG_ERR_INVALID;
+  if (reinterpret_cast<lg::Hier*>(hh)->fp32_only) {
+    lg::g_last_error = "lg_save: an fp32_only hierarchy has released the FP64 arrays a file holds";
+    return LG_ERR_INVALID;
+  }
   LG_API_BEGIN
   lg::save_hierarchy(*reinterpret_cast<lg::Hier*>(hh), path);
   return LG_OK;
@@ -270,6 +274,10 @@ static lg::Hier* H(lg_handle h) { return reinterpret_cast<lg::Hier*>(h); }
 
 int lg_set_precision(lg_handle hh, int32_t precision) {
   if (!hh || (precision != LG_FP64 && precision != LG_FP32_HIER)) return LG_ERR_INVALID;
+  if (precision == LG_FP64 && H(hh)->fp32_only) {
+    lg::g_last_error = "lg_set_precision: an fp32_only hierarchy serves FP32-hierarchy solves only";
+    return LG_ERR_INVALID;
+  }
   H(hh)->opts.precision = precision;
   return LG_OK;
 }
@@ -433,6 +441,10 @@ int lg_level_copy(lg_handle hh, int32_t l, int64_t* rowptr, int32_t* col, double
   if (!hh) return LG_ERR_INVALID;
   lg::Hier& h = *H(hh);
   if (l < 0 || l >= (int32_t)h.levels.size()) return LG_ERR_INVALID;
+  if (h.fp32_only && l > 0 && h.levels[l]->kind != LG_LEVEL_COARSEST) {
+    lg::g_last_error = "lg_level_copy: an fp32_only hierarchy has released this level's FP64 operator";
+    return LG_ERR_INVALID;
+  }
   LG_API_BEGIN
   const lg::Level& L = *h.levels[l];
   cudaStream_t s = h.stream;
@@ -474,6 +486,7 @@ int lg_coarsest_pinv(lg_handle hh, double* out) {
 
 int lg_vcycle(lg_handle hh, const double* f, double* x, int32_t precision) {
   if (!hh || !f || !x || (precision != LG_FP64 && precision != LG_FP32_HIER)) return LG_ERR_INVALID;
+  if (precision == LG_FP64 && H(hh)->fp32_only) return LG_ERR_INVALID;
   LG_API_BEGIN
   lg::Hier& h = *H(hh);
   cudaStream_t s = h.stream;
@@ -506,6 +519,7 @@ int lg_level_apply(lg_handle hh, int32_t level, int32_t precision, const void* x
   if (precision == LG_FP32_HIER ? !h.levels[level]->w32.get() && h.levels[level]->nnz > 0
                                 : !h.levels[level]->w.get() && h.levels[level]->nnz > 0)
     return LG_ERR_INVALID;
+  if (h.fp32_only && level > 0 && h.levels[level]->kind == LG_LEVEL_ELIM) return LG_ERR_INVALID;  // rows released
   LG_API_BEGIN
   lg::NvtxRange range("lg_level_apply");
   lg::level_apply(h, level, precision, x, y, h.stream);
@@ -537,7 +551,7 @@ int lg_level_lp_nnz(lg_handle hh, int32_t l, int64_t* nnz) {
   return LG_OK;
 }
 
-int lg_level_plan(lg_handle hh, int32_t l, int64_t out[6]) {
+int lg_level_plan(lg_handle hh, int32_t l, int64_t out[7]) {
   if (!hh || !out) return LG_ERR_INVALID;
   lg::Hier& h = *H(hh);
   if (l < 0 || l >= (int32_t)h.levels.size()) return LG_ERR_INVALID;
@@ -548,6 +562,7 @@ int lg_level_plan(lg_handle hh, int32_t l, int64_t out[6]) {
   out[3] = p.nlong;
   out[4] = p.nchunks;
   out[5] = p.grid();
+  out[6] = p.nseg_tiles;
   return LG_OK;
 }
 
@@ -575,6 +590,7 @@ int lg_vcycle_batch(lg_handle hh, int32_t k, const double* F, int64_t ldf, doubl
   if (!hh || !F || !X || k < 1 || k > lg::kMaxCols || (precision != LG_FP64 && precision != LG_FP32_HIER))
     return LG_ERR_INVALID;
   lg::Hier& h = *H(hh);
+  if (precision == LG_FP64 && h.fp32_only) return LG_ERR_INVALID;
   const int64_t n = h.levels[0]->n;
   if (ldf < n || ldx < n) return LG_ERR_INVALID;
   LG_API_BEGIN

@@ -310,9 +310,29 @@ struct RowPlan {
   int32_t* lrow_count = nullptr;  // chunks of each long row
   double* partial = nullptr;      // nchunks * kMaxCols partial sums
   unsigned* ticket = nullptr;     // nlong tickets, zero between launches
+  // Column-segmented service of the long rows (k_rows_seg, lg_rows.cuh), for
+  // operators whose vector is short next to their long rows' entries: a
+  // block takes a tile of long rows and walks the columns in segments of
+  // kSegBytes, each staged once in shared memory, so the tile's gathers read
+  // shared memory instead of a 32-byte L2 sector each. A long row may be cut
+  // into several virtual rows (entry ranges) of one tile, whose sums are
+  // added in order. nseg_tiles = 0: the long rows go by chunks.
+  int64_t ncols = 0;                   // length of the gathered vector
+  int nseg_tiles = 0;
+  const int32_t* seg_tile_off = nullptr;  // tile t: virtual rows [seg_tile_off[t], seg_tile_off[t+1])
+  const int32_t* vrow_row = nullptr;      // the row of each virtual row
+  const int64_t* vrow_beg = nullptr;      // its entries [vrow_beg, vrow_end)
+  const int64_t* vrow_end = nullptr;
 
   int grid() const { return (int)nchunks + blk_off[kClasses]; }
 };
+
+// Shared memory of one staged column segment, and the most virtual rows of a
+// tile (32 warps, 8 each).
+constexpr int kSegBytes = 128 * 1024;
+constexpr int kSegThreads = 1024;
+constexpr int kSegRowsPerWarp = 8;
+constexpr int kSegMaxVrows = (kSegThreads / 32) * kSegRowsPerWarp;
 
 constexpr int kMaxCols = 32;  // widest multi-RHS block
 

@@ -168,6 +168,9 @@ struct LpTerm<float> {
   __device__ __forceinline__ float acc(float s, int64_t k, int32_t a, float xa) const {
     return fmaf(ld_stream(&w[k]), xa - ld_keep(&xc[a]), s);
   }
+  __device__ __forceinline__ const float* src() const { return xc; }
+  __device__ __forceinline__ float wload(int64_t k) const { return ld_stream(&w[k]); }
+  __device__ __forceinline__ float accw(float s, float wk, float xj, float xa) const { return fmaf(wk, xa - xj, s); }
   __device__ __forceinline__ float finish(int64_t, float, float s) const { return s; }
 };
 
@@ -181,6 +184,9 @@ struct LpTerm<double> {
   __device__ __forceinline__ double acc(double s, int64_t k, int32_t a, double) const {
     return fma(ld_stream(&w[k]), ld_keep(&xc[a]), s);
   }
+  __device__ __forceinline__ const double* src() const { return xc; }
+  __device__ __forceinline__ double wload(int64_t k) const { return ld_stream(&w[k]); }
+  __device__ __forceinline__ double accw(double s, double wk, double xj, double) const { return fma(wk, xj, s); }
   __device__ __forceinline__ double finish(int64_t i, double, double s) const {
     return fma(__ldg(&d[i]), ld_keep(&xc[__ldg(&agg[i])]), -s);
   }
@@ -827,6 +833,7 @@ std::unique_ptr<Workspace> make_workspace(Hier& h, int k, cudaStream_t s) {
     const size_t n = (size_t)lv.n * k;
     const bool smooth = lv.kind == LG_LEVEL_AGG;
     for (int prec = 0; prec < 2; ++prec) {
+      if (prec == 0 && h.fp32_only) continue;  // FP32-hierarchy solves only: no FP64 cycle vectors
       const bool kc = h.opts.kcycle && smooth && (int)l != h.first_agg;
       auto alloc = [&](auto& V) {
         V.f.alloc(n, s, c);

@@ -232,6 +232,7 @@ struct Hier {
   DBuf<int32_t> perm;                   // level-0 vertex i is the caller's vertex perm[i]
   int first_agg = -1;                   // first aggregation level (-1: none)
   std::shared_ptr<void> many;           // device views of the levels for lg_solve_many (lg_many.cu)
+  bool fp32_only = false;               // FP64 copies released (option fp32_only): FP32 solves only
   bool time_stages = false;             // record setup_stages (set before the setup)
   std::vector<std::pair<std::string, double>> setup_stages;  // device ms per setup stage
   ~Hier();

@@ -140,9 +140,9 @@ struct Checker {
 // A plan over (rows, entries, rowptr) binned with E entries per lane, as the
 // setup built it (build_row_plan bins with E = 4, the tuner may re-bin).
 void plan_with(RowPlanStore& ps, int64_t rows, int64_t entries, const int64_t* rowptr, int E, cudaStream_t s,
-               int64_t* counter) {
+               int64_t* counter, int64_t ncols = 0) {
   if (E != 2 && E != 4 && E != 8) fail(LG_ERR_INVALID, "hierarchy file: row binning");
-  build_row_plan(ps, rows, entries, rowptr, s, counter);
+  build_row_plan(ps, rows, entries, rowptr, s, counter, ncols);
   if (E != ps.plan.E) bin_rows(ps, rows, rowptr, E, s);
 }
 
@@ -282,7 +282,7 @@ void load_hierarchy(Hier& h, const char* path, const lg_options* call_opts) {
     check.ptr(L->rowptr, L->n, L->nnz);
     check.range(L->col, L->nnz, 0, L->n);
     check.require("hierarchy file: operator row pointer or column out of range");
-    plan_with(L->plan, L->n, L->nnz, L->rowptr.get(), E, s, counter);
+    plan_with(L->plan, L->n, L->nnz, L->rowptr.get(), E, s, counter, L->n);
     if (L->kind == LG_LEVEL_AGG) {
       r.arr(L->agg, L->n, s, counter);
       r.arr(L->mem_ptr, L->nc + 1, s, counter);
@@ -304,7 +304,7 @@ void load_hierarchy(Hier& h, const char* path, const lg_options* call_opts) {
         check.ptr(L->lp_ptr, L->n, lpn);
         check.range(L->lp_col, lpn, 0, L->nc);
         check.require("hierarchy file: W row pointer or aggregate id out of range");
-        plan_with(L->lp_plan, L->n, lpn, L->lp_ptr.get(), r.val<int32_t>(), s, counter);
+        plan_with(L->lp_plan, L->n, lpn, L->lp_ptr.get(), r.val<int32_t>(), s, counter, L->nc);
       }
     } else if (L->kind == LG_LEVEL_ELIM) {
       r.arr(L->cmap, L->n, s, counter);

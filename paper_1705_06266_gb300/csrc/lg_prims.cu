@@ -1,5 +1,8 @@
 // Device primitives: scans, stable LSD radix sort, sort-based sparse
 // accumulation and the SpMV row plan.
+#include <algorithm>
+#include <vector>
+
 #include "lg_prims.h"
 
 namespace lg {
@@ -423,8 +426,91 @@ void make_bins(RowBinsStore& b, int64_t n, const int64_t* rowptr, cudaStream_t s
   b.bins = bins_of(p, n);
 }
 
+__global__ void k_long_rows(int64_t nlong, const int32_t* __restrict__ rows, const int64_t* __restrict__ rowptr,
+                            int64_t* __restrict__ span) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nlong; q += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t r = rows[q];
+    span[2 * q] = rowptr[r];
+    span[2 * q + 1] = rowptr[r + 1];
+  }
+}
+
+// Tiles of the column-segmented long-row pass (RowPlan::nseg_tiles), or
+// none. Staging the whole vector costs ncols * sizeof(T) per tile against
+// the tile's entries * (4 + sizeof(T)) bytes streamed, so a tile takes at
+// least 7 ncols entries (staging under a tenth of the stream) and at most
+// the long entries over 4 tiles per SM; with fewer than 2 tiles per SM, or
+// long rows under a quarter of the entries, the long rows stay chunked.
+// Long rows are cut into virtual rows of at most max(kChunk, TE / 128)
+// entries (equal parts); a row's virtual rows share a tile, and a tile
+// holds at most kSegMaxVrows of them and about TE entries.
+static void plan_segments(RowPlanStore& ps, int64_t n, int64_t nnz, const int64_t* rowptr, int64_t ncols,
+                          cudaStream_t s, int64_t* counter) {
+  RowPlan& p = ps.plan;
+  p.nseg_tiles = 0;
+  p.ncols = ncols;
+  const int64_t nlong = n - p.cls_off[kClasses];
+  if (ncols <= 0 || nlong <= 0) return;
+  std::vector<int64_t> span((size_t)(2 * nlong));
+  {
+    DBuf<int64_t> dspan((size_t)(2 * nlong), s);
+    k_long_rows<<<grid_for(nlong, 256, kSMs * 8), 256, 0, s>>>(nlong, ps.rows_by_class.get() + p.cls_off[kClasses],
+                                                               rowptr, dspan.get());
+    LG_LAUNCH_CHECK();
+    LG_CUDA(cudaMemcpyAsync(span.data(), dspan.get(), sizeof(int64_t) * 2 * nlong, cudaMemcpyDeviceToHost, s));
+    LG_CUDA(cudaStreamSynchronize(s));
+  }
+  int64_t long_entries = 0;
+  for (int64_t q = 0; q < nlong; ++q) long_entries += span[2 * q + 1] - span[2 * q];
+  const int64_t te_min = 7 * ncols;
+  const int64_t te = std::max<int64_t>(te_min, long_entries / (4 * kSMs));
+  if (4 * long_entries < nnz || long_entries < 2 * kSMs * te_min) return;
+  const int64_t vr = std::max<int64_t>(kChunk, te / 128);
+  std::vector<int32_t> row_of, tile_off(1, 0);
+  std::vector<int64_t> beg, end;
+  std::vector<int32_t> rows(nlong);
+  LG_CUDA(cudaMemcpyAsync(rows.data(), ps.rows_by_class.get() + p.cls_off[kClasses], sizeof(int32_t) * nlong,
+                          cudaMemcpyDeviceToHost, s));
+  LG_CUDA(cudaStreamSynchronize(s));
+  int64_t tile_entries = 0;
+  int tile_vrows = 0;
+  for (int64_t q = 0; q < nlong; ++q) {
+    const int64_t b = span[2 * q], e = span[2 * q + 1], deg = e - b;
+    int64_t parts = (deg + vr - 1) / vr;
+    if (parts > kSegMaxVrows) parts = kSegMaxVrows;  // a row never spans two tiles
+    if (tile_vrows > 0 && (tile_vrows + parts > kSegMaxVrows || tile_entries + deg > te)) {
+      tile_off.push_back((int32_t)row_of.size());
+      tile_vrows = 0;
+      tile_entries = 0;
+    }
+    for (int64_t k = 0; k < parts; ++k) {
+      row_of.push_back(rows[q]);
+      beg.push_back(b + deg * k / parts);
+      end.push_back(b + deg * (k + 1) / parts);
+    }
+    tile_vrows += (int)parts;
+    tile_entries += deg;
+  }
+  tile_off.push_back((int32_t)row_of.size());
+  const size_t nv = row_of.size(), nt = tile_off.size() - 1;
+  ps.seg_tile_off.alloc(nt + 1, s, counter);
+  ps.vrow_row.alloc(nv, s, counter);
+  ps.vrow_beg.alloc(nv, s, counter);
+  ps.vrow_end.alloc(nv, s, counter);
+  LG_CUDA(cudaMemcpyAsync(ps.seg_tile_off.get(), tile_off.data(), sizeof(int32_t) * (nt + 1), cudaMemcpyHostToDevice, s));
+  LG_CUDA(cudaMemcpyAsync(ps.vrow_row.get(), row_of.data(), sizeof(int32_t) * nv, cudaMemcpyHostToDevice, s));
+  LG_CUDA(cudaMemcpyAsync(ps.vrow_beg.get(), beg.data(), sizeof(int64_t) * nv, cudaMemcpyHostToDevice, s));
+  LG_CUDA(cudaMemcpyAsync(ps.vrow_end.get(), end.data(), sizeof(int64_t) * nv, cudaMemcpyHostToDevice, s));
+  LG_CUDA(cudaStreamSynchronize(s));  // the host vectors go out of scope
+  p.nseg_tiles = (int)nt;
+  p.seg_tile_off = ps.seg_tile_off.get();
+  p.vrow_row = ps.vrow_row.get();
+  p.vrow_beg = ps.vrow_beg.get();
+  p.vrow_end = ps.vrow_end.get();
+}
+
 void build_row_plan(RowPlanStore& ps, int64_t n, int64_t nnz, const int64_t* rowptr, cudaStream_t s,
-                    int64_t* counter) {
+                    int64_t* counter, int64_t ncols) {
   RowPlan& p = ps.plan;
   DBuf<int64_t> nch(n + 1, s), lidx(n + 1, s);
   DBuf<uint8_t> islong(n, s);
@@ -462,8 +548,8 @@ void build_row_plan(RowPlanStore& ps, int64_t n, int64_t nnz, const int64_t* row
   p.lrow_count = ps.lrow_count.get();
   p.partial = ps.partial.get();
   p.ticket = ps.ticket.get();
-  (void)nnz;
   bin_rows(ps, n, rowptr, 4, s);
+  plan_segments(ps, n, nnz, rowptr, ncols, s, counter);
 }
 
 }  // namespace lg

@@ -45,6 +45,8 @@ struct RowPlanStore {
   DBuf<int64_t> chunk_beg;
   DBuf<double> partial;
   DBuf<unsigned> ticket;
+  DBuf<int32_t> seg_tile_off, vrow_row;
+  DBuf<int64_t> vrow_beg, vrow_end;
 };
 // Rows of a CSR structure grouped by length for the setup passes (lg_each.cuh):
 // class c < kClasses holds rows of at most E 2^c entries (the last class: at
@@ -69,9 +71,11 @@ struct RowBinsStore {
 void make_bins(RowBinsStore& b, int64_t n, const int64_t* rowptr, cudaStream_t s);
 
 // Build the plan for a CSR structure with n rows and nnz entries (rows binned
-// with E = 4 entries per lane).
+// with E = 4 entries per lane). ncols > 0 (the length of the vector the rows
+// gather from) lets the long rows be served column-segmented when that
+// vector is short enough next to their entries (see RowPlan).
 void build_row_plan(RowPlanStore& ps, int64_t n, int64_t nnz, const int64_t* rowptr, cudaStream_t s,
-                    int64_t* counter);
+                    int64_t* counter, int64_t ncols = 0);
 // Re-bin the rows of a built plan for E entries per lane.
 void bin_rows(RowPlanStore& ps, int64_t n, const int64_t* rowptr, int E, cudaStream_t s);
 

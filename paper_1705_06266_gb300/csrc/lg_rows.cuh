@@ -66,6 +66,10 @@ struct LapTerm;
 // acc(s, k, j, rv) (s plus the contribution of entry k with column j, as one
 // fused multiply-add where there is a product) and finish(i, rv, s) (the
 // row's result from its entry sum, evaluated once per row).
+// Terms that gather from one vector also give src() (that vector), wload(k)
+// (entry k's weight) and accw(s, wk, xj, rv) (acc from the loaded weight and
+// gathered value), so the column-segmented long-row pass can issue the weight
+// loads early and read xj from a staged copy.
 template <>
 struct LapTerm<float> {
   const float* __restrict__ w;
@@ -75,6 +79,9 @@ struct LapTerm<float> {
   __device__ __forceinline__ float acc(float s, int64_t k, int32_t j, float xi) const {
     return fmaf(ld_stream(&w[k]), xi - ld_keep(&x[j]), s);
   }
+  __device__ __forceinline__ const float* src() const { return x; }
+  __device__ __forceinline__ float wload(int64_t k) const { return ld_stream(&w[k]); }
+  __device__ __forceinline__ float accw(float s, float wk, float xj, float xi) const { return fmaf(wk, xi - xj, s); }
   __device__ __forceinline__ float finish(int64_t, float, float s) const { return s; }
 };
 
@@ -87,9 +94,22 @@ struct LapTerm<double> {
   __device__ __forceinline__ double acc(double s, int64_t k, int32_t j, double) const {
     return fma(ld_stream(&w[k]), ld_keep(&x[j]), s);
   }
+  __device__ __forceinline__ const double* src() const { return x; }
+  __device__ __forceinline__ double wload(int64_t k) const { return ld_stream(&w[k]); }
+  __device__ __forceinline__ double accw(double s, double wk, double xj, double) const { return fma(wk, xj, s); }
   __device__ __forceinline__ double finish(int64_t i, double, double s) const {
     return fma(__ldg(&d[i]), __ldg(&x[i]), -s);
   }
+};
+
+// Whether a term can be served column-segmented (it has src(), wload(), accw()).
+template <class Term, class = void>
+struct SegTerm {
+  static constexpr bool value = false;
+};
+template <class Term>
+struct SegTerm<Term, decltype((void)&Term::src)> {
+  static constexpr bool value = true;
 };
 
 // Plain gather-sum: sum_k v[idx_k] (restriction by aggregate member lists).
@@ -344,11 +364,137 @@ k_rows(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, Term
   }
 }
 
+// Long rows, column-segmented (RowPlan::nseg_tiles > 0). Block t takes tile
+// t's virtual rows, warp w the ones at w, w + 32, ... (at most 8, their
+// partial sums in registers). For each segment of kSegBytes / sizeof(T)
+// columns the block stages that stretch of the gathered vector in shared
+// memory, then every warp advances each of its virtual rows through the
+// entries whose columns fall in the segment (columns ascend within a row, so
+// a per-row cursor marks where the next segment starts), lanes taking 32
+// consecutive entries at a time, four such groups (columns and weights)
+// loaded together; the entries of the last group past the segment's end are
+// loaded again in the next segment. At the
+// end each virtual row's lane partials are added by a fixed xor tree, a
+// row's virtual rows in order, and the epilogue runs once per row. The order
+// of every addition follows from the plan alone, so results are bitwise
+// reproducible.
+template <typename T, class Term, class Epi>
+__global__ void __launch_bounds__(kSegThreads, 1)
+k_rows_seg(const int32_t* __restrict__ col, Term term, RowPlan plan, Epi epi, const double* gate) {
+  if (gate && *gate == 0.0) return;
+  constexpr int kCols = kSegBytes / (int)sizeof(T);
+  constexpr int kWarps = kSegThreads / 32;
+  extern __shared__ __align__(16) unsigned char seg_smem[];
+  T* xs = reinterpret_cast<T*>(seg_smem);
+  int64_t* cur = reinterpret_cast<int64_t*>(seg_smem + kSegBytes);  // per virtual row: next entry
+  T* vsum = reinterpret_cast<T*>(cur + kSegMaxVrows);               // per virtual row: its sum
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int v0 = plan.seg_tile_off[blockIdx.x], nv = plan.seg_tile_off[blockIdx.x + 1] - v0;
+  for (int q = threadIdx.x; q < nv; q += kSegThreads) cur[q] = plan.vrow_beg[v0 + q];
+  T part[kSegRowsPerWarp];
+  T rv[kSegRowsPerWarp];
+#pragma unroll
+  for (int r = 0; r < kSegRowsPerWarp; ++r) {
+    part[r] = T(0);
+    const int q = warp + r * kWarps;
+    rv[r] = q < nv ? term.row(plan.vrow_row[v0 + q]) : T(0);
+  }
+  const T* src = term.src();
+  const int64_t ncols = plan.ncols;
+  for (int64_t c0 = 0; c0 < ncols; c0 += kCols) {
+    const int cn = (int)(ncols - c0 < kCols ? ncols - c0 : kCols);
+    __syncthreads();  // the previous segment's reads of xs and cur are done
+    for (int q = threadIdx.x; q < cn; q += kSegThreads) xs[q] = __ldg(&src[c0 + q]);
+    __syncthreads();
+    const int64_t bound = c0 + cn;
+#pragma unroll
+    for (int r = 0; r < kSegRowsPerWarp; ++r) {
+      const int q = warp + r * kWarps;
+      if (q >= nv) break;  // warp-uniform
+      const int64_t end = plan.vrow_end[v0 + q];
+      int64_t k = cur[q];
+      while (k < end) {
+        int32_t j[4];
+        T wk[4];
+        bool ok[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int64_t e = k + u * 32 + lane;
+          const bool in = e < end;
+          j[u] = in ? ld_stream(&col[e]) : -1;
+          wk[u] = in ? term.wload(e) : T(0);
+        }
+        int taken = 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          // columns ascend from the cursor, so the entries in this segment are
+          // a prefix of the 128; the range test also keeps every shared-memory
+          // index inside the staged segment
+          ok[u] = j[u] >= c0 && (int64_t)j[u] < bound;
+          taken += __popc(__ballot_sync(0xffffffffu, ok[u]));
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (ok[u]) part[r] = term.accw(part[r], wk[u], xs[j[u] - c0], rv[r]);
+        k += taken;
+        if (taken < 128) break;  // the rest of the row lies in later segments
+      }
+      if (lane == 0) cur[q] = k;
+    }
+  }
+  // each virtual row's sum: a fixed xor tree over the lanes
+#pragma unroll
+  for (int r = 0; r < kSegRowsPerWarp; ++r) {
+    T v = part[r];
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int q = warp + r * kWarps;
+    if (lane == 0 && q < nv) vsum[q] = v;
+  }
+  __syncthreads();
+  // a row's virtual rows are consecutive within the tile: the first of them adds them in order
+  double red[1] = {0.0};
+  for (int q = threadIdx.x; q < nv; q += kSegThreads) {
+    const int32_t row = plan.vrow_row[v0 + q];
+    if (q > 0 && plan.vrow_row[v0 + q - 1] == row) continue;
+    T tot = vsum[q];
+    for (int u = q + 1; u < nv && plan.vrow_row[v0 + u] == row; ++u) tot += vsum[u];
+    const T rvr = term.row(row);
+    epi(row, term.finish(row, rvr, tot), epi.pre(row), red);
+  }
+}
+
+template <typename T, class Term, class Epi>
+inline void launch_seg(const int32_t* col, const Term& term, const RowPlan& plan, const Epi& epi, cudaStream_t s,
+                       const double* gate) {
+  constexpr size_t smem = kSegBytes + kSegMaxVrows * (sizeof(int64_t) + sizeof(T));
+  static const cudaError_t attr = cudaFuncSetAttribute(k_rows_seg<T, Term, Epi>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  check_cuda(attr, "cudaFuncSetAttribute(k_rows_seg)");
+  k_rows_seg<T, Term, Epi><<<plan.nseg_tiles, kSegThreads, smem, s>>>(col, term, plan, epi, gate);
+  LG_LAUNCH_CHECK();
+}
+
 template <typename T, int NRED, class Term, class Epi>
 inline void launch_rows(int64_t /*n*/, const int64_t* rowptr, const int32_t* col, const Term& term,
                         const RowPlan& plan, const Epi& epi, cudaStream_t s,
                         double* red_partials = nullptr, unsigned* red_ticket = nullptr,
                         double* red_out = nullptr, const double* gate = nullptr) {
+  if constexpr (NRED == 0 && SegTerm<Term>::value) {
+    if (plan.nseg_tiles > 0) {
+      // the long rows column-segmented, then the binned rows (no chunks)
+      launch_seg<T>(col, term, plan, epi, s, gate);
+      RowPlan rest = plan;
+      rest.nchunks = 0;
+      const int grid = rest.grid();
+      if (grid > 0) {
+        k_rows<T, NRED, Term, Epi><<<grid, kRowThreads, 0, s>>>(rowptr, col, term, rest, epi, red_partials,
+                                                                red_ticket, red_out, gate);
+        LG_LAUNCH_CHECK();
+      }
+      return;
+    }
+  }
   const int grid = plan.grid();
   if (grid <= 0) return;
   k_rows<T, NRED, Term, Epi><<<grid, kRowThreads, 0, s>>>(rowptr, col, term, plan, epi, red_partials, red_ticket,

@@ -255,6 +255,7 @@ int lg_serve_register(lg_server_t s, lg_handle hh) {
   if (!s || !hh) return LG_ERR_INVALID;
   auto* sv = reinterpret_cast<lg::Server*>(s);
   auto* h = reinterpret_cast<lg::Hier*>(hh);
+  if (h->fp32_only && sv->o.precision != LG_FP32_HIER) return LG_ERR_INVALID;  // no FP64 operators to serve
   std::lock_guard<std::mutex> lk(sv->mu);
   if (sv->resident.count(h)) return LG_OK;
   const double b = (double)h->bytes;

@@ -897,6 +897,29 @@ struct FPermEmit {
   __device__ long long finish(int64_t, const Acc&, int64_t, int64_t) const { return 0; }
 };
 
+// ---------------------------------------------------------------------------
+// FP32-only hierarchies: an elimination level below the finest keeps only its
+// eliminated rows (the cycle reads nothing else of its operator: the kept
+// vertices take their coarse value, Section 3.4).
+// ---------------------------------------------------------------------------
+__global__ void k_frow_count(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ cmap,
+                             int64_t* __restrict__ cnt) {
+  LG_GRID_STRIDE(i, n) cnt[i] = cmap[i] < 0 ? rowptr[i + 1] - rowptr[i] : 0;
+}
+
+__global__ void k_frow_copy(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                            const float* __restrict__ w32, const int32_t* __restrict__ cmap,
+                            const int64_t* __restrict__ nptr, int32_t* __restrict__ ncol, float* __restrict__ nw32) {
+  LG_GRID_STRIDE(i, n) {
+    if (cmap[i] >= 0) continue;
+    const int64_t b = rowptr[i], e = rowptr[i + 1], o = nptr[i];
+    for (int64_t k = b; k < e; ++k) {
+      ncol[o + (k - b)] = col[k];
+      nw32[o + (k - b)] = w32[k];
+    }
+  }
+}
+
 // ===========================================================================
 // Host side.
 // ===========================================================================
@@ -916,7 +939,7 @@ static int64_t read_i64(const int64_t* p, cudaStream_t s) {
 
 // Row plan and 1/diag of a level's operator.
 static void prepare_operator(Level& L, cudaStream_t s, int64_t* counter) {
-  build_row_plan(L.plan, L.n, L.nnz, L.rowptr.get(), s, counter);
+  build_row_plan(L.plan, L.n, L.nnz, L.rowptr.get(), s, counter, L.n);
   L.d.alloc(L.n, s, counter);
   L.dinv.alloc(L.n, s, counter);
   launch_rows<double, 0>(L.n, L.rowptr.get(), L.col.get(), WeightTerm{L.w.get()}, L.plan.plan,
@@ -1130,7 +1153,7 @@ static std::unique_ptr<Level> galerkin(Level& L, bool lp, cudaStream_t s, int64_
     L.lp_ptr = std::move(lo.rowptr);
     L.lp_col = std::move(lo.col);
     L.lp_w = std::move(lo.w);
-    build_row_plan(L.lp_plan, n, L.lp_nnz, L.lp_ptr.get(), s, counter);
+    build_row_plan(L.lp_plan, n, L.lp_nnz, L.lp_ptr.get(), s, counter, nc);
     L.lp_d.alloc(n, s, counter);
     DBuf<double> unused(n, s);
     launch_rows<double, 0>(n, L.lp_ptr.get(), L.lp_col.get(), WeightTerm{L.lp_w.get()}, L.lp_plan.plan,
@@ -1268,6 +1291,43 @@ static void tune_level(Level& L, cudaStream_t s) {
   g_tune_cache.emplace(key, best);
 }
 
+// Release what an FP32-hierarchy solve never reads (option fp32_only): the
+// FP64 copies of every operator but the finest (whose FP64 weights and row
+// sums the outer PCG applies), the FP64 W = L P weights and elimination
+// coefficients, and the kept vertices' rows of every elimination level
+// below the finest. The level sizes (n, nnz) keep their logical values.
+static void release_fp64_copies(Hier& h, cudaStream_t s, int64_t* counter) {
+  for (size_t l = 0; l < h.levels.size(); ++l) {
+    Level& L = *h.levels[l];
+    if (L.kind == LG_LEVEL_COARSEST) continue;  // its FP64 pseudo-inverse is the coarsest solve
+    L.lp_w.release();
+    L.lp_d.release();
+    L.pt_coef.release();
+    L.dinv.release();
+    if (l == 0) continue;
+    L.w.release();
+    L.d.release();
+    if (L.kind != LG_LEVEL_ELIM || L.nnz == 0) continue;
+    const int64_t n = L.n;
+    DBuf<int64_t> nptr(n + 1, s, counter);
+    k_frow_count<<<blocks_for(n), kNT, 0, s>>>(n, L.rowptr.get(), L.cmap.get(), nptr.get());
+    LG_LAUNCH_CHECK();
+    exclusive_scan(nptr.get(), nptr.get(), n, s);
+    const int64_t kept = read_i64(nptr.get() + n, s);
+    DBuf<int32_t> ncol(kept, s, counter);
+    DBuf<float> nw32(kept, s, counter);
+    k_frow_copy<<<blocks_for(n), kNT, 0, s>>>(n, L.rowptr.get(), L.col.get(), L.w32.get(), L.cmap.get(), nptr.get(),
+                                              ncol.get(), nw32.get());
+    LG_LAUNCH_CHECK();
+    L.rowptr = std::move(nptr);
+    L.col = std::move(ncol);
+    L.w32 = std::move(nw32);
+    L.plan = RowPlanStore();
+    build_row_plan(L.plan, n, kept, L.rowptr.get(), s, counter);
+  }
+  h.fp32_only = true;
+}
+
 void setup_hierarchy(Hier& h, int64_t n, const int64_t* rowptr, const int32_t* col, const double* w) {
   cudaStream_t s = h.stream;
   const lg_options& o = h.opts;
@@ -1278,6 +1338,7 @@ void setup_hierarchy(Hier& h, int64_t n, const int64_t* rowptr, const int32_t* c
   if (o.max_levels < 1) fail(LG_ERR_INVALID, "max_levels");
   if (o.elim_rounds < 1 || o.elim_rounds > 64) fail(LG_ERR_INVALID, "elim_rounds must be 1..64");
   if (o.reorder < 0 || o.reorder > 2) fail(LG_ERR_INVALID, "reorder must be 0, 1 or 2");
+  if (o.fp32_only && o.precision != LG_FP32_HIER) fail(LG_ERR_INVALID, "fp32_only needs precision LG_FP32_HIER");
 
   h.dev_err.alloc(1, s);
   LG_CUDA(cudaMemsetAsync(h.dev_err.get(), 0, sizeof(int), s));
@@ -1435,6 +1496,10 @@ void setup_hierarchy(Hier& h, int64_t n, const int64_t* rowptr, const int32_t* c
     }
   }
   clk.mark("autotune");
+  if (o.fp32_only) {
+    release_fp64_copies(h, s, counter);
+    clk.mark("fp32_only_release");
+  }
 
   h.first_agg = -1;
   for (size_t l = 0; l < h.levels.size() && h.first_agg < 0; ++l)

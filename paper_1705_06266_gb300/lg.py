@@ -36,7 +36,7 @@ class Options(C.Structure):
         ("cheb_degree", C.c_int32), ("eig_iters", C.c_int32), ("max_coarse_n", C.c_int32),
         ("residual_replace", C.c_int32), ("memory_space", C.c_int32), ("use_graphs", C.c_int32),
         ("autotune", C.c_int32), ("reorder", C.c_int32), ("kcycle", C.c_int32),
-        ("elim_rounds", C.c_int32), ("lp_residual", C.c_int32),
+        ("elim_rounds", C.c_int32), ("lp_residual", C.c_int32), ("fp32_only", C.c_int32),
     ]
 
 
@@ -291,10 +291,10 @@ def lg_profile_read(h, level: int = -1) -> KernelProfile:
 
 
 def lg_level_plan(h, l: int) -> dict:
-    out = (C.c_int64 * 6)()
+    out = (C.c_int64 * 7)()
     _check(_load().lg_level_plan(h, int(l), out), "lg_level_plan")
     return {"E": out[0], "group_rows": out[1], "warp_rows": out[2], "long_rows": out[3], "chunks": out[4],
-            "blocks": out[5]}
+            "blocks": out[5], "seg_tiles": out[6]}
 
 
 def _stream(stream):

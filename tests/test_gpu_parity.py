@@ -54,15 +54,22 @@ def test_laplacian_apply(torch_cuda, lgmod, oracle, inputs, name):
     assert np.all(np.abs(y.cpu().numpy() - ref) <= 1e-12 * scale)
 
 
-@pytest.mark.parametrize("name", ["chunglu_20k", "star_5000", "rmat_12"])
+SEG_GRAPHS = {  # every row above 2048 entries and a short vector: the long rows go column-segmented
+    "complete_3000w": lambda I: I.complete(3000, weights="uniform", seed=5),
+}
+
+
+@pytest.mark.parametrize("name", ["chunglu_20k", "star_5000", "rmat_12", "complete_3000w"])
 def test_level_apply_matches_oracle(torch_cuda, lgmod, oracle, inputs, name):
     """lg_level_apply on every non-coarsest level (the cycle's tuned plans,
     chunked long rows included) against the oracle's L x on that level's CSR:
     FP64 within a few ulps of the row scale, FP32 within its own rounding
     (2^-24 per term, O(degree) terms, the difference form's x_i - x_j)."""
     torch = torch_cuda
-    g = GRAPHS[name](inputs)
+    g = {**GRAPHS, **SEG_GRAPHS}[name](inputs)
     H = lgmod.Hierarchy(g)
+    if name in SEG_GRAPHS:
+        assert lgmod.lg_level_plan(H.h, 0)["seg_tiles"] > 0
     rng = np.random.default_rng(4)
     for l in range(H.nlevels - 1):
         rp, cl, w, _ = H.level(l)
@@ -664,3 +671,23 @@ def test_lp_residual(lgmod, inputs, name):
         assert abs(i1.iterations - i0.iterations) <= 1
     H1.close()
     H0.close()
+
+
+def test_segmented_long_rows_solve(torch_cuda, lgmod, oracle, inputs):
+    """Solves through a hierarchy whose finest operator serves its long rows
+    column-segmented (every pass of level 0: the Chebyshev steps, the
+    residuals, the PCG's q = L p, the true residual) reach the tolerance and
+    the oracle's solution, in both precisions, and repeat bit for bit."""
+    g = SEG_GRAPHS["complete_3000w"](inputs)
+    H = lgmod.Hierarchy(g)
+    assert lgmod.lg_level_plan(H.h, 0)["seg_tiles"] > 0
+    b = inputs.rhs(g.n, seed=6)
+    ref = oracle.dense_solve(g, b)
+    for prec in (lgmod.FP64, lgmod.FP32_HIER):
+        x, info = H.solve(b, precision=prec)
+        assert info.status == lgmod.OK and relres(g, b, x) <= 1e-8
+        xm = x - x.mean()
+        assert np.linalg.norm(xm - ref) <= 1e-6 * np.linalg.norm(ref)
+        x2, info2 = H.solve(b, precision=prec)
+        np.testing.assert_array_equal(x2, x)
+    H.close()
