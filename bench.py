@@ -64,9 +64,10 @@ def parse():
     ap.add_argument("--no-secondary", action="store_true")
     ap.add_argument("--no-many", action="store_true")
     ap.add_argument("--many-graphs", type=int, default=608)
-    ap.add_argument("--serve-graphs", type=int, default=64)
-    ap.add_argument("--serve-nmax", type=int, default=262144)
-    ap.add_argument("--serve-requests", type=int, default=1000)
+    ap.add_argument("--serve-graphs", type=int, default=256)
+    ap.add_argument("--serve-nmax", type=int, default=2000000)
+    ap.add_argument("--serve-requests", type=int, default=1500)
+    ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-load", type=float, default=0.8)
     return ap.parse_args()
 
@@ -422,23 +423,43 @@ def secondary_leg(lg, inputs, torch, dev, name, flush, oracle_ref):
     return out
 
 
-def serve_leg(lg, inputs, args):
-    """Continuous batching over resident hierarchies: a burst of requests
-    measures the saturation rate, then Poisson arrivals at a fraction of it
-    give the latency percentiles (submission to completion, host B and X)."""
-    graphs = inputs.serving_mix(args.serve_graphs, 1000, args.serve_nmax, seed=5)
-    hs = [lg.Hierarchy(g) for g in graphs]
+def serve_leg(lg, inputs, args, torch, dev):
+    """Continuous batching over resident hierarchies (the serving workload):
+    graphs of log-uniform sizes over four families, generated on the device
+    and set up as FP32-only hierarchies (option fp32_only); a burst of
+    requests measures the saturation rate, then Poisson arrivals at 0.5, 0.8
+    and 0.95 of it give the latency percentiles (submission to completion,
+    host B and X) and the served solves per second."""
+    t0 = time.perf_counter()
+    mix = inputs.serving_mix_device(args.serve_graphs, 1000, args.serve_nmax, seed=5, device=str(dev))
+    gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    hs = []
+    for name, n, rp, cl, w in mix:
+        hs.append(lg.Hierarchy(n=n, rowptr=rp, col=cl, w=w, precision=lg.FP32_HIER, fp32_only=1))
+    setup_s = time.perf_counter() - t0
+    sizes = [m[1] for m in mix]
+    nnzs = [int(m[3].numel()) + m[1] for m in mix]
+    del mix
+    torch.cuda.empty_cache()
     rng = np.random.Generator(np.random.PCG64(11))
     # one column-major block of 8 right-hand sides per graph; a request of k takes its first k
-    blocks = [np.ascontiguousarray(inputs.rhs(g.n, 8, seed=20 + q).T) for q, g in enumerate(graphs)]
+    blocks = [np.ascontiguousarray(inputs.rhs(n, 8, seed=20 + q).T) for q, n in enumerate(sizes)]
 
     def requests(count):
-        return [(int(rng.integers(0, len(graphs))), int(rng.integers(1, 9))) for _ in range(count)]
+        return [(int(rng.integers(0, len(hs))), int(rng.integers(1, 9))) for _ in range(count)]
+
+    # one server for every load point: the hierarchies are registered once (which builds their
+    # multi-column plans and a ready workspace each); the statistics restart for each run
+    t0 = time.perf_counter()
+    sv = lg.lg_serve_create(lg.serve_options(slots=args.serve_slots, precision=lg.FP32_HIER,
+                                             hbm_budget_bytes=120e9))
+    for H in hs:
+        lg.lg_serve_register(sv, H.h)
+    register_s = time.perf_counter() - t0
 
     def run(reqs, rate):
-        sv = lg.lg_serve_create(lg.serve_options(slots=8, precision=lg.FP32_HIER, hbm_budget_bytes=120e9))
-        for H in hs:
-            lg.lg_serve_register(sv, H.h)
+        lg.lg_serve_reset_stats(sv)
         live, rhs, failed = {}, 0, 0
         t0 = time.perf_counter()
         arrival = 0.0
@@ -451,7 +472,7 @@ def serve_leg(lg, inputs, args):
                         if done:
                             failed += info.status != lg.OK
                             del live[t]
-            X = np.empty((k, graphs[gi].n))
+            X = np.empty((k, sizes[gi]))
             t = lg.lg_serve_submit(sv, hs[gi].h, k, blocks[gi][:k], X, TOL)
             live[t] = X
             rhs += k
@@ -462,9 +483,7 @@ def serve_leg(lg, inputs, args):
                     failed += info.status != lg.OK
                     del live[t]
         span = time.perf_counter() - t0
-        st = lg.lg_serve_stats(sv)
-        lg.lg_serve_destroy(sv)
-        return st, span, rhs, failed
+        return lg.lg_serve_stats(sv), span, rhs, failed
 
     burst = requests(max(100, args.serve_requests // 4))
     st_b, span_b, rhs_b, fail_b = run(burst, None)
@@ -474,6 +493,8 @@ def serve_leg(lg, inputs, args):
         rate = load * sat_rps
         st, span, rhs, failed = run(requests(args.serve_requests), rate)
         loads[load] = (rate, st, span, rhs, failed)
+    resident = sum(lg.lg_hier_bytes(H.h)[0] for H in hs)
+    lg.lg_serve_destroy(sv)
     for H in hs:
         H.close()
     rate, st, span, rhs, failed = loads[args.serve_load]
@@ -482,19 +503,25 @@ def serve_leg(lg, inputs, args):
         "solves_per_s": rhs / span, "requests_per_s": args.serve_requests / span,
         "offered_rps": rate, "saturation_rps": sat_rps, "saturation_solves_per_s": rhs_b / span_b,
         "saturation_p50_ms": st_b.p50_ms, "saturation_p99_ms": st_b.p99_ms,
+        "saturation_groups": int(st_b.groups), "saturation_packed_groups": int(st_b.packed_groups),
+        "saturation_phase_ms": {"workspaces_made": int(st_b.workspaces_made), "workspace": st_b.workspace_ms,
+                                "copy": st_b.copy_ms, "solve": st_b.solve_ms, "span": span_b * 1e3},
         "by_load": {f"{ld:g}": {"offered_rps": v[0], "p50_ms": v[1].p50_ms, "p99_ms": v[1].p99_ms,
-                                "solves_per_s": v[3] / v[2], "failed": int(v[1].failed + v[4])}
+                                "solves_per_s": v[3] / v[2], "requests": args.serve_requests,
+                                "groups": int(v[1].groups), "packed_groups": int(v[1].packed_groups),
+                                "failed": int(v[1].failed + v[4])}
                     for ld, v in loads.items()},
         "completed": int(st.completed),
         "failed": int(sum(v[1].failed + v[4] for v in loads.values()) + st_b.failed + fail_b),
-        "requests": args.serve_requests, "graphs": len(graphs),
-        "vertices_resident": int(sum(g.n for g in graphs)), "nnz_resident": int(sum(g.nnz for g in graphs)),
-        "resident_bytes": st.resident_bytes,
-        "config": f"{len(graphs)} resident graphs, n log-uniform in [1000, {args.serve_nmax}], type uniform over "
-                  f"2D grid / 3D grid / Chung-Lu 2.1 / R-MAT ef16; k uniform in 1..8; tol 1e-8; FP32 hierarchy; "
-                  f"8 slots; HBM budget 120 GB; Poisson arrivals at 0.5, {args.serve_load} (headline) and 0.95 x "
-                  f"the burst saturation rate, {args.serve_requests} requests each; latency = submission to "
-                  f"completion with host B and X",
+        "requests": args.serve_requests, "graphs": len(hs),
+        "vertices_resident": int(sum(sizes)), "nnz_resident": int(sum(nnzs)),
+        "resident_bytes": float(resident), "generate_s": gen_s, "setup_s": setup_s, "register_s": register_s,
+        "config": f"{len(hs)} resident graphs, n log-uniform in [1000, {args.serve_nmax}], type uniform over "
+                  f"2D grid / 3D grid / Chung-Lu 2.1 / R-MAT ef16 (power-law members generated on the device); "
+                  f"FP32-only hierarchies; k uniform in 1..8; tol 1e-8; {args.serve_slots} slots; HBM budget "
+                  f"120 GB; a burst of {len(burst)} requests for the saturation rate, then Poisson arrivals at "
+                  f"0.5, {args.serve_load} (headline) and 0.95 x that rate, {args.serve_requests} requests each; "
+                  f"latency = submission to completion with host B and X",
     }
 
 
@@ -753,7 +780,7 @@ def main():
             gg = workload(inputs, name)
             graphs.append((name, gg, inputs.rhs(gg.n, seed=2)))
         order = ordering_leg(lg, torch, dev, graphs)
-    serve = None if args.no_serve else serve_leg(lg, inputs, args)
+    serve = None if args.no_serve else serve_leg(lg, inputs, args, torch, dev)
     many = None if args.no_many else many_leg(lg, inputs, args.many_graphs)
     del flush
 

@@ -423,6 +423,12 @@ typedef struct {
   double solves_per_s;      /* completed right-hand sides per second since creation */
   double resident_bytes;    /* device bytes of registered hierarchies */
   int64_t completed, failed, pending, running;
+  int64_t groups;           /* solves started: multi-column batches and packed launches */
+  int64_t packed_groups;    /* of which packed launches of small graphs */
+  int64_t workspaces_made;  /* solve workspaces created (the pool had none to reuse) */
+  double workspace_ms;      /* host time spent creating them */
+  double copy_ms;           /* host time in the groups' host<->device copies of B and X */
+  double solve_ms;          /* host time in the groups' solves (multi-column and packed) */
 } lg_serve_stats_t;
 
 int lg_serve_options_default(lg_serve_options* o);
@@ -436,7 +442,17 @@ int lg_serve_register(lg_server_t s, lg_handle h);
  * Queue k right-hand sides (column-major n x k in HOST memory, B and X) for
  * hierarchy h. Returns at once with a ticket. B and X must stay valid until
  * lg_serve_poll reports done. Requests are admitted as slots and budget free
- * up; admitted requests run concurrently on their own streams.
+ * up, in arrival order except that a request that fits may pass a head
+ * request that does not (at most 16 times per head request). A free slot
+ * takes the first admissible request together with every queued request on
+ * the same hierarchy and tolerance (up to 32 columns in all) and solves them
+ * as one multi-column batch; a single-column request on a graph of at most
+ * 16384 vertices (and 2^22 nonzeros, no K-cycle) instead joins the other such
+ * queued requests (one per hierarchy, same tolerance) in one packed launch,
+ * which uses the hierarchy's default workspace: do not call lg_solve on a
+ * registered handle while the server runs. Each column is computed the same
+ * way whatever it is grouped with, so a request's result is bitwise the same
+ * alone and in any mix. Groups run concurrently on the slots' streams.
  */
 int lg_serve_submit(lg_server_t s, lg_handle h, int32_t k, const double* B, double* X, double tol,
                     uint64_t* ticket);
@@ -458,6 +474,10 @@ int lg_serve_request_bytes(lg_handle h, int32_t k, double* bytes);
 
 /* Latency and throughput statistics over completed requests. */
 int lg_serve_stats(lg_server_t s, lg_serve_stats_t* st);
+
+/* Start the statistics afresh (latencies, counts, phase times, the clock of
+ * solves_per_s): successive measurements on one server. */
+int lg_serve_reset_stats(lg_server_t s);
 
 /* Wait for every queued request, then release the server's threads and streams. */
 void lg_serve_destroy(lg_server_t s);

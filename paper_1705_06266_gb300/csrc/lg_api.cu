@@ -43,6 +43,7 @@ Hier::~Hier() {
   ws.reset();
   wsb.reset();
   many.reset();
+  mplans.reset();
   levels.clear();
   dev_err.release();
   perm.release();
@@ -319,9 +320,11 @@ int lg_solve_batch(lg_handle hh, int32_t k, const double* B, int64_t ldb, double
   lg::DBuf<double> Bd((size_t)n * k, s), Xd((size_t)n * k, s);
   for (int c = 0; c < k; ++c)
     LG_CUDA(cudaMemcpyAsync(Bd.get() + (size_t)c * n, B + (size_t)c * ldb, sizeof(double) * n, cudaMemcpyDefault, s));
-  if (k > 1 && (!h.wsb || h.wsb->k < k)) {
+  int kp = 1;
+  while (kp < k) kp <<= 1;  // multi-column vectors are [n][k rounded up to a power of two]
+  if (k > 1 && (!h.wsb || h.wsb->k < kp)) {
     h.wsb.reset();
-    h.wsb = lg::make_workspace(h, k, s);
+    h.wsb = lg::make_workspace(h, kp, s);
   }
   std::vector<lg_info> own;
   lg_info* out = infos;
@@ -595,9 +598,11 @@ int lg_vcycle_batch(lg_handle hh, int32_t k, const double* F, int64_t ldf, doubl
   if (ldf < n || ldx < n) return LG_ERR_INVALID;
   LG_API_BEGIN
   cudaStream_t s = h.stream;
-  if (!h.wsb || h.wsb->k < k) {
+  int kp = 2;
+  while (kp < k) kp <<= 1;  // multi-column vectors are [n][k rounded up to a power of two]
+  if (!h.wsb || h.wsb->k < kp) {
     h.wsb.reset();
-    h.wsb = lg::make_workspace(h, k < 2 ? 2 : k, s);
+    h.wsb = lg::make_workspace(h, kp, s);
   }
   lg::DBuf<double> Fd((size_t)n * k, s), Xd((size_t)n * k, s);
   for (int c = 0; c < k; ++c)

@@ -822,6 +822,7 @@ Workspace::~Workspace() {
 std::unique_ptr<Workspace> make_workspace(Hier& h, int k, cudaStream_t s) {
   auto ws = std::make_unique<Workspace>();
   ws->k = k;
+  ws->alloc_stream = s;
   int64_t* c = &ws->bytes;
   const size_t L = h.levels.size();
   ws->v64.resize(L);

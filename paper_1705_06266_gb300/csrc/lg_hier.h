@@ -162,6 +162,7 @@ struct Prof {
 // precisions, the FP64 Krylov vectors, reduction scratch and device scalars.
 struct Workspace {
   int k = 1;
+  cudaStream_t alloc_stream = nullptr;  // the stream its memory is allocated and freed on
   std::vector<LevelVecs<double>> v64;
   std::vector<LevelVecs<float>> v32;
   std::vector<LevelScratch> scratch;
@@ -232,6 +233,8 @@ struct Hier {
   DBuf<int32_t> perm;                   // level-0 vertex i is the caller's vertex perm[i]
   int first_agg = -1;                   // first aggregation level (-1: none)
   std::shared_ptr<void> many;           // device views of the levels for lg_solve_many (lg_many.cu)
+  std::shared_ptr<void> mplans;         // SpMM plans of multi-column solves, read by every workspace (lg_batch.cu);
+                                        // released before the handle's stream, with the workspaces' own state
   bool fp32_only = false;               // FP64 copies released (option fp32_only): FP32 solves only
   bool time_stages = false;             // record setup_stages (set before the setup)
   std::vector<std::pair<std::string, double>> setup_stages;  // device ms per setup stage
@@ -270,6 +273,16 @@ void vcycle_apply_batch(Hier& h, Workspace& ws, int k, const double* F, double* 
 double iteration_work(const Hier& h);
 int pcg_solve_batch(Hier& h, Workspace& ws, int k, const double* B, double* X, double tol, int precision,
                     cudaStream_t s, lg_info* infos);
+// Build (and tune, timing passes at width kp) the multi-column plans of h now
+// rather than at its first multi-column solve.
+void prepare_columns(Hier& h, int kp, int precision);
+// Capture ws's multi-column solve loops (every width up to ws.k) on stream s
+// now rather than at their first solves.
+void prepare_column_graphs(Hier& h, Workspace& ws, int precision, cudaStream_t s);
+// The multi-column path for every k (k = 1 included), whose per-column
+// results do not depend on the batch (the server's solves).
+int pcg_solve_columns(Hier& h, Workspace& ws, int k, const double* B, double* X, double tol, int precision,
+                      cudaStream_t s, lg_info* infos);
 
 // ---- save and load (lg_io.cu) ----
 void save_hierarchy(const Hier& h, const char* path);
@@ -279,11 +292,14 @@ void save_hierarchy(const Hier& h, const char* path);
 void load_hierarchy(Hier& h, const char* path, const lg_options* opts);
 
 // ---- many small solves in one launch (lg_many.cu) ----
+// Build h's device views for the packed solver now (else at its first packed solve).
+void prepare_many(Hier& h);
 constexpr int64_t kManyMaxNnz = int64_t(1) << 22;  // largest nnz(L_0) one block solves
 constexpr int kManyMaxLevels = 64;
 // hs: distinct handles on one device; b / x: each graph's vectors in the
 // caller's numbering, device memory where b_dev / x_dev say so, else host.
+// precision: LG_FP64 / LG_FP32_HIER for every graph, or -1 for each handle's own.
 int solve_many(int count, Hier* const* hs, const double* const* b, double* const* x, const bool* b_dev,
-               const bool* x_dev, double tol, lg_info* infos);
+               const bool* x_dev, double tol, lg_info* infos, int precision = -1);
 
 }  // namespace lg

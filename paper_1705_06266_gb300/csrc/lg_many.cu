@@ -769,8 +769,13 @@ struct PinnedStage {
 };
 static PinnedStage g_pin;
 
+void prepare_many(Hier& h) {
+  std::lock_guard<std::mutex> lock(g_pin.m);  // solve_many builds the views under the same lock
+  many_levels(h);
+}
+
 int solve_many(int count, Hier* const* hs, const double* const* b, double* const* x, const bool* b_dev,
-               const bool* x_dev, double tol, lg_info* infos) {
+               const bool* x_dev, double tol, lg_info* infos, int precision) {
   cudaStream_t s = hs[0]->stream;
   // every event of the call is destroyed on every exit, error paths included
   struct Events {
@@ -842,7 +847,7 @@ int solve_many(int count, Hier* const* hs, const double* const* b, double* const
     G.first_agg = h.first_agg;
     G.kcycle = h.opts.kcycle;
     G.deg = h.opts.cheb_degree;
-    G.fp32 = h.opts.precision == LG_FP32_HIER;
+    G.fp32 = (precision < 0 ? h.opts.precision : precision) == LG_FP32_HIER;
     G.maxit = h.opts.max_iter;
     G.every = h.opts.residual_replace > 0 ? h.opts.residual_replace : 1 << 30;
     G.tol = tol;

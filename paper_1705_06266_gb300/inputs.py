@@ -194,6 +194,57 @@ def rmat(scale: int, *, edge_factor: int = 16, a: float = 0.57, b: float = 0.19,
     return from_edges(n, u, v, weights=weights, seed=seed + 7, name=f"rmat_{scale}_{edge_factor}")
 
 
+def _device_csr(n: int, key, *, weights: str, seed: int, device: str):
+    """Deduplicated pair keys lo * n + hi (lo < hi) on a torch device -> the
+    largest component as a symmetric CSR (n, rowptr int64, col int32, w
+    float64), vertices renumbered in id order, rows sorted. Weights: "unit",
+    or "uniform" in [0.5, 1.5) drawn by a seeded torch generator in key order."""
+    import torch
+
+    u, v = key // n, key % n
+    if weights == "unit":
+        wt = torch.ones(key.numel(), dtype=torch.float64, device=device)
+    else:
+        gen = torch.Generator(device=device)
+        gen.manual_seed(seed)
+        wt = 0.5 + torch.rand(key.numel(), generator=gen, device=device, dtype=torch.float64)
+    del key
+    # largest component: labels converge to the smallest id of each component
+    label = torch.arange(n, dtype=torch.int64, device=device)
+    while True:
+        mn = torch.minimum(label[u], label[v])
+        new = label.clone()
+        new.scatter_reduce_(0, u, mn, reduce="amin")
+        new.scatter_reduce_(0, v, mn, reduce="amin")
+        del mn
+        new = new[new]
+        new = new[new]
+        if torch.equal(new, label):
+            break
+        label = new
+    root = torch.bincount(label, minlength=n).argmax()
+    inc = label == root
+    del label, new
+    nid = torch.cumsum(inc.to(torch.int64), 0) - 1
+    keep = inc[u]  # both ends of an edge share a component
+    u, v, wt = nid[u[keep]], nid[v[keep]], wt[keep]
+    nl = int(inc.sum())
+    del nid, keep, inc
+    rows = torch.cat([u, v])
+    cols = torch.cat([v, u])
+    ws = torch.cat([wt, wt])
+    del u, v, wt
+    order = torch.argsort(rows * nl + cols)
+    rows, cols, ws = rows[order], cols[order].to(torch.int32), ws[order]
+    del order
+    rowptr = torch.zeros(nl + 1, dtype=torch.int64, device=device)
+    rowptr[1:] = torch.cumsum(torch.bincount(rows, minlength=nl), 0)
+    del rows
+    if str(device).startswith("cuda"):
+        torch.cuda.empty_cache()  # hand the temporaries' memory back for the solver's own allocations
+    return nl, rowptr, cols, ws
+
+
 def rmat_device(scale: int, *, edge_factor: int = 16, a: float = 0.57, b: float = 0.19, c: float = 0.19,
                 seed: int = 1, device: str = "cuda", chunk: int = 1 << 27):
     """R-MAT (Chakrabarti, Zhan & Faloutsos 2004) generated on a torch device,
@@ -227,42 +278,70 @@ def rmat_device(scale: int, *, edge_factor: int = 16, a: float = 0.57, b: float 
         del lo, hi, keep
     key = torch.unique(torch.cat(parts))
     del parts
-    u, v = key // n, key % n
-    del key
-    # largest component: labels converge to the smallest id of each component
-    label = torch.arange(n, dtype=torch.int64, device=device)
-    while True:
-        mn = torch.minimum(label[u], label[v])
-        new = label.clone()
-        new.scatter_reduce_(0, u, mn, reduce="amin")
-        new.scatter_reduce_(0, v, mn, reduce="amin")
-        del mn
-        new = new[new]
-        new = new[new]
-        if torch.equal(new, label):
-            break
-        label = new
-    root = torch.bincount(label, minlength=n).argmax()
-    inc = label == root
-    del label, new
-    nid = torch.cumsum(inc.to(torch.int64), 0) - 1
-    keep = inc[u]  # both ends of an edge share a component
-    u, v = nid[u[keep]], nid[v[keep]]
-    nl = int(inc.sum())
-    del nid, keep, inc
-    rows = torch.cat([u, v])
-    cols = torch.cat([v, u])
+    return _device_csr(n, key, weights="unit", seed=seed, device=device)
+
+
+def chung_lu_device(n: int, *, exponent: float = 2.1, dmin: float = 1.0, dmax: float = 50000.0,
+                    m_target: int | None = None, seed: int = 1, device: str = "cuda"):
+    """Chung-Lu power-law graph on a torch device (the recipe of chung_lu():
+    expected degrees i.i.d. Pareto with the given exponent truncated to [dmin,
+    dmax], m_target endpoint pairs drawn with probability proportional to the
+    expected degree, self-loops dropped, pairs deduplicated, weights uniform in
+    [0.5, 1.5), largest component). Another generator than chung_lu(): the
+    same distribution, not the same graph at equal seeds."""
+    import torch
+
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    a = exponent - 1.0
+    uu = torch.rand(n, generator=gen, device=device, dtype=torch.float64)
+    theta = dmin * (1.0 - uu * (1.0 - (dmin / dmax) ** a)) ** (-1.0 / a)
+    if m_target is None:
+        m_target = int(theta.sum().item() / 2)
+    cdf = torch.cumsum(theta / theta.sum(), 0)
+    cdf[-1] = 1.0
+    u = torch.searchsorted(cdf, torch.rand(m_target, generator=gen, device=device, dtype=torch.float64), right=True)
+    v = torch.searchsorted(cdf, torch.rand(m_target, generator=gen, device=device, dtype=torch.float64), right=True)
+    u.clamp_(max=n - 1)
+    v.clamp_(max=n - 1)
+    lo, hi = torch.minimum(u, v), torch.maximum(u, v)
     del u, v
-    order = torch.argsort(rows * nl + cols)
-    rows, cols = rows[order], cols[order].to(torch.int32)
-    del order
-    rowptr = torch.zeros(nl + 1, dtype=torch.int64, device=device)
-    rowptr[1:] = torch.cumsum(torch.bincount(rows, minlength=nl), 0)
-    del rows
-    w = torch.ones(cols.numel(), dtype=torch.float64, device=device)
-    if str(device).startswith("cuda"):
-        torch.cuda.empty_cache()  # hand the temporaries' memory back for the solver's own allocations
-    return nl, rowptr, cols, w
+    keep = lo != hi
+    key = torch.unique(lo[keep] * n + hi[keep])
+    del lo, hi, keep
+    return _device_csr(n, key, weights="uniform", seed=seed + 7, device=device)
+
+
+def serving_mix_device(count: int, nmin: int, nmax: int, *, seed: int = 5, device: str = "cuda"):
+    """The serving workload of serving_mix() (the same sizes and types, drawn
+    from the same seed), with the power-law members generated on the device
+    (chung_lu_device, rmat_device) so that hundreds of graphs up to millions of
+    vertices are made in seconds. Returns [(name, n, rowptr, col, w)] with
+    device tensors."""
+    import torch
+
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for q in range(count):
+        n = int(round(math.exp(rng.uniform(math.log(nmin), math.log(nmax)))))
+        kind = int(rng.integers(0, 4))
+        if kind in (0, 1):
+            if kind == 0:
+                side = max(2, int(round(math.sqrt(n))))
+                g = grid2d(side, side)
+            else:
+                side = max(2, int(round(n ** (1.0 / 3.0))))
+                g = grid3d(side, side, side)
+            out.append((g.name, g.n, torch.from_numpy(g.rowptr).to(device), torch.from_numpy(g.col).to(device),
+                        torch.from_numpy(g.w).to(device)))
+        elif kind == 2:
+            nl, rp, cl, w = chung_lu_device(n, m_target=5 * n, seed=1000 + q, device=device)
+            out.append((f"chung_lu_{n}_2.1", nl, rp, cl, w))
+        else:
+            sc = max(6, int(round(math.log2(n))))
+            nl, rp, cl, w = rmat_device(sc, seed=1000 + q, device=device)
+            out.append((f"rmat_{sc}_16", nl, rp, cl, w))
+    return out
 
 
 def random_graph(n: int, avg_degree: float, *, seed: int = 1, weights: str = "uniform") -> Graph:

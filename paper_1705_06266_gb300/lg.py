@@ -64,7 +64,9 @@ class ServeStats(C.Structure):
     _fields_ = [("p50_ms", C.c_double), ("p99_ms", C.c_double), ("mean_ms", C.c_double),
                 ("max_ms", C.c_double), ("solves_per_s", C.c_double), ("resident_bytes", C.c_double),
                 ("completed", C.c_int64), ("failed", C.c_int64), ("pending", C.c_int64),
-                ("running", C.c_int64)]
+                ("running", C.c_int64), ("groups", C.c_int64), ("packed_groups", C.c_int64),
+                ("workspaces_made", C.c_int64), ("workspace_ms", C.c_double), ("copy_ms", C.c_double),
+                ("solve_ms", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -108,6 +110,7 @@ _SIGS = {
     "lg_serve_submit": (C.c_int, [_P, _P, _I32, _P, _P, _D, _P]),
     "lg_serve_poll": (C.c_int, [_P, _U64, _P, _P]),
     "lg_serve_stats": (C.c_int, [_P, _P]),
+    "lg_serve_reset_stats": (C.c_int, [_P]),
     "lg_serve_request_bytes": (C.c_int, [_P, _I32, _P]),
     "lg_serve_destroy": (None, [_P]),
 }
@@ -372,6 +375,10 @@ def lg_serve_stats(s) -> ServeStats:
     st = ServeStats()
     _check(_load().lg_serve_stats(s, C.byref(st)), "lg_serve_stats")
     return st
+
+
+def lg_serve_reset_stats(s):
+    _check(_load().lg_serve_reset_stats(s), "lg_serve_reset_stats")
 
 
 def lg_serve_destroy(s):

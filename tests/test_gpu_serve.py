@@ -1,12 +1,13 @@
 """The continuous-batching server (lg_serve_*).
 
 Requests on graphs of different sizes arrive while others are running; each
-must be admitted as slots and budget free up, overlap on the device with the
-others, and give the same result as when it runs alone. The served solves run
-the same kernels with the same launch plans whatever else is in flight and
-every reduction is in a fixed order, so "the same" is bitwise here; each
-result is also checked for a true relative residual <= 1e-8 recomputed with
-scipy.
+must be admitted as slots and budget free up, join other requests in one
+multi-column batch (same hierarchy) or one packed launch (single columns on
+small graphs), overlap on the device with the others, and give the same
+result as when it runs alone. A column is computed the same way whatever it
+is grouped with and every reduction is in a fixed order, so "the same" is
+bitwise here; each result is also checked for a true relative residual
+<= 1e-8 recomputed with scipy, and against the oracle's solution.
 """
 
 import time
@@ -61,10 +62,23 @@ def request_mix(graphs, inputs, count, seed):
     return [reqs[i] for i in order]
 
 
+@pytest.fixture(scope="module")
+def oracle_x(oracle, graphs):
+    """The oracle's solution of a column (PCG to 1e-12), per graph."""
+    hs = {name: oracle.Hierarchy(g) for name, (g, _) in graphs.items()}
+
+    def solve(name, b):
+        x, st, it, rel = hs[name].pcg(b, tol=1e-12, maxit=1000)
+        assert st == oracle.OK
+        return x - x.mean()
+
+    return solve
+
+
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
-def test_serve_same_alone_and_in_mix(lgmod, inputs, graphs, prec):
+def test_serve_same_alone_and_in_mix(lgmod, inputs, graphs, oracle_x, prec):
     p = lgmod.FP64 if prec == "fp64" else lgmod.FP32_HIER
-    reqs = request_mix(graphs, inputs, 12, seed=7)
+    reqs = request_mix(graphs, inputs, 16, seed=7)
 
     alone = []
     sv = lgmod.Server(slots=1, precision=p)
@@ -91,6 +105,61 @@ def test_serve_same_alone_and_in_mix(lgmod, inputs, graphs, prec):
         assert np.array_equal(Xa, Xm), name
         assert relres_cols(graphs[name][0], B, Xm).max() <= TOL * 1.0001
         assert np.abs(Xm.mean(axis=0)).max() <= 1e-12 * np.abs(Xm).max()
+        for c in range(B.shape[1]):
+            ref = oracle_x(name, B[:, c])
+            assert np.linalg.norm(Xm[:, c] - ref) <= 1e-6 * np.linalg.norm(ref), name
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_serve_merges_and_packs(lgmod, inputs, graphs, prec):
+    """Requests queued behind a running one are taken together: the ones on
+    one hierarchy as one multi-column batch, the single columns on small
+    graphs as one packed launch; results equal those of each request alone."""
+    p = lgmod.FP64 if prec == "fp64" else lgmod.FP32_HIER
+    g_big, H_big = graphs["chunglu_30k"]
+    smalls = ["grid2d_40", "grid3d_12", "rmat_13"]
+    reqs = [("chunglu_30k", rhs2(inputs, g_big.n, 2, 200 + q)) for q in range(4)]  # 8 columns: one batch
+    reqs += [(name, rhs2(inputs, graphs[name][0].n, 1, 300 + q)) for q, name in enumerate(smalls)]
+    sv = lgmod.Server(slots=1, precision=p)
+    for _, H in graphs.values():
+        sv.register(H)
+    alone = []
+    for name, B in reqs:
+        X, info = sv.wait(sv.submit(graphs[name][1], B, TOL))
+        assert info.status == lgmod.OK
+        alone.append(X)
+    sv.close()
+    sv = lgmod.Server(slots=1, precision=p)
+    for _, H in graphs.values():
+        sv.register(H)
+    blocker = sv.submit(H_big, rhs2(inputs, g_big.n, 8, 99), TOL)  # holds the one slot while the rest queue up
+    tickets = [sv.submit(graphs[name][1], B, TOL) for name, B in reqs]
+    sv.wait(blocker)
+    mixed = [sv.wait(t) for t in tickets]
+    st = sv.stats()
+    sv.close()
+    assert st.completed == len(reqs) + 1
+    assert st.packed_groups >= 1
+    assert st.groups <= 3  # the blocker, one batch of the four requests on one graph, one packed launch
+    for (name, B), Xa, (Xm, info) in zip(reqs, alone, mixed):
+        assert info.status == lgmod.OK
+        assert np.array_equal(Xa, Xm), name
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_batch_columns_independent_of_width(lgmod, inputs, prec):
+    """lg_solve_batch's columns do not depend on the batch: 5 columns solved
+    together equal the same columns solved as batches of 2 and 3."""
+    p = lgmod.FP64 if prec == "fp64" else lgmod.FP32_HIER
+    g = inputs.chung_lu(20000, m_target=100000, seed=3)
+    H = lgmod.Hierarchy(g)
+    B = inputs.rhs(g.n, 5, seed=8).reshape(g.n, 5)
+    X5, i5 = H.solve_batch(B, precision=p)
+    X2, i2 = H.solve_batch(np.ascontiguousarray(B[:, :2]), precision=p)
+    X3, i3 = H.solve_batch(np.ascontiguousarray(B[:, 2:]), precision=p)
+    np.testing.assert_array_equal(X5, np.concatenate([X2, X3], axis=1))
+    assert [i.iterations for i in i5] == [i.iterations for i in i2 + i3]
+    H.close()
 
 
 def test_serve_short_request_overtakes_long(lgmod, inputs):

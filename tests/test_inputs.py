@@ -61,3 +61,28 @@ def test_serving_mix(oracle, inputs):
     for g in gs:
         assert oracle.check_graph(g) == oracle.OK
         assert 30 <= g.n <= 5200
+
+
+def test_chung_lu_on_the_device_generator_runs_on_cpu(oracle, inputs):
+    pytest.importorskip("torch")
+    n, rp, cl, w = inputs.chung_lu_device(6000, m_target=30000, seed=4, device="cpu")
+    g = inputs.Graph(int(n), rp.numpy(), cl.numpy(), w.numpy())
+    assert oracle.check_graph(g) == oracle.OK  # the largest component, symmetric, sorted
+    assert 3000 < g.n <= 6000
+    assert g.w.min() >= 0.5 and g.w.max() < 1.5
+    deg = np.diff(g.rowptr)
+    assert deg.max() > 10 * deg.mean()  # heavy-tailed, as the host recipe
+
+
+def test_serving_mix_on_the_device_matches_the_host_recipe(oracle, inputs):
+    pytest.importorskip("torch")
+    host = inputs.serving_mix(8, 500, 5000, seed=9)
+    dev = inputs.serving_mix_device(8, 500, 5000, seed=9, device="cpu")
+    assert len(dev) == 8
+    for g, (name, n, rp, cl, w) in zip(host, dev):
+        gd = inputs.Graph(int(n), rp.numpy(), cl.numpy(), w.numpy())
+        assert oracle.check_graph(gd) == oracle.OK
+        kind = g.name.split("_")[0]
+        assert name.split("_")[0] == kind  # same type per slot
+        if kind == "grid2d" or kind == "grid3d":
+            assert np.array_equal(gd.rowptr, g.rowptr) and np.array_equal(gd.col, g.col)
