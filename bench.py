@@ -30,6 +30,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -66,7 +67,7 @@ def parse():
     ap.add_argument("--many-graphs", type=int, default=608)
     ap.add_argument("--serve-graphs", type=int, default=256)
     ap.add_argument("--serve-nmax", type=int, default=2000000)
-    ap.add_argument("--serve-requests", type=int, default=1500)
+    ap.add_argument("--serve-requests", type=int, default=600)
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-load", type=float, default=0.8)
     return ap.parse_args()
@@ -485,12 +486,34 @@ def serve_leg(lg, inputs, args, torch, dev):
         span = time.perf_counter() - t0
         return lg.lg_serve_stats(sv), span, rhs, failed
 
-    burst = requests(max(100, args.serve_requests // 4))
+    def closed_loop(reqs):
+        """slots requests in flight at all times (a new one as one completes): the capacity
+        without queueing, hence without merging."""
+        lg.lg_serve_reset_stats(sv)
+        live, rhs, nxt = {}, 0, 0
+        t0 = time.perf_counter()
+        while nxt < len(reqs) or live:
+            while nxt < len(reqs) and len(live) < args.serve_slots:
+                gi, k = reqs[nxt]
+                X = np.empty((k, sizes[gi]))
+                live[lg.lg_serve_submit(sv, hs[gi].h, k, blocks[gi][:k], X, TOL)] = X
+                rhs += k
+                nxt += 1
+            for t in list(live):
+                done, info = lg.lg_serve_poll(sv, t)
+                if done:
+                    del live[t]
+        return lg.lg_serve_stats(sv), time.perf_counter() - t0, rhs
+
+    n_probe = max(100, args.serve_requests // 4)
+    st_c, span_c, rhs_c = closed_loop(requests(n_probe))
+    cap_rps = n_probe / span_c
+    burst = requests(n_probe)  # every request queued at once: the most merging
     st_b, span_b, rhs_b, fail_b = run(burst, None)
     sat_rps = len(burst) / span_b
     loads = {}
     for load in sorted({0.5, args.serve_load, 0.95}):
-        rate = load * sat_rps
+        rate = load * cap_rps
         st, span, rhs, failed = run(requests(args.serve_requests), rate)
         loads[load] = (rate, st, span, rhs, failed)
     resident = sum(lg.lg_hier_bytes(H.h)[0] for H in hs)
@@ -501,7 +524,8 @@ def serve_leg(lg, inputs, args, torch, dev):
     return {
         "p50_ms": st.p50_ms, "p99_ms": st.p99_ms, "mean_ms": st.mean_ms, "max_ms": st.max_ms,
         "solves_per_s": rhs / span, "requests_per_s": args.serve_requests / span,
-        "offered_rps": rate, "saturation_rps": sat_rps, "saturation_solves_per_s": rhs_b / span_b,
+        "offered_rps": rate, "capacity_rps": cap_rps, "capacity_solves_per_s": rhs_c / span_c,
+        "capacity_p50_ms": st_c.p50_ms, "saturation_rps": sat_rps, "saturation_solves_per_s": rhs_b / span_b,
         "saturation_p50_ms": st_b.p50_ms, "saturation_p99_ms": st_b.p99_ms,
         "saturation_groups": int(st_b.groups), "saturation_packed_groups": int(st_b.packed_groups),
         "saturation_phase_ms": {"workspaces_made": int(st_b.workspaces_made), "workspace": st_b.workspace_ms,
@@ -519,9 +543,10 @@ def serve_leg(lg, inputs, args, torch, dev):
         "config": f"{len(hs)} resident graphs, n log-uniform in [1000, {args.serve_nmax}], type uniform over "
                   f"2D grid / 3D grid / Chung-Lu 2.1 / R-MAT ef16 (power-law members generated on the device); "
                   f"FP32-only hierarchies; k uniform in 1..8; tol 1e-8; {args.serve_slots} slots; HBM budget "
-                  f"120 GB; a burst of {len(burst)} requests for the saturation rate, then Poisson arrivals at "
-                  f"0.5, {args.serve_load} (headline) and 0.95 x that rate, {args.serve_requests} requests each; "
-                  f"latency = submission to completion with host B and X",
+                  f"120 GB; capacity = completion rate of {n_probe} requests with one in flight per slot (no "
+                  f"queue, no merging); saturation = completion rate of a burst of {len(burst)} queued at once (the "
+                  f"most merging); then Poisson arrivals at 0.5, {args.serve_load} (headline) and 0.95 x capacity, "
+                  f"{args.serve_requests} requests each; latency = submission to completion with host B and X",
     }
 
 
@@ -631,6 +656,7 @@ def load_main(args, inputs, torch, dev):
 
 
 def main():
+    t_main = time.perf_counter()
     args = parse()
     world, rank, local = dist_init()
     if args.impl == "reference":
@@ -704,9 +730,22 @@ def main():
         step_ms = ev0.elapsed_time(ev1) / args.steps
 
         # After the timed region, on one more (bitwise identical) hierarchy:
-        # the FP32 per-level pass table, each result's error against an FP64
-        # solve to 1e-12, and the end-to-end solves from host buffers.
-        h = lg.lg_setup(n, rp, cl, w, opts)
+        # its setup's stage times (from the library's setup log), the FP32
+        # per-level pass table, each result's error against an FP64 solve to
+        # 1e-12, and the end-to-end solves from host buffers.
+        log_path = os.path.join(tempfile.gettempdir(), f"lg_setup_{os.getpid()}.jsonl")
+        os.environ["LG_LOG"] = log_path
+        try:
+            h = lg.lg_setup(n, rp, cl, w, opts)
+        finally:
+            del os.environ["LG_LOG"]
+        setup_stages = None
+        try:
+            with open(log_path) as f:
+                setup_stages = json.loads(f.readlines()[-1]).get("stages_ms")
+            os.remove(log_path)
+        except (OSError, ValueError, IndexError):
+            pass
         nlev = lg.lg_hier_info(h).levels
         lg.lg_set_precision(h, lg.FP32_HIER)
         lg.lg_profile(h, True)
@@ -845,7 +884,7 @@ def main():
                                 "(value and fp32_hier from the solves without events)",
                         "l2": "flushed (512 MiB write) before setup and before each solve",
                         "parallelism": "replicas" if world > 1 else "single GPU"}, **desc),
-        "solve_ms": solve64_ms, "setup_ms": setup_ms,
+        "solve_ms": solve64_ms, "setup_ms": setup_ms, "setup_stages_ms": setup_stages,
         "iterations": i64.iterations, "relres": i64.relres, "levels": i64.levels,
         "op_complexity": recs[-1][0].op_complexity,
         "setup_inclusive_nnz_per_s": world * nnz / ((setup_ms + solve64_ms) * 1e-3),
@@ -896,6 +935,7 @@ def main():
                      f"sample: ")
         else:
             line["cpu_baseline"] = cpu_baseline(args.workload, g_host, b)
+    line["bench_wall_s"] = time.perf_counter() - t_main
     print(json.dumps(line), flush=True)
 
 

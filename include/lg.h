@@ -126,6 +126,16 @@ typedef struct {
                                only: lg_set_precision(LG_FP64), FP64 lg_vcycle / lg_vcycle_batch /
                                lg_level_apply, lg_level_copy of a released level, lg_save, and
                                registration with an FP64 server return LG_ERR_INVALID. */
+  int32_t const_weights;    /* 1: when every weight of the finest operator is the same value (an
+                               unweighted graph), keep its pattern only and apply the value as a
+                               constant: each pass over L_0 streams the 4-byte column ids alone
+                               (not 8 + 4 bytes per entry in FP64). Solves give bitwise the same
+                               results either way. 0: always store the weights. */
+  int32_t row_sorts;        /* 1: the setup's sparse products whose entries are produced row by row
+                               (the vertex renumbering, the Schur complement, W = L P) sort each
+                               row's entries on its own instead of sorting all entries by (row,
+                               column) with a global radix sort; the order, and so every sum and
+                               the hierarchy, is the same bit for bit. 0: global sorts. */
 } lg_options;
 
 /* Logging: with the environment variable LG_LOG naming a file, lg_setup and
@@ -330,8 +340,10 @@ int lg_profile(lg_handle h, int32_t enable);
  * their chunks, out[5] = blocks of one pass served by chunks, out[6] = tiles
  * of the column-segmented long-row pass (0: the long rows go by chunks; else
  * they go column-segmented, with the gathered vector staged in shared memory,
- * in passes that reduce nothing across the grid). */
-int lg_level_plan(lg_handle h, int32_t l, int64_t out[7]);
+ * in passes that reduce nothing across the grid), out[7] = 1 when the level's
+ * weights are one constant kept in place of its weight arrays (option
+ * const_weights), else 0. */
+int lg_level_plan(lg_handle h, int32_t l, int64_t out[8]);
 int lg_profile_read(lg_handle h, int32_t level, lg_kernel_profile* out);
 
 /* One multi-column V-cycle on k right-hand sides at once (1 <= k <= 32): X =

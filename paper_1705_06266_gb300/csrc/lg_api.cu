@@ -62,6 +62,22 @@ static bool is_device_ptr(const void* p, int memory_space) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+__global__ void k_fill_value(double* __restrict__ a, double v, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    a[i] = v;
+}
+
+// n copies of v into a (device or host memory), ordered on stream s.
+static void fill_value(double* a, double v, int64_t n, int memory_space, cudaStream_t s) {
+  if (is_device_ptr(a, memory_space)) {
+    k_fill_value<<<grid_for(n, 256, kSMs * 8), 256, 0, s>>>(a, v, n);
+    LG_LAUNCH_CHECK();
+  } else {
+    LG_CUDA(cudaStreamSynchronize(s));
+    std::fill_n(a, n, v);
+  }
+}
+
 // One JSON line per setup and per solved right-hand side, appended to the
 // file named by the environment variable LG_LOG (nothing when it is unset).
 static std::mutex g_log_mu;
@@ -158,6 +174,9 @@ int lg_options_default(lg_options* o) {
   o->kcycle = 0;
   o->elim_rounds = 1;
   o->lp_residual = 1;
+  o->fp32_only = 0;
+  o->const_weights = 1;
+  o->row_sorts = 1;
   return LG_OK;
 }
 
@@ -453,7 +472,12 @@ int lg_level_copy(lg_handle hh, int32_t l, int64_t* rowptr, int32_t* col, double
   cudaStream_t s = h.stream;
   if (rowptr) LG_CUDA(cudaMemcpyAsync(rowptr, L.rowptr.get(), sizeof(int64_t) * (L.n + 1), cudaMemcpyDefault, s));
   if (col && L.nnz) LG_CUDA(cudaMemcpyAsync(col, L.col.get(), sizeof(int32_t) * L.nnz, cudaMemcpyDefault, s));
-  if (w && L.nnz) LG_CUDA(cudaMemcpyAsync(w, L.w.get(), sizeof(double) * L.nnz, cudaMemcpyDefault, s));
+  if (w && L.nnz) {
+    if (L.wconst_on)
+      lg::fill_value(w, L.wconst, L.nnz, h.opts.memory_space, s);
+    else
+      LG_CUDA(cudaMemcpyAsync(w, L.w.get(), sizeof(double) * L.nnz, cudaMemcpyDefault, s));
+  }
   if (map) {
     if (L.kind == LG_LEVEL_AGG)
       LG_CUDA(cudaMemcpyAsync(map, L.agg.get(), sizeof(int32_t) * L.n, cudaMemcpyDefault, s));
@@ -519,8 +543,8 @@ int lg_level_apply(lg_handle hh, int32_t level, int32_t precision, const void* x
   if (!hh || !x || !y || (precision != LG_FP64 && precision != LG_FP32_HIER)) return LG_ERR_INVALID;
   lg::Hier& h = *H(hh);
   if (level < 0 || level >= (int)h.levels.size() || h.levels[level]->kind == LG_LEVEL_COARSEST) return LG_ERR_INVALID;
-  if (precision == LG_FP32_HIER ? !h.levels[level]->w32.get() && h.levels[level]->nnz > 0
-                                : !h.levels[level]->w.get() && h.levels[level]->nnz > 0)
+  const lg::Level& Lv = *h.levels[level];
+  if (Lv.nnz > 0 && !Lv.wconst_on && (precision == LG_FP32_HIER ? !Lv.w32.get() : !Lv.w.get()))
     return LG_ERR_INVALID;
   if (h.fp32_only && level > 0 && h.levels[level]->kind == LG_LEVEL_ELIM) return LG_ERR_INVALID;  // rows released
   LG_API_BEGIN
@@ -554,7 +578,7 @@ int lg_level_lp_nnz(lg_handle hh, int32_t l, int64_t* nnz) {
   return LG_OK;
 }
 
-int lg_level_plan(lg_handle hh, int32_t l, int64_t out[7]) {
+int lg_level_plan(lg_handle hh, int32_t l, int64_t out[8]) {
   if (!hh || !out) return LG_ERR_INVALID;
   lg::Hier& h = *H(hh);
   if (l < 0 || l >= (int32_t)h.levels.size()) return LG_ERR_INVALID;
@@ -566,6 +590,7 @@ int lg_level_plan(lg_handle hh, int32_t l, int64_t out[7]) {
   out[4] = p.nchunks;
   out[5] = p.grid();
   out[6] = p.nseg_tiles;
+  out[7] = h.levels[l]->wconst_on ? 1 : 0;
   return LG_OK;
 }
 

@@ -181,25 +181,27 @@ template <typename T>
 struct MLap;
 
 template <>
-struct MLap<float> {  // difference form, as the single-vector FP32 pass
+struct MLap<float> {  // difference form, as the single-vector FP32 pass (null w: every weight wc)
   const float* __restrict__ w;
   const float* __restrict__ x;
   int ld;
+  float wc;
   __device__ __forceinline__ const float* src() const { return x; }
-  __device__ __forceinline__ float coef(int64_t e) const { return ld_stream(&w[e]); }
+  __device__ __forceinline__ float coef(int64_t e) const { return w ? ld_stream(&w[e]) : wc; }
   __device__ __forceinline__ float rowv(int64_t i, int c) const { return x[i * ld + c]; }
   __device__ __forceinline__ float step(float s, float wk, float xj, float xi) const { return fmaf(wk, xi - xj, s); }
   __device__ __forceinline__ float finish(int64_t, int, float, float s) const { return s; }
 };
 
 template <>
-struct MLap<double> {  // d_i x_i - sum_j w_ij x_j, as the single-vector FP64 pass
+struct MLap<double> {  // d_i x_i - sum_j w_ij x_j, as the single-vector FP64 pass (null w: every weight wc)
   const double* __restrict__ w;
   const double* __restrict__ x;
   const double* __restrict__ d;
   int ld;
+  double wc;
   __device__ __forceinline__ const double* src() const { return x; }
-  __device__ __forceinline__ double coef(int64_t e) const { return ld_stream(&w[e]); }
+  __device__ __forceinline__ double coef(int64_t e) const { return w ? ld_stream(&w[e]) : wc; }
   __device__ __forceinline__ double rowv(int64_t, int) const { return 0.0; }
   __device__ __forceinline__ double step(double s, double wk, double xj, double) const { return fma(wk, xj, s); }
   __device__ __forceinline__ double finish(int64_t i, int c, double, double s) const {
@@ -512,7 +514,8 @@ struct MEpiTrueRes {
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void k_m_elim_prolong(int64_t n, int ld, const int64_t* __restrict__ rowptr,
-                                 const int32_t* __restrict__ col, const T* __restrict__ w, const T* __restrict__ dinv,
+                                 const int32_t* __restrict__ col, const T* __restrict__ w, T wc,
+                                 const T* __restrict__ dinv,
                                  const int32_t* __restrict__ cmap, const T* __restrict__ f, const T* __restrict__ xc,
                                  T* __restrict__ x) {
   LG_GRID_STRIDE(e, n * ld) {
@@ -523,7 +526,7 @@ __global__ void k_m_elim_prolong(int64_t n, int ld, const int64_t* __restrict__ 
       x[e] = xc[(int64_t)cm * ld + c];
     } else {
       T s = f[e];
-      for (int64_t q = rowptr[i]; q < rowptr[i + 1]; ++q) s += w[q] * xc[(int64_t)cmap[col[q]] * ld + c];
+      for (int64_t q = rowptr[i]; q < rowptr[i + 1]; ++q) s += (w ? w[q] : wc) * xc[(int64_t)cmap[col[q]] * ld + c];
       x[e] = s * dinv[i];
     }
   }
@@ -920,11 +923,11 @@ template <typename T>
 static MLap<T> mlap(const OpView<T>& op, const T* x, int ld);
 template <>
 MLap<float> mlap<float>(const OpView<float>& op, const float* x, int ld) {
-  return MLap<float>{op.w, x, ld};
+  return MLap<float>{op.w, x, ld, op.wc};
 }
 template <>
 MLap<double> mlap<double>(const OpView<double>& op, const double* x, int ld) {
-  return MLap<double>{op.w, x, op.d, ld};
+  return MLap<double>{op.w, x, op.d, ld, op.wc};
 }
 
 template <typename T>
@@ -963,7 +966,7 @@ static void mcycle(Hier& h, Workspace& ws, BatchState& bs, int l, int kp, cudaSt
                     MEpiElimRestrict<T>{V.f.get(), L.cfine.get(), C.f.get(), d0n, dinvn, itn, kp}, s);
     mcycle<T>(h, ws, bs, l + 1, kp, s);
     const OpView<T> op = L.op<T>();
-    k_m_elim_prolong<T><<<bblocks(n * kp), kBT, 0, s>>>(n, kp, op.rowptr, op.col, op.w, op.dinv, L.cmap.get(),
+    k_m_elim_prolong<T><<<bblocks(n * kp), kBT, 0, s>>>(n, kp, op.rowptr, op.col, op.w, op.wc, op.dinv, L.cmap.get(),
                                                         V.f.get(), C.x.get(), V.x.get());
     LG_LAUNCH_CHECK();
     return;

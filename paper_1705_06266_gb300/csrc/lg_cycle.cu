@@ -231,8 +231,11 @@ struct EpiPost {
 // Algorithmic bytes of one row pass over an operator with elements of size t:
 // the CSR arrays once, the gathered vector once, and `streams` further
 // length-n vector streams (reads or writes) of the epilogue.
-static double pass_bytes(int64_t n, int64_t nnz, int t, int streams) {
-  return (double)nnz * (4.0 + t) + (double)(n + 1) * 8.0 + (double)n * t * (1 + streams);
+// Algorithmic bytes of one pass: the CSR stream (the weights only when the
+// operator stores them), the row pointers, the gathered vector once, and the
+// epilogue's vector streams.
+static double pass_bytes(int64_t n, int64_t nnz, int t, int streams, bool weights = true) {
+  return (double)nnz * (4.0 + (weights ? t : 0)) + (double)(n + 1) * 8.0 + (double)n * t * (1 + streams);
 }
 
 template <typename T>
@@ -248,7 +251,7 @@ static void op_pass(Workspace& ws, int level, const OpView<T>& op, const Term& t
   const bool timed = ws.prof.on && gate == nullptr;  // a gated pass may do nothing: not timed
   if (timed) ws.prof.begin(s);
   launch_rows<T, NRED>(op.n, op.rowptr, op.col, term, op.plan, epi, s, rp, rt, ro, gate);
-  if (timed) ws.prof.end(s, level, pass_bytes(op.n, op.nnz, (int)sizeof(T), streams));
+  if (timed) ws.prof.end(s, level, pass_bytes(op.n, op.nnz, (int)sizeof(T), streams, op.w != nullptr));
 }
 
 // The PCG's reduction over the preconditioned residual z (see k_z_reduce),
@@ -267,7 +270,8 @@ __device__ void z_sums_finish(int64_t n, double* scal, int first);
 // of a PCG iteration the same kernel also forms the sums over z = x (zs).
 template <typename T, bool kZ>
 __global__ void k_elim_prolong(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                               const T* __restrict__ w, const T* __restrict__ dinv, const int32_t* __restrict__ cmap,
+                               const T* __restrict__ w, T wc, const T* __restrict__ dinv,
+                               const int32_t* __restrict__ cmap,
                                const T* __restrict__ f, const T* __restrict__ xc, T* __restrict__ x, ZSums zs) {
   int first = 0;
   double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
@@ -279,7 +283,7 @@ __global__ void k_elim_prolong(int64_t n, const int64_t* __restrict__ rowptr, co
       v = xc[c];
     } else {
       T s = f[i];
-      for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) s += w[k] * xc[cmap[col[k]]];
+      for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) s += (w ? w[k] : wc) * xc[cmap[col[k]]];
       v = s * dinv[i];
     }
     x[i] = v;
@@ -477,10 +481,10 @@ static void cycle_level(Hier& h, Workspace& ws, int l, cudaStream_t s, const ZSu
     cycle_level<T>(h, ws, l + 1, s);
     const OpView<T> op = L.op<T>();
     if (zs.r)
-      k_elim_prolong<T, true><<<vblocks(n), kVT, 0, s>>>(n, op.rowptr, op.col, op.w, op.dinv, L.cmap.get(),
+      k_elim_prolong<T, true><<<vblocks(n), kVT, 0, s>>>(n, op.rowptr, op.col, op.w, op.wc, op.dinv, L.cmap.get(),
                                                         V.f.get(), C.x.get(), V.x.get(), zs);
     else
-      k_elim_prolong<T, false><<<vblocks(n), kVT, 0, s>>>(n, op.rowptr, op.col, op.w, op.dinv, L.cmap.get(),
+      k_elim_prolong<T, false><<<vblocks(n), kVT, 0, s>>>(n, op.rowptr, op.col, op.w, op.wc, op.dinv, L.cmap.get(),
                                                          V.f.get(), C.x.get(), V.x.get(), zs);
     LG_LAUNCH_CHECK();
     return;
@@ -496,13 +500,13 @@ static void cycle_level(Hier& h, Workspace& ws, int l, cudaStream_t s, const ZSu
   for (int st = 1; st < deg; ++st) {  // pre-smoothing from x = 0
     const EpiCheb<T> e{g, rin, V.r.get(), op.dinv, gn, V.x.get(), st == 1 ? 1 : 2, st == deg - 1,
                        (T)ch.c1[st], (T)ch.c2[st]};
-    op_pass<T, 0>(ws, l, op, LapTerm<T>{op.w, g, op.d}, e, cheb_streams(e), s);
+    op_pass<T, 0>(ws, l, op, lap_term<T>(op, g), e, cheb_streams(e), s);
     rin = V.r.get();
     std::swap(g, gn);
   }
   {  // residual r = f - L x of the pre-smoothed x (for degree 1 also x = d_0)
     const EpiCheb<T> e{g, rin, V.r.get(), op.dinv, nullptr, deg == 1 ? V.x.get() : nullptr, 1, 0, T(0), T(0)};
-    op_pass<T, 0>(ws, l, op, LapTerm<T>{op.w, g, op.d}, e, cheb_streams(e), s);
+    op_pass<T, 0>(ws, l, op, lap_term<T>(op, g), e, cheb_streams(e), s);
   }
   // r_c = R r, then the coarse cycle
   launch_rows<T, 0>(L.nc, L.mem_ptr.get(), L.mem.get(), GatherTerm<T>{V.r.get()}, sc.mem.bind(L.mem_plan.plan),
@@ -520,14 +524,14 @@ static void cycle_level(Hier& h, Workspace& ws, int l, cudaStream_t s, const ZSu
     LG_LAUNCH_CHECK();
     // post-smoothing from x: r_0 = f - L x, d_0 = D^-1 r_0 / theta
     const EpiCheb<T> e{V.x.get(), V.f.get(), V.r.get(), op.dinv, V.dA.get(), nullptr, 0, 0, T(0), (T)ch.inv_theta};
-    op_pass<T, 0>(ws, l, op, LapTerm<T>{op.w, V.x.get(), op.d}, e, cheb_streams(e), s);
+    op_pass<T, 0>(ws, l, op, lap_term<T>(op, V.x.get()), e, cheb_streams(e), s);
   }
   g = V.dA.get();
   gn = V.dB.get();
   for (int st = 1; st < deg; ++st) {
     const EpiCheb<T> e{g, V.r.get(), V.r.get(), op.dinv, gn, V.x.get(), 2, st == deg - 1, (T)ch.c1[st],
                        (T)ch.c2[st]};
-    op_pass<T, 0>(ws, l, op, LapTerm<T>{op.w, g, op.d}, e, cheb_streams(e), s);
+    op_pass<T, 0>(ws, l, op, lap_term<T>(op, g), e, cheb_streams(e), s);
     std::swap(g, gn);
   }
   if (deg == 1) {
@@ -553,14 +557,14 @@ static void kcycle_level(Hier& h, Workspace& ws, int l, cudaStream_t s) {
   double* ks = ws.kscal.get() + (size_t)kKScal * l;
   const int vb = vblocks(n);
   cycle_level<T>(h, ws, l, s, ZSums{}, true);  // c1 in V.x
-  op_pass<T, 0>(ws, l, op, LapTerm<T>{op.w, V.x.get(), op.d}, EpiKStore<T>{V.kv1.get()}, 1, s);
+  op_pass<T, 0>(ws, l, op, lap_term<T>(op, V.x.get()), EpiKStore<T>{V.kv1.get()}, 1, s);
   k_kfirst<T><<<vb, kVT, 0, s>>>(n, V.x.get(), V.kv1.get(), V.f.get(), V.kc1.get(), ks, ws.partials.get(),
                                  ws.tickets.get());
   LG_LAUNCH_CHECK();
   k_kres<T><<<vb, kVT, 0, s>>>(n, V.f.get(), V.kv1.get(), op.dinv, (T)h.cheb[l].inv_theta, V.dA.get(), ks);
   LG_LAUNCH_CHECK();
   cycle_level<T>(h, ws, l, s, ZSums{}, true);  // c2 in V.x
-  op_pass<T, 0>(ws, l, op, LapTerm<T>{op.w, V.x.get(), op.d}, EpiKStore<T>{V.kv2.get()}, 1, s);
+  op_pass<T, 0>(ws, l, op, lap_term<T>(op, V.x.get()), EpiKStore<T>{V.kv2.get()}, 1, s);
   k_ksecond<T><<<vb, kVT, 0, s>>>(n, V.x.get(), V.kv1.get(), V.kv2.get(), V.f.get(), ks, ws.partials.get(),
                                   ws.tickets.get());
   LG_LAUNCH_CHECK();
@@ -616,7 +620,7 @@ static void level_apply_t(Hier& h, int l, const T* x, T* y, cudaStream_t s) {
   const Level& L = *h.levels[l];
   OpView<T> op = L.op<T>();
   op.plan = h.ws->scratch[l].op.bind(op.plan);
-  launch_rows<T, 0>(op.n, op.rowptr, op.col, LapTerm<T>{op.w, x, op.d}, op.plan, EpiY<T>{y}, s);
+  launch_rows<T, 0>(op.n, op.rowptr, op.col, lap_term<T>(op, x), op.plan, EpiY<T>{y}, s);
 }
 
 void level_apply(Hier& h, int l, int precision, const void* x, void* y, cudaStream_t s) {
@@ -902,7 +906,7 @@ static void pcg_body(Hier& h, Workspace& ws, cudaStream_t s, cudaGraphConditiona
   LG_LAUNCH_CHECK();
   OpView<double> op = L0.op<double>();
   op.plan = ws.scratch[0].op.bind(op.plan);
-  op_pass<double, 0>(ws, 0, op, LapTerm<double>{op.w, ws.p.get(), op.d}, EpiQ{ws.q.get()}, 1, s);
+  op_pass<double, 0>(ws, 0, op, lap_term<double>(op, ws.p.get()), EpiQ{ws.q.get()}, 1, s);
   k_pq_dot<<<vblocks(n), kVT, 0, s>>>(n, ws.p.get(), ws.q.get(), scal, ws.partials.get(), ws.tickets.get());
   LG_LAUNCH_CHECK();
   k_xr_update<<<vblocks(n), kVT, 0, s>>>(n, ws.x.get(), ws.r.get(), ws.ro.get(), ws.p.get(), ws.q.get(), scal,
@@ -917,7 +921,7 @@ static void true_residual(Hier& h, Workspace& ws, cudaStream_t s, const double* 
   OpView<double> op = L0.op<double>();
   op.plan = ws.scratch[0].op.bind(op.plan);
   double* scal = ws.scal.get();
-  op_pass<double, 0>(ws, 0, op, LapTerm<double>{op.w, ws.x.get(), op.d}, EpiTrueRes{ws.bm.get(), ws.r.get()}, 2, s,
+  op_pass<double, 0>(ws, 0, op, lap_term<double>(op, ws.x.get()), EpiTrueRes{ws.bm.get(), ws.r.get()}, 2, s,
                      nullptr, nullptr, nullptr, gate);
   k_rr<<<vblocks(L0.n), kVT, 0, s>>>(L0.n, ws.r.get(), scal, ws.partials.get(), ws.tickets.get(), gate, loop, handle,
                                      in_graph);

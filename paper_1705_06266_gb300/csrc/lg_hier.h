@@ -47,6 +47,7 @@ struct OpView {
   const T* dinv = nullptr;
   const double* d = nullptr;  // FP64 row sums (used by the FP64 passes)
   RowPlan plan;
+  T wc = T(0);                // every weight, when w is null (a constant-weight operator)
 };
 
 struct Level {
@@ -58,6 +59,10 @@ struct Level {
   DBuf<float> w32, dinv32;
   RowPlanStore plan;
   double lambda = 0.0;
+  // A finest operator whose weights are all equal (an unweighted graph) keeps
+  // that value instead of its weight arrays (w and w32 released after setup).
+  bool wconst_on = false;
+  double wconst = 0.0;
   // aggregation
   DBuf<int32_t> agg, mem;
   DBuf<int64_t> mem_ptr;
@@ -83,10 +88,10 @@ struct Level {
 };
 
 template <> inline OpView<double> Level::op<double>() const {
-  return OpView<double>{n, nnz, rowptr.get(), col.get(), w.get(), dinv.get(), d.get(), plan.plan};
+  return OpView<double>{n, nnz, rowptr.get(), col.get(), w.get(), dinv.get(), d.get(), plan.plan, wconst};
 }
 template <> inline OpView<float> Level::op<float>() const {
-  return OpView<float>{n, nnz, rowptr.get(), col.get(), w32.get(), dinv32.get(), d.get(), plan.plan};
+  return OpView<float>{n, nnz, rowptr.get(), col.get(), w32.get(), dinv32.get(), d.get(), plan.plan, (float)wconst};
 }
 // W = L P as an operator view: its rows' entries, and lp_d in place of d.
 template <> inline OpView<double> Level::lp<double>() const {

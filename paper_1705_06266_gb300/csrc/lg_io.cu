@@ -8,11 +8,14 @@
 //
 // Layout: a header (magic, format version, sizeof(lg_options), the options,
 // level count, n_0, nnz(L_0), setup time, first aggregation level), the
-// vertex order, then per level its sizes and kind, its arrays (each a count
+// vertex order, then per level its sizes and kind, whether its weights are
+// one constant (and the constant; the weight arrays are then empty), its
+// arrays (each a count
 // followed by the values, counts checked against the sizes on load), its
 // plans' binning and its Chebyshev constants. Host byte order; a file is
 // meant to be read back on the machine (or the same architecture) that wrote
 // it.
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <memory>
@@ -25,7 +28,7 @@ namespace lg {
 namespace {
 
 constexpr char kMagic[8] = {'L', 'G', 'H', 'I', 'E', 'R', 'F', '1'};
-constexpr uint32_t kVersion = 1;
+constexpr uint32_t kVersion = 2;
 constexpr size_t kStageBytes = size_t(64) << 20;  // host staging of one array at a time
 
 struct File {
@@ -175,9 +178,11 @@ void save_hierarchy(const Hier& h, const char* path) {
     w.val(L.nf);
     w.val(L.lambda);
     w.val<int32_t>(L.plan.plan.E);
+    w.val<int32_t>(L.wconst_on ? 1 : 0);
+    w.val(L.wconst);
     w.arr(L.rowptr, (size_t)L.n + 1, s);
     w.arr(L.col, (size_t)L.nnz, s);
-    w.arr(L.w, (size_t)L.nnz, s);
+    w.arr(L.w, L.wconst_on ? 0 : (size_t)L.nnz, s);
     w.arr(L.d, L.d.size(), s);
     w.arr(L.dinv, L.dinv.size(), s);
     w.arr(L.w32, L.w32.size(), s);
@@ -266,18 +271,25 @@ void load_hierarchy(Hier& h, const char* path, const lg_options* call_opts) {
     L->nf = r.val<int64_t>();
     L->lambda = r.val<double>();
     const int E = r.val<int32_t>();
+    const int32_t wconst_on = r.val<int32_t>();
+    const double wconst = r.val<double>();
     const bool last = l == nl - 1;
     if (L->n != expect_n || L->nnz < 0 || L->nnz > L->n * (L->n - 1) ||
         (last != (L->kind == LG_LEVEL_COARSEST)) ||
         (L->kind != LG_LEVEL_AGG && L->kind != LG_LEVEL_ELIM && L->kind != LG_LEVEL_COARSEST) ||
         (!last && (L->nc < 1 || L->nc > L->n)))
       fail(LG_ERR_INVALID, "hierarchy file: level sizes");
+    if (wconst_on != 0 && (wconst_on != 1 || l != 0 || !(wconst > 0.0) || !std::isfinite(wconst)))
+      fail(LG_ERR_INVALID, "hierarchy file: constant weight");
+    L->wconst_on = wconst_on == 1;
+    L->wconst = L->wconst_on ? wconst : 0.0;
+    const int64_t nw = L->wconst_on ? 0 : L->nnz;
     r.arr(L->rowptr, L->n + 1, s, counter);
     r.arr(L->col, L->nnz, s, counter);
-    r.arr(L->w, L->nnz, s, counter);
+    r.arr(L->w, nw, s, counter);
     r.arr(L->d, L->n, s, counter);
     r.arr(L->dinv, L->n, s, counter);
-    r.arr(L->w32, L->nnz, s, counter);
+    r.arr(L->w32, nw, s, counter);
     r.arr(L->dinv32, L->n, s, counter);
     check.ptr(L->rowptr, L->n, L->nnz);
     check.range(L->col, L->nnz, 0, L->n);

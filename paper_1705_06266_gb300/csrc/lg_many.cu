@@ -63,6 +63,7 @@ struct MLevel {
   const float* lp_w32 = nullptr;
   const double *w = nullptr, *d = nullptr, *dinv = nullptr;
   const float *w32 = nullptr, *dinv32 = nullptr;
+  double wc = 0.0;  // every weight of the operator when w and w32 are null
   const int32_t *agg = nullptr, *cmap = nullptr, *cfine = nullptr;
   const double* pt_coef = nullptr;
   const float* pt_coef32 = nullptr;
@@ -180,24 +181,26 @@ template <typename T>
 struct MLap;
 
 template <>
-struct MLap<float> {  // difference form: sum_j w_ij (x_i - x_j)
+struct MLap<float> {  // difference form: sum_j w_ij (x_i - x_j); null w: every weight wc
   const float* w;
   const float* x;
+  float wc;
   __device__ __forceinline__ float row(int64_t i) const { return x[i]; }
   __device__ __forceinline__ float acc(float s, int64_t k, int32_t j, float xi) const {
-    return fmaf(__ldg(&w[k]), xi - x[j], s);
+    return fmaf(w ? __ldg(&w[k]) : wc, xi - x[j], s);
   }
   __device__ __forceinline__ float fin(int64_t, float, float s) const { return s; }
 };
 
 template <>
-struct MLap<double> {  // d_i x_i - sum_j w_ij x_j
+struct MLap<double> {  // d_i x_i - sum_j w_ij x_j; null w: every weight wc
   const double* w;
   const double* x;
   const double* d;
+  double wc;
   __device__ __forceinline__ double row(int64_t) const { return 0.0; }
   __device__ __forceinline__ double acc(double s, int64_t k, int32_t j, double) const {
-    return fma(__ldg(&w[k]), x[j], s);
+    return fma(w ? __ldg(&w[k]) : wc, x[j], s);
   }
   __device__ __forceinline__ double fin(int64_t i, double, double s) const { return fma(__ldg(&d[i]), x[i], -s); }
 };
@@ -206,11 +209,11 @@ template <typename T>
 __device__ __forceinline__ MLap<T> m_lap(const MLevel& L, const T* x);
 template <>
 __device__ __forceinline__ MLap<float> m_lap<float>(const MLevel& L, const float* x) {
-  return MLap<float>{L.w32, x};
+  return MLap<float>{L.w32, x, (float)L.wc};
 }
 template <>
 __device__ __forceinline__ MLap<double> m_lap<double>(const MLevel& L, const double* x) {
-  return MLap<double>{L.w, x, L.d};
+  return MLap<double>{L.w, x, L.d, L.wc};
 }
 
 // (L P x_c)_i over W = L P off the own aggregate (the forms of LpTerm).
@@ -410,7 +413,8 @@ __device__ void m_up(const MGraph& G, int l, MShared& sm) {
       } else {
         T s = V.f[i];
         const int64_t e = __ldg(&L.op.ptr[i + 1]);
-        for (int64_t k = __ldg(&L.op.ptr[i]); k < e; ++k) s += __ldg(&w[k]) * xc[__ldg(&L.cmap[__ldg(&L.op.idx[k])])];
+        for (int64_t k = __ldg(&L.op.ptr[i]); k < e; ++k)
+          s += (w ? __ldg(&w[k]) : (T)L.wc) * xc[__ldg(&L.cmap[__ldg(&L.op.idx[k])])];
         v = s * __ldg(&dinv[i]);
       }
       V.x[i] = v;
@@ -566,7 +570,7 @@ __device__ void m_cycle(const MGraph& G, MShared& sm) {
 // r = b_m - L x and ||r||^2.
 __device__ __noinline__ double m_true_res(const MLevel& L0, const double* bm, const double* x, double* r,
                                           MShared& sm) {
-  m_pass<double>(L0.op, MLap<double>{L0.w, x, L0.d}, [=](int64_t i, double s) { r[i] = bm[i] - s; }, sm);
+  m_pass<double>(L0.op, MLap<double>{L0.w, x, L0.d, L0.wc}, [=](int64_t i, double s) { r[i] = bm[i] - s; }, sm);
   double acc[1] = {0.0};
   LG_BLOCK_LOOP(i, L0.n) acc[0] += r[i] * r[i];
   m_sum<1>(acc, sm);
@@ -717,6 +721,7 @@ static const MLevel* many_levels(Hier& h) {
     m.dinv = L.dinv.get();
     m.w32 = L.w32.get();
     m.dinv32 = L.dinv32.get();
+    m.wc = L.wconst_on ? L.wconst : 0.0;
     if (L.kind == LG_LEVEL_AGG) {
       m.mem = rows_of(L.nc, L.mem_ptr.get(), L.mem.get(), L.mem_plan.plan);
       m.agg = L.agg.get();

@@ -274,10 +274,260 @@ __global__ void k_rowptr_from_keys(const uint64_t* __restrict__ segkey, int64_t 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Sort within rows. When the entries come grouped by row (row r's at
+// [rp[r], rp[r+1]) in the order they were emitted, the rows' key bits equal
+// within a row and ascending from row to row), sorting every row's entries
+// stably by key gives the order a global stable sort would, with one read
+// and one write of the entries instead of one per 8 key bits. By length:
+//  - rows of at most 32 entries: a group of 2^c lanes per row, each entry
+//    ranked by comparing it with the others (ties by position);
+//  - rows of at most kWrBlockMax entries: one block per row, a bitonic
+//    network in shared memory over (column, position) pairs, which are
+//    distinct, so the result is the stable order;
+//  - longer rows: gathered into one array (row replaced by its index among
+//    them) and radix sorted together, then written back.
+// Rows are independent, so which block takes which row does not matter.
+// ---------------------------------------------------------------------------
+constexpr int kWrBlockMax = 16384;
+constexpr int kWrClasses = 16;  // 0: <= 1 entry; 1..5: lane groups; 6..14: blocks of 2^c; 15: long
+
+__device__ __forceinline__ int wr_class(int64_t len) {
+  if (len <= 1) return 0;
+  if (len > kWrBlockMax) return kWrClasses - 1;
+  int c = 1;
+  while ((int64_t(1) << c) < len) ++c;
+  return c;
+}
+
+// Pass 0 counts the rows of each class; pass 1 lists them (off: class offsets,
+// fill: per-class cursors). One block-level histogram per block.
+__global__ void k_wr_bin(int64_t nrows, const int64_t* __restrict__ rp, int pass, int64_t* __restrict__ cnt,
+                         const int64_t* __restrict__ off, unsigned long long* __restrict__ fill,
+                         int32_t* __restrict__ rows) {
+  __shared__ unsigned int h[kWrClasses];
+  __shared__ unsigned long long base[kWrClasses];
+  const int64_t per = (nrows + gridDim.x - 1) / gridDim.x;
+  const int64_t r0 = (int64_t)blockIdx.x * per, r1 = r0 + per < nrows ? r0 + per : nrows;
+  if (threadIdx.x < kWrClasses) h[threadIdx.x] = 0;
+  __syncthreads();
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) atomicAdd(&h[wr_class(rp[r + 1] - rp[r])], 1u);
+  __syncthreads();
+  if (pass == 0) {
+    if (threadIdx.x < kWrClasses && h[threadIdx.x]) atomicAdd((unsigned long long*)&cnt[threadIdx.x], h[threadIdx.x]);
+    return;
+  }
+  if (threadIdx.x < kWrClasses) {
+    base[threadIdx.x] = h[threadIdx.x] ? (unsigned long long)off[threadIdx.x] + atomicAdd(&fill[threadIdx.x], h[threadIdx.x]) : 0ull;
+    h[threadIdx.x] = 0;
+  }
+  __syncthreads();
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+    const int c = wr_class(rp[r + 1] - rp[r]);
+    rows[base[c] + atomicAdd(&h[c], 1u)] = (int32_t)r;
+  }
+}
+
+__global__ void k_wr_copy1(const int32_t* __restrict__ rows, int64_t nr, const int64_t* __restrict__ rp,
+                           const uint64_t* __restrict__ kin, const uint64_t* __restrict__ vin,
+                           uint64_t* __restrict__ kout, uint64_t* __restrict__ vout) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nr; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = rp[rows[q]];
+    if (rp[rows[q] + 1] > b) {
+      kout[b] = kin[b];
+      vout[b] = vin[b];
+    }
+  }
+}
+
+// Rows of at most G entries, one group of G lanes each.
+template <int G>
+__global__ void k_wr_rank(const int32_t* __restrict__ rows, int64_t nr, const int64_t* __restrict__ rp,
+                          const uint64_t* __restrict__ kin, const uint64_t* __restrict__ vin,
+                          uint64_t* __restrict__ kout, uint64_t* __restrict__ vout) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t gi = t / G;
+  const int l = (int)(t & (G - 1));
+  int64_t b = 0;
+  int len = 0;
+  if (gi < nr) {
+    const int32_t r = rows[gi];
+    b = rp[r];
+    len = (int)(rp[r + 1] - b);
+  }
+  uint64_t k = ~0ull, v = 0;
+  if (l < len) {
+    k = kin[b + l];
+    v = vin[b + l];
+  }
+  int rank = 0;
+#pragma unroll
+  for (int m = 0; m < G; ++m) {
+    const uint64_t km = __shfl_sync(0xffffffffu, k, m, G);
+    rank += (m < len) & ((km < k) | ((km == k) & (m < l)));
+  }
+  if (l < len) {
+    kout[b + rank] = k;
+    vout[b + rank] = v;
+  }
+}
+
+// Rows of at most P entries (P a power of two, 64..kWrBlockMax), one block each.
+template <int P>
+__global__ void __launch_bounds__(P / 2 < 1024 ? P / 2 : 1024)
+k_wr_block(const int32_t* __restrict__ rows, const int64_t* __restrict__ rp, const uint64_t* __restrict__ kin,
+           const uint64_t* __restrict__ vin, uint64_t* __restrict__ kout, uint64_t* __restrict__ vout,
+           uint64_t cmask) {
+  constexpr int T = P / 2 < 1024 ? P / 2 : 1024;
+  constexpr int PB = P <= 64 ? 6 : P <= 128 ? 7 : P <= 256 ? 8 : P <= 512 ? 9 : P <= 1024 ? 10 : P <= 2048 ? 11
+                   : P <= 4096 ? 12 : P <= 8192 ? 13 : 14;
+  static_assert((1 << PB) == P, "P must be a power of two");
+  extern __shared__ uint64_t wr_sk[];
+  const int32_t r = rows[blockIdx.x];
+  const int64_t b = rp[r];
+  const int len = (int)(rp[r + 1] - b);
+  for (int i = threadIdx.x; i < P; i += T) wr_sk[i] = i < len ? ((kin[b + i] & cmask) << PB) | (uint64_t)i : ~0ull;
+  __syncthreads();
+  for (int size = 2; size <= P; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int t = threadIdx.x; t < P / 2; t += T) {
+        const int lo = 2 * t - (t & (stride - 1)), hi = lo + stride;
+        const uint64_t a = wr_sk[lo], c = wr_sk[hi];
+        if ((a > c) == ((lo & size) == 0)) {
+          wr_sk[lo] = c;
+          wr_sk[hi] = a;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < len; i += T) {
+    const int pos = (int)(wr_sk[i] & (uint64_t)(P - 1));
+    kout[b + i] = kin[b + pos];
+    vout[b + i] = vin[b + pos];
+  }
+}
+
+// Long rows: to one array, keyed (index among the long rows, column), and back.
+__global__ void k_wr_gather(const int32_t* __restrict__ lrows, const int64_t* __restrict__ rp,
+                            const int64_t* __restrict__ loff, const uint64_t* __restrict__ kin,
+                            const uint64_t* __restrict__ vin, uint64_t* __restrict__ tk, uint64_t* __restrict__ tv,
+                            int cbits) {
+  const int32_t r = lrows[blockIdx.x];
+  const int64_t b = rp[r], len = rp[r + 1] - b, o = loff[blockIdx.x];
+  const uint64_t cmask = (1ull << cbits) - 1ull;
+  for (int64_t q = threadIdx.x; q < len; q += blockDim.x) {
+    tk[o + q] = ((uint64_t)blockIdx.x << cbits) | (kin[b + q] & cmask);
+    tv[o + q] = vin[b + q];
+  }
+}
+
+__global__ void k_wr_scatter(const int32_t* __restrict__ lrows, const int64_t* __restrict__ rp,
+                             const int64_t* __restrict__ loff, const uint64_t* __restrict__ kin,
+                             const uint64_t* __restrict__ tk, const uint64_t* __restrict__ tv,
+                             uint64_t* __restrict__ kout, uint64_t* __restrict__ vout, int cbits) {
+  const int32_t r = lrows[blockIdx.x];
+  const int64_t b = rp[r], len = rp[r + 1] - b, o = loff[blockIdx.x];
+  const uint64_t cmask = (1ull << cbits) - 1ull;
+  const uint64_t rowbits = kin[b] & ~cmask;
+  for (int64_t q = threadIdx.x; q < len; q += blockDim.x) {
+    kout[b + q] = rowbits | (tk[o + q] & cmask);
+    vout[b + q] = tv[o + q];
+  }
+}
+
+__global__ void k_wr_long_len(const int32_t* __restrict__ lrows, int64_t nl, const int64_t* __restrict__ rp,
+                              int64_t* __restrict__ len) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nl; q += (int64_t)gridDim.x * blockDim.x)
+    len[q] = rp[lrows[q] + 1] - rp[lrows[q]];
+}
+
+template <int P>
+static void wr_block_launch(const int32_t* rows, int64_t nr, const int64_t* rp, const uint64_t* kin,
+                            const uint64_t* vin, uint64_t* kout, uint64_t* vout, uint64_t cmask, cudaStream_t s) {
+  constexpr int T = P / 2 < 1024 ? P / 2 : 1024;
+  const size_t smem = sizeof(uint64_t) * P;
+  if (smem > 48 * 1024)
+    LG_CUDA(cudaFuncSetAttribute(k_wr_block<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  for (int64_t q0 = 0; q0 < nr; q0 += 1 << 30) {
+    const int64_t m = nr - q0 < (1 << 30) ? nr - q0 : (1 << 30);
+    k_wr_block<P><<<(unsigned)m, T, smem, s>>>(rows + q0, rp, kin, vin, kout, vout, cmask);
+    LG_LAUNCH_CHECK();
+  }
+}
+
+void sort_within_rows(DBuf<uint64_t>& keys, DBuf<uint64_t>& vals, int64_t nent, const int64_t* rp, int64_t ngroups,
+                      int cbits, cudaStream_t s) {
+  if (nent <= 1 || ngroups <= 0) return;
+  DBuf<uint64_t> kout(nent, s), vout(nent, s);
+  DBuf<int64_t> cnt(kWrClasses, s);
+  DBuf<unsigned long long> fill(kWrClasses, s);
+  DBuf<int32_t> rows(ngroups, s);
+  LG_CUDA(cudaMemsetAsync(cnt.get(), 0, sizeof(int64_t) * kWrClasses, s));
+  LG_CUDA(cudaMemsetAsync(fill.get(), 0, sizeof(unsigned long long) * kWrClasses, s));
+  const int gb = grid_for(ngroups, 256, kSMs * 8);
+  k_wr_bin<<<gb, 256, 0, s>>>(ngroups, rp, 0, cnt.get(), nullptr, nullptr, nullptr);
+  LG_LAUNCH_CHECK();
+  int64_t hc[kWrClasses], ho[kWrClasses + 1];
+  LG_CUDA(cudaMemcpyAsync(hc, cnt.get(), sizeof(hc), cudaMemcpyDeviceToHost, s));
+  LG_CUDA(cudaStreamSynchronize(s));
+  ho[0] = 0;
+  for (int c = 0; c < kWrClasses; ++c) ho[c + 1] = ho[c] + hc[c];
+  LG_CUDA(cudaMemcpyAsync(cnt.get(), ho, sizeof(int64_t) * kWrClasses, cudaMemcpyHostToDevice, s));
+  k_wr_bin<<<gb, 256, 0, s>>>(ngroups, rp, 1, nullptr, cnt.get(), fill.get(), rows.get());
+  LG_LAUNCH_CHECK();
+  const uint64_t *kin = keys.get(), *vin = vals.get();
+  uint64_t *ko = kout.get(), *vo = vout.get();
+  const uint64_t cmask = (1ull << cbits) - 1ull;
+  for (int c = 0; c < kWrClasses; ++c) {
+    const int64_t nr = hc[c];
+    if (!nr) continue;
+    const int32_t* rl = rows.get() + ho[c];
+    const auto lanes = [&](int G) { return grid_for(nr * G, 256, 1 << 30); };
+    switch (c) {
+      case 0: k_wr_copy1<<<grid_for(nr, 256, kSMs * 16), 256, 0, s>>>(rl, nr, rp, kin, vin, ko, vo); break;
+      case 1: k_wr_rank<2><<<lanes(2), 256, 0, s>>>(rl, nr, rp, kin, vin, ko, vo); break;
+      case 2: k_wr_rank<4><<<lanes(4), 256, 0, s>>>(rl, nr, rp, kin, vin, ko, vo); break;
+      case 3: k_wr_rank<8><<<lanes(8), 256, 0, s>>>(rl, nr, rp, kin, vin, ko, vo); break;
+      case 4: k_wr_rank<16><<<lanes(16), 256, 0, s>>>(rl, nr, rp, kin, vin, ko, vo); break;
+      case 5: k_wr_rank<32><<<lanes(32), 256, 0, s>>>(rl, nr, rp, kin, vin, ko, vo); break;
+      case 6: wr_block_launch<64>(rl, nr, rp, kin, vin, ko, vo, cmask, s); break;
+      case 7: wr_block_launch<128>(rl, nr, rp, kin, vin, ko, vo, cmask, s); break;
+      case 8: wr_block_launch<256>(rl, nr, rp, kin, vin, ko, vo, cmask, s); break;
+      case 9: wr_block_launch<512>(rl, nr, rp, kin, vin, ko, vo, cmask, s); break;
+      case 10: wr_block_launch<1024>(rl, nr, rp, kin, vin, ko, vo, cmask, s); break;
+      case 11: wr_block_launch<2048>(rl, nr, rp, kin, vin, ko, vo, cmask, s); break;
+      case 12: wr_block_launch<4096>(rl, nr, rp, kin, vin, ko, vo, cmask, s); break;
+      case 13: wr_block_launch<8192>(rl, nr, rp, kin, vin, ko, vo, cmask, s); break;
+      case 14: wr_block_launch<16384>(rl, nr, rp, kin, vin, ko, vo, cmask, s); break;
+      default: {
+        DBuf<int64_t> loff(nr + 1, s);
+        k_wr_long_len<<<grid_for(nr, 256, kSMs * 8), 256, 0, s>>>(rl, nr, rp, loff.get());
+        LG_LAUNCH_CHECK();
+        exclusive_scan(loff.get(), loff.get(), nr, s);
+        int64_t nl = 0;
+        LG_CUDA(cudaMemcpyAsync(&nl, loff.get() + nr, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        LG_CUDA(cudaStreamSynchronize(s));
+        DBuf<uint64_t> tk(nl, s), tv(nl, s);
+        k_wr_gather<<<(unsigned)nr, 256, 0, s>>>(rl, rp, loff.get(), kin, vin, tk.get(), tv.get(), cbits);
+        LG_LAUNCH_CHECK();
+        radix_sort_pairs(tk.get(), tv.get(), nl, bits_for(nr) + cbits, s);
+        k_wr_scatter<<<(unsigned)nr, 256, 0, s>>>(rl, rp, loff.get(), kin, tk.get(), tv.get(), ko, vo, cbits);
+        break;
+      }
+    }
+    LG_LAUNCH_CHECK();
+  }
+  keys = std::move(kout);
+  vals = std::move(vout);
+}
+
 void accumulate_csr(DBuf<uint64_t>& keys, DBuf<uint64_t>& vals, int64_t nent, int64_t nrows, int cbits,
-                    CsrOut& out, cudaStream_t s, int64_t* counter) {
-  const int rbits = bits_for(nrows);
-  radix_sort_pairs(keys.get(), vals.get(), nent, rbits + cbits, s);
+                    CsrOut& out, cudaStream_t s, int64_t* counter, const int64_t* grouped, int64_t ngroups) {
+  if (grouped)
+    sort_within_rows(keys, vals, nent, grouped, ngroups, cbits, s);
+  else
+    radix_sort_pairs(keys.get(), vals.get(), nent, bits_for(nrows) + cbits, s);
   int64_t nseg = 0;
   DBuf<uint8_t> head(nent, s);
   DBuf<int64_t> segid(nent + 1, s);

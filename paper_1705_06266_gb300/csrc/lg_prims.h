@@ -18,10 +18,20 @@ void exclusive_scan_flags(const uint8_t* flag, int64_t* out, int64_t n, cudaStre
 // keys/vals are sorted in place (tmp buffers are allocated internally).
 void radix_sort_pairs(uint64_t* keys, uint64_t* vals, int64_t n, int bits, cudaStream_t s);
 
+// Stable sort of the entries of each group [rp[g], rp[g+1]) by key, for
+// entries emitted grouped by row (the row bits of the key equal within a
+// group and ascending from group to group), which then end up sorted as a
+// global stable sort would leave them. keys/vals are replaced by the sorted
+// arrays.
+void sort_within_rows(DBuf<uint64_t>& keys, DBuf<uint64_t>& vals, int64_t nent, const int64_t* rp, int64_t ngroups,
+                      int cbits, cudaStream_t s);
+
 // Sparse accumulation: entries (key = row << cbits | col, value) are sorted
 // stably by key and equal keys summed in their input order. Produces a CSR
 // with nrows rows: rowptr (nrows+1), col, w. `vals` holds doubles bit-cast to
-// uint64. Returns the number of distinct entries.
+// uint64. Returns the number of distinct entries. With `grouped` (ngroups + 1
+// offsets), the entries come grouped by row as sort_within_rows takes them
+// and are sorted within their groups instead of globally.
 struct CsrOut {
   DBuf<int64_t> rowptr;
   DBuf<int32_t> col;
@@ -29,7 +39,8 @@ struct CsrOut {
   int64_t nnz = 0;
 };
 void accumulate_csr(DBuf<uint64_t>& keys, DBuf<uint64_t>& vals, int64_t nent, int64_t nrows,
-                    int cbits, CsrOut& out, cudaStream_t s, int64_t* counter);
+                    int cbits, CsrOut& out, cudaStream_t s, int64_t* counter, const int64_t* grouped = nullptr,
+                    int64_t ngroups = 0);
 
 // Bits needed to hold values 0..v-1.
 inline int bits_for(int64_t v) {

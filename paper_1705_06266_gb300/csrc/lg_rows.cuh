@@ -70,17 +70,20 @@ struct LapTerm;
 // (entry k's weight) and accw(s, wk, xj, rv) (acc from the loaded weight and
 // gathered value), so the column-segmented long-row pass can issue the weight
 // loads early and read xj from a staged copy.
+// A null w means every weight is wc (a constant-weight operator): the pass
+// then streams the column indices alone.
 template <>
 struct LapTerm<float> {
   const float* __restrict__ w;
   const float* __restrict__ x;
   const double* __restrict__ d;  // unused
+  float wc;
   __device__ __forceinline__ float row(int64_t i) const { return __ldg(&x[i]); }
   __device__ __forceinline__ float acc(float s, int64_t k, int32_t j, float xi) const {
-    return fmaf(ld_stream(&w[k]), xi - ld_keep(&x[j]), s);
+    return fmaf(w ? ld_stream(&w[k]) : wc, xi - ld_keep(&x[j]), s);
   }
   __device__ __forceinline__ const float* src() const { return x; }
-  __device__ __forceinline__ float wload(int64_t k) const { return ld_stream(&w[k]); }
+  __device__ __forceinline__ float wload(int64_t k) const { return w ? ld_stream(&w[k]) : wc; }
   __device__ __forceinline__ float accw(float s, float wk, float xj, float xi) const { return fmaf(wk, xi - xj, s); }
   __device__ __forceinline__ float finish(int64_t, float, float s) const { return s; }
 };
@@ -90,17 +93,24 @@ struct LapTerm<double> {
   const double* __restrict__ w;
   const double* __restrict__ x;
   const double* __restrict__ d;
+  double wc;
   __device__ __forceinline__ double row(int64_t) const { return 0.0; }
   __device__ __forceinline__ double acc(double s, int64_t k, int32_t j, double) const {
-    return fma(ld_stream(&w[k]), ld_keep(&x[j]), s);
+    return fma(w ? ld_stream(&w[k]) : wc, ld_keep(&x[j]), s);
   }
   __device__ __forceinline__ const double* src() const { return x; }
-  __device__ __forceinline__ double wload(int64_t k) const { return ld_stream(&w[k]); }
+  __device__ __forceinline__ double wload(int64_t k) const { return w ? ld_stream(&w[k]) : wc; }
   __device__ __forceinline__ double accw(double s, double wk, double xj, double) const { return fma(wk, xj, s); }
   __device__ __forceinline__ double finish(int64_t i, double, double s) const {
     return fma(__ldg(&d[i]), __ldg(&x[i]), -s);
   }
 };
+
+// The Laplacian term of an operator view (its weights, or its constant weight).
+template <typename T, class View>
+__device__ __host__ inline LapTerm<T> lap_term(const View& op, const T* x) {
+  return LapTerm<T>{op.w, x, op.d, op.wc};
+}
 
 // Whether a term can be served column-segmented (it has src(), wload(), accw()).
 template <class Term, class = void>

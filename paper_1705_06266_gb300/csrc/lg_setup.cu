@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstring>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -255,6 +256,119 @@ struct FSchurCount {
     return 0;
   }
 };
+
+// Entries of the Schur complement per kept row a, for the emission grouped by
+// row (k_schur_emit_rows): a's kept neighbours, plus deg(f) - 1 fill entries
+// for each eliminated neighbour f (F is independent, so f's other neighbours
+// are kept). Eliminated rows emit nothing.
+struct FSchurCountRows {
+  const int64_t* __restrict__ rowptr;
+  const int32_t* __restrict__ col;
+  const uint8_t* __restrict__ is_f;
+  int64_t* __restrict__ cnt;
+  struct Acc {
+    long long c;
+  };
+  __device__ Acc init(int64_t, int64_t, int64_t) const { return Acc{0}; }
+  __device__ void add(Acc& a, int64_t, int64_t k) const {
+    const int32_t j = col[k];
+    a.c += is_f[j] ? rowptr[j + 1] - rowptr[j] - 1 : 1;
+  }
+  __device__ void merge(Acc& a, const Acc& o) const { a.c += o.c; }
+  __device__ Acc shfl(const Acc& a, int o) const { return Acc{each_shfl(a.c, o)}; }
+  __device__ long long finish(int64_t i, const Acc& a, int64_t, int64_t) const {
+    cnt[i] = is_f[i] ? 0 : a.c;
+    return 0;
+  }
+};
+
+// The same entries as ESchur, emitted by kept row a (one warp per row) into
+// a's own range, so that they come grouped by coarse row. Within the row,
+// the order reproduces the global stable sort's ties: contributions to one
+// key come in the order of the fine row that ESchur emits them from, i.e.
+// the fill of each eliminated neighbour f < a (in a's row order), then a's
+// own entries, then the fill of each f > a. Fill values are computed from
+// f's row exactly as ESchur does (d_f summed in f's row order, w_fa w_fy / d_f).
+__global__ void k_schur_emit_rows(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                  const double* __restrict__ w, const uint8_t* __restrict__ is_f,
+                                  const int32_t* __restrict__ cmap, const int64_t* __restrict__ off, int cbits,
+                                  uint64_t* __restrict__ keys, uint64_t* __restrict__ vals) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t a = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; a < n; a += warps) {
+    if (is_f[a]) continue;
+    const int64_t b = rowptr[a], e = rowptr[a + 1];
+    const uint64_t rowkey = (uint64_t)cmap[a] << cbits;
+    // counts of the three parts: fill before a, own entries, fill after a
+    long long nlt = 0, nown = 0;
+    for (int64_t k0 = b; k0 < e; k0 += 32) {
+      const int64_t k = k0 + lane;
+      long long clt = 0, cown = 0;
+      if (k < e) {
+        const int32_t j = col[k];
+        if (is_f[j]) clt = j < a ? rowptr[j + 1] - rowptr[j] - 1 : 0;
+        else cown = 1;
+      }
+      for (int o = 16; o >= 1; o >>= 1) {
+        clt += __shfl_xor_sync(0xffffffffu, clt, o);
+        cown += __shfl_xor_sync(0xffffffffu, cown, o);
+      }
+      nlt += clt;
+      nown += cown;
+    }
+    int64_t plt = off[a], pown = off[a] + nlt, pgt = off[a] + nlt + nown;
+    for (int64_t k0 = b; k0 < e; k0 += 32) {
+      const int64_t k = k0 + lane;
+      long long clt = 0, cown = 0, cgt = 0;
+      int32_t j = -1;
+      int64_t fb = 0, fe = 0;
+      if (k < e) {
+        j = col[k];
+        if (is_f[j]) {
+          fb = rowptr[j];
+          fe = rowptr[j + 1];
+          (j < a ? clt : cgt) = fe - fb - 1;
+        } else {
+          cown = 1;
+        }
+      }
+      // exclusive prefix over the lanes (row order) of each part
+      long long slt = clt, sown = cown, sgt = cgt;
+      for (int o = 1; o < 32; o <<= 1) {
+        const long long tl = __shfl_up_sync(0xffffffffu, slt, o), to = __shfl_up_sync(0xffffffffu, sown, o),
+                        tg = __shfl_up_sync(0xffffffffu, sgt, o);
+        if (lane >= o) {
+          slt += tl;
+          sown += to;
+          sgt += tg;
+        }
+      }
+      if (k < e) {
+        if (cown) {
+          const int64_t p = pown + sown - 1;
+          keys[p] = rowkey | (uint64_t)cmap[j];
+          vals[p] = (uint64_t)__double_as_longlong(w[k]);
+        } else if (fe > fb) {
+          int64_t p = (j < a ? plt + slt - clt : pgt + sgt - cgt);
+          double df = 0.0, wfa = 0.0;
+          for (int64_t q = fb; q < fe; ++q) {
+            df += w[q];
+            if (col[q] == (int32_t)a) wfa = w[q];
+          }
+          for (int64_t q = fb; q < fe; ++q) {
+            if (col[q] == (int32_t)a) continue;
+            keys[p] = rowkey | (uint64_t)cmap[col[q]];
+            vals[p] = (uint64_t)__double_as_longlong(wfa * w[q] / df);
+            ++p;
+          }
+        }
+      }
+      plt += __shfl_sync(0xffffffffu, slt, 31);
+      pown += __shfl_sync(0xffffffffu, sown, 31);
+      pgt += __shfl_sync(0xffffffffu, sgt, 31);
+    }
+  }
+}
 
 // Keys are (coarse row << cbits) | coarse col; values are FP64 bit patterns.
 // Entries are written in fine-row order, kept rows in column order, fill in
@@ -623,6 +737,23 @@ struct EGal {
   }
 };
 
+// Offsets of the Galerkin entries grouped by aggregate: the members of each
+// aggregate in ascending order (the member lists), each member's entries in
+// its row order, which is the order the fine-row emission gives every key,
+// so a sort within aggregates sums as the global sort does.
+__global__ void k_member_counts(int64_t n, const int32_t* __restrict__ mem, const int64_t* __restrict__ off,
+                                int64_t* __restrict__ mc) {
+  LG_GRID_STRIDE(m, n) mc[m] = off[mem[m] + 1] - off[mem[m]];
+}
+__global__ void k_member_offsets(int64_t n, const int32_t* __restrict__ mem, const int64_t* __restrict__ pos,
+                                 int64_t* __restrict__ offg) {
+  LG_GRID_STRIDE(m, n) offg[mem[m]] = pos[m];
+}
+__global__ void k_group_offsets(int64_t nc, const int64_t* __restrict__ mem_ptr, const int64_t* __restrict__ pos,
+                                int64_t* __restrict__ gp) {
+  LG_GRID_STRIDE(a, nc + 1) gp[a] = pos[mem_ptr[a]];
+}
+
 // Entries of W = L P off the own aggregate: (i << cbits | agg_j, w_ij) for
 // every stored (i, j) with agg_j != agg_i, in row order. Summed over equal
 // keys they give W_ia = sum of w_ij over i's neighbours j in aggregate a, so
@@ -863,6 +994,12 @@ __global__ void k_random_keys(int64_t n, uint64_t seed, uint64_t* __restrict__ k
   }
 }
 
+// Degrees in the new numbering.
+__global__ void k_perm_degrees(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ inv,
+                               int64_t* __restrict__ deg_new) {
+  LG_GRID_STRIDE(i, n) deg_new[inv[i]] = rowptr[i + 1] - rowptr[i];
+}
+
 __global__ void k_perm_from_sorted(int64_t n, const uint64_t* __restrict__ val, int32_t* __restrict__ perm,
                                    int32_t* __restrict__ inv) {
   LG_GRID_STRIDE(i, n) {
@@ -877,20 +1014,28 @@ __global__ void k_iota_i32(int64_t n, int32_t* __restrict__ a) {
 }
 
 // Entries of the renumbered graph: (inv[i], inv[j]) for every stored (i, j).
+// Entries of the renumbered operator, keyed (new row, new column). With
+// rp_new (the new rows' offsets) each row's entries go where the new row
+// starts, so they come grouped by new row for a sort within rows; without,
+// they stay at their old positions for a global sort.
 struct FPermEmit {
   const int32_t* __restrict__ col;
   const double* __restrict__ w;
   const int32_t* __restrict__ inv;
+  const int64_t* __restrict__ rp_new;
   int cbits;
   uint64_t* __restrict__ keys;
   uint64_t* __restrict__ vals;
   struct Acc {
     unsigned long long row;
+    int64_t shift;
   };
-  __device__ Acc init(int64_t i, int64_t, int64_t) const { return Acc{(unsigned long long)inv[i] << cbits}; }
+  __device__ Acc init(int64_t i, int64_t beg, int64_t) const {
+    return Acc{(unsigned long long)inv[i] << cbits, rp_new ? rp_new[inv[i]] - beg : 0};
+  }
   __device__ void add(Acc& a, int64_t, int64_t k) const {
-    keys[k] = a.row | (uint64_t)inv[col[k]];
-    vals[k] = (uint64_t)__double_as_longlong(w[k]);
+    keys[a.shift + k] = a.row | (uint64_t)inv[col[k]];
+    vals[a.shift + k] = (uint64_t)__double_as_longlong(w[k]);
   }
   __device__ void merge(Acc&, const Acc&) const {}
   __device__ Acc shfl(const Acc& a, int) const { return a; }
@@ -1041,7 +1186,8 @@ int64_t run_aggregate(int64_t n, const int64_t* rowptr, const int32_t* col, cons
 }
 
 // Elimination stage: fills L's ELIM fields and returns the Schur complement level.
-static std::unique_ptr<Level> eliminate(Level& L, const uint8_t* is_f, int64_t nf, cudaStream_t s, int64_t* counter) {
+static std::unique_ptr<Level> eliminate(Level& L, const uint8_t* is_f, int64_t nf, bool grouped, cudaStream_t s,
+                                        int64_t* counter) {
   const int64_t n = L.n;
   DBuf<uint8_t> keep(n, s);
   DBuf<int64_t> cid(n + 1, s), cnt(n + 1, s);
@@ -1057,18 +1203,30 @@ static std::unique_ptr<Level> eliminate(Level& L, const uint8_t* is_f, int64_t n
   k_elim_maps<<<blocks_for(n), kNT, 0, s>>>(n, is_f, cid.get(), L.cmap.get(), L.cfine.get());
   LG_LAUNCH_CHECK();
 
-  // Schur complement entries, sorted and summed into the coarse CSR.
-  each_row(FSchurCount{L.col.get(), is_f, cnt.get()}, L.rowptr.get(), bins_of(L.plan.plan, n), s);
+  // Schur complement entries, sorted and summed into the coarse CSR: emitted
+  // by kept row and sorted within rows, or emitted by fine row and sorted
+  // globally; both give the same order and sums.
+  if (grouped)
+    each_row(FSchurCountRows{L.rowptr.get(), L.col.get(), is_f, cnt.get()}, L.rowptr.get(), bins_of(L.plan.plan, n),
+             s);
+  else
+    each_row(FSchurCount{L.col.get(), is_f, cnt.get()}, L.rowptr.get(), bins_of(L.plan.plan, n), s);
   exclusive_scan(cnt.get(), cnt.get(), n, s);
   const int64_t nent = read_i64(cnt.get() + n, s);
   const int cbits = bits_for(nc);
   auto C = std::make_unique<Level>();
   {
     DBuf<uint64_t> keys(nent, s), vals(nent, s);
-    emit_rows(ESchur{L.col.get(), L.w.get(), is_f, L.cmap.get(), cbits, keys.get(), vals.get()}, L.rowptr.get(),
-              cnt.get(), bins_of(L.plan.plan, n), s);
+    if (grouped) {
+      k_schur_emit_rows<<<grid_for(n * 32, kNT, kSMs * 16), kNT, 0, s>>>(
+          n, L.rowptr.get(), L.col.get(), L.w.get(), is_f, L.cmap.get(), cnt.get(), cbits, keys.get(), vals.get());
+      LG_LAUNCH_CHECK();
+    } else {
+      emit_rows(ESchur{L.col.get(), L.w.get(), is_f, L.cmap.get(), cbits, keys.get(), vals.get()}, L.rowptr.get(),
+                cnt.get(), bins_of(L.plan.plan, n), s);
+    }
     CsrOut out;
-    accumulate_csr(keys, vals, nent, nc, cbits, out, s, counter);
+    accumulate_csr(keys, vals, nent, nc, cbits, out, s, counter, grouped ? cnt.get() : nullptr, n);
     C->n = nc;
     C->nnz = out.nnz;
     C->rowptr = std::move(out.rowptr);
@@ -1104,7 +1262,8 @@ constexpr int64_t kLpMinRows = 4096;
 
 // Aggregation stage products: member CSR of R, the Galerkin level, and
 // W = L P when `lp` (levels of at least kLpMinRows vertices).
-static std::unique_ptr<Level> galerkin(Level& L, bool lp, cudaStream_t s, int64_t* counter, StageClock& clk) {
+static std::unique_ptr<Level> galerkin(Level& L, bool lp, bool grouped, cudaStream_t s, int64_t* counter,
+                                       StageClock& clk) {
   const int64_t n = L.n, nc = L.nc;
   // member lists, ascending vertex order inside each aggregate (stable sort by aggregate)
   {
@@ -1129,10 +1288,24 @@ static std::unique_ptr<Level> galerkin(Level& L, bool lp, cudaStream_t s, int64_
   auto C = std::make_unique<Level>();
   {
     DBuf<uint64_t> keys(nent, s), vals(nent, s);
-    emit_rows(EGal{L.col.get(), L.w.get(), L.agg.get(), cbits, keys.get(), vals.get()}, L.rowptr.get(), cnt.get(),
-              bins_of(L.plan.plan, n), s);
+    DBuf<int64_t> offg, gp;
+    if (grouped) {  // each fine row's entries where its aggregate's group places them
+      DBuf<int64_t> pos(n + 1, s);
+      offg.alloc(n, s);
+      gp.alloc(nc + 1, s);
+      k_member_counts<<<blocks_for(n), kNT, 0, s>>>(n, L.mem.get(), cnt.get(), pos.get());
+      LG_LAUNCH_CHECK();
+      exclusive_scan(pos.get(), pos.get(), n, s);
+      k_member_offsets<<<blocks_for(n), kNT, 0, s>>>(n, L.mem.get(), pos.get(), offg.get());
+      LG_LAUNCH_CHECK();
+      k_group_offsets<<<blocks_for(nc + 1), kNT, 0, s>>>(nc, L.mem_ptr.get(), pos.get(), gp.get());
+      LG_LAUNCH_CHECK();
+    }
+    emit_rows(EGal{L.col.get(), L.w.get(), L.agg.get(), cbits, keys.get(), vals.get()}, L.rowptr.get(),
+              grouped ? offg.get() : cnt.get(), bins_of(L.plan.plan, n), s);
+    offg.release();
     CsrOut out;
-    accumulate_csr(keys, vals, nent, nc, cbits, out, s, counter);
+    accumulate_csr(keys, vals, nent, nc, cbits, out, s, counter, grouped ? gp.get() : nullptr, nc);
     C->n = nc;
     C->nnz = out.nnz;
     C->rowptr = std::move(out.rowptr);
@@ -1148,7 +1321,7 @@ static std::unique_ptr<Level> galerkin(Level& L, bool lp, cudaStream_t s, int64_
     emit_rows(ELp{L.col.get(), L.w.get(), L.agg.get(), cbits, lkeys.get(), lvals.get()}, L.rowptr.get(), cnt.get(),
               bins_of(L.plan.plan, n), s);
     CsrOut lo;
-    accumulate_csr(lkeys, lvals, nent, n, cbits, lo, s, counter);
+    accumulate_csr(lkeys, lvals, nent, n, cbits, lo, s, counter, grouped ? cnt.get() : nullptr, n);
     L.lp_nnz = lo.nnz;
     L.lp_ptr = std::move(lo.rowptr);
     L.lp_col = std::move(lo.col);
@@ -1213,8 +1386,52 @@ static void coarsest_pinv(Level& L, int* err, cudaStream_t s, int64_t* counter) 
   LG_LAUNCH_CHECK();
 }
 
+// Smallest and largest weight of an operator as IEEE bit patterns: the
+// weights are validated positive, where the bit order is the value order.
+__global__ void k_wrange(int64_t nnz, const double* __restrict__ w, unsigned long long* mm) {
+  unsigned long long lo = ~0ull, hi = 0ull;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz; k += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(w[k]);
+    lo = b < lo ? b : lo;
+    hi = b > hi ? b : hi;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long a = __shfl_xor_sync(0xffffffffu, lo, o), c = __shfl_xor_sync(0xffffffffu, hi, o);
+    lo = a < lo ? a : lo;
+    hi = c > hi ? c : hi;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(&mm[0], lo);
+    atomicMax(&mm[1], hi);
+  }
+}
+
+// A finest operator whose weights are all one value (an unweighted graph,
+// or one scaled uniformly) keeps only its pattern: the passes take the
+// value as a constant and stream 4 bytes per entry instead of 8 + 4 (FP64)
+// or 4 + 4 (FP32). The products are bitwise those of the stored weights.
+// Runs once the coarser levels, which read the finest weights, are built.
+static void detect_constant_weights(Level& L, cudaStream_t s) {
+  if (L.nnz == 0 || !L.w.get()) return;
+  DBuf<unsigned long long> mm(2, s);
+  const unsigned long long init[2] = {~0ull, 0ull};
+  LG_CUDA(cudaMemcpyAsync(mm.get(), init, sizeof(init), cudaMemcpyHostToDevice, s));
+  k_wrange<<<grid_for(L.nnz, kNT, kSMs * 8), kNT, 0, s>>>(L.nnz, L.w.get(), mm.get());
+  LG_LAUNCH_CHECK();
+  unsigned long long out[2];
+  LG_CUDA(cudaMemcpyAsync(out, mm.get(), sizeof(out), cudaMemcpyDeviceToHost, s));
+  LG_CUDA(cudaStreamSynchronize(s));
+  if (out[0] != out[1]) return;
+  double v;
+  std::memcpy(&v, &out[0], sizeof(v));
+  L.wconst_on = true;
+  L.wconst = v;
+  L.w.release();
+  L.w32.release();
+}
+
 static void make_f32(Level& L, cudaStream_t s, int64_t* counter) {
-  if (L.nnz > 0) {
+  if (L.nnz > 0 && L.w.get()) {
     L.w32.alloc(L.nnz, s, counter);
     k_to_f32<<<blocks_for(L.nnz), kNT, 0, s>>>(L.nnz, L.w.get(), L.w32.get());
     LG_LAUNCH_CHECK();
@@ -1245,7 +1462,7 @@ static std::map<std::pair<int64_t, int64_t>, int> g_tune_cache;
 template <typename T>
 static float time_apply(const Level& L, const T* x, T* y, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
   OpView<T> op = L.op<T>();
-  const LapTerm<T> term{op.w, x, op.d};
+  const LapTerm<T> term = lap_term(op, x);
   launch_rows<T, 0>(op.n, op.rowptr, op.col, term, op.plan, EpiStore<T>{y}, s);
   LG_CUDA(cudaEventRecord(e0, s));
   for (int r = 0; r < 3; ++r) launch_rows<T, 0>(op.n, op.rowptr, op.col, term, op.plan, EpiStore<T>{y}, s);
@@ -1406,10 +1623,17 @@ void setup_hierarchy(Hier& h, int64_t n, const int64_t* rowptr, const int32_t* c
     LG_LAUNCH_CHECK();
     const int cbits = bits_for(n);
     DBuf<uint64_t> keys(nnz, s), vals(nnz, s);
-    each_row(FPermEmit{cur->col.get(), cur->w.get(), inv.get(), cbits, keys.get(), vals.get()}, cur->rowptr.get(),
-             in_bins.bins, s);
+    DBuf<int64_t> rp_new;
+    if (o.row_sorts) {
+      rp_new.alloc(n + 1, s);
+      k_perm_degrees<<<blocks_for(n), kNT, 0, s>>>(n, cur->rowptr.get(), inv.get(), rp_new.get());
+      LG_LAUNCH_CHECK();
+      exclusive_scan(rp_new.get(), rp_new.get(), n, s);
+    }
+    each_row(FPermEmit{cur->col.get(), cur->w.get(), inv.get(), rp_new.get(), cbits, keys.get(), vals.get()},
+             cur->rowptr.get(), in_bins.bins, s);
     CsrOut out;
-    accumulate_csr(keys, vals, nnz, n, cbits, out, s, counter);
+    accumulate_csr(keys, vals, nnz, n, cbits, out, s, counter, rp_new.get(), n);
     cur->rowptr = std::move(out.rowptr);
     cur->col = std::move(out.col);
     cur->w = std::move(out.w);
@@ -1438,7 +1662,7 @@ void setup_hierarchy(Hier& h, int64_t n, const int64_t* rowptr, const int32_t* c
                                          is_f.get(), s);
       clk.mark("elim_select");
       if (!((double)nf > o.elim_min_frac * (double)cur->n)) break;
-      auto next = eliminate(*cur, is_f.get(), nf, s, counter);
+      auto next = eliminate(*cur, is_f.get(), nf, o.row_sorts != 0, s, counter);
       clk.mark("elim_schur");
       h.levels.push_back(std::move(cur));
       cur = std::move(next);
@@ -1472,7 +1696,7 @@ void setup_hierarchy(Hier& h, int64_t n, const int64_t* rowptr, const int32_t* c
     lanczos(*cur, o, level, lz_dev.get() + level, s);
     clk.mark("lanczos");
     lam_level.push_back(level);
-    auto next = galerkin(*cur, o.lp_residual != 0, s, counter, clk);
+    auto next = galerkin(*cur, o.lp_residual != 0, o.row_sorts != 0, s, counter, clk);
     h.levels.push_back(std::move(cur));
     cur = std::move(next);
     prepare_operator(*cur, s, counter);
@@ -1485,6 +1709,8 @@ void setup_hierarchy(Hier& h, int64_t n, const int64_t* rowptr, const int32_t* c
   }
   clk.mark("coarsest_pinv");
   h.levels.push_back(std::move(cur));
+  if (o.const_weights) detect_constant_weights(*h.levels[0], s);
+  clk.mark("constant_weights");
   for (auto& L : h.levels) make_f32(*L, s, counter);
   clk.mark("fp32_copies");
   if (read_err(h.dev_err, s)) fail(LG_ERR_SETUP, "coarsest pseudo-inverse failed");

@@ -37,6 +37,7 @@ class Options(C.Structure):
         ("residual_replace", C.c_int32), ("memory_space", C.c_int32), ("use_graphs", C.c_int32),
         ("autotune", C.c_int32), ("reorder", C.c_int32), ("kcycle", C.c_int32),
         ("elim_rounds", C.c_int32), ("lp_residual", C.c_int32), ("fp32_only", C.c_int32),
+        ("const_weights", C.c_int32), ("row_sorts", C.c_int32),
     ]
 
 
@@ -274,6 +275,12 @@ def lg_vcycle(h, f, x, precision: int = FP64):
     _check(_load().lg_vcycle(h, _ptr(f), _ptr(x), int(precision)), "lg_vcycle")
 
 
+def lg_vcycle_batch(h, k: int, F, ldf: int, X, ldx: int, precision: int = FP64):
+    """X = M F on k column-major columns (leading dimensions ldf, ldx), host or device."""
+    _check(_load().lg_vcycle_batch(h, int(k), _ptr(F), int(ldf), _ptr(X), int(ldx), int(precision)),
+           "lg_vcycle_batch")
+
+
 def lg_kernel_launches() -> int:
     return int(_load().lg_kernel_launches())
 
@@ -294,10 +301,10 @@ def lg_profile_read(h, level: int = -1) -> KernelProfile:
 
 
 def lg_level_plan(h, l: int) -> dict:
-    out = (C.c_int64 * 7)()
+    out = (C.c_int64 * 8)()
     _check(_load().lg_level_plan(h, int(l), out), "lg_level_plan")
     return {"E": out[0], "group_rows": out[1], "warp_rows": out[2], "long_rows": out[3], "chunks": out[4],
-            "blocks": out[5], "seg_tiles": out[6]}
+            "blocks": out[5], "seg_tiles": out[6], "const_weights": out[7]}
 
 
 def _stream(stream):

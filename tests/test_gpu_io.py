@@ -120,13 +120,17 @@ def _level0_offsets(lgmod, data, n0):
     kind = int(np.frombuffer(data, dtype=np.int32, count=1, offset=at)[0])
     n, nnz, nc = (int(v) for v in np.frombuffer(data, dtype=np.int64, count=3, offset=at + 4))
     at += 4 + 5 * 8 + 4                    # kind, n, nnz, nc, nf, lambda, binning
+    wconst = int(np.frombuffer(data, dtype=np.int32, count=1, offset=at)[0])
+    assert wconst in (0, 1)
+    at += 4 + 8                            # constant-weight flag and value
+    nw = 0 if wconst else nnz              # a constant-weight level stores no weight arrays
     assert n == n0 and u64(at) == n + 1
     at += 8 + 8 * (n + 1)                  # rowptr
     rowptr_at = at - 8 * (n + 1)
     assert u64(at) == nnz
     col_at = at + 8
     at += 8 + 4 * nnz
-    for count, size in ((nnz, 8), (n, 8), (n, 8), (nnz, 4), (n, 4)):  # w, d, dinv, w32, dinv32
+    for count, size in ((nw, 8), (n, 8), (n, 8), (nw, 4), (n, 4)):  # w, d, dinv, w32, dinv32
         assert u64(at) == count
         at += 8 + size * count
     agg_at = None
