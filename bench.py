@@ -454,7 +454,7 @@ def serve_leg(lg, inputs, args, torch, dev):
     # multi-column plans and a ready workspace each); the statistics restart for each run
     t0 = time.perf_counter()
     sv = lg.lg_serve_create(lg.serve_options(slots=args.serve_slots, precision=lg.FP32_HIER,
-                                             hbm_budget_bytes=120e9))
+                                             hbm_budget_bytes=120e9, policy=lg.SERVE_LEAST_WORK))
     for H in hs:
         lg.lg_serve_register(sv, H.h)
     register_s = time.perf_counter() - t0
@@ -516,6 +516,9 @@ def serve_leg(lg, inputs, args, torch, dev):
         rate = load * cap_rps
         st, span, rhs, failed = run(requests(args.serve_requests), rate)
         loads[load] = (rate, st, span, rhs, failed)
+    # the headline load again in arrival order (bounded bypass), for comparison
+    lg.lg_serve_set_policy(sv, lg.SERVE_ARRIVAL)
+    st_a, span_a, rhs_a, fail_a = run(requests(args.serve_requests), args.serve_load * cap_rps)
     resident = sum(lg.lg_hier_bytes(H.h)[0] for H in hs)
     lg.lg_serve_destroy(sv)
     for H in hs:
@@ -535,14 +538,18 @@ def serve_leg(lg, inputs, args, torch, dev):
                                 "groups": int(v[1].groups), "packed_groups": int(v[1].packed_groups),
                                 "failed": int(v[1].failed + v[4])}
                     for ld, v in loads.items()},
+        "arrival_order": {"load": args.serve_load, "p50_ms": st_a.p50_ms, "p99_ms": st_a.p99_ms,
+                          "solves_per_s": rhs_a / span_a, "groups": int(st_a.groups),
+                          "failed": int(st_a.failed + fail_a)},
         "completed": int(st.completed),
-        "failed": int(sum(v[1].failed + v[4] for v in loads.values()) + st_b.failed + fail_b),
+        "failed": int(sum(v[1].failed + v[4] for v in loads.values()) + st_b.failed + fail_b + st_a.failed + fail_a),
         "requests": args.serve_requests, "graphs": len(hs),
         "vertices_resident": int(sum(sizes)), "nnz_resident": int(sum(nnzs)),
         "resident_bytes": float(resident), "generate_s": gen_s, "setup_s": setup_s, "register_s": register_s,
         "config": f"{len(hs)} resident graphs, n log-uniform in [1000, {args.serve_nmax}], type uniform over "
                   f"2D grid / 3D grid / Chung-Lu 2.1 / R-MAT ef16 (power-law members generated on the device); "
-                  f"FP32-only hierarchies; k uniform in 1..8; tol 1e-8; {args.serve_slots} slots; HBM budget "
+                  f"FP32-only hierarchies; k uniform in 1..8; tol 1e-8; {args.serve_slots} slots; policy least "
+                  f"work first with aging (arrival order at the headline load in arrival_order); HBM budget "
                   f"120 GB; capacity = completion rate of {n_probe} requests with one in flight per slot (no "
                   f"queue, no merging); saturation = completion rate of a burst of {len(burst)} queued at once (the "
                   f"most merging); then Poisson arrivals at 0.5, {args.serve_load} (headline) and 0.95 x capacity, "

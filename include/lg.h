@@ -426,8 +426,11 @@ typedef struct {
   int32_t slots;            /* concurrent solves on the device (one stream each), 1..64 */
   int32_t max_queue;        /* pending requests before lg_serve_submit returns LG_ERR_BUSY */
   int32_t precision;        /* V-cycle precision of served solves */
-  int32_t reserved;
+  int32_t policy;           /* which queued request leads the next group: LG_SERVE_ARRIVAL (default)
+                               or LG_SERVE_LEAST_WORK (see lg_serve_submit) */
 } lg_serve_options;
+
+enum { LG_SERVE_ARRIVAL = 0, LG_SERVE_LEAST_WORK = 1 };
 
 typedef struct {
   double p50_ms, p99_ms;    /* request latency, submit to completion */
@@ -454,11 +457,15 @@ int lg_serve_register(lg_server_t s, lg_handle h);
  * Queue k right-hand sides (column-major n x k in HOST memory, B and X) for
  * hierarchy h. Returns at once with a ticket. B and X must stay valid until
  * lg_serve_poll reports done. Requests are admitted as slots and budget free
- * up, in arrival order except that a request that fits may pass a head
- * request that does not (at most 16 times per head request). A free slot
- * takes the first admissible request together with every queued request on
- * the same hierarchy and tolerance (up to 32 columns in all) and solves them
- * as one multi-column batch; a single-column request on a graph of at most
+ * up. Policy LG_SERVE_ARRIVAL: in arrival order, except that a request that
+ * fits may pass a head request that does not (at most 16 times per head
+ * request). Policy LG_SERVE_LEAST_WORK: the admissible request with the least
+ * work (k times the entries of all its hierarchy's operators) leads, but a
+ * request passed over 16 times leads as soon as it is admissible (the oldest
+ * first). A free slot takes the lead request together with the queued
+ * requests on the same hierarchy and tolerance (up to 8 columns in all; a
+ * wider request runs alone) and solves them as one multi-column batch; a
+ * single-column request on a graph of at most
  * 16384 vertices (and 2^22 nonzeros, no K-cycle) instead joins the other such
  * queued requests (one per hierarchy, same tolerance) in one packed launch,
  * which uses the hierarchy's default workspace: do not call lg_solve on a
@@ -490,6 +497,9 @@ int lg_serve_stats(lg_server_t s, lg_serve_stats_t* st);
 /* Start the statistics afresh (latencies, counts, phase times, the clock of
  * solves_per_s): successive measurements on one server. */
 int lg_serve_reset_stats(lg_server_t s);
+/* Switch the policy (LG_SERVE_ARRIVAL or LG_SERVE_LEAST_WORK) of a running
+ * server; it applies from the next group a slot takes. */
+int lg_serve_set_policy(lg_server_t s, int32_t policy);
 
 /* Wait for every queued request, then release the server's threads and streams. */
 void lg_serve_destroy(lg_server_t s);

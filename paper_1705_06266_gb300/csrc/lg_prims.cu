@@ -279,18 +279,21 @@ __global__ void k_rowptr_from_keys(const uint64_t* __restrict__ segkey, int64_t 
 // [rp[r], rp[r+1]) in the order they were emitted, the rows' key bits equal
 // within a row and ascending from row to row), sorting every row's entries
 // stably by key gives the order a global stable sort would, with one read
-// and one write of the entries instead of one per 8 key bits. By length:
+// and one write of the entries instead of one per 8 key bits. In place, by
+// length:
 //  - rows of at most 32 entries: a group of 2^c lanes per row, each entry
 //    ranked by comparing it with the others (ties by position);
 //  - rows of at most kWrBlockMax entries: one block per row, a bitonic
 //    network in shared memory over (column, position) pairs, which are
 //    distinct, so the result is the stable order;
-//  - longer rows: gathered into one array (row replaced by its index among
-//    them) and radix sorted together, then written back.
+//  - longer rows: gathered, a batch of rows at a time, into one array (row
+//    replaced by its index in the batch), radix sorted together and written
+//    back; batches of about kWrBatch entries bound the scratch memory.
 // Rows are independent, so which block takes which row does not matter.
 // ---------------------------------------------------------------------------
-constexpr int kWrBlockMax = 16384;
-constexpr int kWrClasses = 16;  // 0: <= 1 entry; 1..5: lane groups; 6..14: blocks of 2^c; 15: long
+constexpr int kWrBlockMax = 8192;
+constexpr int64_t kWrBatch = int64_t(1) << 28;
+constexpr int kWrClasses = 15;  // 0: <= 1 entry; 1..5: lane groups; 6..13: blocks of 2^c; 14: long
 
 __device__ __forceinline__ int wr_class(int64_t len) {
   if (len <= 1) return 0;
@@ -328,23 +331,11 @@ __global__ void k_wr_bin(int64_t nrows, const int64_t* __restrict__ rp, int pass
   }
 }
 
-__global__ void k_wr_copy1(const int32_t* __restrict__ rows, int64_t nr, const int64_t* __restrict__ rp,
-                           const uint64_t* __restrict__ kin, const uint64_t* __restrict__ vin,
-                           uint64_t* __restrict__ kout, uint64_t* __restrict__ vout) {
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nr; q += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t b = rp[rows[q]];
-    if (rp[rows[q] + 1] > b) {
-      kout[b] = kin[b];
-      vout[b] = vin[b];
-    }
-  }
-}
-
-// Rows of at most G entries, one group of G lanes each.
+// Rows of at most G entries, one group of G lanes each. Every lane of a group
+// reads its entry before the shuffles, so the writes may overwrite the row.
 template <int G>
 __global__ void k_wr_rank(const int32_t* __restrict__ rows, int64_t nr, const int64_t* __restrict__ rp,
-                          const uint64_t* __restrict__ kin, const uint64_t* __restrict__ vin,
-                          uint64_t* __restrict__ kout, uint64_t* __restrict__ vout) {
+                          uint64_t* keys, uint64_t* vals) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t gi = t / G;
   const int l = (int)(t & (G - 1));
@@ -357,8 +348,8 @@ __global__ void k_wr_rank(const int32_t* __restrict__ rows, int64_t nr, const in
   }
   uint64_t k = ~0ull, v = 0;
   if (l < len) {
-    k = kin[b + l];
-    v = vin[b + l];
+    k = keys[b + l];
+    v = vals[b + l];
   }
   int rank = 0;
 #pragma unroll
@@ -367,26 +358,35 @@ __global__ void k_wr_rank(const int32_t* __restrict__ rows, int64_t nr, const in
     rank += (m < len) & ((km < k) | ((km == k) & (m < l)));
   }
   if (l < len) {
-    kout[b + rank] = k;
-    vout[b + rank] = v;
+    keys[b + rank] = k;
+    vals[b + rank] = v;
   }
 }
 
-// Rows of at most P entries (P a power of two, 64..kWrBlockMax), one block each.
+// Rows of at most P entries (P a power of two, 64..kWrBlockMax), one block
+// each; the row's values are held in shared memory beside the pairs.
 template <int P>
 __global__ void __launch_bounds__(P / 2 < 1024 ? P / 2 : 1024)
-k_wr_block(const int32_t* __restrict__ rows, const int64_t* __restrict__ rp, const uint64_t* __restrict__ kin,
-           const uint64_t* __restrict__ vin, uint64_t* __restrict__ kout, uint64_t* __restrict__ vout,
+k_wr_block(const int32_t* __restrict__ rows, const int64_t* __restrict__ rp, uint64_t* keys, uint64_t* vals,
            uint64_t cmask) {
   constexpr int T = P / 2 < 1024 ? P / 2 : 1024;
   constexpr int PB = P <= 64 ? 6 : P <= 128 ? 7 : P <= 256 ? 8 : P <= 512 ? 9 : P <= 1024 ? 10 : P <= 2048 ? 11
-                   : P <= 4096 ? 12 : P <= 8192 ? 13 : 14;
+                   : P <= 4096 ? 12 : 13;
   static_assert((1 << PB) == P, "P must be a power of two");
-  extern __shared__ uint64_t wr_sk[];
+  extern __shared__ uint64_t wr_sk[];  // P pairs, then P values
+  uint64_t* sv = wr_sk + P;
   const int32_t r = rows[blockIdx.x];
   const int64_t b = rp[r];
   const int len = (int)(rp[r + 1] - b);
-  for (int i = threadIdx.x; i < P; i += T) wr_sk[i] = i < len ? ((kin[b + i] & cmask) << PB) | (uint64_t)i : ~0ull;
+  const uint64_t rowbits = keys[b] & ~cmask;
+  for (int i = threadIdx.x; i < P; i += T) {
+    if (i < len) {
+      wr_sk[i] = ((keys[b + i] & cmask) << PB) | (uint64_t)i;
+      sv[i] = vals[b + i];
+    } else {
+      wr_sk[i] = ~0ull;
+    }
+  }
   __syncthreads();
   for (int size = 2; size <= P; size <<= 1) {
     for (int stride = size >> 1; stride > 0; stride >>= 1) {
@@ -402,37 +402,37 @@ k_wr_block(const int32_t* __restrict__ rows, const int64_t* __restrict__ rp, con
     }
   }
   for (int i = threadIdx.x; i < len; i += T) {
-    const int pos = (int)(wr_sk[i] & (uint64_t)(P - 1));
-    kout[b + i] = kin[b + pos];
-    vout[b + i] = vin[b + pos];
+    const uint64_t c = wr_sk[i];
+    keys[b + i] = rowbits | (c >> PB);
+    vals[b + i] = sv[c & (uint64_t)(P - 1)];
   }
 }
 
-// Long rows: to one array, keyed (index among the long rows, column), and back.
+// Long rows of one batch: to one array, keyed (index in the batch, column), and back.
 __global__ void k_wr_gather(const int32_t* __restrict__ lrows, const int64_t* __restrict__ rp,
-                            const int64_t* __restrict__ loff, const uint64_t* __restrict__ kin,
-                            const uint64_t* __restrict__ vin, uint64_t* __restrict__ tk, uint64_t* __restrict__ tv,
+                            const int64_t* __restrict__ loff, int64_t o0, const uint64_t* __restrict__ keys,
+                            const uint64_t* __restrict__ vals, uint64_t* __restrict__ tk, uint64_t* __restrict__ tv,
                             int cbits) {
   const int32_t r = lrows[blockIdx.x];
-  const int64_t b = rp[r], len = rp[r + 1] - b, o = loff[blockIdx.x];
+  const int64_t b = rp[r], len = rp[r + 1] - b, o = loff[blockIdx.x] - o0;
   const uint64_t cmask = (1ull << cbits) - 1ull;
   for (int64_t q = threadIdx.x; q < len; q += blockDim.x) {
-    tk[o + q] = ((uint64_t)blockIdx.x << cbits) | (kin[b + q] & cmask);
-    tv[o + q] = vin[b + q];
+    tk[o + q] = ((uint64_t)blockIdx.x << cbits) | (keys[b + q] & cmask);
+    tv[o + q] = vals[b + q];
   }
 }
 
 __global__ void k_wr_scatter(const int32_t* __restrict__ lrows, const int64_t* __restrict__ rp,
-                             const int64_t* __restrict__ loff, const uint64_t* __restrict__ kin,
-                             const uint64_t* __restrict__ tk, const uint64_t* __restrict__ tv,
-                             uint64_t* __restrict__ kout, uint64_t* __restrict__ vout, int cbits) {
+                             const int64_t* __restrict__ loff, int64_t o0, const uint64_t* __restrict__ tk,
+                             const uint64_t* __restrict__ tv, uint64_t* keys, uint64_t* vals, int cbits) {
   const int32_t r = lrows[blockIdx.x];
-  const int64_t b = rp[r], len = rp[r + 1] - b, o = loff[blockIdx.x];
+  const int64_t b = rp[r], len = rp[r + 1] - b, o = loff[blockIdx.x] - o0;
   const uint64_t cmask = (1ull << cbits) - 1ull;
-  const uint64_t rowbits = kin[b] & ~cmask;
+  const uint64_t rowbits = keys[b] & ~cmask;  // every entry of the row has the same row bits
+  __syncthreads();  // the block's reads of keys[b] come before any write to the row
   for (int64_t q = threadIdx.x; q < len; q += blockDim.x) {
-    kout[b + q] = rowbits | (tk[o + q] & cmask);
-    vout[b + q] = tv[o + q];
+    keys[b + q] = rowbits | (tk[o + q] & cmask);
+    vals[b + q] = tv[o + q];
   }
 }
 
@@ -443,15 +443,45 @@ __global__ void k_wr_long_len(const int32_t* __restrict__ lrows, int64_t nl, con
 }
 
 template <int P>
-static void wr_block_launch(const int32_t* rows, int64_t nr, const int64_t* rp, const uint64_t* kin,
-                            const uint64_t* vin, uint64_t* kout, uint64_t* vout, uint64_t cmask, cudaStream_t s) {
+static void wr_block_launch(const int32_t* rows, int64_t nr, const int64_t* rp, uint64_t* keys, uint64_t* vals,
+                            uint64_t cmask, cudaStream_t s) {
   constexpr int T = P / 2 < 1024 ? P / 2 : 1024;
-  const size_t smem = sizeof(uint64_t) * P;
+  const size_t smem = 2 * sizeof(uint64_t) * P;
   if (smem > 48 * 1024)
     LG_CUDA(cudaFuncSetAttribute(k_wr_block<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   for (int64_t q0 = 0; q0 < nr; q0 += 1 << 30) {
     const int64_t m = nr - q0 < (1 << 30) ? nr - q0 : (1 << 30);
-    k_wr_block<P><<<(unsigned)m, T, smem, s>>>(rows + q0, rp, kin, vin, kout, vout, cmask);
+    k_wr_block<P><<<(unsigned)m, T, smem, s>>>(rows + q0, rp, keys, vals, cmask);
+    LG_LAUNCH_CHECK();
+  }
+}
+
+static void wr_long(const int32_t* rl, int64_t nr, const int64_t* rp, uint64_t* keys, uint64_t* vals, int cbits,
+                    cudaStream_t s) {
+  DBuf<int64_t> loff(nr + 1, s);
+  k_wr_long_len<<<grid_for(nr, 256, kSMs * 8), 256, 0, s>>>(rl, nr, rp, loff.get());
+  LG_LAUNCH_CHECK();
+  exclusive_scan(loff.get(), loff.get(), nr, s);
+  std::vector<int64_t> ho((size_t)nr + 1);
+  LG_CUDA(cudaMemcpyAsync(ho.data(), loff.get(), sizeof(int64_t) * (nr + 1), cudaMemcpyDeviceToHost, s));
+  LG_CUDA(cudaStreamSynchronize(s));
+  int64_t biggest = 0;
+  for (int64_t q0 = 0, q1; q0 < nr; q0 = q1) {  // batches of whole rows, about kWrBatch entries each
+    for (q1 = q0 + 1; q1 < nr && ho[q1 + 1] - ho[q0] <= kWrBatch; ++q1) {
+    }
+    biggest = std::max(biggest, ho[q1] - ho[q0]);
+  }
+  DBuf<uint64_t> tk(biggest, s), tv(biggest, s);
+  for (int64_t q0 = 0, q1; q0 < nr; q0 = q1) {
+    for (q1 = q0 + 1; q1 < nr && ho[q1 + 1] - ho[q0] <= kWrBatch; ++q1) {
+    }
+    const int64_t m = ho[q1] - ho[q0];
+    k_wr_gather<<<(unsigned)(q1 - q0), 256, 0, s>>>(rl + q0, rp, loff.get() + q0, ho[q0], keys, vals, tk.get(),
+                                                     tv.get(), cbits);
+    LG_LAUNCH_CHECK();
+    radix_sort_pairs(tk.get(), tv.get(), m, bits_for(q1 - q0) + cbits, s);
+    k_wr_scatter<<<(unsigned)(q1 - q0), 256, 0, s>>>(rl + q0, rp, loff.get() + q0, ho[q0], tk.get(), tv.get(),
+                                                      keys, vals, cbits);
     LG_LAUNCH_CHECK();
   }
 }
@@ -459,7 +489,6 @@ static void wr_block_launch(const int32_t* rows, int64_t nr, const int64_t* rp, 
 void sort_within_rows(DBuf<uint64_t>& keys, DBuf<uint64_t>& vals, int64_t nent, const int64_t* rp, int64_t ngroups,
                       int cbits, cudaStream_t s) {
   if (nent <= 1 || ngroups <= 0) return;
-  DBuf<uint64_t> kout(nent, s), vout(nent, s);
   DBuf<int64_t> cnt(kWrClasses, s);
   DBuf<unsigned long long> fill(kWrClasses, s);
   DBuf<int32_t> rows(ngroups, s);
@@ -476,50 +505,31 @@ void sort_within_rows(DBuf<uint64_t>& keys, DBuf<uint64_t>& vals, int64_t nent, 
   LG_CUDA(cudaMemcpyAsync(cnt.get(), ho, sizeof(int64_t) * kWrClasses, cudaMemcpyHostToDevice, s));
   k_wr_bin<<<gb, 256, 0, s>>>(ngroups, rp, 1, nullptr, cnt.get(), fill.get(), rows.get());
   LG_LAUNCH_CHECK();
-  const uint64_t *kin = keys.get(), *vin = vals.get();
-  uint64_t *ko = kout.get(), *vo = vout.get();
+  uint64_t *k = keys.get(), *v = vals.get();
   const uint64_t cmask = (1ull << cbits) - 1ull;
-  for (int c = 0; c < kWrClasses; ++c) {
+  for (int c = 1; c < kWrClasses; ++c) {  // class 0 (at most one entry) is sorted already
     const int64_t nr = hc[c];
     if (!nr) continue;
     const int32_t* rl = rows.get() + ho[c];
     const auto lanes = [&](int G) { return grid_for(nr * G, 256, 1 << 30); };
     switch (c) {
-      case 0: k_wr_copy1<<<grid_for(nr, 256, kSMs * 16), 256, 0, s>>>(rl, nr, rp, kin, vin, ko, vo); break;
-      case 1: k_wr_rank<2><<<lanes(2), 256, 0, s>>>(rl, nr, rp, kin, vin, ko, vo); break;
-      case 2: k_wr_rank<4><<<lanes(4), 256, 0, s>>>(rl, nr, rp, kin, vin, ko, vo); break;
-      case 3: k_wr_rank<8><<<lanes(8), 256, 0, s>>>(rl, nr, rp, kin, vin, ko, vo); break;
-      case 4: k_wr_rank<16><<<lanes(16), 256, 0, s>>>(rl, nr, rp, kin, vin, ko, vo); break;
-      case 5: k_wr_rank<32><<<lanes(32), 256, 0, s>>>(rl, nr, rp, kin, vin, ko, vo); break;
-      case 6: wr_block_launch<64>(rl, nr, rp, kin, vin, ko, vo, cmask, s); break;
-      case 7: wr_block_launch<128>(rl, nr, rp, kin, vin, ko, vo, cmask, s); break;
-      case 8: wr_block_launch<256>(rl, nr, rp, kin, vin, ko, vo, cmask, s); break;
-      case 9: wr_block_launch<512>(rl, nr, rp, kin, vin, ko, vo, cmask, s); break;
-      case 10: wr_block_launch<1024>(rl, nr, rp, kin, vin, ko, vo, cmask, s); break;
-      case 11: wr_block_launch<2048>(rl, nr, rp, kin, vin, ko, vo, cmask, s); break;
-      case 12: wr_block_launch<4096>(rl, nr, rp, kin, vin, ko, vo, cmask, s); break;
-      case 13: wr_block_launch<8192>(rl, nr, rp, kin, vin, ko, vo, cmask, s); break;
-      case 14: wr_block_launch<16384>(rl, nr, rp, kin, vin, ko, vo, cmask, s); break;
-      default: {
-        DBuf<int64_t> loff(nr + 1, s);
-        k_wr_long_len<<<grid_for(nr, 256, kSMs * 8), 256, 0, s>>>(rl, nr, rp, loff.get());
-        LG_LAUNCH_CHECK();
-        exclusive_scan(loff.get(), loff.get(), nr, s);
-        int64_t nl = 0;
-        LG_CUDA(cudaMemcpyAsync(&nl, loff.get() + nr, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-        LG_CUDA(cudaStreamSynchronize(s));
-        DBuf<uint64_t> tk(nl, s), tv(nl, s);
-        k_wr_gather<<<(unsigned)nr, 256, 0, s>>>(rl, rp, loff.get(), kin, vin, tk.get(), tv.get(), cbits);
-        LG_LAUNCH_CHECK();
-        radix_sort_pairs(tk.get(), tv.get(), nl, bits_for(nr) + cbits, s);
-        k_wr_scatter<<<(unsigned)nr, 256, 0, s>>>(rl, rp, loff.get(), kin, tk.get(), tv.get(), ko, vo, cbits);
-        break;
-      }
+      case 1: k_wr_rank<2><<<lanes(2), 256, 0, s>>>(rl, nr, rp, k, v); break;
+      case 2: k_wr_rank<4><<<lanes(4), 256, 0, s>>>(rl, nr, rp, k, v); break;
+      case 3: k_wr_rank<8><<<lanes(8), 256, 0, s>>>(rl, nr, rp, k, v); break;
+      case 4: k_wr_rank<16><<<lanes(16), 256, 0, s>>>(rl, nr, rp, k, v); break;
+      case 5: k_wr_rank<32><<<lanes(32), 256, 0, s>>>(rl, nr, rp, k, v); break;
+      case 6: wr_block_launch<64>(rl, nr, rp, k, v, cmask, s); break;
+      case 7: wr_block_launch<128>(rl, nr, rp, k, v, cmask, s); break;
+      case 8: wr_block_launch<256>(rl, nr, rp, k, v, cmask, s); break;
+      case 9: wr_block_launch<512>(rl, nr, rp, k, v, cmask, s); break;
+      case 10: wr_block_launch<1024>(rl, nr, rp, k, v, cmask, s); break;
+      case 11: wr_block_launch<2048>(rl, nr, rp, k, v, cmask, s); break;
+      case 12: wr_block_launch<4096>(rl, nr, rp, k, v, cmask, s); break;
+      case 13: wr_block_launch<8192>(rl, nr, rp, k, v, cmask, s); break;
+      default: wr_long(rl, nr, rp, k, v, cbits, s); break;
     }
     LG_LAUNCH_CHECK();
   }
-  keys = std::move(kout);
-  vals = std::move(vout);
 }
 
 void accumulate_csr(DBuf<uint64_t>& keys, DBuf<uint64_t>& vals, int64_t nent, int64_t nrows, int cbits,

@@ -5,9 +5,9 @@
 // CUDA stream, as soon as a slot is free and the HBM budget (registered
 // hierarchies + workspaces of running groups) has room. A worker takes work
 // in groups:
-//  - a multi-column group: the first admissible request plus every queued
-//    request on the same hierarchy with the same tolerance, up to 32 columns
-//    in all, solved together as one SpMM batch (lg_batch.cu);
+//  - a multi-column group: the lead request plus every queued request on the
+//    same hierarchy with the same tolerance, up to kMergeCols columns in all,
+//    solved together as one SpMM batch (lg_batch.cu);
 //  - a packed group: single-column requests on small graphs (many different
 //    hierarchies), solved in one k_solve_many launch, a thread block per
 //    graph (lg_many.cu).
@@ -17,9 +17,15 @@
 // column independently of the other columns and graphs in its group, so a
 // request's result is bitwise the same alone and in any mix.
 //
-// Admission is in arrival order, except that a request that fits the budget
-// may pass a head request that does not, at most kMaxBypass times per head
-// request; after that the head waits for room and nothing passes it.
+// Which request leads the next group (the policy of lg_serve_options):
+//  - arrival order: the first admissible request; one that fits the budget
+//    may pass a head request that does not, at most kMaxBypass times per
+//    head request, after which the head waits for room and nothing passes it;
+//  - least work first: the admissible request with the least work (k times
+//    the entries of its hierarchy's operators), except that a request passed
+//    over kMaxBypass times leads as soon as it is admissible (the oldest such
+//    first, and nothing passes it while it waits for room). Short solves then
+//    no longer queue behind long ones, and no request waits forever.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -49,8 +55,9 @@ struct Request {
   double* X = nullptr;
   double tol = 1e-8;
   double ws_bytes = 0.0;
+  double work = 0.0;    // k times the entries of every level's operator
   bool packed = false;  // single column on a small graph: the packed path
-  int bypassed = 0;
+  int bypassed = 0;     // groups that started with a younger request as lead
   Clock::time_point submitted;
   bool done = false;
   lg_info info{};
@@ -157,32 +164,54 @@ static std::vector<Request*> take_group(Server* sv, double& bytes) {
   bytes = 0.0;
   Request* lead = nullptr;
   size_t lead_at = 0;
-  for (size_t q = 0; q < sv->queue.size(); ++q) {
-    Request* rq = sv->queue[q];
-    if (rq->packed) {
-      if (sv->packing.count(rq->h)) continue;  // that handle is in a running launch
-      lead = rq;
-      lead_at = q;
-      break;
+  const bool least_work = sv->o.policy == LG_SERVE_LEAST_WORK;
+  // room: the budget has space for the request (or nothing runs); busy: a
+  // packed request whose handle is in a running launch (it waits for that)
+  const auto room = [&](const Request* rq) {
+    return rq->packed || sv->resident_bytes + sv->inflight_bytes + rq->ws_bytes <= sv->o.hbm_budget_bytes ||
+           sv->running == 0;
+  };
+  const auto busy = [&](const Request* rq) { return rq->packed && sv->packing.count(rq->h) > 0; };
+  if (!least_work) {
+    for (size_t q = 0; q < sv->queue.size(); ++q) {
+      Request* rq = sv->queue[q];
+      if (!busy(rq) && room(rq)) {
+        lead = rq;
+        lead_at = q;
+        break;
+      }
+      if (q == 0 && !rq->packed && rq->bypassed >= kMaxBypass) return group;  // the head has waited long enough
     }
-    if (sv->resident_bytes + sv->inflight_bytes + rq->ws_bytes <= sv->o.hbm_budget_bytes || sv->running == 0) {
-      lead = rq;
-      lead_at = q;
-      break;
+    if (!lead) return group;
+    if (lead_at > 0 && !sv->queue.front()->packed) sv->queue.front()->bypassed += 1;
+  } else {
+    for (size_t q = 0; q < sv->queue.size(); ++q) {
+      Request* rq = sv->queue[q];
+      if (busy(rq)) continue;
+      if (rq->bypassed >= kMaxBypass) {  // the oldest aged request leads, or waits for room
+        if (!room(rq)) return group;
+        lead = rq;
+        lead_at = q;
+        break;
+      }
+      if (room(rq) && (!lead || rq->work < lead->work)) {
+        lead = rq;
+        lead_at = q;
+      }
     }
-    if (q == 0 && rq->bypassed >= kMaxBypass) return group;  // the head has waited long enough
+    if (!lead) return group;
+    for (size_t q = 0; q < lead_at; ++q) sv->queue[q]->bypassed += 1;  // every older request was passed
   }
-  if (!lead) return group;
-  if (lead_at > 0 && !sv->queue.front()->packed) sv->queue.front()->bypassed += 1;
+  const size_t from = least_work ? 0 : lead_at + 1;  // merging looks at older requests too under least work
   std::vector<char> take(sv->queue.size(), 0);
   take[lead_at] = 1;
   group.push_back(lead);
   if (lead->packed) {
     // other single-column small-graph requests with the same tolerance, one per handle
     std::unordered_set<Hier*> seen{lead->h};
-    for (size_t q = lead_at + 1; q < sv->queue.size() && (int)group.size() < kPackMaxGraphs; ++q) {
+    for (size_t q = from; q < sv->queue.size() && (int)group.size() < kPackMaxGraphs; ++q) {
       Request* rq = sv->queue[q];
-      if (!rq->packed || rq->tol != lead->tol || seen.count(rq->h) || sv->packing.count(rq->h)) continue;
+      if (take[q] || !rq->packed || rq->tol != lead->tol || seen.count(rq->h) || sv->packing.count(rq->h)) continue;
       seen.insert(rq->h);
       take[q] = 1;
       group.push_back(rq);
@@ -195,9 +224,9 @@ static std::vector<Request*> take_group(Server* sv, double& bytes) {
     // the queued requests on the same hierarchy and tolerance, up to the widest batch
     int cols = lead->k;
     bytes = lead->ws_bytes;
-    for (size_t q = lead_at + 1; q < sv->queue.size(); ++q) {
+    for (size_t q = from; q < sv->queue.size(); ++q) {
       Request* rq = sv->queue[q];
-      if (rq->packed || rq->h != lead->h || rq->tol != lead->tol || cols + rq->k > kMergeCols) continue;
+      if (take[q] || rq->packed || rq->h != lead->h || rq->tol != lead->tol || cols + rq->k > kMergeCols) continue;
       const double b = workspace_bytes(*lead->h, pow2_width(cols + rq->k));
       if (sv->resident_bytes + sv->inflight_bytes + b > sv->o.hbm_budget_bytes) continue;  // the budget holds
       cols += rq->k;
@@ -398,7 +427,7 @@ int lg_serve_options_default(lg_serve_options* o) {
   o->slots = 8;
   o->max_queue = 1 << 16;
   o->precision = LG_FP32_HIER;
-  o->reserved = 0;
+  o->policy = LG_SERVE_ARRIVAL;
   return LG_OK;
 }
 
@@ -407,7 +436,9 @@ int lg_serve_create(const lg_serve_options* o, lg_server_t* out) {
   *out = nullptr;
   lg_serve_options opt;
   if (o) opt = *o; else lg_serve_options_default(&opt);
-  if (opt.slots < 1 || opt.slots > 64 || opt.max_queue < 1 || !(opt.hbm_budget_bytes > 0.0)) return LG_ERR_INVALID;
+  if (opt.slots < 1 || opt.slots > 64 || opt.max_queue < 1 || !(opt.hbm_budget_bytes > 0.0) ||
+      (opt.policy != LG_SERVE_ARRIVAL && opt.policy != LG_SERVE_LEAST_WORK))
+    return LG_ERR_INVALID;
   auto* sv = new lg::Server();
   sv->o = opt;
   if (cudaGetDevice(&sv->device) != cudaSuccess) {
@@ -523,6 +554,8 @@ int lg_serve_submit(lg_server_t s, lg_handle hh, int32_t k, const double* B, dou
                (int)h->levels.size() <= lg::kManyMaxLevels && !h->opts.kcycle;
   // a packed request runs in its handle's default workspace: only its staging is extra
   rq->ws_bytes = rq->packed ? 16.0 * (double)h->levels[0]->n + 4096.0 : lg::workspace_bytes(*h, lg::pow2_width(k));
+  for (const auto& L : h->levels) rq->work += (double)(L->nnz + L->n);
+  rq->work *= k;
   rq->submitted = lg::Clock::now();
   {
     std::lock_guard<std::mutex> lk(sv->mu);
@@ -614,6 +647,17 @@ int lg_serve_reset_stats(lg_server_t s) {
   sv->completed = sv->failed = sv->rhs_done = sv->groups = sv->packed_groups = sv->ws_made = 0;
   sv->ws_ms = sv->copy_ms = sv->solve_ms = 0.0;
   sv->created = lg::Clock::now();
+  return LG_OK;
+}
+
+int lg_serve_set_policy(lg_server_t s, int32_t policy) {
+  if (!s || (policy != LG_SERVE_ARRIVAL && policy != LG_SERVE_LEAST_WORK)) return LG_ERR_INVALID;
+  auto* sv = reinterpret_cast<lg::Server*>(s);
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->o.policy = policy;
+  }
+  sv->cv_work.notify_all();
   return LG_OK;
 }
 

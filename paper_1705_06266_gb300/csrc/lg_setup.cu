@@ -282,91 +282,190 @@ struct FSchurCountRows {
   }
 };
 
-// The same entries as ESchur, emitted by kept row a (one warp per row) into
-// a's own range, so that they come grouped by coarse row. Within the row,
-// the order reproduces the global stable sort's ties: contributions to one
-// key come in the order of the fine row that ESchur emits them from, i.e.
-// the fill of each eliminated neighbour f < a (in a's row order), then a's
-// own entries, then the fill of each f > a. Fill values are computed from
-// f's row exactly as ESchur does (d_f summed in f's row order, w_fa w_fy / d_f).
-__global__ void k_schur_emit_rows(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                                  const double* __restrict__ w, const uint8_t* __restrict__ is_f,
-                                  const int32_t* __restrict__ cmap, const int64_t* __restrict__ off, int cbits,
-                                  uint64_t* __restrict__ keys, uint64_t* __restrict__ vals) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t a = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; a < n; a += warps) {
-    if (is_f[a]) continue;
-    const int64_t b = rowptr[a], e = rowptr[a + 1];
+// The same entries as ESchur, emitted by kept row a into a's own range, so
+// that they come grouped by coarse row. Within the row, the order reproduces
+// the global stable sort's ties: contributions to one key come in the order
+// of the fine row that ESchur emits them from, i.e. the fill of each
+// eliminated neighbour f < a (in a's row order), then a's own entries, then
+// the fill of each f > a. Fill values are computed from f's row exactly as
+// ESchur does (d_f summed in f's row order, w_fa w_fy / d_f). Rows are taken
+// from the length bins: a group of 2^c lanes per row, a whole block for rows
+// above kChunk entries (a hub's row must not serialise on one warp).
+struct SchurRows {
+  const int64_t* __restrict__ rowptr;
+  const int32_t* __restrict__ col;
+  const double* __restrict__ w;
+  const uint8_t* __restrict__ is_f;
+  const int32_t* __restrict__ cmap;
+  const int64_t* __restrict__ off;
+  int cbits;
+  uint64_t* __restrict__ keys;
+  uint64_t* __restrict__ vals;
+
+  // entry k of kept row a: its counts in the three parts (fill before a, own, fill after a)
+  __device__ __forceinline__ void counts(int64_t a, int64_t k, int64_t e, long long& clt, long long& cown,
+                                         long long& cgt) const {
+    clt = cown = cgt = 0;
+    if (k >= e) return;
+    const int32_t j = col[k];
+    if (is_f[j]) {
+      const long long c = rowptr[j + 1] - rowptr[j] - 1;
+      (j < a ? clt : cgt) = c;
+    } else {
+      cown = 1;
+    }
+  }
+  // writes entry k's contribution at p (own) or from p on (fill)
+  __device__ __forceinline__ void emit(int64_t a, int64_t k, int64_t p) const {
+    const int32_t j = col[k];
     const uint64_t rowkey = (uint64_t)cmap[a] << cbits;
-    // counts of the three parts: fill before a, own entries, fill after a
-    long long nlt = 0, nown = 0;
-    for (int64_t k0 = b; k0 < e; k0 += 32) {
-      const int64_t k = k0 + lane;
-      long long clt = 0, cown = 0;
-      if (k < e) {
-        const int32_t j = col[k];
-        if (is_f[j]) clt = j < a ? rowptr[j + 1] - rowptr[j] - 1 : 0;
-        else cown = 1;
-      }
-      for (int o = 16; o >= 1; o >>= 1) {
-        clt += __shfl_xor_sync(0xffffffffu, clt, o);
-        cown += __shfl_xor_sync(0xffffffffu, cown, o);
-      }
-      nlt += clt;
-      nown += cown;
+    if (!is_f[j]) {
+      keys[p] = rowkey | (uint64_t)cmap[j];
+      vals[p] = (uint64_t)__double_as_longlong(w[k]);
+      return;
     }
-    int64_t plt = off[a], pown = off[a] + nlt, pgt = off[a] + nlt + nown;
-    for (int64_t k0 = b; k0 < e; k0 += 32) {
-      const int64_t k = k0 + lane;
-      long long clt = 0, cown = 0, cgt = 0;
-      int32_t j = -1;
-      int64_t fb = 0, fe = 0;
-      if (k < e) {
-        j = col[k];
-        if (is_f[j]) {
-          fb = rowptr[j];
-          fe = rowptr[j + 1];
-          (j < a ? clt : cgt) = fe - fb - 1;
-        } else {
-          cown = 1;
-        }
-      }
-      // exclusive prefix over the lanes (row order) of each part
-      long long slt = clt, sown = cown, sgt = cgt;
-      for (int o = 1; o < 32; o <<= 1) {
-        const long long tl = __shfl_up_sync(0xffffffffu, slt, o), to = __shfl_up_sync(0xffffffffu, sown, o),
-                        tg = __shfl_up_sync(0xffffffffu, sgt, o);
-        if (lane >= o) {
-          slt += tl;
-          sown += to;
-          sgt += tg;
-        }
-      }
-      if (k < e) {
-        if (cown) {
-          const int64_t p = pown + sown - 1;
-          keys[p] = rowkey | (uint64_t)cmap[j];
-          vals[p] = (uint64_t)__double_as_longlong(w[k]);
-        } else if (fe > fb) {
-          int64_t p = (j < a ? plt + slt - clt : pgt + sgt - cgt);
-          double df = 0.0, wfa = 0.0;
-          for (int64_t q = fb; q < fe; ++q) {
-            df += w[q];
-            if (col[q] == (int32_t)a) wfa = w[q];
-          }
-          for (int64_t q = fb; q < fe; ++q) {
-            if (col[q] == (int32_t)a) continue;
-            keys[p] = rowkey | (uint64_t)cmap[col[q]];
-            vals[p] = (uint64_t)__double_as_longlong(wfa * w[q] / df);
-            ++p;
-          }
-        }
-      }
-      plt += __shfl_sync(0xffffffffu, slt, 31);
-      pown += __shfl_sync(0xffffffffu, sown, 31);
-      pgt += __shfl_sync(0xffffffffu, sgt, 31);
+    const int64_t fb = rowptr[j], fe = rowptr[j + 1];
+    double df = 0.0, wfa = 0.0;
+    for (int64_t q = fb; q < fe; ++q) {
+      df += w[q];
+      if (col[q] == (int32_t)a) wfa = w[q];
     }
+    for (int64_t q = fb; q < fe; ++q) {
+      if (col[q] == (int32_t)a) continue;
+      keys[p] = rowkey | (uint64_t)cmap[col[q]];
+      vals[p] = (uint64_t)__double_as_longlong(wfa * w[q] / df);
+      ++p;
+    }
+  }
+};
+
+// inclusive scan of three counts over the G lanes of a group (lane order)
+template <int G>
+__device__ __forceinline__ void scan3(long long& x, long long& y, long long& z, int gl, unsigned mask) {
+#pragma unroll
+  for (int o = 1; o < G; o <<= 1) {
+    const long long px = __shfl_up_sync(mask, x, o, G), py = __shfl_up_sync(mask, y, o, G),
+                    pz = __shfl_up_sync(mask, z, o, G);
+    if (gl >= o) {
+      x += px;
+      y += py;
+      z += pz;
+    }
+  }
+}
+
+template <int G>
+__device__ __forceinline__ void schur_group(const SchurRows& S, const RowBins& b, int c, int64_t bb) {
+  constexpr int kPer = kEachThreads / G;
+  const int64_t idx = b.off[c] + bb * kPer + threadIdx.x / G;
+  if (idx >= b.off[c + 1]) return;  // whole groups leave together
+  const int64_t a = b.rows[idx];
+  if (S.is_f[a]) return;
+  const int gl = threadIdx.x & (G - 1);
+  const unsigned mask = group_mask<G>();
+  const int64_t beg = S.rowptr[a], end = S.rowptr[a + 1];
+  long long nlt = 0, nown = 0;
+  for (int64_t k0 = beg; k0 < end; k0 += G) {
+    long long x, y, z;
+    S.counts(a, k0 + gl, end, x, y, z);
+    scan3<G>(x, y, z, gl, mask);
+    nlt += __shfl_sync(mask, x, G - 1, G);
+    nown += __shfl_sync(mask, y, G - 1, G);
+  }
+  int64_t plt = S.off[a], pown = plt + nlt, pgt = pown + nown;
+  for (int64_t k0 = beg; k0 < end; k0 += G) {
+    const int64_t k = k0 + gl;
+    long long cx, cy, cz;
+    S.counts(a, k, end, cx, cy, cz);
+    long long x = cx, y = cy, z = cz;
+    scan3<G>(x, y, z, gl, mask);
+    if (k < end) {
+      if (cy) S.emit(a, k, pown + y - 1);
+      else if (cx) S.emit(a, k, plt + x - cx);
+      else if (cz) S.emit(a, k, pgt + z - cz);
+    }
+    plt += __shfl_sync(mask, x, G - 1, G);
+    pown += __shfl_sync(mask, y, G - 1, G);
+    pgt += __shfl_sync(mask, z, G - 1, G);
+  }
+}
+
+// A long row with the whole block: warp scans, then the warps' totals in order.
+__device__ __forceinline__ void schur_long(const SchurRows& S, int64_t a) {
+  __shared__ long long wt[3][kEachThreads / 32];
+  if (S.is_f[a]) return;  // uniform over the block
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t beg = S.rowptr[a], end = S.rowptr[a + 1];
+  const auto block_scan = [&](long long& x, long long& y, long long& z, long long& tx, long long& ty,
+                              long long& tz) {
+    scan3<32>(x, y, z, lane, 0xffffffffu);
+    if (lane == 31) {
+      wt[0][warp] = x;
+      wt[1][warp] = y;
+      wt[2][warp] = z;
+    }
+    __syncthreads();
+    long long bx = 0, by = 0, bz = 0;
+    tx = ty = tz = 0;
+    for (int q = 0; q < kEachThreads / 32; ++q) {
+      if (q < warp) {
+        bx += wt[0][q];
+        by += wt[1][q];
+        bz += wt[2][q];
+      }
+      tx += wt[0][q];
+      ty += wt[1][q];
+      tz += wt[2][q];
+    }
+    x += bx;
+    y += by;
+    z += bz;
+    __syncthreads();  // wt is reused by the next step
+  };
+  long long nlt = 0, nown = 0;
+  for (int64_t k0 = beg; k0 < end; k0 += kEachThreads) {
+    long long x, y, z, tx, ty, tz;
+    S.counts(a, k0 + threadIdx.x, end, x, y, z);
+    block_scan(x, y, z, tx, ty, tz);
+    nlt += tx;
+    nown += ty;
+  }
+  int64_t plt = S.off[a], pown = plt + nlt, pgt = pown + nown;
+  for (int64_t k0 = beg; k0 < end; k0 += kEachThreads) {
+    const int64_t k = k0 + threadIdx.x;
+    long long cx, cy, cz, tx, ty, tz;
+    S.counts(a, k, end, cx, cy, cz);
+    long long x = cx, y = cy, z = cz;
+    block_scan(x, y, z, tx, ty, tz);
+    if (k < end) {
+      if (cy) S.emit(a, k, pown + y - 1);
+      else if (cx) S.emit(a, k, plt + x - cx);
+      else if (cz) S.emit(a, k, pgt + z - cz);
+    }
+    plt += tx;
+    pown += ty;
+    pgt += tz;
+  }
+}
+
+__global__ void __launch_bounds__(kEachThreads) k_schur_emit_rows(SchurRows S, RowBins b) {
+  const int bid = blockIdx.x;
+  const int64_t nlong = b.off[kClasses + 1] - b.off[kClasses];
+  if (bid < nlong) {
+    schur_long(S, b.rows[b.off[kClasses] + bid]);
+    return;
+  }
+  int c = 0;
+#pragma unroll
+  for (int q = 0; q < kClasses - 1; ++q) c += bid < b.blk[q];
+  const int64_t bb = bid - b.blk[c];
+  switch (c) {
+    case 0: schur_group<1>(S, b, 0, bb); break;
+    case 1: schur_group<2>(S, b, 1, bb); break;
+    case 2: schur_group<4>(S, b, 2, bb); break;
+    case 3: schur_group<8>(S, b, 3, bb); break;
+    case 4: schur_group<16>(S, b, 4, bb); break;
+    default: schur_group<32>(S, b, 5, bb); break;
   }
 }
 
@@ -1218,9 +1317,14 @@ static std::unique_ptr<Level> eliminate(Level& L, const uint8_t* is_f, int64_t n
   {
     DBuf<uint64_t> keys(nent, s), vals(nent, s);
     if (grouped) {
-      k_schur_emit_rows<<<grid_for(n * 32, kNT, kSMs * 16), kNT, 0, s>>>(
-          n, L.rowptr.get(), L.col.get(), L.w.get(), is_f, L.cmap.get(), cnt.get(), cbits, keys.get(), vals.get());
-      LG_LAUNCH_CHECK();
+      const RowBins bins = bins_of(L.plan.plan, n);
+      if (bins.grid > 0) {
+        k_schur_emit_rows<<<bins.grid, kEachThreads, 0, s>>>(
+            SchurRows{L.rowptr.get(), L.col.get(), L.w.get(), is_f, L.cmap.get(), cnt.get(), cbits, keys.get(),
+                      vals.get()},
+            bins);
+        LG_LAUNCH_CHECK();
+      }
     } else {
       emit_rows(ESchur{L.col.get(), L.w.get(), is_f, L.cmap.get(), cbits, keys.get(), vals.get()}, L.rowptr.get(),
                 cnt.get(), bins_of(L.plan.plan, n), s);
@@ -1545,7 +1649,59 @@ static void release_fp64_copies(Hier& h, cudaStream_t s, int64_t* counter) {
   h.fp32_only = true;
 }
 
+// While any setup runs, device memory its stages free stays in the device's
+// stream-ordered pool instead of going back to the driver at each
+// synchronisation, so that the next stage's allocation (tens of GB at scale
+// 26) is not mapped again. The pool's threshold is put back when the last
+// running setup ends; the memory held above it is released at the next
+// synchronisation.
+class PoolHold {
+ public:
+  explicit PoolHold(int device) {
+    std::lock_guard<std::mutex> lk(mu());
+    if (users()++ > 0) return;
+    if (cudaDeviceGetDefaultMemPool(&pool(), device) != cudaSuccess) {
+      cudaGetLastError();
+      pool() = nullptr;
+      return;
+    }
+    uint64_t keep = ~0ull;
+    if (cudaMemPoolGetAttribute(pool(), cudaMemPoolAttrReleaseThreshold, &saved()) != cudaSuccess ||
+        cudaMemPoolSetAttribute(pool(), cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) {
+      cudaGetLastError();
+      pool() = nullptr;
+    }
+  }
+  ~PoolHold() {
+    std::lock_guard<std::mutex> lk(mu());
+    if (--users() > 0 || !pool()) return;
+    if (cudaMemPoolSetAttribute(pool(), cudaMemPoolAttrReleaseThreshold, &saved()) != cudaSuccess) cudaGetLastError();
+    pool() = nullptr;
+  }
+  PoolHold(const PoolHold&) = delete;
+  PoolHold& operator=(const PoolHold&) = delete;
+
+ private:
+  static std::mutex& mu() {
+    static std::mutex m;
+    return m;
+  }
+  static int& users() {
+    static int u = 0;
+    return u;
+  }
+  static cudaMemPool_t& pool() {
+    static cudaMemPool_t p = nullptr;
+    return p;
+  }
+  static uint64_t& saved() {
+    static uint64_t v = 0;
+    return v;
+  }
+};
+
 void setup_hierarchy(Hier& h, int64_t n, const int64_t* rowptr, const int32_t* col, const double* w) {
+  PoolHold hold(h.device);
   cudaStream_t s = h.stream;
   const lg_options& o = h.opts;
   int64_t* counter = &h.bytes;

@@ -22,6 +22,7 @@ OK, ERR_INVALID, ERR_DISCONNECTED, ERR_SETUP, ERR_NOMEM, ERR_NOT_CONVERGED, ERR_
 FP64, FP32_HIER = 0, 1
 AUTO, HOST, DEVICE = -1, 0, 1
 LEVEL_AGG, LEVEL_ELIM, LEVEL_COARSEST = 1, 2, 3
+SERVE_ARRIVAL, SERVE_LEAST_WORK = 0, 1
 DECIDED, UNDECIDED, SEED = 0, 1, 2
 
 
@@ -58,7 +59,7 @@ class KernelProfile(C.Structure):
 
 class ServeOptions(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_double), ("slots", C.c_int32), ("max_queue", C.c_int32),
-                ("precision", C.c_int32), ("reserved", C.c_int32)]
+                ("precision", C.c_int32), ("policy", C.c_int32)]
 
 
 class ServeStats(C.Structure):
@@ -112,6 +113,7 @@ _SIGS = {
     "lg_serve_poll": (C.c_int, [_P, _U64, _P, _P]),
     "lg_serve_stats": (C.c_int, [_P, _P]),
     "lg_serve_reset_stats": (C.c_int, [_P]),
+    "lg_serve_set_policy": (C.c_int, [_P, _I32]),
     "lg_serve_request_bytes": (C.c_int, [_P, _I32, _P]),
     "lg_serve_destroy": (None, [_P]),
 }
@@ -386,6 +388,10 @@ def lg_serve_stats(s) -> ServeStats:
 
 def lg_serve_reset_stats(s):
     _check(_load().lg_serve_reset_stats(s), "lg_serve_reset_stats")
+
+
+def lg_serve_set_policy(s, policy: int):
+    _check(_load().lg_serve_set_policy(s, int(policy)), "lg_serve_set_policy")
 
 
 def lg_serve_destroy(s):

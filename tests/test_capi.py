@@ -39,7 +39,20 @@ def test_options_defaults_match_paper(lgmod):
     assert o.cheb_degree == 2 and o.cheb_lo == 0.3 and o.cheb_hi == 1.1 and o.eig_iters == 10
     assert o.kcycle == 0 and o.elim_rounds == 1  # V-cycle, one elimination round (Sections 3.4, 4)
     assert o.lp_residual == 1
+    assert o.const_weights == 1 and o.row_sorts == 1 and o.fp32_only == 0
+    assert lgmod.serve_options().policy == lgmod.SERVE_ARRIVAL
     assert lgmod.lib().lg_error_string(0) == b"ok"
+
+
+def test_serve_options_checked_without_gpu_work(lgmod):
+    import ctypes as C
+
+    lib = lgmod.lib()
+    s = C.c_void_p()
+    for bad in ({"policy": 2}, {"policy": -1}, {"slots": 0}, {"hbm_budget_bytes": 0.0}):
+        o = lgmod.serve_options(**bad)
+        assert lib.lg_serve_create(C.byref(o), C.byref(s)) == lgmod.ERR_INVALID
+    assert lib.lg_serve_set_policy(None, 1) == lgmod.ERR_INVALID
 
 
 def test_bad_arguments_rejected_without_gpu_work(lgmod):

@@ -162,6 +162,45 @@ def test_batch_columns_independent_of_width(lgmod, inputs, prec):
     H.close()
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_serve_least_work_policy(lgmod, inputs, graphs, oracle_x, prec):
+    """Policy least work first: with the one slot held, three long requests
+    (8 columns each, so none merge) and then a short one queue up. Under
+    arrival order the short request is served last; under least work it
+    leads the next group and finishes before every queued long one. Each
+    result is bitwise the same under both policies (a column does not depend
+    on its group) and matches the oracle."""
+    p = lgmod.FP64 if prec == "fp64" else lgmod.FP32_HIER
+    g_big, H_big = graphs["chunglu_30k"]
+    g_s, H_s = graphs["grid2d_40"]
+    longs = [rhs2(inputs, g_big.n, 8, 400 + q) for q in range(3)]
+    Bs = rhs2(inputs, g_s.n, 2, 500)
+    runs = {}
+    for pol in (lgmod.SERVE_ARRIVAL, lgmod.SERVE_LEAST_WORK):
+        sv = lgmod.Server(slots=1, precision=p, policy=pol)
+        for _, H in graphs.values():
+            sv.register(H)
+        blocker = sv.submit(H_big, rhs2(inputs, g_big.n, 8, 99), TOL)
+        tl = [sv.submit(H_big, B, TOL) for B in longs]
+        ts = sv.submit(H_s, Bs, TOL)
+        outs = [sv.wait(t) for t in tl]
+        short = sv.wait(ts)
+        sv.wait(blocker)
+        sv.close()
+        assert all(i.status == lgmod.OK for _, i in outs) and short[1].status == lgmod.OK
+        runs[pol] = (outs, short)
+    arr_long, arr_short = runs[lgmod.SERVE_ARRIVAL]
+    lw_long, lw_short = runs[lgmod.SERVE_LEAST_WORK]
+    assert arr_short[1].solve_ms > max(i.solve_ms for _, i in arr_long)
+    assert lw_short[1].solve_ms < min(i.solve_ms for _, i in lw_long)
+    for (Xa, _), (Xl, _) in zip(arr_long, lw_long):
+        assert np.array_equal(Xa, Xl)
+    assert np.array_equal(arr_short[0], lw_short[0])
+    for c in range(Bs.shape[1]):
+        ref = oracle_x("grid2d_40", Bs[:, c])
+        assert np.linalg.norm(lw_short[0][:, c] - ref) <= 1e-6 * np.linalg.norm(ref)
+
+
 def test_serve_short_request_overtakes_long(lgmod, inputs):
     """A short request submitted right after a long one finishes first: it is
     admitted into a free slot while the long one is still on the device."""
