@@ -272,8 +272,17 @@ def multi_rhs_leg(lg, inputs, torch, dev, k):
             inf = lg.lg_solve(h, Bd[c], Xd[c], TOL)
             seq_ms += inf.solve_ms
             seq_it.append(inf.iterations)
-        levels = [lg.lg_level_info(h, l) for l in range(lg.lg_hier_info(h).levels)]
+        nlev = lg.lg_hier_info(h).levels
+        levels = [lg.lg_level_info(h, l) for l in range(nlev)]
+        sched = [lg.lg_batch_plan(h, l) for l in range(nlev)]
         lg.lg_destroy(h)
+        # the same batched solve on the fixed schedule (no timing-based choices: stretches of 256 entries, E = 4)
+        hf = lg.lg_setup(g.n, g.rowptr, g.col, g.w, lg.options(autotune=0))
+        lg.lg_set_precision(hf, lg.FP32_HIER)
+        lg.lg_solve_batch(hf, k, Bd, g.n, Xd, g.n, TOL)
+        torch.cuda.synchronize()
+        fixed_ms = lg.lg_solve_batch(hf, k, Bd, g.n, Xd, g.n, TOL)[0].solve_ms
+        lg.lg_destroy(hf)
         out[name] = {
             "n": g.n, "nnz": g.nnz, "k": k,
             "levels": [{q: lv[q] for q in ("kind", "n", "nnz", "nc")} for lv in levels],
@@ -283,6 +292,8 @@ def multi_rhs_leg(lg, inputs, torch, dev, k):
             "sequential_ms": seq_ms, "sequential_nnz_per_s": g.nnz * k / (seq_ms * 1e-3),
             "sequential_iterations_max": max(seq_it),
             "speedup": seq_ms / batch_ms,
+            "schedule": [dict(s, level=l) for l, s in enumerate(sched) if s["op_ch"] or s["w_ch"]],
+            "fixed_schedule_ms": fixed_ms, "tuned_vs_fixed": fixed_ms / batch_ms,
         }
     return out
 

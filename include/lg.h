@@ -344,6 +344,13 @@ int lg_profile(lg_handle h, int32_t enable);
  * weights are one constant kept in place of its weight arrays (option
  * const_weights), else 0. */
 int lg_level_plan(lg_handle h, int32_t l, int64_t out[8]);
+/* Multi-column schedule of level l (the SpMM passes of lg_solve_batch and the
+ * server), as the autotuner chose it: out[0] = entries per stretch of a long
+ * row in the operator passes (64, 256 or 1024, timed per level shape; 0 when
+ * the level has no multi-column operator pass), out[1] = their virtual rows,
+ * out[2] and out[3] the same for the W = L P pass. LG_ERR_INVALID until the
+ * first multi-column solve (or server registration) has built the plans. */
+int lg_batch_plan(lg_handle h, int32_t l, int64_t out[4]);
 int lg_profile_read(lg_handle h, int32_t level, lg_kernel_profile* out);
 
 /* One multi-column V-cycle on k right-hand sides at once (1 <= k <= 32): X =

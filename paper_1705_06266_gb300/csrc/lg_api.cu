@@ -578,6 +578,17 @@ int lg_level_lp_nnz(lg_handle hh, int32_t l, int64_t* nnz) {
   return LG_OK;
 }
 
+int lg_batch_plan(lg_handle hh, int32_t l, int64_t out[4]) {
+  if (!hh || !out) return LG_ERR_INVALID;
+  const lg::Hier& h = *H(hh);
+  if (l < 0 || l >= (int32_t)h.levels.size()) return LG_ERR_INVALID;
+  if (!lg::batch_plan_info(h, l, out)) {
+    lg::g_last_error = "lg_batch_plan: no multi-column plans yet (they are built by the first multi-column solve)";
+    return LG_ERR_INVALID;
+  }
+  return LG_OK;
+}
+
 int lg_level_plan(lg_handle hh, int32_t l, int64_t out[8]) {
   if (!hh || !out) return LG_ERR_INVALID;
   lg::Hier& h = *H(hh);

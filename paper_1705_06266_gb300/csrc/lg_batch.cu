@@ -1516,4 +1516,19 @@ void vcycle_apply_batch(Hier& h, Workspace& ws, int k, const double* F, double* 
   else mcycle_apply<double>(h, ws, k, F, X, s);
 }
 
+// The multi-column schedule of level l, once built: the stretch length and
+// the virtual rows of its operator plan and of its W plan (0 where none).
+bool batch_plan_info(const Hier& h, int level, int64_t out[4]) {
+  std::lock_guard<std::mutex> lk(g_plans_mu);
+  const auto* hp = static_cast<const HierPlans*>(h.mplans.get());
+  if (!hp || level < 0 || level >= (int)hp->op.size()) return false;
+  const MPlanStore* op = hp->op[level].get();
+  const MPlanStore* lp = hp->lp[level].get();
+  out[0] = op && op->plan.nv ? op->plan.ch : 0;
+  out[1] = op ? op->plan.nv : 0;
+  out[2] = lp && lp->plan.nv ? lp->plan.ch : 0;
+  out[3] = lp ? lp->plan.nv : 0;
+  return true;
+}
+
 }  // namespace lg

@@ -281,6 +281,9 @@ int pcg_solve_batch(Hier& h, Workspace& ws, int k, const double* B, double* X, d
 // Build (and tune, timing passes at width kp) the multi-column plans of h now
 // rather than at its first multi-column solve.
 void prepare_columns(Hier& h, int kp, int precision);
+// Level l's multi-column schedule (stretch length and virtual rows of its
+// operator and W plans); false until the plans are built.
+bool batch_plan_info(const Hier& h, int level, int64_t out[4]);
 // Capture ws's multi-column solve loops (every width up to ws.k) on stream s
 // now rather than at their first solves.
 void prepare_column_graphs(Hier& h, Workspace& ws, int precision, cudaStream_t s);

@@ -285,15 +285,17 @@ __global__ void k_rowptr_from_keys(const uint64_t* __restrict__ segkey, int64_t 
 //    ranked by comparing it with the others (ties by position);
 //  - rows of at most kWrBlockMax entries: one block per row, a bitonic
 //    network in shared memory over (column, position) pairs, which are
-//    distinct, so the result is the stable order;
+//    distinct, so the result is the stable order (the values wait in shared
+//    memory up to 8192 entries, in registers beyond);
 //  - longer rows: gathered, a batch of rows at a time, into one array (row
 //    replaced by its index in the batch), radix sorted together and written
 //    back; batches of about kWrBatch entries bound the scratch memory.
 // Rows are independent, so which block takes which row does not matter.
 // ---------------------------------------------------------------------------
-constexpr int kWrBlockMax = 8192;
+constexpr int kWrBlockMax = 16384;
+constexpr int kWrSmemVals = 8192;  // longest row whose values the block keeps in shared memory
 constexpr int64_t kWrBatch = int64_t(1) << 28;
-constexpr int kWrClasses = 15;  // 0: <= 1 entry; 1..5: lane groups; 6..13: blocks of 2^c; 14: long
+constexpr int kWrClasses = 16;  // 0: <= 1 entry; 1..5: lane groups; 6..14: blocks of 2^c; 15: long
 
 __device__ __forceinline__ int wr_class(int64_t len) {
   if (len <= 1) return 0;
@@ -364,16 +366,19 @@ __global__ void k_wr_rank(const int32_t* __restrict__ rows, int64_t nr, const in
 }
 
 // Rows of at most P entries (P a power of two, 64..kWrBlockMax), one block
-// each; the row's values are held in shared memory beside the pairs.
+// each; the row's values are held in shared memory beside the pairs (up to
+// kWrSmemVals entries), or gathered into registers after the sort, every read
+// of the row done before the first write.
 template <int P>
 __global__ void __launch_bounds__(P / 2 < 1024 ? P / 2 : 1024)
 k_wr_block(const int32_t* __restrict__ rows, const int64_t* __restrict__ rp, uint64_t* keys, uint64_t* vals,
            uint64_t cmask) {
   constexpr int T = P / 2 < 1024 ? P / 2 : 1024;
   constexpr int PB = P <= 64 ? 6 : P <= 128 ? 7 : P <= 256 ? 8 : P <= 512 ? 9 : P <= 1024 ? 10 : P <= 2048 ? 11
-                   : P <= 4096 ? 12 : 13;
+                   : P <= 4096 ? 12 : P <= 8192 ? 13 : 14;
   static_assert((1 << PB) == P, "P must be a power of two");
-  extern __shared__ uint64_t wr_sk[];  // P pairs, then P values
+  constexpr bool kSmemVals = P <= kWrSmemVals;
+  extern __shared__ uint64_t wr_sk[];  // P pairs, then (kSmemVals) P values
   uint64_t* sv = wr_sk + P;
   const int32_t r = rows[blockIdx.x];
   const int64_t b = rp[r];
@@ -382,7 +387,7 @@ k_wr_block(const int32_t* __restrict__ rows, const int64_t* __restrict__ rp, uin
   for (int i = threadIdx.x; i < P; i += T) {
     if (i < len) {
       wr_sk[i] = ((keys[b + i] & cmask) << PB) | (uint64_t)i;
-      sv[i] = vals[b + i];
+      if constexpr (kSmemVals) sv[i] = vals[b + i];
     } else {
       wr_sk[i] = ~0ull;
     }
@@ -401,10 +406,29 @@ k_wr_block(const int32_t* __restrict__ rows, const int64_t* __restrict__ rp, uin
       __syncthreads();
     }
   }
-  for (int i = threadIdx.x; i < len; i += T) {
-    const uint64_t c = wr_sk[i];
-    keys[b + i] = rowbits | (c >> PB);
-    vals[b + i] = sv[c & (uint64_t)(P - 1)];
+  if constexpr (kSmemVals) {
+    for (int i = threadIdx.x; i < len; i += T) {
+      const uint64_t c = wr_sk[i];
+      keys[b + i] = rowbits | (c >> PB);
+      vals[b + i] = sv[c & (uint64_t)(P - 1)];
+    }
+  } else {
+    constexpr int kPer = P / T;
+    uint64_t v[kPer];
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int i = threadIdx.x + q * T;
+      if (i < len) v[q] = vals[b + (int64_t)(wr_sk[i] & (uint64_t)(P - 1))];
+    }
+    __syncthreads();  // every value of the row is read before the row is overwritten
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int i = threadIdx.x + q * T;
+      if (i < len) {
+        keys[b + i] = rowbits | (wr_sk[i] >> PB);
+        vals[b + i] = v[q];
+      }
+    }
   }
 }
 
@@ -446,7 +470,7 @@ template <int P>
 static void wr_block_launch(const int32_t* rows, int64_t nr, const int64_t* rp, uint64_t* keys, uint64_t* vals,
                             uint64_t cmask, cudaStream_t s) {
   constexpr int T = P / 2 < 1024 ? P / 2 : 1024;
-  const size_t smem = 2 * sizeof(uint64_t) * P;
+  const size_t smem = (P <= kWrSmemVals ? 2 : 1) * sizeof(uint64_t) * P;
   if (smem > 48 * 1024)
     LG_CUDA(cudaFuncSetAttribute(k_wr_block<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   for (int64_t q0 = 0; q0 < nr; q0 += 1 << 30) {
@@ -526,6 +550,7 @@ void sort_within_rows(DBuf<uint64_t>& keys, DBuf<uint64_t>& vals, int64_t nent, 
       case 11: wr_block_launch<2048>(rl, nr, rp, k, v, cmask, s); break;
       case 12: wr_block_launch<4096>(rl, nr, rp, k, v, cmask, s); break;
       case 13: wr_block_launch<8192>(rl, nr, rp, k, v, cmask, s); break;
+      case 14: wr_block_launch<16384>(rl, nr, rp, k, v, cmask, s); break;
       default: wr_long(rl, nr, rp, k, v, cbits, s); break;
     }
     LG_LAUNCH_CHECK();

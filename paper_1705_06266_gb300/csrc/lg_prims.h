@@ -22,7 +22,7 @@ void radix_sort_pairs(uint64_t* keys, uint64_t* vals, int64_t n, int bits, cudaS
 // entries emitted grouped by row (the row bits of the key equal within a
 // group and ascending from group to group), which then end up sorted as a
 // global stable sort would leave them. keys/vals are sorted in place; the
-// scratch is bounded (rows of more than 8192 entries are sorted a batch of
+// scratch is bounded (rows of more than 16384 entries are sorted a batch of
 // about 2^28 entries at a time).
 void sort_within_rows(DBuf<uint64_t>& keys, DBuf<uint64_t>& vals, int64_t nent, const int64_t* rp, int64_t ngroups,
                       int cbits, cudaStream_t s);

@@ -102,6 +102,7 @@ _SIGS = {
     "lg_profile": (C.c_int, [_P, _I32]),
     "lg_profile_read": (C.c_int, [_P, _I32, _P]),
     "lg_level_plan": (C.c_int, [_P, _I32, _P]),
+    "lg_batch_plan": (C.c_int, [_P, _I32, _P]),
     "lg_solve_many": (C.c_int, [_I32, _P, _P, _P, _D, _P]),
     "lg_level_lp_nnz": (C.c_int, [_P, _I32, _P]),
     "lg_save": (C.c_int, [_P, C.c_char_p]),
@@ -300,6 +301,12 @@ def lg_profile_read(h, level: int = -1) -> KernelProfile:
     p = KernelProfile()
     _check(_load().lg_profile_read(h, int(level), C.byref(p)), "lg_profile_read")
     return p
+
+
+def lg_batch_plan(h, l: int) -> dict:
+    out = (C.c_int64 * 4)()
+    _check(_load().lg_batch_plan(h, int(l), out), "lg_batch_plan")
+    return {"op_ch": out[0], "op_vrows": out[1], "w_ch": out[2], "w_vrows": out[3]}
 
 
 def lg_level_plan(h, l: int) -> dict:

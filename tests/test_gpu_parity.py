@@ -413,6 +413,27 @@ def test_solve_batch_matches_single(lgmod, oracle, inputs, name, k, prec):
     H.close()
 
 
+def test_batch_plan_reports_schedule(lgmod, inputs):
+    """lg_batch_plan: refused before the first multi-column solve builds the
+    plans; afterwards the operator plan of every aggregation level (and of
+    the finest) has a stretch length from the tuner's set and virtual rows at
+    least its rows, and a level with W = L P has a W plan too."""
+    g = inputs.chung_lu(20000, m_target=100000, seed=3)
+    H = lgmod.Hierarchy(g, precision=lgmod.FP32_HIER)
+    with pytest.raises(lgmod.LGError):
+        lgmod.lg_batch_plan(H.h, 0)
+    H.solve_batch(inputs.rhs(g.n, 4, seed=2))
+    for l in range(H.nlevels):
+        info, plan = H.level_info(l), lgmod.lg_batch_plan(H.h, l)
+        if info["kind"] == lgmod.LEVEL_AGG or l == 0:
+            assert plan["op_ch"] in (64, 256, 1024) and plan["op_vrows"] >= info["n"]
+        else:
+            assert plan["op_ch"] == 0 and plan["op_vrows"] == 0
+        assert plan["w_ch"] in (0, 64, 256, 1024)
+    assert any(lgmod.lg_batch_plan(H.h, l)["w_vrows"] > 0 for l in range(H.nlevels))
+    H.close()
+
+
 def test_batch_columns_independent(lgmod, inputs):
     g = inputs.grid2d(48, 48)
     B = inputs.rhs(g.n, 4, seed=12)

@@ -4,9 +4,10 @@ row's entries on its own instead of radix sorting all of them by (row,
 column). Both orders are the same stable order, so the hierarchy must be the
 same bit for bit: every level's CSR, map and the solves (which also read W).
 The graphs reach every path of the within-row sort: rows of one entry, lane
-groups, block sorts of 64..16384 entries and the radix-sorted long rows (the
-star's centre when renumbered; the two hubs of K_2,m, whose Schur rows hold
-m fill entries of one key each, summed in a fixed order)."""
+groups, block sorts of 64..16384 entries (values in shared memory up to
+8192, in registers above) and the radix-sorted long rows (the star's centre
+when renumbered; the two hubs of K_2,m, whose Schur rows hold m fill entries
+of one key each, summed in a fixed order)."""
 
 import numpy as np
 import pytest
@@ -29,7 +30,9 @@ GRAPHS = {
     "rmat_13_random_order": (lambda I: I.rmat(13, seed=2), {"reorder": 2}),
     "grid3d_12_kept_order": (lambda I: I.grid3d(12, 12, 12), {"reorder": 0}),
     "star_20000": (lambda I: I.star(20000, weights="uniform", seed=3), {}),
+    "star_12000": (lambda I: I.star(12000, weights="uniform", seed=3), {}),
     "k2_20000": (lambda I: k2m(I, 20000), {}),
+    "k2_12000": (lambda I: k2m(I, 12000), {}),
     "complete_3000w": (lambda I: I.complete(3000, weights="uniform", seed=5), {}),
 }
 
