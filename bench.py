@@ -778,6 +778,7 @@ def main():
         prof32 = per_level(h, nlev)
         lg.lg_profile(h, False)
         lg.lg_solve(h, bd, x32, TOL)
+        x32_full = x32.clone()  # compared with the FP32-only hierarchy's solve below
         lg.lg_set_precision(h, lg.FP64)
         lg.lg_solve(h, bd, x64, TOL)
         xref = torch.zeros_like(x64)
@@ -821,6 +822,19 @@ def main():
                 ms.append(lg.lg_solve(h0, bd, x, TOL).solve_ms)
             direct[tag] = sorted(ms)[1]
         lg.lg_destroy(h0)
+        # the FP32-only hierarchy (option fp32_only): its footprint and its FP32-hierarchy solve, which must give the
+        # bits of the full hierarchy's
+        hl = lg.lg_setup(n, rp, cl, w, lg.options(stream=stream.cuda_stream, precision=lg.FP32_HIER, fp32_only=1))
+        xl = torch.zeros_like(x32)
+        flush.fill_(2.0)
+        lg.lg_solve(hl, bd, xl, TOL)
+        flush.fill_(2.0)
+        inf_l = lg.lg_solve(hl, bd, xl, TOL)
+        lean = {"hierarchy_bytes": lg.lg_hier_bytes(hl)[0], "workspace_bytes": lg.lg_hier_bytes(hl)[1],
+                "fp32_solve_ms": inf_l.solve_ms, "iterations": inf_l.iterations,
+                "same_bits_as_full": bool(torch.equal(xl, x32_full))}
+        lg.lg_destroy(hl)
+        del xl, x32_full
         stream.synchronize()
     del rp, cl, w, bd, x64, x32
     torch.cuda.synchronize()
@@ -924,7 +938,7 @@ def main():
                                f"relres {ref_info.relres:.1e}); relative 2-norm error of the mean-removed x"},
         "tda_ms_per_digit": solve64_ms / -math.log10(max(i64.relres, 1e-300)),
         "wda": i64.work_units / -math.log10(max(i64.relres, 1e-300)),
-        "hierarchy_bytes": recs[-1][4][0], "workspace_bytes": recs[-1][4][1],
+        "hierarchy_bytes": recs[-1][4][0], "workspace_bytes": recs[-1][4][1], "fp32_only": lean,
         "e2e": {"value": world * nnz / e2e64_s, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
                 "d2h_bytes_per_step": 8 * n, "fp32_hier_value": world * nnz / e2e32_s,
                 "setup_from_host_ms": None if setup_e2e is None else setup_e2e * 1e3,

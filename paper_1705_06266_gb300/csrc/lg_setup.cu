@@ -1093,6 +1093,15 @@ __global__ void k_random_keys(int64_t n, uint64_t seed, uint64_t* __restrict__ k
   }
 }
 
+// Columns and weights of sorted (row << cbits | column, weight bits) entries.
+__global__ void k_unpack_entries(int64_t nent, const uint64_t* __restrict__ keys, const uint64_t* __restrict__ vals,
+                                 uint64_t cmask, int32_t* __restrict__ col, double* __restrict__ w) {
+  LG_GRID_STRIDE(k, nent) {
+    col[k] = (int32_t)(keys[k] & cmask);
+    w[k] = __longlong_as_double((long long)vals[k]);
+  }
+}
+
 // Degrees in the new numbering.
 __global__ void k_perm_degrees(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ inv,
                                int64_t* __restrict__ deg_new) {
@@ -1781,18 +1790,33 @@ void setup_hierarchy(Hier& h, int64_t n, const int64_t* rowptr, const int32_t* c
     DBuf<uint64_t> keys(nnz, s), vals(nnz, s);
     DBuf<int64_t> rp_new;
     if (o.row_sorts) {
-      rp_new.alloc(n + 1, s);
+      rp_new.alloc(n + 1, s, counter);
       k_perm_degrees<<<blocks_for(n), kNT, 0, s>>>(n, cur->rowptr.get(), inv.get(), rp_new.get());
       LG_LAUNCH_CHECK();
       exclusive_scan(rp_new.get(), rp_new.get(), n, s);
     }
     each_row(FPermEmit{cur->col.get(), cur->w.get(), inv.get(), rp_new.get(), cbits, keys.get(), vals.get()},
              cur->rowptr.get(), in_bins.bins, s);
-    CsrOut out;
-    accumulate_csr(keys, vals, nnz, n, cbits, out, s, counter, rp_new.get(), n);
-    cur->rowptr = std::move(out.rowptr);
-    cur->col = std::move(out.col);
-    cur->w = std::move(out.w);
+    if (o.row_sorts) {
+      // the validated input repeats no entry, so the rows sorted in place are
+      // the renumbered CSR as they stand (no sums: the accumulation would
+      // reproduce them value for value)
+      sort_within_rows(keys, vals, nnz, rp_new.get(), n, cbits, s);
+      DBuf<int32_t> ncol(nnz, s, counter);
+      DBuf<double> nw(nnz, s, counter);
+      k_unpack_entries<<<blocks_for(nnz), kNT, 0, s>>>(nnz, keys.get(), vals.get(), (1ull << cbits) - 1ull,
+                                                      ncol.get(), nw.get());
+      LG_LAUNCH_CHECK();
+      cur->rowptr = std::move(rp_new);
+      cur->col = std::move(ncol);
+      cur->w = std::move(nw);
+    } else {
+      CsrOut out;
+      accumulate_csr(keys, vals, nnz, n, cbits, out, s, counter);
+      cur->rowptr = std::move(out.rowptr);
+      cur->col = std::move(out.col);
+      cur->w = std::move(out.w);
+    }
   } else {
     k_iota_i32<<<blocks_for(n), kNT, 0, s>>>(n, h.perm.get());
     LG_LAUNCH_CHECK();
