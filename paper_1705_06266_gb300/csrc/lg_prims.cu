@@ -283,17 +283,17 @@ __global__ void k_rowptr_from_keys(const uint64_t* __restrict__ segkey, int64_t 
 // length:
 //  - rows of at most 32 entries: a group of 2^c lanes per row, each entry
 //    ranked by comparing it with the others (ties by position);
-//  - rows of at most kWrBlockMax entries: one block per row, a bitonic
-//    network in shared memory over (column, position) pairs, which are
-//    distinct, so the result is the stable order (the values wait in shared
-//    memory up to 8192 entries, in registers beyond);
+//  - rows of at most 512 entries: one block per row, a bitonic network in
+//    shared memory over (column, position) pairs, which are distinct, so the
+//    result is the stable order;
+//  - rows of at most kWrBlockMax entries: one block per row, a stable LSD
+//    radix sort of the row in shared memory (k_wr_radix);
 //  - longer rows: gathered, a batch of rows at a time, into one array (row
 //    replaced by its index in the batch), radix sorted together and written
 //    back; batches of about kWrBatch entries bound the scratch memory.
 // Rows are independent, so which block takes which row does not matter.
 // ---------------------------------------------------------------------------
 constexpr int kWrBlockMax = 16384;
-constexpr int kWrSmemVals = 8192;  // longest row whose values the block keeps in shared memory
 constexpr int64_t kWrBatch = int64_t(1) << 28;
 constexpr int kWrClasses = 16;  // 0: <= 1 entry; 1..5: lane groups; 6..14: blocks of 2^c; 15: long
 
@@ -365,20 +365,16 @@ __global__ void k_wr_rank(const int32_t* __restrict__ rows, int64_t nr, const in
   }
 }
 
-// Rows of at most P entries (P a power of two, 64..kWrBlockMax), one block
-// each; the row's values are held in shared memory beside the pairs (up to
-// kWrSmemVals entries), or gathered into registers after the sort, every read
-// of the row done before the first write.
+// Rows of at most P entries (P a power of two, 64..512), one block each; the
+// row's values are held in shared memory beside the pairs.
 template <int P>
-__global__ void __launch_bounds__(P / 2 < 1024 ? P / 2 : 1024)
+__global__ void __launch_bounds__(P / 2)
 k_wr_block(const int32_t* __restrict__ rows, const int64_t* __restrict__ rp, uint64_t* keys, uint64_t* vals,
            uint64_t cmask) {
-  constexpr int T = P / 2 < 1024 ? P / 2 : 1024;
-  constexpr int PB = P <= 64 ? 6 : P <= 128 ? 7 : P <= 256 ? 8 : P <= 512 ? 9 : P <= 1024 ? 10 : P <= 2048 ? 11
-                   : P <= 4096 ? 12 : P <= 8192 ? 13 : 14;
-  static_assert((1 << PB) == P, "P must be a power of two");
-  constexpr bool kSmemVals = P <= kWrSmemVals;
-  extern __shared__ uint64_t wr_sk[];  // P pairs, then (kSmemVals) P values
+  constexpr int T = P / 2;
+  constexpr int PB = P <= 64 ? 6 : P <= 128 ? 7 : P <= 256 ? 8 : 9;
+  static_assert((1 << PB) == P, "P must be a power of two, 64..512");
+  extern __shared__ uint64_t wr_sk[];  // P pairs, then P values
   uint64_t* sv = wr_sk + P;
   const int32_t r = rows[blockIdx.x];
   const int64_t b = rp[r];
@@ -387,7 +383,7 @@ k_wr_block(const int32_t* __restrict__ rows, const int64_t* __restrict__ rp, uin
   for (int i = threadIdx.x; i < P; i += T) {
     if (i < len) {
       wr_sk[i] = ((keys[b + i] & cmask) << PB) | (uint64_t)i;
-      if constexpr (kSmemVals) sv[i] = vals[b + i];
+      sv[i] = vals[b + i];
     } else {
       wr_sk[i] = ~0ull;
     }
@@ -406,29 +402,10 @@ k_wr_block(const int32_t* __restrict__ rows, const int64_t* __restrict__ rp, uin
       __syncthreads();
     }
   }
-  if constexpr (kSmemVals) {
-    for (int i = threadIdx.x; i < len; i += T) {
-      const uint64_t c = wr_sk[i];
-      keys[b + i] = rowbits | (c >> PB);
-      vals[b + i] = sv[c & (uint64_t)(P - 1)];
-    }
-  } else {
-    constexpr int kPer = P / T;
-    uint64_t v[kPer];
-#pragma unroll
-    for (int q = 0; q < kPer; ++q) {
-      const int i = threadIdx.x + q * T;
-      if (i < len) v[q] = vals[b + (int64_t)(wr_sk[i] & (uint64_t)(P - 1))];
-    }
-    __syncthreads();  // every value of the row is read before the row is overwritten
-#pragma unroll
-    for (int q = 0; q < kPer; ++q) {
-      const int i = threadIdx.x + q * T;
-      if (i < len) {
-        keys[b + i] = rowbits | (wr_sk[i] >> PB);
-        vals[b + i] = v[q];
-      }
-    }
+  for (int i = threadIdx.x; i < len; i += T) {
+    const uint64_t c = wr_sk[i];
+    keys[b + i] = rowbits | (c >> PB);
+    vals[b + i] = sv[c & (uint64_t)(P - 1)];
   }
 }
 
@@ -466,13 +443,137 @@ __global__ void k_wr_long_len(const int32_t* __restrict__ lrows, int64_t nl, con
     len[q] = rp[lrows[q] + 1] - rp[lrows[q]];
 }
 
+// Rows of at most P entries (P a power of two, 1024..kWrBlockMax), one block
+// each: a stable LSD radix sort in shared memory over the column bits, 8 a
+// pass. The row's columns stay in place (32-bit); each pass moves 16-bit
+// positions. A warp takes a contiguous stretch of the current order, 32
+// positions a round, and ranks the entries of a digit by (warp, round, lane),
+// so equal digits keep their order and the result is the stable order. The
+// values are gathered into registers at the end, every read of the row
+// before the first write.
+template <int P>
+__global__ void __launch_bounds__(P / 4 < 1024 ? P / 4 : 1024)
+k_wr_radix(const int32_t* __restrict__ rows, const int64_t* __restrict__ rp, uint64_t* keys, uint64_t* vals,
+           int cbits) {
+  constexpr int T = P / 4 < 1024 ? P / 4 : 1024;
+  constexpr int W = T / 32;       // warps
+  constexpr int EPT = P / T;      // positions per lane
+  static_assert(P <= 65536, "positions are 16-bit");
+  extern __shared__ __align__(16) unsigned char wr_raw[];
+  uint32_t* scol = reinterpret_cast<uint32_t*>(wr_raw);            // P columns
+  uint16_t* ia = reinterpret_cast<uint16_t*>(scol + P);            // P positions
+  uint16_t* ib = ia + P;                                            // P positions
+  uint16_t* cnt = ib + P;                                           // W x 256 counts, then starts
+  __shared__ uint32_t wsum[8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  const int32_t r = rows[blockIdx.x];
+  const int64_t b = rp[r];
+  const int len = (int)(rp[r + 1] - b);
+  const uint64_t cmask = (1ull << cbits) - 1ull;
+  const uint64_t rowbits = keys[b] & ~cmask;
+  for (int i = threadIdx.x; i < len; i += T) {
+    scol[i] = (uint32_t)(keys[b + i] & cmask);
+    ia[i] = (uint16_t)i;
+  }
+  uint16_t *in = ia, *out = ib;
+  for (int shift = 0; shift < cbits; shift += 8) {
+    for (int i = threadIdx.x; i < W * 256; i += T) cnt[i] = 0;
+    __syncthreads();
+    const int base = warp * EPT * 32;
+    // counts per (warp, digit)
+    for (int q = 0; q < EPT; ++q) {
+      const int pos = base + q * 32 + lane;
+      const bool valid = pos < len;
+      const unsigned act = __ballot_sync(0xffffffffu, valid);
+      if (valid) {
+        const unsigned d = (scol[in[pos]] >> shift) & 255u;
+        const unsigned peers = __match_any_sync(act, d);
+        if ((peers & lt) == 0) cnt[warp * 256 + d] += (uint16_t)__popc(peers);
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+    // starts: digit-major, then warp
+    if (threadIdx.x < 256) {
+      const int d = threadIdx.x;
+      uint32_t tot = 0;
+      for (int w = 0; w < W; ++w) tot += cnt[w * 256 + d];
+      uint32_t x = tot;  // inclusive scan over the 256 digits
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      if (lane == 31) wsum[warp] = x;
+      __syncwarp();
+      asm volatile("bar.sync 1, 256;");
+      uint32_t before = x - tot;
+      for (int w = 0; w < warp; ++w) before += wsum[w];
+      for (int w = 0; w < W; ++w) {
+        const uint16_t c = cnt[w * 256 + d];
+        cnt[w * 256 + d] = (uint16_t)before;
+        before += c;
+      }
+    }
+    __syncthreads();
+    // scatter
+    for (int q = 0; q < EPT; ++q) {
+      const int pos = base + q * 32 + lane;
+      const bool valid = pos < len;
+      const unsigned act = __ballot_sync(0xffffffffu, valid);
+      unsigned d = 0, peers = 0;
+      uint16_t e = 0;
+      if (valid) {
+        e = in[pos];
+        d = (scol[e] >> shift) & 255u;
+        peers = __match_any_sync(act, d);
+        out[cnt[warp * 256 + d] + __popc(peers & lt)] = e;
+      }
+      __syncwarp();
+      if (valid && (peers & lt) == 0) cnt[warp * 256 + d] += (uint16_t)__popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();
+    uint16_t* t = in;
+    in = out;
+    out = t;
+  }
+  uint64_t v[EPT];
+#pragma unroll
+  for (int q = 0; q < EPT; ++q) {
+    const int i = threadIdx.x + q * T;
+    if (i < len) v[q] = vals[b + in[i]];
+  }
+  __syncthreads();  // every value of the row is read before the row is overwritten
+#pragma unroll
+  for (int q = 0; q < EPT; ++q) {
+    const int i = threadIdx.x + q * T;
+    if (i < len) {
+      keys[b + i] = rowbits | scol[in[i]];
+      vals[b + i] = v[q];
+    }
+  }
+}
+
+template <int P>
+static void wr_radix_launch(const int32_t* rows, int64_t nr, const int64_t* rp, uint64_t* keys, uint64_t* vals,
+                            int cbits, cudaStream_t s) {
+  constexpr int T = P / 4 < 1024 ? P / 4 : 1024;
+  const size_t smem = (size_t)P * (4 + 2 + 2) + (size_t)(T / 32) * 256 * 2;
+  // the kernel's own static shared memory counts against the same 48 KB default
+  LG_CUDA(cudaFuncSetAttribute(k_wr_radix<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  for (int64_t q0 = 0; q0 < nr; q0 += 1 << 30) {
+    const int64_t m = nr - q0 < (1 << 30) ? nr - q0 : (1 << 30);
+    k_wr_radix<P><<<(unsigned)m, T, smem, s>>>(rows + q0, rp, keys, vals, cbits);
+    LG_LAUNCH_CHECK();
+  }
+}
+
 template <int P>
 static void wr_block_launch(const int32_t* rows, int64_t nr, const int64_t* rp, uint64_t* keys, uint64_t* vals,
                             uint64_t cmask, cudaStream_t s) {
-  constexpr int T = P / 2 < 1024 ? P / 2 : 1024;
-  const size_t smem = (P <= kWrSmemVals ? 2 : 1) * sizeof(uint64_t) * P;
-  if (smem > 48 * 1024)
-    LG_CUDA(cudaFuncSetAttribute(k_wr_block<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  constexpr int T = P / 2;
+  const size_t smem = 2 * sizeof(uint64_t) * P;
   for (int64_t q0 = 0; q0 < nr; q0 += 1 << 30) {
     const int64_t m = nr - q0 < (1 << 30) ? nr - q0 : (1 << 30);
     k_wr_block<P><<<(unsigned)m, T, smem, s>>>(rows + q0, rp, keys, vals, cmask);
@@ -546,11 +647,11 @@ void sort_within_rows(DBuf<uint64_t>& keys, DBuf<uint64_t>& vals, int64_t nent, 
       case 7: wr_block_launch<128>(rl, nr, rp, k, v, cmask, s); break;
       case 8: wr_block_launch<256>(rl, nr, rp, k, v, cmask, s); break;
       case 9: wr_block_launch<512>(rl, nr, rp, k, v, cmask, s); break;
-      case 10: wr_block_launch<1024>(rl, nr, rp, k, v, cmask, s); break;
-      case 11: wr_block_launch<2048>(rl, nr, rp, k, v, cmask, s); break;
-      case 12: wr_block_launch<4096>(rl, nr, rp, k, v, cmask, s); break;
-      case 13: wr_block_launch<8192>(rl, nr, rp, k, v, cmask, s); break;
-      case 14: wr_block_launch<16384>(rl, nr, rp, k, v, cmask, s); break;
+      case 10: wr_radix_launch<1024>(rl, nr, rp, k, v, cbits, s); break;
+      case 11: wr_radix_launch<2048>(rl, nr, rp, k, v, cbits, s); break;
+      case 12: wr_radix_launch<4096>(rl, nr, rp, k, v, cbits, s); break;
+      case 13: wr_radix_launch<8192>(rl, nr, rp, k, v, cbits, s); break;
+      case 14: wr_radix_launch<16384>(rl, nr, rp, k, v, cbits, s); break;
       default: wr_long(rl, nr, rp, k, v, cbits, s); break;
     }
     LG_LAUNCH_CHECK();

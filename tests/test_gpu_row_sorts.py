@@ -4,10 +4,10 @@ row's entries on its own instead of radix sorting all of them by (row,
 column). Both orders are the same stable order, so the hierarchy must be the
 same bit for bit: every level's CSR, map and the solves (which also read W).
 The graphs reach every path of the within-row sort: rows of one entry, lane
-groups, block sorts of 64..16384 entries (values in shared memory up to
-8192, in registers above) and the radix-sorted long rows (the star's centre
-when renumbered; the two hubs of K_2,m, whose Schur rows hold m fill entries
-of one key each, summed in a fixed order)."""
+groups, bitonic block sorts of 64..512 entries, radix block sorts of
+1024..16384 entries in shared memory, and the radix-sorted long rows (the
+star's centre when renumbered; the two hubs of K_2,m, whose Schur rows hold
+m fill entries of one key each, summed in a fixed order)."""
 
 import numpy as np
 import pytest
@@ -33,6 +33,8 @@ GRAPHS = {
     "star_12000": (lambda I: I.star(12000, weights="uniform", seed=3), {}),
     "k2_20000": (lambda I: k2m(I, 20000), {}),
     "k2_12000": (lambda I: k2m(I, 12000), {}),
+    "k2_6000": (lambda I: k2m(I, 6000), {}),
+    "star_1500": (lambda I: I.star(1500, weights="uniform", seed=3), {}),
     "complete_3000w": (lambda I: I.complete(3000, weights="uniform", seed=5), {}),
 }
 
