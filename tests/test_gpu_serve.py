@@ -201,6 +201,43 @@ def test_serve_least_work_policy(lgmod, inputs, graphs, oracle_x, prec):
         assert np.linalg.norm(lw_short[0][:, c] - ref) <= 1e-6 * np.linalg.norm(ref)
 
 
+def test_serve_least_work_ages_passed_requests(lgmod, inputs, graphs):
+    """Under least work first a long request is passed by every short one,
+    but only 16 times: with the one slot held, a long request and then 90
+    single-column requests on the small graphs (packed, at most one per graph
+    and group) queue up; the long request leads once 16 groups have started
+    ahead of it, so it finishes before the last of the short ones, after at
+    most 16 groups of them."""
+    g_big, H_big = graphs["chunglu_30k"]
+    smalls = ["grid2d_40", "grid3d_12", "rmat_13"]
+    sv = lgmod.Server(slots=1, precision=lgmod.FP32_HIER, policy=lgmod.SERVE_LEAST_WORK)
+    for _, H in graphs.values():
+        sv.register(H)
+    blocker = sv.submit(H_big, rhs2(inputs, g_big.n, 8, 98), TOL)
+    t_long = time.perf_counter()
+    tl = sv.submit(H_big, rhs2(inputs, g_big.n, 8, 97), TOL)
+    shorts = []
+    for q in range(90):
+        name = smalls[q % 3]
+        shorts.append((time.perf_counter(), sv.submit(graphs[name][1], rhs2(inputs, graphs[name][0].n, 1, 600 + q),
+                                                       TOL)))
+    _, info_l = sv.wait(tl)
+    done_long = t_long + info_l.solve_ms * 1e-3
+    done_short = []
+    for t0, t in shorts:
+        _, inf = sv.wait(t)
+        assert inf.status == lgmod.OK
+        done_short.append(t0 + inf.solve_ms * 1e-3)
+    sv.wait(blocker)
+    st = sv.stats()
+    sv.close()
+    assert info_l.status == lgmod.OK
+    before = sum(d < done_long for d in done_short)
+    assert before < len(done_short)  # not starved: some short requests finish after it
+    assert before <= 16 * 3  # at most 16 groups of at most one request per small graph went first
+    assert st.packed_groups >= 16
+
+
 def test_serve_short_request_overtakes_long(lgmod, inputs):
     """A short request submitted right after a long one finishes first: it is
     admitted into a free slot while the long one is still on the device."""
