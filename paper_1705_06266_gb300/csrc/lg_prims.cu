@@ -288,9 +288,9 @@ __global__ void k_rowptr_from_keys(const uint64_t* __restrict__ segkey, int64_t 
 //    result is the stable order;
 //  - rows of at most kWrBlockMax entries: one block per row, a stable LSD
 //    radix sort of the row in shared memory (k_wr_radix);
-//  - longer rows: gathered, a batch of rows at a time, into one array (row
-//    replaced by its index in the batch), radix sorted together and written
-//    back; batches of about kWrBatch entries bound the scratch memory.
+//  - longer rows: one block per row, the same radix sort with the row's
+//    columns and positions in global scratch (k_wr_radix_long), a batch of
+//    rows of about kWrBatch entries at a time, which bounds the scratch.
 // Rows are independent, so which block takes which row does not matter.
 // ---------------------------------------------------------------------------
 constexpr int kWrBlockMax = 16384;
@@ -406,34 +406,6 @@ k_wr_block(const int32_t* __restrict__ rows, const int64_t* __restrict__ rp, uin
     const uint64_t c = wr_sk[i];
     keys[b + i] = rowbits | (c >> PB);
     vals[b + i] = sv[c & (uint64_t)(P - 1)];
-  }
-}
-
-// Long rows of one batch: to one array, keyed (index in the batch, column), and back.
-__global__ void k_wr_gather(const int32_t* __restrict__ lrows, const int64_t* __restrict__ rp,
-                            const int64_t* __restrict__ loff, int64_t o0, const uint64_t* __restrict__ keys,
-                            const uint64_t* __restrict__ vals, uint64_t* __restrict__ tk, uint64_t* __restrict__ tv,
-                            int cbits) {
-  const int32_t r = lrows[blockIdx.x];
-  const int64_t b = rp[r], len = rp[r + 1] - b, o = loff[blockIdx.x] - o0;
-  const uint64_t cmask = (1ull << cbits) - 1ull;
-  for (int64_t q = threadIdx.x; q < len; q += blockDim.x) {
-    tk[o + q] = ((uint64_t)blockIdx.x << cbits) | (keys[b + q] & cmask);
-    tv[o + q] = vals[b + q];
-  }
-}
-
-__global__ void k_wr_scatter(const int32_t* __restrict__ lrows, const int64_t* __restrict__ rp,
-                             const int64_t* __restrict__ loff, int64_t o0, const uint64_t* __restrict__ tk,
-                             const uint64_t* __restrict__ tv, uint64_t* keys, uint64_t* vals, int cbits) {
-  const int32_t r = lrows[blockIdx.x];
-  const int64_t b = rp[r], len = rp[r + 1] - b, o = loff[blockIdx.x] - o0;
-  const uint64_t cmask = (1ull << cbits) - 1ull;
-  const uint64_t rowbits = keys[b] & ~cmask;  // every entry of the row has the same row bits
-  __syncthreads();  // the block's reads of keys[b] come before any write to the row
-  for (int64_t q = threadIdx.x; q < len; q += blockDim.x) {
-    keys[b + q] = rowbits | (tk[o + q] & cmask);
-    vals[b + q] = tv[o + q];
   }
 }
 
@@ -581,6 +553,102 @@ static void wr_block_launch(const int32_t* rows, int64_t nr, const int64_t* rp, 
   }
 }
 
+// A long row, one block: the same stable LSD radix sort as k_wr_radix, with
+// the row's columns and positions in global scratch at o (this row's offset
+// in the batch) instead of shared memory. Warp w ranks the w-th contiguous
+// stretch of the current order, 32 positions a round, so equal digits keep
+// their order. At the end the values go through scratch (tv), every read of
+// the row before the first write.
+constexpr int kWrLongThreads = 1024;
+__global__ void __launch_bounds__(kWrLongThreads)
+k_wr_radix_long(const int32_t* __restrict__ lrows, const int64_t* __restrict__ rp, const int64_t* __restrict__ loff,
+                int64_t o0, uint64_t* keys, uint64_t* vals, uint32_t* __restrict__ scol, uint32_t* __restrict__ pa,
+                uint32_t* __restrict__ pb, uint64_t* __restrict__ tv, int cbits) {
+  constexpr int W = kWrLongThreads / 32;
+  __shared__ uint32_t cnt[W * 256];
+  __shared__ uint32_t wsum[8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  const int32_t r = lrows[blockIdx.x];
+  const int64_t b = rp[r];
+  const int64_t len = rp[r + 1] - b, o = loff[blockIdx.x] - o0;
+  const uint64_t cmask = (1ull << cbits) - 1ull;
+  const uint64_t rowbits = keys[b] & ~cmask;
+  uint32_t* col = scol + o;
+  uint32_t *in = pa + o, *out = pb + o;
+  for (int64_t i = threadIdx.x; i < len; i += kWrLongThreads) {
+    col[i] = (uint32_t)(keys[b + i] & cmask);
+    in[i] = (uint32_t)i;
+  }
+  const int64_t stretch = ((len + W - 1) / W + 31) / 32 * 32;  // positions per warp, whole rounds
+  const int64_t p0 = warp * stretch, p1 = p0 + stretch < len ? p0 + stretch : len;
+  for (int shift = 0; shift < cbits; shift += 8) {
+    for (int i = threadIdx.x; i < W * 256; i += kWrLongThreads) cnt[i] = 0;
+    __syncthreads();
+    for (int64_t q = p0; q < p0 + stretch; q += 32) {
+      const int64_t pos = q + lane;
+      const bool valid = pos < p1;
+      const unsigned act = __ballot_sync(0xffffffffu, valid);
+      if (valid) {
+        const unsigned d = (col[in[pos]] >> shift) & 255u;
+        const unsigned peers = __match_any_sync(act, d);
+        if ((peers & lt) == 0) cnt[warp * 256 + d] += (uint32_t)__popc(peers);
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+    if (threadIdx.x < 256) {
+      const int d = threadIdx.x;
+      uint32_t tot = 0;
+      for (int w = 0; w < W; ++w) tot += cnt[w * 256 + d];
+      uint32_t x = tot;
+      for (int k = 1; k < 32; k <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, k);
+        if (lane >= k) x += y;
+      }
+      if (lane == 31) wsum[warp] = x;
+      __syncwarp();
+      asm volatile("bar.sync 1, 256;");
+      uint32_t before = x - tot;
+      for (int w = 0; w < warp; ++w) before += wsum[w];
+      for (int w = 0; w < W; ++w) {
+        const uint32_t c = cnt[w * 256 + d];
+        cnt[w * 256 + d] = before;
+        before += c;
+      }
+    }
+    __syncthreads();
+    for (int64_t q = p0; q < p0 + stretch; q += 32) {
+      const int64_t pos = q + lane;
+      const bool valid = pos < p1;
+      const unsigned act = __ballot_sync(0xffffffffu, valid);
+      unsigned d = 0, peers = 0;
+      if (valid) {
+        const uint32_t e = in[pos];
+        d = (col[e] >> shift) & 255u;
+        peers = __match_any_sync(act, d);
+        out[cnt[warp * 256 + d] + __popc(peers & lt)] = e;
+      }
+      __syncwarp();
+      if (valid && (peers & lt) == 0) cnt[warp * 256 + d] += (uint32_t)__popc(peers);
+      __syncwarp();
+    }
+    // every warp is done with this pass's starts (cnt) and has written all of
+    // `out` before the next pass clears cnt and reads `out` as its input
+    __syncthreads();
+    uint32_t* t = in;
+    in = out;
+    out = t;
+  }
+  uint64_t* v = tv + o;
+  for (int64_t i = threadIdx.x; i < len; i += kWrLongThreads) v[i] = vals[b + in[i]];
+  __syncthreads();  // every value of the row is read before the row is overwritten
+  for (int64_t i = threadIdx.x; i < len; i += kWrLongThreads) {
+    keys[b + i] = rowbits | col[in[i]];
+    vals[b + i] = v[i];
+  }
+}
+
 static void wr_long(const int32_t* rl, int64_t nr, const int64_t* rp, uint64_t* keys, uint64_t* vals, int cbits,
                     cudaStream_t s) {
   DBuf<int64_t> loff(nr + 1, s);
@@ -596,17 +664,14 @@ static void wr_long(const int32_t* rl, int64_t nr, const int64_t* rp, uint64_t* 
     }
     biggest = std::max(biggest, ho[q1] - ho[q0]);
   }
-  DBuf<uint64_t> tk(biggest, s), tv(biggest, s);
+  if (biggest >= (int64_t(1) << 32)) fail(LG_ERR_INVALID, "a row of 2^32 or more entries");
+  DBuf<uint32_t> scol(biggest, s), pa(biggest, s), pb(biggest, s);
+  DBuf<uint64_t> tv(biggest, s);
   for (int64_t q0 = 0, q1; q0 < nr; q0 = q1) {
     for (q1 = q0 + 1; q1 < nr && ho[q1 + 1] - ho[q0] <= kWrBatch; ++q1) {
     }
-    const int64_t m = ho[q1] - ho[q0];
-    k_wr_gather<<<(unsigned)(q1 - q0), 256, 0, s>>>(rl + q0, rp, loff.get() + q0, ho[q0], keys, vals, tk.get(),
-                                                     tv.get(), cbits);
-    LG_LAUNCH_CHECK();
-    radix_sort_pairs(tk.get(), tv.get(), m, bits_for(q1 - q0) + cbits, s);
-    k_wr_scatter<<<(unsigned)(q1 - q0), 256, 0, s>>>(rl + q0, rp, loff.get() + q0, ho[q0], tk.get(), tv.get(),
-                                                      keys, vals, cbits);
+    k_wr_radix_long<<<(unsigned)(q1 - q0), kWrLongThreads, 0, s>>>(rl + q0, rp, loff.get() + q0, ho[q0], keys, vals,
+                                                                   scol.get(), pa.get(), pb.get(), tv.get(), cbits);
     LG_LAUNCH_CHECK();
   }
 }
