@@ -349,7 +349,8 @@ int lg_level_plan(lg_handle h, int32_t l, int64_t out[8]);
  * row in the operator passes (64, 256 or 1024, timed per level shape; 0 when
  * the level has no multi-column operator pass), out[1] = their virtual rows,
  * out[2] and out[3] the same for the W = L P pass. LG_ERR_INVALID until the
- * first multi-column solve (or server registration) has built the plans. */
+ * first multi-column solve (or server registration) has built the plans.
+ * The paper has no counterpart (its solver applies one right-hand side). */
 int lg_batch_plan(lg_handle h, int32_t l, int64_t out[4]);
 int lg_profile_read(lg_handle h, int32_t level, lg_kernel_profile* out);
 
@@ -505,7 +506,8 @@ int lg_serve_stats(lg_server_t s, lg_serve_stats_t* st);
  * solves_per_s): successive measurements on one server. */
 int lg_serve_reset_stats(lg_server_t s);
 /* Switch the policy (LG_SERVE_ARRIVAL or LG_SERVE_LEAST_WORK) of a running
- * server; it applies from the next group a slot takes. */
+ * server; it applies from the next group a slot takes. Serving has no
+ * counterpart in the paper. */
 int lg_serve_set_policy(lg_server_t s, int32_t policy);
 
 /* Wait for every queued request, then release the server's threads and streams. */
