@@ -288,18 +288,25 @@ __global__ void k_rowptr_from_keys(const uint64_t* __restrict__ segkey, int64_t 
 //    result is the stable order;
 //  - rows of at most kWrBlockMax entries: one block per row, a stable LSD
 //    radix sort of the row in shared memory (k_wr_radix);
-//  - longer rows: one block per row, the same radix sort with the row's
-//    columns and positions in global scratch (k_wr_radix_long), a batch of
-//    rows of about kWrBatch entries at a time, which bounds the scratch.
+//  - rows of at most kWrOneBlockMax entries: one block per row, the same radix
+//    sort with the row's columns and positions in global scratch
+//    (k_wr_radix_long), a batch of rows of about kWrBatch entries at a time,
+//    which bounds the scratch;
+//  - longer rows (the hubs'): one block would take too long over one of
+//    them, so they are gathered, a batch at a time, into one array keyed
+//    (index in the batch, column), radix sorted together by the whole GPU and
+//    written back.
 // Rows are independent, so which block takes which row does not matter.
 // ---------------------------------------------------------------------------
 constexpr int kWrBlockMax = 16384;
+constexpr int64_t kWrOneBlockMax = 65536;
 constexpr int64_t kWrBatch = int64_t(1) << 28;
-constexpr int kWrClasses = 16;  // 0: <= 1 entry; 1..5: lane groups; 6..14: blocks of 2^c; 15: long
+constexpr int kWrClasses = 17;  // 0: <= 1 entry; 1..5: lane groups; 6..14: blocks of 2^c; 15: long; 16: hub
 
 __device__ __forceinline__ int wr_class(int64_t len) {
   if (len <= 1) return 0;
-  if (len > kWrBlockMax) return kWrClasses - 1;
+  if (len > kWrOneBlockMax) return kWrClasses - 1;
+  if (len > kWrBlockMax) return kWrClasses - 2;
   int c = 1;
   while ((int64_t(1) << c) < len) ++c;
   return c;
@@ -406,6 +413,34 @@ k_wr_block(const int32_t* __restrict__ rows, const int64_t* __restrict__ rp, uin
     const uint64_t c = wr_sk[i];
     keys[b + i] = rowbits | (c >> PB);
     vals[b + i] = sv[c & (uint64_t)(P - 1)];
+  }
+}
+
+// Hub rows of one batch: to one array, keyed (index in the batch, column), and back.
+__global__ void k_wr_gather(const int32_t* __restrict__ lrows, const int64_t* __restrict__ rp,
+                            const int64_t* __restrict__ loff, int64_t o0, const uint64_t* __restrict__ keys,
+                            const uint64_t* __restrict__ vals, uint64_t* __restrict__ tk, uint64_t* __restrict__ tv,
+                            int cbits) {
+  const int32_t r = lrows[blockIdx.x];
+  const int64_t b = rp[r], len = rp[r + 1] - b, o = loff[blockIdx.x] - o0;
+  const uint64_t cmask = (1ull << cbits) - 1ull;
+  for (int64_t q = threadIdx.x; q < len; q += blockDim.x) {
+    tk[o + q] = ((uint64_t)blockIdx.x << cbits) | (keys[b + q] & cmask);
+    tv[o + q] = vals[b + q];
+  }
+}
+
+__global__ void k_wr_scatter(const int32_t* __restrict__ lrows, const int64_t* __restrict__ rp,
+                             const int64_t* __restrict__ loff, int64_t o0, const uint64_t* __restrict__ tk,
+                             const uint64_t* __restrict__ tv, uint64_t* keys, uint64_t* vals, int cbits) {
+  const int32_t r = lrows[blockIdx.x];
+  const int64_t b = rp[r], len = rp[r + 1] - b, o = loff[blockIdx.x] - o0;
+  const uint64_t cmask = (1ull << cbits) - 1ull;
+  const uint64_t rowbits = keys[b] & ~cmask;  // every entry of the row has the same row bits
+  __syncthreads();  // the block's reads of keys[b] come before any write to the row
+  for (int64_t q = threadIdx.x; q < len; q += blockDim.x) {
+    keys[b + q] = rowbits | (tk[o + q] & cmask);
+    vals[b + q] = tv[o + q];
   }
 }
 
@@ -650,7 +685,7 @@ k_wr_radix_long(const int32_t* __restrict__ lrows, const int64_t* __restrict__ r
 }
 
 static void wr_long(const int32_t* rl, int64_t nr, const int64_t* rp, uint64_t* keys, uint64_t* vals, int cbits,
-                    cudaStream_t s) {
+                    bool hubs, cudaStream_t s) {
   DBuf<int64_t> loff(nr + 1, s);
   k_wr_long_len<<<grid_for(nr, 256, kSMs * 8), 256, 0, s>>>(rl, nr, rp, loff.get());
   LG_LAUNCH_CHECK();
@@ -664,7 +699,21 @@ static void wr_long(const int32_t* rl, int64_t nr, const int64_t* rp, uint64_t* 
     }
     biggest = std::max(biggest, ho[q1] - ho[q0]);
   }
-  if (biggest >= (int64_t(1) << 32)) fail(LG_ERR_INVALID, "a row of 2^32 or more entries");
+  if (hubs) {  // the whole GPU on each batch: gather, a global radix sort, scatter
+    DBuf<uint64_t> tk(biggest, s), tv(biggest, s);
+    for (int64_t q0 = 0, q1; q0 < nr; q0 = q1) {
+      for (q1 = q0 + 1; q1 < nr && ho[q1 + 1] - ho[q0] <= kWrBatch; ++q1) {
+      }
+      k_wr_gather<<<(unsigned)(q1 - q0), 256, 0, s>>>(rl + q0, rp, loff.get() + q0, ho[q0], keys, vals, tk.get(),
+                                                       tv.get(), cbits);
+      LG_LAUNCH_CHECK();
+      radix_sort_pairs(tk.get(), tv.get(), ho[q1] - ho[q0], bits_for(q1 - q0) + cbits, s);
+      k_wr_scatter<<<(unsigned)(q1 - q0), 256, 0, s>>>(rl + q0, rp, loff.get() + q0, ho[q0], tk.get(), tv.get(),
+                                                        keys, vals, cbits);
+      LG_LAUNCH_CHECK();
+    }
+    return;
+  }
   DBuf<uint32_t> scol(biggest, s), pa(biggest, s), pb(biggest, s);
   DBuf<uint64_t> tv(biggest, s);
   for (int64_t q0 = 0, q1; q0 < nr; q0 = q1) {
@@ -717,7 +766,8 @@ void sort_within_rows(DBuf<uint64_t>& keys, DBuf<uint64_t>& vals, int64_t nent, 
       case 12: wr_radix_launch<4096>(rl, nr, rp, k, v, cbits, s); break;
       case 13: wr_radix_launch<8192>(rl, nr, rp, k, v, cbits, s); break;
       case 14: wr_radix_launch<16384>(rl, nr, rp, k, v, cbits, s); break;
-      default: wr_long(rl, nr, rp, k, v, cbits, s); break;
+      case 15: wr_long(rl, nr, rp, k, v, cbits, false, s); break;
+      default: wr_long(rl, nr, rp, k, v, cbits, true, s); break;
     }
     LG_LAUNCH_CHECK();
   }

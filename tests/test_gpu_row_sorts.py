@@ -5,9 +5,10 @@ column). Both orders are the same stable order, so the hierarchy must be the
 same bit for bit: every level's CSR, map and the solves (which also read W).
 The graphs reach every path of the within-row sort: rows of one entry, lane
 groups, bitonic block sorts of 64..512 entries, radix block sorts of
-1024..16384 entries in shared memory, and the radix-sorted long rows (the
-star's centre when renumbered; the two hubs of K_2,m, whose Schur rows hold
-m fill entries of one key each, summed in a fixed order)."""
+1024..16384 entries in shared memory, one block per row of up to 65536
+entries with global scratch, and the hubs' rows beyond, radix sorted by the
+whole GPU (the star's centre when renumbered; the two hubs of K_2,m, whose
+Schur rows hold m fill entries of one key each, summed in a fixed order)."""
 
 import numpy as np
 import pytest
@@ -29,8 +30,10 @@ GRAPHS = {
     "rmat_13": (lambda I: I.rmat(13, seed=2), {}),
     "rmat_13_random_order": (lambda I: I.rmat(13, seed=2), {"reorder": 2}),
     "grid3d_12_kept_order": (lambda I: I.grid3d(12, 12, 12), {"reorder": 0}),
+    "star_70000": (lambda I: I.star(70000, weights="uniform", seed=3), {}),
     "star_20000": (lambda I: I.star(20000, weights="uniform", seed=3), {}),
     "star_12000": (lambda I: I.star(12000, weights="uniform", seed=3), {}),
+    "k2_70000": (lambda I: k2m(I, 70000), {}),
     "k2_20000": (lambda I: k2m(I, 20000), {}),
     "k2_12000": (lambda I: k2m(I, 12000), {}),
     "k2_6000": (lambda I: k2m(I, 6000), {}),
